@@ -1,0 +1,554 @@
+/*
+ * mg_oracle.c -- CPU reference ("oracle") for the Magnetic Gaussian slice
+ * renderer.
+ *
+ * TEST INFRASTRUCTURE ONLY. It is called by the tests, by the smoke check and
+ * by the benchmark's CPU-baseline leg, never by the product path. It shares no
+ * code, header or constant table with the CUDA library; both sides implement
+ * the same written definitions.
+ *
+ * Plain loops, FP64 evaluation, no blocking or fusion, so that it can be read
+ * against the paper:
+ *
+ *   Sec. 3.2, Eq. E3:  Sigma = R S S^T R^T, R from the unit quaternion,
+ *                      S = diag(scale) (scale = exp(s), taken as input).
+ *   Sec. 3.3.2, E7:    I(x) = sum_i alpha_i exp(-1/2 (x-mu_i)^T Sigma_i^-1 (x-mu_i)),
+ *                      an additive mixture, no compositing and no sort.
+ *   Slice profile:     a slice voxel integrates I along the slice normal n
+ *                      against a unit-integral Gaussian profile of variance
+ *                      sig2 = FWHM^2 / (8 ln 2). Convolving a Gaussian with a
+ *                      Gaussian adds covariances, so each term becomes
+ *                      alpha sqrt(|Sigma| / |Sigma'|) exp(-1/2 y^T Sigma'^-1 y),
+ *                      Sigma' = Sigma + sig2 n n^T, y = x - mu. With sig2 = 0
+ *                      this is E7 exactly.
+ *   Truncation:        the paper already restricts the sum to a local set
+ *                      G_local (Sec. 3.3.1). Here the local set of a slice
+ *                      voxel is the set of Gaussians whose record for that
+ *                      slice lists the voxel's 16x16 tile (record predicate
+ *                      below, K-sigma ellipsoid of Sigma').
+ *
+ * Record predicate (evaluated in FP32, IEEE round-to-nearest, every operation
+ * rounded, no fused multiply-add, in the order written; compile with
+ * -ffp-contract=off). For Gaussian (mu, q=(w,x,y,z), s) and slice (Q, t):
+ *   R    = standard rotation of q (entries as in quat_rot_f below)
+ *   M    = R diag(s);  Sigma_rc = (M_r0 M_c0 + M_r1 M_c1) + M_r2 M_c2
+ *   p    = mu - t;  e_u, e_v, e_n = columns of Q;  a.b = (a0 b0 + a1 b1) + a2 b2
+ *   w0 = e_n.p, u0 = e_u.p, v0 = e_v.p
+ *   Lww = e_n.(Sigma e_n), Luw = e_u.(Sigma e_n), Lvw = e_v.(Sigma e_n),
+ *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v), (Sigma a)_r = (S_r0 a0 + S_r1 a1) + S_r2 a2
+ *   Sww = Lww + sig2;  K2 = K*K
+ *   record exists only if  w0*w0 <= K2*Sww  (the K-sigma slab test)
+ *   r2 = max(K2 - (w0*w0)/Sww, 0)
+ *   Cuu = max(Luu - (Luw*Luw)/Sww, 0),  Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0)
+ *   cu = u0 - (Luw*w0)/Sww,  cv = v0 - (Lvw*w0)/Sww
+ *   ru = sqrt(r2*Cuu),  rv = sqrt(r2*Cvv)
+ *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx), hx = 0.5*(W-1)
+ *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy), hy = 0.5*(H-1)
+ *   the record also needs il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0
+ *   (false for NaN); then il,jl are clamped up to 0 and ih,jh down to W-1,H-1
+ *   tiles: [il/16, ih/16] x [jl/16, jh/16]  (integer division)
+ *   sig2 = (float)(thickness^2 * 0.18033688011112042) computed in double.
+ * (u,v) bounds of the ellipse {y : y^T Sigma'^-1 y <= K^2} cut by the plane
+ * w = 0 are cu +- ru, cv +- rv: the in-plane conditional covariance of Sigma'
+ * is C = Sigma'_uv - Sigma'_uv,w Sigma'_w,uv / Sww and the cut ellipse has
+ * "radius^2" r2 = K^2 - w0^2/Sww.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_TILE 16
+#define OR_FWHM2VAR 0.18033688011112042 /* 1 / (8 ln 2) */
+
+/* ------------------------------------------------------------------ */
+/* per-slice table built from the stack descriptors                   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int H, W, TX, TY;
+    float dx, dy, thk;
+    const float *xf;   /* 12 floats: Q row-major, then t (record predicate) */
+    double dxd, dyd, thkd;
+    const double *xfd; /* the same in FP64 (evaluation) */
+    int64_t out_base;  /* offset of this slice's [H,W] image in the output */
+} or_slice;
+
+static or_slice *or_build_slices(int n_stacks, const int32_t *nsl, const int32_t *H, const int32_t *W,
+                                 const float *dx, const float *dy, const float *thk, const float *xform,
+                                 const double *dxd, const double *dyd, const double *thkd, const double *xformd,
+                                 int *S_out)
+{
+    int S = 0;
+    for (int s = 0; s < n_stacks; ++s) S += nsl[s];
+    or_slice *sl = (or_slice *)calloc((size_t)(S > 0 ? S : 1), sizeof(or_slice));
+    int k = 0;
+    int64_t base = 0;
+    for (int s = 0; s < n_stacks; ++s) {
+        for (int j = 0; j < nsl[s]; ++j, ++k) {
+            sl[k].H = H[s];
+            sl[k].W = W[s];
+            sl[k].TX = (W[s] + OR_TILE - 1) / OR_TILE;
+            sl[k].TY = (H[s] + OR_TILE - 1) / OR_TILE;
+            if (xform) {
+                sl[k].dx = dx[s];
+                sl[k].dy = dy[s];
+                sl[k].thk = thk[s];
+                sl[k].xf = xform + (size_t)k * 12;
+            }
+            if (xformd) {
+                sl[k].dxd = dxd[s];
+                sl[k].dyd = dyd[s];
+                sl[k].thkd = thkd[s];
+                sl[k].xfd = xformd + (size_t)k * 12;
+            }
+            sl[k].out_base = base;
+            base += (int64_t)H[s] * W[s];
+        }
+    }
+    *S_out = S;
+    return sl;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP32 record predicate (the written specification above)             */
+/* ------------------------------------------------------------------ */
+static void quat_rot_f(const float *q, float R[3][3])
+{
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    float xx = x * x, yy = y * y, zz = z * z;
+    float xy = x * y, xz = x * z, yz = y * z;
+    float wx = w * x, wy = w * y, wz = w * z;
+    R[0][0] = 1.0f - 2.0f * (yy + zz);
+    R[0][1] = 2.0f * (xy - wz);
+    R[0][2] = 2.0f * (xz + wy);
+    R[1][0] = 2.0f * (xy + wz);
+    R[1][1] = 1.0f - 2.0f * (xx + zz);
+    R[1][2] = 2.0f * (yz - wx);
+    R[2][0] = 2.0f * (xz - wy);
+    R[2][1] = 2.0f * (yz + wx);
+    R[2][2] = 1.0f - 2.0f * (xx + yy);
+}
+
+static float dot3f(const float a[3], const float b[3])
+{
+    float t = a[0] * b[0] + a[1] * b[1];
+    return t + a[2] * b[2];
+}
+
+/* returns 1 and the tile rectangle if the (Gaussian, slice) record exists */
+static int record_predicate(const float *mu, const float *q, const float *s, const or_slice *sl, float K,
+                            int32_t rect[4])
+{
+    float R[3][3], M[3][3], Sg[3][3];
+    quat_rot_f(q, R);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[r][c] = R[r][c] * s[c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = r; c < 3; ++c) {
+            float t = M[r][0] * M[c][0] + M[r][1] * M[c][1];
+            Sg[r][c] = t + M[r][2] * M[c][2];
+            Sg[c][r] = Sg[r][c];
+        }
+    const float *Q = sl->xf;
+    float eu[3] = {Q[0], Q[3], Q[6]};
+    float ev[3] = {Q[1], Q[4], Q[7]};
+    float en[3] = {Q[2], Q[5], Q[8]};
+    float p[3] = {mu[0] - Q[9], mu[1] - Q[10], mu[2] - Q[11]};
+    float w0 = dot3f(en, p), u0 = dot3f(eu, p), v0 = dot3f(ev, p);
+    float sn[3], su[3], sv[3];
+    for (int r = 0; r < 3; ++r) {
+        sn[r] = dot3f(Sg[r], en);
+        su[r] = dot3f(Sg[r], eu);
+        sv[r] = dot3f(Sg[r], ev);
+    }
+    float Lww = dot3f(en, sn), Luw = dot3f(eu, sn), Lvw = dot3f(ev, sn);
+    float Luu = dot3f(eu, su), Lvv = dot3f(ev, sv);
+    float sig2 = (float)((double)sl->thk * (double)sl->thk * OR_FWHM2VAR);
+    float Sww = Lww + sig2;
+    float K2 = K * K;
+    float ww = w0 * w0;
+    if (!(ww <= K2 * Sww)) return 0;
+    float r2 = K2 - ww / Sww;
+    if (r2 < 0.0f) r2 = 0.0f;
+    float Cuu = Luu - (Luw * Luw) / Sww;
+    if (Cuu < 0.0f) Cuu = 0.0f;
+    float Cvv = Lvv - (Lvw * Lvw) / Sww;
+    if (Cvv < 0.0f) Cvv = 0.0f;
+    float cu = u0 - (Luw * w0) / Sww;
+    float cv = v0 - (Lvw * w0) / Sww;
+    float ru = sqrtf(r2 * Cuu), rv = sqrtf(r2 * Cvv);
+    float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
+    float il = ceilf((cu - ru) / sl->dx + hx);
+    float ih = floorf((cu + ru) / sl->dx + hx);
+    float jl = ceilf((cv - rv) / sl->dy + hy);
+    float jh = floorf((cv + rv) / sl->dy + hy);
+    float Wm1 = (float)(sl->W - 1), Hm1 = (float)(sl->H - 1);
+    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) return 0;
+    if (il < 0.0f) il = 0.0f;
+    if (jl < 0.0f) jl = 0.0f;
+    if (ih > Wm1) ih = Wm1;
+    if (jh > Hm1) jh = Hm1;
+    rect[0] = (int32_t)il / OR_TILE;
+    rect[1] = (int32_t)jl / OR_TILE;
+    rect[2] = (int32_t)ih / OR_TILE;
+    rect[3] = (int32_t)jh / OR_TILE;
+    return 1;
+}
+
+/* Records, slice-major (all stacks' slices in order), ascending Gaussian id
+ * within a slice. Returns the total; fills at most cap. */
+int64_t or_make_records(int64_t n, const float *mean, const float *quat, const float *scale, int n_stacks,
+                        const int32_t *nsl, const int32_t *H, const int32_t *W, const float *dx, const float *dy,
+                        const float *thk, const float *xform, float K, int64_t cap, int32_t *rec_slice,
+                        int32_t *rec_gid, int32_t *rec_rect)
+{
+    int S;
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, dx, dy, thk, xform, NULL, NULL, NULL, NULL, &S);
+    int64_t *cnt = (int64_t *)calloc((size_t)S + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < S; ++k) {
+        int64_t c = 0;
+        int32_t rect[4];
+        for (int64_t g = 0; g < n; ++g)
+            c += record_predicate(mean + 3 * g, quat + 4 * g, scale + 3 * g, &sl[k], K, rect);
+        cnt[k + 1] = c;
+    }
+    for (int k = 0; k < S; ++k) cnt[k + 1] += cnt[k];
+    int64_t total = cnt[S];
+    if (rec_slice && cap > 0) {
+#pragma omp parallel for schedule(dynamic)
+        for (int k = 0; k < S; ++k) {
+            int64_t pos = cnt[k];
+            int32_t rect[4];
+            for (int64_t g = 0; g < n && pos < cap; ++g) {
+                if (record_predicate(mean + 3 * g, quat + 4 * g, scale + 3 * g, &sl[k], K, rect)) {
+                    rec_slice[pos] = k;
+                    rec_gid[pos] = (int32_t)g;
+                    memcpy(rec_rect + 4 * pos, rect, sizeof(rect));
+                    ++pos;
+                }
+            }
+        }
+    }
+    free(cnt);
+    free(sl);
+    return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP64 Gaussian algebra                                               */
+/* ------------------------------------------------------------------ */
+static void quat_rot_d(const double *qf, double R[3][3])
+{
+    double w = qf[0], x = qf[1], y = qf[2], z = qf[3];
+    R[0][0] = 1 - 2 * (y * y + z * z);
+    R[0][1] = 2 * (x * y - w * z);
+    R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);
+    R[1][1] = 1 - 2 * (x * x + z * z);
+    R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);
+    R[2][1] = 2 * (y * z + w * x);
+    R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+/* d R_rc / d q_m for the same formula (m = w,x,y,z) */
+static void quat_rot_grad_d(const double *qf, double dR[4][3][3])
+{
+    double w = qf[0], x = qf[1], y = qf[2], z = qf[3];
+    memset(dR, 0, sizeof(double) * 36);
+    /* R00 = 1 - 2(y^2 + z^2) */
+    dR[2][0][0] = -4 * y; dR[3][0][0] = -4 * z;
+    /* R01 = 2(xy - wz) */
+    dR[0][0][1] = -2 * z; dR[1][0][1] = 2 * y; dR[2][0][1] = 2 * x; dR[3][0][1] = -2 * w;
+    /* R02 = 2(xz + wy) */
+    dR[0][0][2] = 2 * y; dR[1][0][2] = 2 * z; dR[2][0][2] = 2 * w; dR[3][0][2] = 2 * x;
+    /* R10 = 2(xy + wz) */
+    dR[0][1][0] = 2 * z; dR[1][1][0] = 2 * y; dR[2][1][0] = 2 * x; dR[3][1][0] = 2 * w;
+    /* R11 = 1 - 2(x^2 + z^2) */
+    dR[1][1][1] = -4 * x; dR[3][1][1] = -4 * z;
+    /* R12 = 2(yz - wx) */
+    dR[0][1][2] = -2 * x; dR[1][1][2] = -2 * w; dR[2][1][2] = 2 * z; dR[3][1][2] = 2 * y;
+    /* R20 = 2(xz - wy) */
+    dR[0][2][0] = -2 * y; dR[1][2][0] = 2 * z; dR[2][2][0] = -2 * w; dR[3][2][0] = 2 * x;
+    /* R21 = 2(yz + wx) */
+    dR[0][2][1] = 2 * x; dR[1][2][1] = 2 * w; dR[2][2][1] = 2 * z; dR[3][2][1] = 2 * y;
+    /* R22 = 1 - 2(x^2 + y^2) */
+    dR[1][2][2] = -4 * x; dR[2][2][2] = -4 * y;
+}
+
+/* Sigma = R diag(s^2) R^T */
+static void cov_d(const double *qf, const double *sf, double Sg[3][3], double R[3][3])
+{
+    quat_rot_d(qf, R);
+    double s2[3] = {sf[0] * sf[0], sf[1] * sf[1], sf[2] * sf[2]};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int m = 0; m < 3; ++m) acc += R[r][m] * s2[m] * R[c][m];
+            Sg[r][c] = acc;
+        }
+}
+
+static double det3(const double A[3][3])
+{
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+/* inverse by the adjugate */
+static void inv3(const double A[3][3], double Ai[3][3], double *det_out)
+{
+    double d = det3(A);
+    Ai[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / d;
+    Ai[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / d;
+    Ai[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / d;
+    Ai[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / d;
+    Ai[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / d;
+    Ai[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / d;
+    Ai[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / d;
+    Ai[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / d;
+    Ai[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / d;
+    if (det_out) *det_out = d;
+}
+
+/* Everything one (Gaussian, slice) term needs in FP64. */
+typedef struct {
+    double mu[3], alpha, R[3][3], Sg[3][3], Sgi[3][3], Sp[3][3], P[3][3], c;
+} or_term;
+
+static void term_setup(const double *mu, const double *q, const double *s, double alpha, const or_slice *sl,
+                       or_term *T)
+{
+    cov_d(q, s, T->Sg, T->R);
+    double dS;
+    inv3(T->Sg, T->Sgi, &dS);
+    const double *Q = sl->xfd;
+    double n[3] = {Q[2], Q[5], Q[8]};
+    double sig2 = sl->thkd * sl->thkd * OR_FWHM2VAR;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) T->Sp[r][c] = T->Sg[r][c] + sig2 * n[r] * n[c];
+    double dSp;
+    inv3(T->Sp, T->P, &dSp);
+    T->c = sqrt(dS / dSp);
+    T->alpha = alpha;
+    for (int r = 0; r < 3; ++r) T->mu[r] = mu[r];
+}
+
+static void pixel_world(const or_slice *sl, int i, int j, double x[3])
+{
+    const double *Q = sl->xfd;
+    double u = (i - 0.5 * (sl->W - 1)) * sl->dxd;
+    double v = (j - 0.5 * (sl->H - 1)) * sl->dyd;
+    for (int r = 0; r < 3; ++r) x[r] = Q[3 * r + 0] * u + Q[3 * r + 1] * v + Q[9 + r];
+}
+
+/* Mahalanobis form y^T P y and P y */
+static double quad_form(const or_term *T, const double x[3], double y[3], double Py[3])
+{
+    for (int r = 0; r < 3; ++r) y[r] = x[r] - T->mu[r];
+    double qf = 0;
+    for (int r = 0; r < 3; ++r) {
+        Py[r] = T->P[r][0] * y[0] + T->P[r][1] * y[1] + T->P[r][2] * y[2];
+        qf += y[r] * Py[r];
+    }
+    return qf;
+}
+
+/* ------------------------------------------------------------------ */
+/* renders                                                             */
+/* ------------------------------------------------------------------ */
+
+/* exact = 0: S^bin from the records; exact = 1: every Gaussian at every pixel. */
+void or_render(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
+               const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy,
+               const double *thk, const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
+               const int32_t *rec_rect, int exact, double *out)
+{
+    int S;
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, dx, dy, thk, xform, &S);
+    int64_t total = 0;
+    for (int k = 0; k < S; ++k) total += (int64_t)sl[k].H * sl[k].W;
+    memset(out, 0, sizeof(double) * (size_t)total);
+    if (exact) {
+#pragma omp parallel for schedule(dynamic)
+        for (int k = 0; k < S; ++k) {
+            double *img = out + sl[k].out_base;
+            for (int64_t g = 0; g < n; ++g) {
+                or_term T;
+                term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
+                for (int j = 0; j < sl[k].H; ++j)
+                    for (int i = 0; i < sl[k].W; ++i) {
+                        double x[3], y[3], Py[3];
+                        pixel_world(&sl[k], i, j, x);
+                        double qf = quad_form(&T, x, y, Py);
+                        img[(int64_t)j * sl[k].W + i] += T.alpha * T.c * exp(-0.5 * qf);
+                    }
+            }
+        }
+    } else {
+        /* records are slice-major: find each slice's record range, then one
+           thread per slice owns that slice's image */
+        int64_t *first = (int64_t *)malloc(sizeof(int64_t) * ((size_t)S + 1));
+        for (int k = 0; k <= S; ++k) first[k] = nrec;
+        for (int64_t r = nrec - 1; r >= 0; --r) first[rec_slice[r]] = r;
+        for (int k = S - 1; k >= 0; --k)
+            if (first[k] > first[k + 1]) first[k] = first[k + 1];
+#pragma omp parallel for schedule(dynamic)
+        for (int k = 0; k < S; ++k) {
+            double *img = out + sl[k].out_base;
+            for (int64_t r = first[k]; r < first[k + 1]; ++r) {
+                int64_t g = rec_gid[r];
+                or_term T;
+                term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
+                const int32_t *rc = rec_rect + 4 * r;
+                int i0 = rc[0] * OR_TILE, j0 = rc[1] * OR_TILE;
+                int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
+                if (i1 > sl[k].W) i1 = sl[k].W;
+                if (j1 > sl[k].H) j1 = sl[k].H;
+                for (int j = j0; j < j1; ++j)
+                    for (int i = i0; i < i1; ++i) {
+                        double x[3], y[3], Py[3];
+                        pixel_world(&sl[k], i, j, x);
+                        double qf = quad_form(&T, x, y, Py);
+                        img[(int64_t)j * sl[k].W + i] += T.alpha * T.c * exp(-0.5 * qf);
+                    }
+            }
+        }
+        free(first);
+    }
+    free(sl);
+}
+
+/*
+ * Analytic FP64 gradient of L = sum_pixels gout * S^bin with the records held
+ * fixed, w.r.t. mean, quat (the 4 components entering the rotation formula),
+ * scale and alpha. Per term f = alpha c e, c = sqrt(|Sigma|/|Sigma'|),
+ * e = exp(-1/2 y^T P y), P = Sigma'^-1, y = x - mu:
+ *   df/dalpha = c e
+ *   df/dmu    = f P y
+ *   df/dSigma = f/2 (Sigma^-1 - P + P y y^T P)     (as a symmetric matrix)
+ * then Sigma = R diag(s^2) R^T gives
+ *   dL/dR = 2 G R diag(s^2),  dL/ds_c = 2 s_c (R^T G R)_cc
+ * and dL/dq from dR/dq.
+ */
+void or_grad(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
+             const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy, const double *thk,
+             const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
+             const int32_t *rec_rect, const double *gout, double *gmean, double *gquat, double *gscale,
+             double *galpha)
+{
+    int S;
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, dx, dy, thk, xform, &S);
+    double *rg = (double *)calloc((size_t)(nrec > 0 ? nrec : 1) * 11, sizeof(double));
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t r = 0; r < nrec; ++r) {
+        int k = rec_slice[r];
+        int64_t g = rec_gid[r];
+        or_term T;
+        term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
+        const double *go = gout + sl[k].out_base;
+        const int32_t *rc = rec_rect + 4 * r;
+        int i0 = rc[0] * OR_TILE, j0 = rc[1] * OR_TILE;
+        int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
+        if (i1 > sl[k].W) i1 = sl[k].W;
+        if (j1 > sl[k].H) j1 = sl[k].H;
+        double ga = 0, gmu[3] = {0, 0, 0}, GS[3][3];
+        memset(GS, 0, sizeof(GS));
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) {
+                double G = go[(int64_t)j * sl[k].W + i];
+                if (G == 0.0) continue;
+                double x[3], y[3], Py[3];
+                pixel_world(&sl[k], i, j, x);
+                double qf = quad_form(&T, x, y, Py);
+                double e = exp(-0.5 * qf);
+                double f = T.alpha * T.c * e;
+                ga += G * T.c * e;
+                for (int a = 0; a < 3; ++a) gmu[a] += G * f * Py[a];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        GS[a][b] += G * f * 0.5 * (T.Sgi[a][b] - T.P[a][b] + Py[a] * Py[b]);
+            }
+        /* chain Sigma -> R, s -> q */
+        const double *s = scale + 3 * g;
+        double dLdR[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0;
+                for (int b = 0; b < 3; ++b) acc += GS[a][b] * T.R[b][c];
+                dLdR[a][c] = 2.0 * acc * s[c] * s[c];
+            }
+        double gs[3];
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) acc += T.R[a][c] * GS[a][b] * T.R[b][c];
+            gs[c] = 2.0 * s[c] * acc;
+        }
+        double dR[4][3][3];
+        quat_rot_grad_d(quat + 4 * g, dR);
+        double gq[4];
+        for (int m = 0; m < 4; ++m) {
+            double acc = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) acc += dLdR[a][c] * dR[m][a][c];
+            gq[m] = acc;
+        }
+        double *o = rg + 11 * r;
+        o[0] = gmu[0]; o[1] = gmu[1]; o[2] = gmu[2];
+        o[3] = gq[0]; o[4] = gq[1]; o[5] = gq[2]; o[6] = gq[3];
+        o[7] = gs[0]; o[8] = gs[1]; o[9] = gs[2];
+        o[10] = ga;
+    }
+    memset(gmean, 0, sizeof(double) * 3 * (size_t)n);
+    memset(gquat, 0, sizeof(double) * 4 * (size_t)n);
+    memset(gscale, 0, sizeof(double) * 3 * (size_t)n);
+    memset(galpha, 0, sizeof(double) * (size_t)n);
+    for (int64_t r = 0; r < nrec; ++r) {
+        int64_t g = rec_gid[r];
+        const double *o = rg + 11 * r;
+        for (int a = 0; a < 3; ++a) gmean[3 * g + a] += o[a];
+        for (int a = 0; a < 4; ++a) gquat[4 * g + a] += o[3 + a];
+        for (int a = 0; a < 3; ++a) gscale[3 * g + a] += o[7 + a];
+        galpha[g] += o[10];
+    }
+    free(rg);
+    free(sl);
+}
+
+/* counts[0] = pairs (record, pixel in a listed tile) with y^T Sigma'^-1 y <= K^2
+ * (FP64), counts[1] = all evaluated pairs (record, pixel in a listed tile). */
+void or_pair_counts(int64_t n_unused, const double *mean, const double *quat, const double *scale, const double *alpha,
+                    int n_stacks, const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx,
+                    const double *dy, const double *thk, const double *xform, int64_t nrec, const int32_t *rec_slice,
+                    const int32_t *rec_gid, const int32_t *rec_rect, double K, int64_t *counts)
+{
+    (void)n_unused;
+    int S;
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, dx, dy, thk, xform, &S);
+    int64_t inside = 0, evald = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : inside, evald)
+    for (int64_t r = 0; r < nrec; ++r) {
+        int k = rec_slice[r];
+        int64_t g = rec_gid[r];
+        or_term T;
+        term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
+        const int32_t *rc = rec_rect + 4 * r;
+        int i0 = rc[0] * OR_TILE, j0 = rc[1] * OR_TILE;
+        int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
+        if (i1 > sl[k].W) i1 = sl[k].W;
+        if (j1 > sl[k].H) j1 = sl[k].H;
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) {
+                double x[3], y[3], Py[3];
+                pixel_world(&sl[k], i, j, x);
+                double qf = quad_form(&T, x, y, Py);
+                inside += (qf <= K * K);
+                evald += 1;
+            }
+    }
+    counts[0] = inside;
+    counts[1] = evald;
+    free(sl);
+}

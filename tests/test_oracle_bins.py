@@ -1,0 +1,118 @@
+"""Pins of the oracle's FP32 record predicate (the K-sigma slab test plus the
+tile rectangle of the cut ellipse) against brute force in FP64.
+
+* conservativeness: every slice pixel inside the K-sigma ellipsoid of the
+  profile-convolved covariance lies in a listed tile of that Gaussian's
+  record for the slice;
+* tightness: the tile rectangle equals the one obtained from the FP64 extents
+  of the cut ellipse, found here by an eigen-decomposition of the in-plane
+  quadratic form (a different route from the Schur complement the predicate
+  uses), up to an FP32 margin;
+* existence: a record exists exactly when that FP64 rectangle meets the image.
+"""
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import mg_synth as ms
+import oracle as orc
+
+FWHM2VAR = 1.0 / (8.0 * np.log(2.0))
+TILE = 16
+
+
+def _plane_quadratic(mu, q, s, xf, sig2):
+    """q(u,v) = y^T Sigma'^-1 y for y = R_k (u,v,0) + t_k - mu as (A [2x2], b [2], c)."""
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    Sg = R @ np.diag(np.asarray(s, np.float64) ** 2) @ R.T
+    Rk = xf[:9].reshape(3, 3)
+    n = Rk[:, 2]
+    P = np.linalg.inv(Sg + sig2 * np.outer(n, n))
+    B = Rk[:, :2]               # world = B (u,v) + t
+    d0 = xf[9:] - mu            # y = B uv + d0
+    A = B.T @ P @ B
+    b = B.T @ P @ d0
+    c = d0 @ P @ d0
+    return A, b, c
+
+
+def _fp64_tile_rect(A, b, c, K, st, margin_px):
+    """Tile rectangle of the ellipse {uv : q(uv) <= K^2} from its FP64 extents,
+    extents grown by ``margin_px`` pixels (negative shrinks). None if empty."""
+    ctr = -np.linalg.solve(A, b)
+    qmin = c + b @ ctr
+    r2 = K * K - qmin
+    if r2 < 0:
+        return None
+    w, V = np.linalg.eigh(A)
+    th = np.linspace(0, 2 * np.pi, 4001)
+    pts = ctr[:, None] + V @ (np.sqrt(r2 / w)[:, None] * np.stack([np.cos(th), np.sin(th)]))
+    hx, hy = 0.5 * (st.W - 1), 0.5 * (st.H - 1)
+    fx = pts[0] / st.dx + hx
+    fy = pts[1] / st.dy + hy
+    il, ih = np.ceil(fx.min() - margin_px), np.floor(fx.max() + margin_px)
+    jl, jh = np.ceil(fy.min() - margin_px), np.floor(fy.max() + margin_px)
+    if il > ih or jl > jh or il > st.W - 1 or ih < 0 or jl > st.H - 1 or jh < 0:
+        return None
+    il, jl = max(il, 0), max(jl, 0)
+    ih, jh = min(ih, st.W - 1), min(jh, st.H - 1)
+    return (int(il) // TILE, int(jl) // TILE, int(ih) // TILE, int(jh) // TILE)
+
+
+def _contains(outer, inner):
+    if inner is None:
+        return True
+    if outer is None:
+        return False
+    return outer[0] <= inner[0] and outer[1] <= inner[1] and outer[2] >= inner[2] and outer[3] >= inner[3]
+
+
+@pytest.mark.parametrize("seed,K", [(0, 3.0), (1, 3.0), (2, 2.0), (3, 4.5)])
+def test_records_vs_brute_force(seed, K):
+    rng = np.random.default_rng(seed)
+    G = ms.random_gaussians(80, 50 + seed, box=(-26, 26), sigma=(0.6, 4.0), aniso=4.0)
+    stacks = [ms.make_stack(ms.AXIAL, 5, 40, 37, 1.0, 1.2, 3.0, 2.5),
+              ms.make_stack(ms.random_rotations(1, rng)[0], 4, 33, 50, 0.8, 0.9, 2.0, 3.0,
+                            rng=rng, max_rot_deg=5.0, max_trans_mm=1.0),
+              ms.make_stack(ms.SAGITTAL, 3, 20, 20, 1.5, 1.5, 0.0, 4.0)]
+    rec = orc.records(G, stacks, K)
+    have = {(int(k), int(g)): tuple(int(v) for v in r) for k, g, r in zip(rec.slice, rec.gid, rec.rect)}
+    # slice-major, ascending Gaussian id
+    key = rec.slice.astype(np.int64) * G.n + rec.gid
+    assert np.all(np.diff(key) > 0)
+    k0 = 0
+    for st in stacks:
+        sig2 = st.thickness ** 2 * FWHM2VAR
+        ii, jj = np.meshgrid(np.arange(st.W), np.arange(st.H), indexing="xy")
+        uv = np.stack([(ii - 0.5 * (st.W - 1)) * st.dx, (jj - 0.5 * (st.H - 1)) * st.dy], axis=-1)
+        for k in range(st.n_slices):
+            xf = st.xform[k].astype(np.float64)
+            for g in range(G.n):
+                q = G.quat[g].astype(np.float64)
+                q /= np.linalg.norm(q)
+                A, b, c = _plane_quadratic(G.mean[g].astype(np.float64), q, G.scale[g], xf, sig2)
+                qv = np.einsum("hwi,ij,hwj->hw", uv, A, uv) + 2 * uv @ b + c
+                got = have.get((k0 + k, g))
+                inside = qv <= K * K * (1 - 1e-5)
+                if inside.any():
+                    assert got is not None, (k, g)
+                    jin, iin = np.nonzero(inside)
+                    tx, ty = iin // TILE, jin // TILE
+                    assert got[0] <= tx.min() and got[2] >= tx.max() and got[1] <= ty.min() and got[3] >= ty.max()
+                lo = _fp64_tile_rect(A, b, c, K * (1 - 1e-5), st, -1e-3)
+                hi = _fp64_tile_rect(A, b, c, K * (1 + 1e-5), st, 1e-3)
+                assert _contains(got, lo), (k, g, got, lo)
+                assert _contains(hi, got), (k, g, got, hi)
+        k0 += st.n_slices
+
+
+def test_record_count_and_tile_bins_consistent():
+    G = ms.random_gaussians(50, 9, box=(-15, 15), sigma=(0.8, 3.0), aniso=3.0)
+    stacks = [ms.make_stack(ms.CORONAL, 6, 35, 48, 1.0, 1.0, 3.0, 3.0)]
+    rec = orc.records(G, stacks, 3.0)
+    counts, offs, ids = orc.tile_bins(rec, stacks)
+    areas = (rec.rect[:, 2] - rec.rect[:, 0] + 1) * (rec.rect[:, 3] - rec.rect[:, 1] + 1)
+    assert counts.sum() == areas.sum() == ids.size
+    for t in range(counts.size):
+        seg = ids[offs[t]:offs[t + 1]]
+        assert np.all(np.diff(seg) > 0)
