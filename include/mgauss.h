@@ -1,0 +1,215 @@
+/*
+ * mgauss.h -- C ABI of the B300 (sm_103a) Magnetic Gaussian slice renderer.
+ *
+ * The library implements the rendering path of M-Gaussian (arxiv 2603.00145):
+ * anisotropic 3D Gaussians G_i = {mu_i, Sigma_i, alpha_i} (Sec. 3.2, Eq. E2),
+ * Sigma_i = R_i S_i S_i^T R_i^T with R_i from a unit quaternion and S_i the
+ * diagonal of scales (Eq. E3), evaluated as the additive mixture of Eq. E7
+ * (Sec. 3.3.2: no compositing, no sort) at the voxels of thick acquired slices
+ * after each slice's rigid transform T_k, integrated along the slice normal
+ * against a unit-integral Gaussian slice profile of FWHM = slice thickness.
+ * Convolving a Gaussian with the profile adds covariances, so the term of
+ * Gaussian i at a slice voxel x of slice k is
+ *
+ *     alpha_i sqrt(|Sigma_i| / |Sigma'_i|) exp(-1/2 (x-mu_i)^T Sigma'_i^-1 (x-mu_i)),
+ *     Sigma'_i = Sigma_i + sig_s^2 n_k n_k^T,   sig_s^2 = FWHM^2 / (8 ln 2),
+ *
+ * which is Eq. E7 exactly when the thickness is 0 (volume sampling, Sec. 3.1).
+ * Like the paper's local Gaussian set G_local (Sec. 3.3.1), the sum is
+ * restricted per 16x16 voxel tile: Gaussian i contributes to every voxel of a
+ * tile of slice k iff its (i,k) record lists that tile (the record predicate
+ * below: a K-sigma slab test plus the tile rectangle of the cut ellipse).
+ *
+ * CONVENTIONS
+ *   Units are mm. Gaussians: mean [n,3], quat [n,4] = (w,x,y,z) with unit norm
+ *   (normalise before calling; the rotation formula assumes it), scale [n,3]
+ *   = per-axis standard deviations exp(s) > 0, alpha [n] (any real). All are
+ *   FP32, C-contiguous, in DEVICE memory unless stated otherwise.
+ *   A stack has n_slices slices of H x W pixels at dx x dy mm. xform
+ *   [n_slices,12] (device) holds per slice the rotation R (3x3, row-major;
+ *   columns e_u, e_v, e_n) and translation t: world = R (u,v,w)^T + t, the slice
+ *   plane is w = 0. Pixel (i,j) (column i, row j) lies at u = (i-(W-1)/2) dx,
+ *   v = (j-(H-1)/2) dy. Slices are written [n_slices,H,W], stacks concatenated
+ *   in call order.
+ *
+ * RECORD PREDICATE (FP32, round-to-nearest, every operation rounded, no fused
+ * multiply-add, in this order). q = (w,x,y,z), xx = x*x, ..., wz = w*z:
+ *   R = [[1-2(yy+zz), 2(xy-wz), 2(xz+wy)], [2(xy+wz), 1-2(xx+zz), 2(yz-wx)],
+ *        [2(xz-wy), 2(yz+wx), 1-2(xx+yy)]];  M_rc = R_rc s_c;
+ *   Sigma_rc = (M_r0 M_c0 + M_r1 M_c1) + M_r2 M_c2;  a.b = (a0 b0 + a1 b1) + a2 b2;
+ *   p = mu - t;  w0 = e_n.p, u0 = e_u.p, v0 = e_v.p;  (Sigma a)_r = Sigma_r . a;
+ *   Lww = e_n.(Sigma e_n), Luw = e_u.(Sigma e_n), Lvw = e_v.(Sigma e_n),
+ *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v);  Sww = Lww + sig2;  K2 = K*K;
+ *   sig2 = (float)(thickness^2 * 0.18033688011112042) (computed in double);
+ *   the record exists iff  w0*w0 <= K2*Sww  and its pixel box below is non-empty:
+ *   r2 = max(K2 - (w0*w0)/Sww, 0);  Cuu = max(Luu - (Luw*Luw)/Sww, 0);
+ *   Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0);  cu = u0 - (Luw*w0)/Sww;  cv = v0 - (Lvw*w0)/Sww;
+ *   ru = sqrt(r2*Cuu), rv = sqrt(r2*Cvv);  hx = 0.5*(W-1), hy = 0.5*(H-1);
+ *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx),
+ *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy);
+ *   non-empty iff il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0 (NaN: empty);
+ *   clamp il,jl up to 0 and ih,jh down to W-1,H-1; tiles [il/16, ih/16] x [jl/16, jh/16].
+ *   Tile (tx,ty) of a slice covers pixels 16tx..16tx+15 x 16ty..16ty+15.
+ *   The count of records and of (record, tile) entries is therefore exact
+ *   and reproducible bit for bit by any IEEE FP32 implementation.
+ *
+ * OWNERSHIP AND ERRORS
+ *   The caller owns every buffer; the library never allocates device memory
+ *   in a compute call. Scratch comes from a caller-provided workspace of the
+ *   size the matching *_workspace_size query returns (256-byte aligned).
+ *   Calls are asynchronous on `stream` (NULL = the legacy default stream):
+ *   host-visible argument errors return immediately; capacity overflow and
+ *   non-finite inputs are detected on the device, recorded in the workspace
+ *   and reported by mg_render_stats_get (which synchronises the stream).
+ *   On MG_ERR_CUDA the message of the CUDA error is in mg_last_error().
+ *   Every function is thread-safe for distinct workspaces; mg_last_error is
+ *   per thread.
+ */
+#ifndef MGAUSS_H
+#define MGAUSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mg_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,     /* bad pointer, size, shape or option; nothing launched */
+    MG_ERR_CUDA = 2,            /* a CUDA runtime call failed; see mg_last_error() */
+    MG_ERR_CAPACITY = 3,        /* records/entries did not fit the workspace; grow and retry */
+    MG_ERR_DEVICE_TIMEOUT = 4,  /* reserved: no kernel of this library waits on another */
+    MG_ERR_NOT_FINITE = 5,      /* a Gaussian or transform had a NaN/Inf or a scale <= 0 */
+    MG_ERR_STALE_WORKSPACE = 6  /* backward called without the matching forward on this workspace */
+} mg_status;
+
+typedef struct {
+    int64_t n;
+    const float *mean;  /* [n,3] */
+    const float *quat;  /* [n,4] (w,x,y,z), unit */
+    const float *scale; /* [n,3] std-devs, > 0 */
+    const float *alpha; /* [n] */
+} mg_gaussians;
+
+typedef struct {
+    int32_t n_slices, H, W; /* 1 <= H, W <= 1024 */
+    float dx, dy;           /* pixel spacing (mm), > 0 */
+    float thickness;        /* slice-profile FWHM (mm), >= 0; 0 = point sampling (Eq. E7) */
+    const float *xform;     /* device [n_slices,12] */
+} mg_stack;
+
+typedef struct {
+    float cutoff_k;      /* K of the K-sigma record predicate; default 3 */
+    float f64_ratio;     /* record geometry in FP64 when max(scale)/min(scale) > f64_ratio; default 100; <= 0: never */
+    int64_t cap_records; /* workspace capacity in records; 0 = n * total slices (upper bound) capped at 2^28 */
+    int64_t cap_entries; /* workspace capacity in (record, tile) entries; 0 = 8 * cap_records capped at 2^30 */
+} mg_opts;
+
+/* Filled by mg_render_stats_get from the workspace of the last forward call. */
+typedef struct {
+    int64_t records;         /* (Gaussian, slice) records that exist */
+    int64_t entries;         /* (record, tile) entries = evaluated (record, 16x16 tile) pairs */
+    int64_t tiles;           /* tiles over all slices */
+    int64_t cap_records, cap_entries;
+    int32_t status;          /* MG_OK, MG_ERR_CAPACITY or MG_ERR_NOT_FINITE */
+    int32_t reserved;
+} mg_render_stats;
+
+/* Default options (K = 3, f64_ratio = 100, capacities from the bounds above). */
+mg_opts mg_default_opts(void);
+
+/*
+ * Workspace bytes for mg_render_fwd / mg_render_bwd with these Gaussians
+ * (only n is read), stacks (shapes only) and options. Returns 0 on invalid
+ * arguments. The same (n, stacks, opts) must be passed to fwd and bwd.
+ */
+size_t mg_render_workspace_size(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts);
+
+/*
+ * Forward render (Sec. 3.3.2, Eq. E7 with the slice profile; Sec. 3.3.1 local
+ * set via records): out[total voxels] (device, FP32) is overwritten with the
+ * slice values of all stacks. n_stacks in [1, 32]. Runs the record pass, the
+ * tile binning (count, exclusive scan, stable scatter) and the per-tile
+ * evaluation. The workspace keeps the records and bins for mg_render_bwd.
+ * Capacity overflow leaves `out` undefined and is reported by
+ * mg_render_stats_get as MG_ERR_CAPACITY with the required counts.
+ */
+mg_status mg_render_fwd(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts, float *out,
+                        void *ws, size_t ws_bytes, mg_stream_t stream);
+
+/*
+ * Adjoint of mg_render_fwd (the paper trains by differentiable rendering,
+ * Sec. 3.1): given grad_out = dL/d(out) (device, FP32, total voxels), writes
+ * dL/dmean [n,3], dL/dquat [n,4] (derivative of the rotation formula above in
+ * the four quaternion components, as given), dL/dscale [n,3] and dL/dalpha [n]
+ * (device, FP32, overwritten). The records are held fixed (the sum is
+ * piecewise constant in them). Must follow mg_render_fwd on the same
+ * workspace with the same arguments (else MG_ERR_STALE_WORKSPACE); the
+ * per-pair terms are recomputed per tile, nothing per pair is stored.
+ */
+mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                        const float *grad_out, float *g_mean, float *g_quat, float *g_scale, float *g_alpha, void *ws,
+                        size_t ws_bytes, mg_stream_t stream);
+
+/*
+ * Read-only introspection of a render workspace (for tests and tools): byte
+ * offsets, inside the workspace, of the per-record arrays and of the tile
+ * bins written by mg_render_fwd / mg_sample_volume. Records are ordered by
+ * global slice, then ascending Gaussian id (the first `records` entries of
+ * each array are valid): rec_gid int32, rec_slice int32, rec_rect uint16x4
+ * (tx0, ty0, tx1, ty1). Bins: tile_off uint32 [tiles+1] (exclusive offsets,
+ * global tile order = stacks, slices, ty*TX+tx), entries uint32 (record
+ * ids). Returns MG_ERR_INVALID_ARG on bad arguments.
+ */
+typedef struct {
+    uint64_t rec_gid, rec_slice, rec_rect, tile_off, entries, total_bytes;
+} mg_ws_layout;
+mg_status mg_render_ws_layout(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                              mg_ws_layout *out);
+mg_status mg_sample_ws_layout(int64_t n, int32_t G, const mg_opts *opts, mg_ws_layout *out);
+
+/* Synchronises `stream`, then reads the counters and status of the last
+ * forward on this workspace. Returns that status (or MG_ERR_CUDA/INVALID_ARG). */
+mg_status mg_render_stats_get(const void *ws, size_t ws_bytes, mg_render_stats *stats, mg_stream_t stream);
+
+/*
+ * Inference sampling (Sec. 3.1 and Fig. 1c): the mixture of Eq. E7 (no slice
+ * profile) on the isotropic grid of G^3 voxels, voxel (c,j,i) at
+ * (cx + (i-(G-1)/2) h, cy + (j-(G-1)/2) h, float(cz + h (c-(G-1)/2))), the last
+ * coordinate evaluated in double and rounded to float. centre is a HOST
+ * array of 3 floats. out: device [G,G,G] (z,y,x) FP32, overwritten. Uses the
+ * same record/binning/evaluation kernels with G z-planes as one stack.
+ */
+size_t mg_sample_workspace_size(int64_t n, int32_t G, const mg_opts *opts);
+mg_status mg_sample_volume(const mg_gaussians *g, const float centre[3], float spacing, int32_t G, const mg_opts *opts,
+                           float *out, void *ws, size_t ws_bytes, mg_stream_t stream);
+
+/*
+ * FP64 loss reduction of the plain-fit workload (Sec. 3.5.2 with the L1 + L2
+ * slice loss): loss = mean|r| + mean r^2 over n voxels, r = pred - target,
+ * accumulated in FP64 in a fixed order (deterministic). loss_out: device
+ * double [2] = {loss, sum r^2}. grad (device FP32 [n], may be NULL) receives
+ * dloss/dpred = (sign(r) + 2 r) / n.
+ */
+size_t mg_reduce_workspace_size(int64_t n);
+mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float *grad, double *loss_out, void *ws,
+                       size_t ws_bytes, mg_stream_t stream);
+
+/* FP64 sum of squared differences (for MSE / PSNR, Sec. 4.1.3): out: device
+ * double [1] = sum (a-b)^2, fixed-order FP64 accumulation. */
+mg_status mg_sq_diff_sum(const float *a, const float *b, int64_t n, double *out, void *ws, size_t ws_bytes,
+                         mg_stream_t stream);
+
+const char *mg_status_string(mg_status s);
+const char *mg_last_error(void);
+/* Library version string. */
+const char *mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGAUSS_H */

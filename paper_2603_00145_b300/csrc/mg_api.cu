@@ -1,0 +1,480 @@
+// mg_api.cu -- the C ABI (include/mgauss.h): argument checks, workspace
+// layout and the launch sequence of each entry point.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "mg_internal.cuh"
+
+int mg_reduce_blocks(long long n);
+void mg_launch_loss_l1l2(const float *pred, const float *target, long long n, float *grad, double *out,
+                         double *part, cudaStream_t st);
+void mg_launch_sq_diff(const float *a, const float *b, long long n, double *out, double *part, cudaStream_t st);
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mg_status fail(mg_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+mg_status check_cuda(const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return MG_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr double FWHM2VAR = 0.18033688011112042;  // 1 / (8 ln 2)
+
+struct StackDesc {
+    int n_slices, H, W;
+    float dx, dy, thickness;
+    const float *xform;
+};
+
+mg_opts resolve_opts(const mg_opts *o, long long n, long long S)
+{
+    mg_opts r = mg_default_opts();
+    if (o) r = *o;
+    if (!(r.cutoff_k > 0.f)) r.cutoff_k = 3.0f;
+    long long bound = n * S;
+    if (r.cap_records <= 0) r.cap_records = bound < (1ll << 28) ? bound : (1ll << 28);
+    if (r.cap_records < 1) r.cap_records = 1;
+    if (r.cap_entries <= 0) {
+        long long e = 8 * r.cap_records;
+        r.cap_entries = e < (1ll << 30) ? e : (1ll << 30);
+    }
+    return r;
+}
+
+bool valid_stacks(const std::vector<StackDesc> &st, bool need_xform, std::string &why)
+{
+    if (st.empty() || st.size() > MG_MAX_STACKS) {
+        why = "n_stacks must be in [1, 32]";
+        return false;
+    }
+    for (size_t s = 0; s < st.size(); ++s) {
+        const StackDesc &d = st[s];
+        if (d.n_slices < 1 || d.H < 1 || d.W < 1 || d.H > 1024 || d.W > 1024) {
+            why = "stack " + std::to_string(s) + ": need n_slices >= 1 and 1 <= H, W <= 1024";
+            return false;
+        }
+        if (!(d.dx > 0.f) || !(d.dy > 0.f) || !(d.thickness >= 0.f) || !isfinite(d.dx) || !isfinite(d.dy) ||
+            !isfinite(d.thickness)) {
+            why = "stack " + std::to_string(s) + ": need dx, dy > 0 and thickness >= 0, finite";
+            return false;
+        }
+        if (need_xform && !d.xform) {
+            why = "stack " + std::to_string(s) + ": xform is NULL";
+            return false;
+        }
+    }
+    return true;
+}
+
+WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opts &o)
+{
+    WsLayout L;
+    memset(&L, 0, sizeof(L));
+    long long S = 0, tiles = 0, tmax = 0;
+    for (const StackDesc &d : st) {
+        long long TX = (d.W + MG_TILE - 1) / MG_TILE, TY = (d.H + MG_TILE - 1) / MG_TILE;
+        S += d.n_slices;
+        tiles += (long long)d.n_slices * TX * TY;
+        if (TX * TY > tmax) tmax = TX * TY;
+    }
+    L.S = S;
+    L.NB = (n + 255) / 256;
+    L.cap_records = o.cap_records;
+    L.cap_entries = o.cap_entries;
+    L.cap_chunks = o.cap_records / MG_CHUNK + S + 1;
+    L.n_tiles = tiles;
+    L.max_tiles = tmax;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align256(off + bytes);
+        return at;
+    };
+    L.hdr = take(sizeof(WsHeader));
+    L.slices = take(sizeof(SliceDev) * (size_t)S);
+    L.cnt = take(sizeof(unsigned) * (size_t)(S * L.NB + 1));
+    L.scan_part = take(sizeof(unsigned long long) * MG_SCAN_BLOCKS);
+    L.rec_geo = take(16 * (size_t)L.cap_records);
+    L.rec_geo2 = take(8 * (size_t)L.cap_records);
+    L.rec_gid = take(4 * (size_t)L.cap_records);
+    L.rec_slice = take(4 * (size_t)L.cap_records);
+    L.rec_rect = take(8 * (size_t)L.cap_records);
+    L.rec_mom = take(32 * (size_t)L.cap_records);
+    L.chunk_base = take(sizeof(unsigned) * 2 * (size_t)(S + 1));
+    L.hist = take(sizeof(unsigned) * (size_t)L.cap_chunks * (size_t)tmax);
+    L.tile_cnt = take(sizeof(unsigned) * (size_t)tiles);
+    L.tile_off = take(sizeof(unsigned) * (size_t)(tiles + 1));
+    L.entries = take(sizeof(unsigned) * (size_t)L.cap_entries);
+    L.total = off;
+    return L;
+}
+
+StackTable make_table(const std::vector<StackDesc> &st)
+{
+    StackTable t;
+    memset(&t, 0, sizeof(t));
+    t.n_stacks = (int)st.size();
+    int tb = 0, sb = 0;
+    long long pb = 0;
+    int tmax = 0;
+    for (size_t s = 0; s < st.size(); ++s) {
+        const StackDesc &d = st[s];
+        int TX = (d.W + MG_TILE - 1) / MG_TILE, TY = (d.H + MG_TILE - 1) / MG_TILE;
+        t.tile_base[s] = tb;
+        t.slice_base[s] = sb;
+        t.pix_base[s] = pb;
+        t.TX[s] = TX;
+        t.TY[s] = TY;
+        t.W[s] = d.W;
+        t.H[s] = d.H;
+        tb += d.n_slices * TX * TY;
+        sb += d.n_slices;
+        pb += (long long)d.n_slices * d.H * d.W;
+        if (TX * TY > tmax) tmax = TX * TY;
+    }
+    t.tile_base[st.size()] = tb;
+    t.slice_base[st.size()] = sb;
+    t.pix_base[st.size()] = pb;
+    t.n_slices_total = sb;
+    t.n_tiles_total = tb;
+    t.max_tiles_slice = tmax;
+    return t;
+}
+
+StackIn make_stack_in(const std::vector<StackDesc> &st)
+{
+    StackIn in;
+    memset(&in, 0, sizeof(in));
+    in.n_stacks = (int)st.size();
+    for (size_t s = 0; s < st.size(); ++s) {
+        in.n_slices[s] = st[s].n_slices;
+        in.H[s] = st[s].H;
+        in.W[s] = st[s].W;
+        in.dx[s] = st[s].dx;
+        in.dy[s] = st[s].dy;
+        in.sig2[s] = (float)((double)st[s].thickness * (double)st[s].thickness * FWHM2VAR);
+        in.xform[s] = st[s].xform;
+    }
+    return in;
+}
+
+std::vector<StackDesc> to_desc(const mg_stack *stacks, int n_stacks)
+{
+    std::vector<StackDesc> v;
+    if (!stacks || n_stacks < 1 || n_stacks > MG_MAX_STACKS) return v;
+    for (int s = 0; s < n_stacks; ++s)
+        v.push_back({stacks[s].n_slices, stacks[s].H, stacks[s].W, stacks[s].dx, stacks[s].dy, stacks[s].thickness,
+                     stacks[s].xform});
+    return v;
+}
+
+bool valid_gauss(const mg_gaussians *g, std::string &why, bool need_ptrs = true)
+{
+    if (!g) {
+        why = "gaussians is NULL";
+        return false;
+    }
+    if (g->n < 0 || g->n > 0x7fffffffll) {
+        why = "n must be in [0, 2^31)";
+        return false;
+    }
+    if (need_ptrs && g->n > 0 && (!g->mean || !g->quat || !g->scale || !g->alpha)) {
+        why = "a Gaussian parameter pointer is NULL";
+        return false;
+    }
+    return true;
+}
+
+// what the backward needs to know about the forward that filled a workspace
+struct FwdTag {
+    long long n;
+    const void *p[4];
+    std::vector<float> stack_key;
+    std::vector<const void *> xforms;
+    float K, f64;
+    long long capr, cape;
+};
+
+std::mutex g_tag_mu;
+std::unordered_map<const void *, FwdTag> g_tags;
+
+FwdTag make_tag(const mg_gaussians *g, const std::vector<StackDesc> &st, const mg_opts &o)
+{
+    FwdTag t;
+    t.n = g->n;
+    t.p[0] = g->mean;
+    t.p[1] = g->quat;
+    t.p[2] = g->scale;
+    t.p[3] = g->alpha;
+    for (const StackDesc &d : st) {
+        t.stack_key.insert(t.stack_key.end(), {(float)d.n_slices, (float)d.H, (float)d.W, d.dx, d.dy, d.thickness});
+        t.xforms.push_back(d.xform);
+    }
+    t.K = o.cutoff_k;
+    t.f64 = o.f64_ratio;
+    t.capr = o.cap_records;
+    t.cape = o.cap_entries;
+    return t;
+}
+
+bool same_tag(const FwdTag &a, const FwdTag &b)
+{
+    return a.n == b.n && memcmp(a.p, b.p, sizeof(a.p)) == 0 && a.stack_key == b.stack_key && a.xforms == b.xforms &&
+           a.K == b.K && a.f64 == b.f64 && a.capr == b.capr && a.cape == b.cape;
+}
+
+mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &st, const StackIn &in,
+                          const mg_opts *opts, float *out, void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    std::string why;
+    if (!valid_gauss(g, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (!valid_stacks(st, !in.planes, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (!out || !ws) return fail(MG_ERR_INVALID_ARG, "out or workspace is NULL");
+    if (((uintptr_t)ws & 255) != 0) return fail(MG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    long long S = 0, tiles = 0;
+    for (const StackDesc &d : st) {
+        S += d.n_slices;
+        tiles += (long long)d.n_slices * ((d.W + 15) / 16) * ((d.H + 15) / 16);
+    }
+    if (tiles >= (1ll << 31) || S >= (1ll << 20)) return fail(MG_ERR_INVALID_ARG, "too many slices or tiles");
+    mg_opts o = resolve_opts(opts, g->n, S);
+    if (o.cap_records >= (1ll << 31) || o.cap_entries >= (1ll << 32) - 1)
+        return fail(MG_ERR_INVALID_ARG, "capacities must be below 2^31 records and 2^32-1 entries");
+    WsLayout L = make_layout(g->n, st, o);
+    if (ws_bytes < L.total)
+        return fail(MG_ERR_INVALID_ARG, "workspace too small: need " + std::to_string(L.total) + " bytes");
+    char *w = (char *)ws;
+    SliceDev *slices = (SliceDev *)(w + L.slices);
+    StackTable tab = make_table(st);
+    mg_launch_build_slices(in, slices, (int)S, stream);
+    if (g->n > 0) {
+        mg_launch_bin(L, w, slices, tab, g->mean, g->quat, g->scale, g->alpha, g->n, o.cutoff_k, o.f64_ratio, stream);
+    } else {
+        cudaMemsetAsync(w + L.hdr, 0, sizeof(WsHeader), stream);
+        cudaMemsetAsync(w + L.tile_off, 0, sizeof(unsigned) * (size_t)(tiles + 1), stream);
+    }
+    mg_launch_render_fwd(L, w, tab, out, stream);
+    mg_status s = check_cuda("mg_render_fwd");
+    if (s != MG_OK) return s;
+    {
+        std::lock_guard<std::mutex> lk(g_tag_mu);
+        g_tags[ws] = make_tag(g, st, o);
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_opts mg_default_opts(void)
+{
+    mg_opts o;
+    o.cutoff_k = 3.0f;
+    o.f64_ratio = 100.0f;
+    o.cap_records = 0;
+    o.cap_entries = 0;
+    return o;
+}
+
+const char *mg_version(void) { return "mgauss 0.1 (sm_103a)"; }
+
+const char *mg_last_error(void) { return g_last_error.c_str(); }
+
+const char *mg_status_string(mg_status s)
+{
+    switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_CAPACITY: return "workspace capacity exceeded";
+    case MG_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case MG_ERR_NOT_FINITE: return "non-finite or non-positive input";
+    case MG_ERR_STALE_WORKSPACE: return "workspace does not hold the matching forward";
+    }
+    return "unknown status";
+}
+
+size_t mg_render_workspace_size(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts)
+{
+    std::string why;
+    if (!valid_gauss(g, why, false)) return 0;
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (!valid_stacks(st, false, why)) return 0;
+    long long S = 0;
+    for (const StackDesc &d : st) S += d.n_slices;
+    mg_opts o = resolve_opts(opts, g->n, S);
+    return make_layout(g->n, st, o).total;
+}
+
+mg_status mg_render_fwd(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts, float *out,
+                        void *ws, size_t ws_bytes, mg_stream_t stream)
+{
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (st.empty()) return fail(MG_ERR_INVALID_ARG, "stacks is NULL or n_stacks not in [1, 32]");
+    StackIn in = make_stack_in(st);
+    return render_fwd_impl(g, st, in, opts, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                        const float *grad_out, float *g_mean, float *g_quat, float *g_scale, float *g_alpha, void *ws,
+                        size_t ws_bytes, mg_stream_t stream)
+{
+    std::string why;
+    if (!valid_gauss(g, why)) return fail(MG_ERR_INVALID_ARG, why);
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (!valid_stacks(st, true, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (!grad_out || !ws) return fail(MG_ERR_INVALID_ARG, "grad_out or workspace is NULL");
+    if (g->n > 0 && (!g_mean || !g_quat || !g_scale || !g_alpha))
+        return fail(MG_ERR_INVALID_ARG, "a gradient output pointer is NULL");
+    long long S = 0;
+    for (const StackDesc &d : st) S += d.n_slices;
+    mg_opts o = resolve_opts(opts, g->n, S);
+    WsLayout L = make_layout(g->n, st, o);
+    if (ws_bytes < L.total) return fail(MG_ERR_INVALID_ARG, "workspace too small");
+    {
+        std::lock_guard<std::mutex> lk(g_tag_mu);
+        auto it = g_tags.find(ws);
+        if (it == g_tags.end() || !same_tag(it->second, make_tag(g, st, o)))
+            return fail(MG_ERR_STALE_WORKSPACE, "mg_render_bwd: no matching mg_render_fwd on this workspace");
+    }
+    if (g->n == 0) return MG_OK;
+    char *w = (char *)ws;
+    StackTable tab = make_table(st);
+    mg_launch_render_bwd(L, w, (const SliceDev *)(w + L.slices), tab, grad_out, g->mean, g->quat, g->scale, g->alpha,
+                         g->n, o.f64_ratio, g_mean, g_quat, g_scale, g_alpha, (cudaStream_t)stream);
+    return check_cuda("mg_render_bwd");
+}
+
+static mg_status fill_layout(const WsLayout &L, mg_ws_layout *out)
+{
+    out->rec_gid = L.rec_gid;
+    out->rec_slice = L.rec_slice;
+    out->rec_rect = L.rec_rect;
+    out->tile_off = L.tile_off;
+    out->entries = L.entries;
+    out->total_bytes = L.total;
+    return MG_OK;
+}
+
+mg_status mg_render_ws_layout(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                              mg_ws_layout *out)
+{
+    std::string why;
+    if (!out || !valid_gauss(g, why, false)) return fail(MG_ERR_INVALID_ARG, out ? why : "out is NULL");
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (!valid_stacks(st, false, why)) return fail(MG_ERR_INVALID_ARG, why);
+    long long S = 0;
+    for (const StackDesc &d : st) S += d.n_slices;
+    return fill_layout(make_layout(g->n, st, resolve_opts(opts, g->n, S)), out);
+}
+
+mg_status mg_sample_ws_layout(int64_t n, int32_t G, const mg_opts *opts, mg_ws_layout *out)
+{
+    if (!out || n < 0 || G < 1 || G > 1024) return fail(MG_ERR_INVALID_ARG, "bad arguments");
+    std::vector<StackDesc> st = {{G, G, G, 1.f, 1.f, 0.f, nullptr}};
+    return fill_layout(make_layout(n, st, resolve_opts(opts, n, G)), out);
+}
+
+mg_status mg_render_stats_get(const void *ws, size_t ws_bytes, mg_render_stats *stats, mg_stream_t stream)
+{
+    if (!ws || !stats || ws_bytes < sizeof(WsHeader)) return fail(MG_ERR_INVALID_ARG, "bad workspace or stats");
+    FwdTag tag;
+    {
+        std::lock_guard<std::mutex> lk(g_tag_mu);
+        auto it = g_tags.find(ws);
+        if (it == g_tags.end()) return fail(MG_ERR_STALE_WORKSPACE, "no forward recorded on this workspace");
+        tag = it->second;
+    }
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return check_cuda("mg_render_stats_get");
+    WsHeader h;
+    if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return check_cuda("mg_render_stats_get");
+    memset(stats, 0, sizeof(*stats));
+    stats->records = (int64_t)h.n_records;
+    stats->entries = (int64_t)h.n_entries;
+    long long tiles = 0;
+    for (size_t s = 0; s < tag.stack_key.size() / 6; ++s) {
+        long long ns = (long long)tag.stack_key[6 * s], H = (long long)tag.stack_key[6 * s + 1],
+                  W = (long long)tag.stack_key[6 * s + 2];
+        tiles += ns * ((W + 15) / 16) * ((H + 15) / 16);
+    }
+    stats->tiles = tiles;
+    stats->cap_records = tag.capr;
+    stats->cap_entries = tag.cape;
+    mg_status st = MG_OK;
+    if (h.flags & MG_FLAG_NOT_FINITE) st = MG_ERR_NOT_FINITE;
+    if ((long long)h.n_records > tag.capr || (long long)h.n_entries > tag.cape || (h.flags & MG_FLAG_CAP_CHUNKS))
+        st = MG_ERR_CAPACITY;
+    stats->status = st;
+    return st;
+}
+
+size_t mg_sample_workspace_size(int64_t n, int32_t G, const mg_opts *opts)
+{
+    if (n < 0 || G < 1 || G > 1024) return 0;
+    std::vector<StackDesc> st = {{G, G, G, 1.f, 1.f, 0.f, nullptr}};
+    mg_opts o = resolve_opts(opts, n, G);
+    return make_layout(n, st, o).total;
+}
+
+mg_status mg_sample_volume(const mg_gaussians *g, const float centre[3], float spacing, int32_t G, const mg_opts *opts,
+                           float *out, void *ws, size_t ws_bytes, mg_stream_t stream)
+{
+    if (!centre || !(spacing > 0.f) || !isfinite(spacing) || G < 1 || G > 1024)
+        return fail(MG_ERR_INVALID_ARG, "need a centre, spacing > 0 and 1 <= G <= 1024");
+    if (!isfinite(centre[0]) || !isfinite(centre[1]) || !isfinite(centre[2]))
+        return fail(MG_ERR_INVALID_ARG, "centre must be finite");
+    std::vector<StackDesc> st = {{G, G, G, spacing, spacing, 0.f, nullptr}};
+    StackIn in = make_stack_in(st);
+    in.planes = 1;
+    in.cx = centre[0];
+    in.cy = centre[1];
+    in.cz = centre[2];
+    in.h = spacing;
+    return render_fwd_impl(g, st, in, opts, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t mg_reduce_workspace_size(int64_t n)
+{
+    if (n < 0) return 0;
+    return align256(sizeof(double) * 2 * (size_t)mg_reduce_blocks(n));
+}
+
+mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float *grad, double *loss_out, void *ws,
+                       size_t ws_bytes, mg_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!pred || !target)) || !loss_out || !ws)
+        return fail(MG_ERR_INVALID_ARG, "bad pointer or size");
+    if (ws_bytes < mg_reduce_workspace_size(n)) return fail(MG_ERR_INVALID_ARG, "workspace too small");
+    mg_launch_loss_l1l2(pred, target, n, grad, loss_out, (double *)ws, (cudaStream_t)stream);
+    return check_cuda("mg_loss_l1l2");
+}
+
+mg_status mg_sq_diff_sum(const float *a, const float *b, int64_t n, double *out, void *ws, size_t ws_bytes,
+                         mg_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!a || !b)) || !out || !ws) return fail(MG_ERR_INVALID_ARG, "bad pointer or size");
+    if (ws_bytes < mg_reduce_workspace_size(n)) return fail(MG_ERR_INVALID_ARG, "workspace too small");
+    mg_launch_sq_diff(a, b, n, out, (double *)ws, (cudaStream_t)stream);
+    return check_cuda("mg_sq_diff_sum");
+}
+
+}  // extern "C"

@@ -1,0 +1,696 @@
+// mg_bin.cu -- record pass and tile binning (count, exclusive scan, stable scatter).
+//
+// Sec. 3.3.1 of the paper restricts each voxel's sum to a local Gaussian set;
+// here that set is decided per (Gaussian, slice) record and per 16x16 tile:
+//   K1  k1_count / k1_emit : per (Gaussian, slice) K-sigma slab test of the
+//       profile-convolved covariance and the tile rectangle of the cut
+//       ellipse (the FP32 record predicate of mgauss.h, bit-exact), then the
+//       record's evaluation geometry (2D centre, conic, amplitude).
+//   K2  three-phase exclusive scans (no inter-block waiting).
+//   K3  bin_hist / bin_colscan / bin_scatter : a counting sort of (record,
+//       tile) entries by tile, chunked per slice, with warp-level ranking by
+//       __match_any_sync so the order inside each tile list is reproducible.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "mg_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// slice table
+// ---------------------------------------------------------------------------
+__global__ void k_build_slices(StackIn in, SliceDev *out, int S)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    int s = 0, base = 0, tile_base = 0;
+    long long pix = 0;
+    while (s < in.n_stacks && k >= base + in.n_slices[s]) {
+        int TX = (in.W[s] + MG_TILE - 1) / MG_TILE, TY = (in.H[s] + MG_TILE - 1) / MG_TILE;
+        tile_base += in.n_slices[s] * TX * TY;
+        pix += (long long)in.n_slices[s] * in.H[s] * in.W[s];
+        base += in.n_slices[s];
+        ++s;
+    }
+    int kk = k - base;
+    SliceDev d;
+    d.W = in.W[s];
+    d.H = in.H[s];
+    d.TX = (d.W + MG_TILE - 1) / MG_TILE;
+    d.TY = (d.H + MG_TILE - 1) / MG_TILE;
+    d.tile_base = tile_base + kk * d.TX * d.TY;
+    d.pix_base = pix + (long long)kk * d.H * d.W;
+    d.stack = s;
+    d.dx = in.dx[s];
+    d.dy = in.dy[s];
+    d.sig2 = in.sig2[s];
+    d.hx = 0.5f * (float)(d.W - 1);
+    d.hy = 0.5f * (float)(d.H - 1);
+    if (in.planes) {
+        for (int i = 0; i < 9; ++i) d.Q[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+        d.t[0] = in.cx;
+        d.t[1] = in.cy;
+        // plane height evaluated in double, rounded once to float
+        d.t[2] = (float)__dadd_rn((double)in.cz, __dmul_rn((double)in.h, (double)kk - 0.5 * (double)(in.n_slices[0] - 1)));
+    } else {
+        const float *x = in.xform[s] + (size_t)kk * 12;
+        for (int i = 0; i < 9; ++i) d.Q[i] = x[i];
+        for (int i = 0; i < 3; ++i) d.t[i] = x[9 + i];
+    }
+    out[k] = d;
+}
+
+void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_t st)
+{
+    k_build_slices<<<(S + 127) / 128, 128, 0, st>>>(in, out, S);
+}
+
+// ---------------------------------------------------------------------------
+// three-phase exclusive scan of uint32 (totals in uint64, outputs saturate)
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long *total)
+{
+    __shared__ unsigned long long wsum[NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = (lane < NT / 32) ? wsum[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NT / 32) wsum[lane] = s;  // inclusive
+    }
+    __syncthreads();
+    unsigned long long pre = (w > 0 ? wsum[w - 1] : 0ull) + x - v;
+    if (total) *total = wsum[NT / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+constexpr int SCAN_NT = 512;
+constexpr int SCAN_ITEMS = 4;
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const unsigned *in, long long n,
+                                                         unsigned long long *part)
+{
+    long long per = (n + gridDim.x - 1) / gridDim.x;
+    long long b0 = (long long)blockIdx.x * per;
+    long long b1 = b0 + per < n ? b0 + per : n;
+    unsigned long long s = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += SCAN_NT) s += in[i];
+    unsigned long long tot;
+    block_exclusive_scan<SCAN_NT>(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_part(unsigned long long *part, int nb,
+                                                       unsigned long long *total_out)
+{
+    unsigned long long v = threadIdx.x < nb ? part[threadIdx.x] : 0ull;
+    unsigned long long tot;
+    unsigned long long pre = block_exclusive_scan<SCAN_NT>(v, &tot);
+    if (threadIdx.x < nb) part[threadIdx.x] = pre;
+    if (threadIdx.x == 0 && total_out) *total_out = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_down(const unsigned *in, unsigned *out, long long n,
+                                                       const unsigned long long *part, int write_end)
+{
+    long long per = (n + gridDim.x - 1) / gridDim.x;
+    long long b0 = (long long)blockIdx.x * per;
+    long long b1 = b0 + per < n ? b0 + per : n;
+    unsigned long long run = part[blockIdx.x];
+    for (long long base = b0; base < b1; base += (long long)SCAN_NT * SCAN_ITEMS) {
+        unsigned v[SCAN_ITEMS];
+        unsigned long long s = 0;
+        long long i0 = base + (long long)threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            v[j] = (i0 + j < b1) ? in[i0 + j] : 0u;
+            s += v[j];
+        }
+        unsigned long long tot;
+        unsigned long long pre = block_exclusive_scan<SCAN_NT>(s, &tot) + run;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            if (i0 + j < b1) out[i0 + j] = pre > 0xffffffffull ? 0xffffffffu : (unsigned)pre;
+            pre += v[j];
+        }
+        run += tot;
+    }
+    if (write_end && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        out[n] = run > 0xffffffffull ? 0xffffffffu : (unsigned)run;
+}
+
+void mg_launch_scan_u32(const unsigned *in, unsigned *out, long long n_host, const unsigned long long *n_dev,
+                        unsigned long long *part, unsigned long long *total_out, cudaStream_t st)
+{
+    (void)n_dev;
+    int nb = MG_SCAN_BLOCKS;
+    k_scan_reduce<<<nb, SCAN_NT, 0, st>>>(in, n_host, part);
+    k_scan_part<<<1, SCAN_NT, 0, st>>>(part, nb, total_out);
+    k_scan_down<<<nb, SCAN_NT, 0, st>>>(in, out, n_host, part, 1);
+}
+
+// ---------------------------------------------------------------------------
+// the FP32 record predicate (specified operation by operation in mgauss.h)
+// ---------------------------------------------------------------------------
+struct GaussPred {
+    float mu[3];
+    float Sg[3][3];  // covariance, FP32 as specified
+};
+
+__device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0, float b1, float b2)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));
+}
+
+__device__ __forceinline__ bool finite_f(float x) { return isfinite(x); }
+
+// loads one Gaussian; false if any value is not finite or a scale is <= 0
+__device__ bool load_gauss_pred(const float *mean, const float *quat, const float *scale, const float *alpha,
+                                long long g, GaussPred &G)
+{
+    float m0 = mean[3 * g], m1 = mean[3 * g + 1], m2 = mean[3 * g + 2];
+    float w = quat[4 * g], x = quat[4 * g + 1], y = quat[4 * g + 2], z = quat[4 * g + 3];
+    float s0 = scale[3 * g], s1 = scale[3 * g + 1], s2 = scale[3 * g + 2];
+    float a = alpha[g];
+    bool ok = finite_f(m0) && finite_f(m1) && finite_f(m2) && finite_f(w) && finite_f(x) && finite_f(y) &&
+              finite_f(z) && finite_f(s0) && finite_f(s1) && finite_f(s2) && finite_f(a) && s0 > 0.f && s1 > 0.f &&
+              s2 > 0.f;
+    G.mu[0] = m0;
+    G.mu[1] = m1;
+    G.mu[2] = m2;
+    float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+    float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+    float R[3][3];
+    R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    R[0][1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    R[0][2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    R[1][0] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    R[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    R[1][2] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    R[2][0] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    R[2][1] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    R[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+    float s[3] = {s0, s1, s2};
+    float M[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[r][c] = __fmul_rn(R[r][c], s[c]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            float v = dot3_rn(M[r][0], M[r][1], M[r][2], M[c][0], M[c][1], M[c][2]);
+            G.Sg[r][c] = v;
+            G.Sg[c][r] = v;
+        }
+    return ok;
+}
+
+struct PredOut {
+    float w0, u0, v0, Sww, Luw, Lvw;
+    int il, ih, jl, jh;  // clamped pixel box
+};
+
+// slab test only (cheap prefilter) then the full predicate; returns existence
+__device__ __forceinline__ bool record_predicate(const GaussPred &G, const SliceDev &S, float K2, PredOut &o)
+{
+    const float *Q = S.Q;
+    float p0 = __fsub_rn(G.mu[0], S.t[0]), p1 = __fsub_rn(G.mu[1], S.t[1]), p2 = __fsub_rn(G.mu[2], S.t[2]);
+    float en0 = Q[2], en1 = Q[5], en2 = Q[8];
+    float w0 = dot3_rn(en0, en1, en2, p0, p1, p2);
+    float sn0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], en0, en1, en2);
+    float sn1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], en0, en1, en2);
+    float sn2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], en0, en1, en2);
+    float Lww = dot3_rn(en0, en1, en2, sn0, sn1, sn2);
+    float Sww = __fadd_rn(Lww, S.sig2);
+    float ww = __fmul_rn(w0, w0);
+    if (!(ww <= __fmul_rn(K2, Sww))) return false;
+    float eu0 = Q[0], eu1 = Q[3], eu2 = Q[6];
+    float ev0 = Q[1], ev1 = Q[4], ev2 = Q[7];
+    float u0 = dot3_rn(eu0, eu1, eu2, p0, p1, p2);
+    float v0 = dot3_rn(ev0, ev1, ev2, p0, p1, p2);
+    float Luw = dot3_rn(eu0, eu1, eu2, sn0, sn1, sn2);
+    float Lvw = dot3_rn(ev0, ev1, ev2, sn0, sn1, sn2);
+    float su0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], eu0, eu1, eu2);
+    float su1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], eu0, eu1, eu2);
+    float su2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], eu0, eu1, eu2);
+    float Luu = dot3_rn(eu0, eu1, eu2, su0, su1, su2);
+    float sv0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], ev0, ev1, ev2);
+    float sv1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], ev0, ev1, ev2);
+    float sv2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], ev0, ev1, ev2);
+    float Lvv = dot3_rn(ev0, ev1, ev2, sv0, sv1, sv2);
+    float r2 = __fsub_rn(K2, __fdiv_rn(ww, Sww));
+    if (r2 < 0.0f) r2 = 0.0f;
+    float Cuu = __fsub_rn(Luu, __fdiv_rn(__fmul_rn(Luw, Luw), Sww));
+    if (Cuu < 0.0f) Cuu = 0.0f;
+    float Cvv = __fsub_rn(Lvv, __fdiv_rn(__fmul_rn(Lvw, Lvw), Sww));
+    if (Cvv < 0.0f) Cvv = 0.0f;
+    float cu = __fsub_rn(u0, __fdiv_rn(__fmul_rn(Luw, w0), Sww));
+    float cv = __fsub_rn(v0, __fdiv_rn(__fmul_rn(Lvw, w0), Sww));
+    float ru = __fsqrt_rn(__fmul_rn(r2, Cuu));
+    float rv = __fsqrt_rn(__fmul_rn(r2, Cvv));
+    float il = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cu, ru), S.dx), S.hx));
+    float ih = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(cu, ru), S.dx), S.hx));
+    float jl = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cv, rv), S.dy), S.hy));
+    float jh = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(cv, rv), S.dy), S.hy));
+    float Wm1 = (float)(S.W - 1), Hm1 = (float)(S.H - 1);
+    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) return false;
+    if (il < 0.0f) il = 0.0f;
+    if (jl < 0.0f) jl = 0.0f;
+    if (ih > Wm1) ih = Wm1;
+    if (jh > Hm1) jh = Hm1;
+    o.il = (int)il;
+    o.ih = (int)ih;
+    o.jl = (int)jl;
+    o.jh = (int)jh;
+    o.w0 = w0;
+    o.u0 = u0;
+    o.v0 = v0;
+    o.Sww = Sww;
+    o.Luw = Luw;
+    o.Lvw = Lvw;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// record geometry for the evaluation kernels (not bit-specified; FP32, or
+// FP64 for near-degenerate Gaussians). Profile-convolved covariance
+// Sigma' = Sigma_L + sig2 e_w e_w^T in slice coordinates; its precision block
+// on the plane (Sherman-Morrison on Sigma_L^-1 = g g^T, g = Q^T R diag(1/s)),
+// conditional centre and amplitude alpha |Sigma_L|^1/2 |Sigma'|^-1/2 e^{-w0^2/2Sww}.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RecGeomT {
+    T pcx, pcy, A, B2, C, amp;
+};
+
+template <typename T>
+__device__ __forceinline__ T t_exp(T x);
+template <>
+__device__ __forceinline__ float t_exp<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double t_exp<double>(double x) { return exp(x); }
+
+template <typename T>
+__device__ __forceinline__ T t_rsqrt(T x);
+template <>
+__device__ __forceinline__ float t_rsqrt<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double t_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
+
+template <typename T>
+__device__ void record_geometry(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
+                                RecGeomT<T> &o)
+{
+    T w = q[0], x = q[1], y = q[2], z = q[3];
+    T R[3][3];
+    R[0][0] = 1 - 2 * (y * y + z * z);
+    R[0][1] = 2 * (x * y - w * z);
+    R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);
+    R[1][1] = 1 - 2 * (x * x + z * z);
+    R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);
+    R[2][1] = 2 * (y * z + w * x);
+    R[2][2] = 1 - 2 * (x * x + y * y);
+    T sc[3] = {s[0], s[1], s[2]};
+    T P[3][3];  // P[a][c] = e_a . R_c,  a in (u, v, w)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            P[a][c] = (T)S.Q[a] * R[0][c] + (T)S.Q[3 + a] * R[1][c] + (T)S.Q[6 + a] * R[2][c];
+    T p0 = (T)mu[0] - (T)S.t[0], p1 = (T)mu[1] - (T)S.t[1], p2 = (T)mu[2] - (T)S.t[2];
+    T du = (T)S.Q[0] * p0 + (T)S.Q[3] * p1 + (T)S.Q[6] * p2;
+    T dv = (T)S.Q[1] * p0 + (T)S.Q[4] * p1 + (T)S.Q[7] * p2;
+    T w0 = (T)S.Q[2] * p0 + (T)S.Q[5] * p1 + (T)S.Q[8] * p2;
+    T g[3][3], L[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            g[a][c] = P[a][c] / sc[c];
+            L[a][c] = P[a][c] * sc[c];
+        }
+    T Huu = g[0][0] * g[0][0] + g[0][1] * g[0][1] + g[0][2] * g[0][2];
+    T Huv = g[0][0] * g[1][0] + g[0][1] * g[1][1] + g[0][2] * g[1][2];
+    T Hvv = g[1][0] * g[1][0] + g[1][1] * g[1][1] + g[1][2] * g[1][2];
+    T Huw = g[0][0] * g[2][0] + g[0][1] * g[2][1] + g[0][2] * g[2][2];
+    T Hvw = g[1][0] * g[2][0] + g[1][1] * g[2][1] + g[1][2] * g[2][2];
+    T Hww = g[2][0] * g[2][0] + g[2][1] * g[2][1] + g[2][2] * g[2][2];
+    T Suw = L[0][0] * L[2][0] + L[0][1] * L[2][1] + L[0][2] * L[2][2];
+    T Svw = L[1][0] * L[2][0] + L[1][1] * L[2][1] + L[1][2] * L[2][2];
+    T Sww = L[2][0] * L[2][0] + L[2][1] * L[2][1] + L[2][2] * L[2][2] + (T)S.sig2;
+    T sig2 = (T)S.sig2;
+    T D = 1 + sig2 * Hww;
+    T f = sig2 / D;
+    T Kuu = Huu - f * Huw * Huw;
+    T Kuv = Huv - f * Huw * Hvw;
+    T Kvv = Hvv - f * Hvw * Hvw;
+    T cu = du - Suw * w0 / Sww;
+    T cv = dv - Svw * w0 / Sww;
+    const T kap = (T)(-0.72134752044448170368);  // -log2(e)/2
+    T dx = S.dx, dy = S.dy;
+    o.pcx = cu / dx + (T)S.hx;
+    o.pcy = cv / dy + (T)S.hy;
+    o.A = kap * Kuu * dx * dx;
+    o.B2 = 2 * kap * Kuv * dx * dy;
+    o.C = kap * Kvv * dy * dy;
+    o.amp = (T)alpha * t_rsqrt<T>(D) * t_exp<T>((T)(-0.5) * w0 * w0 / Sww);
+}
+
+__device__ __forceinline__ bool is_degenerate(const float *s, float ratio)
+{
+    if (!(ratio > 0.0f)) return false;
+    float mx = fmaxf(fmaxf(s[0], s[1]), s[2]);
+    float mn = fminf(fminf(s[0], s[1]), s[2]);
+    return mx > ratio * mn;
+}
+
+// ---------------------------------------------------------------------------
+// K1: count and emit records, grid (Gaussian blocks of 256, slice groups)
+// ---------------------------------------------------------------------------
+constexpr int K1_NT = 256;
+constexpr int K1_SG = 16;  // slices per group
+
+__global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *slices, int S, const float *mean,
+                                                  const float *quat, const float *scale, const float *alpha,
+                                                  long long n, float K2, unsigned *cnt, int NB, WsHeader *hdr)
+{
+    __shared__ SliceDev ssl[K1_SG];
+    const int k0 = blockIdx.y * K1_SG;
+    const int nk = min(K1_SG, S - k0);
+    for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
+    __syncthreads();
+    long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    GaussPred G;
+    bool valid = false;
+    if (g < n) {
+        valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
+        if (!valid && blockIdx.y == 0) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
+    }
+    for (int kk = 0; kk < nk; ++kk) {
+        PredOut po;
+        int f = valid ? (int)record_predicate(G, ssl[kk], K2, po) : 0;
+        int c = __syncthreads_count(f);
+        if (threadIdx.x == 0) cnt[(long long)(k0 + kk) * NB + blockIdx.x] = (unsigned)c;
+    }
+}
+
+__global__ void __launch_bounds__(K1_NT) k1_emit(const SliceDev *slices, int S, const float *mean, const float *quat,
+                                                 const float *scale, const float *alpha, long long n, float K2,
+                                                 float f64_ratio, const unsigned *off, int NB, Records rec)
+{
+    __shared__ SliceDev ssl[K1_SG];
+    __shared__ unsigned wc[2][K1_NT / 32];
+    const int k0 = blockIdx.y * K1_SG;
+    const int nk = min(K1_SG, S - k0);
+    for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
+    __syncthreads();
+    long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    GaussPred G;
+    bool valid = false;
+    bool degen = false;
+    float sc[3] = {1.f, 1.f, 1.f}, qv[4] = {1.f, 0.f, 0.f, 0.f}, av = 0.f;
+    if (g < n) {
+        valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
+        sc[0] = scale[3 * g];
+        sc[1] = scale[3 * g + 1];
+        sc[2] = scale[3 * g + 2];
+        qv[0] = quat[4 * g];
+        qv[1] = quat[4 * g + 1];
+        qv[2] = quat[4 * g + 2];
+        qv[3] = quat[4 * g + 3];
+        av = alpha[g];
+        degen = is_degenerate(sc, f64_ratio);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int kk = 0; kk < nk; ++kk) {
+        PredOut po;
+        bool f = valid && record_predicate(G, ssl[kk], K2, po);
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wc[kk & 1][w] = __popc(bal);
+        __syncthreads();
+        if (f) {
+            unsigned long long pos = off[(long long)(k0 + kk) * NB + blockIdx.x];
+            for (int u = 0; u < w; ++u) pos += wc[kk & 1][u];
+            pos += __popc(bal & lanemask_lt());
+            if ((long long)pos < rec.cap) {
+                const SliceDev &Sd = ssl[kk];
+                float4 geo;
+                float2 geo2;
+                if (degen) {
+                    RecGeomT<double> r;
+                    record_geometry<double>(G.mu, qv, sc, av, Sd, r);
+                    geo = make_float4((float)r.pcx, (float)r.pcy, (float)r.A, (float)r.B2);
+                    geo2 = make_float2((float)r.C, (float)r.amp);
+                } else {
+                    RecGeomT<float> r;
+                    record_geometry<float>(G.mu, qv, sc, av, Sd, r);
+                    geo = make_float4(r.pcx, r.pcy, r.A, r.B2);
+                    geo2 = make_float2(r.C, r.amp);
+                }
+                rec.geo[pos] = geo;
+                rec.geo2[pos] = geo2;
+                rec.gid[pos] = (int)g;
+                rec.slice[pos] = k0 + kk;
+                rec.rect[pos] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
+                                             (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: per-slice chunks of records, chunk histograms, column scan, scatter
+// ---------------------------------------------------------------------------
+// one block: slice record ranges (clamped to capacity) and chunk offsets
+__global__ void __launch_bounds__(1024) k_chunk_setup(const unsigned *rec_off, int S, int NB,
+                                                      unsigned *slice_rs, unsigned *chunk_base, long long cap_rec,
+                                                      long long cap_chunks, WsHeader *hdr)
+{
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    unsigned long long total = hdr->n_records;
+    for (int base = 0; base < S; base += 1024) {
+        int k = base + threadIdx.x;
+        unsigned long long nch = 0;
+        if (k < S) {
+            unsigned long long rs = rec_off[(long long)k * NB];
+            unsigned long long re = (k + 1 < S) ? rec_off[(long long)(k + 1) * NB] : total;
+            if (rs > (unsigned long long)cap_rec) rs = cap_rec;
+            if (re > (unsigned long long)cap_rec) re = cap_rec;
+            slice_rs[k] = (unsigned)rs;
+            if (k == S - 1) slice_rs[S] = (unsigned)re;
+            nch = (re > rs) ? (re - rs + MG_CHUNK - 1) / MG_CHUNK : 0;
+        }
+        // block scan with 1024 threads
+        __shared__ unsigned long long ws[32];
+        unsigned long long x = nch;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            unsigned long long s = ws[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            ws[lane] = s;
+        }
+        __syncthreads();
+        unsigned long long pre = carry + (w > 0 ? ws[w - 1] : 0ull) + x - nch;
+        if (k < S) chunk_base[k] = (unsigned)pre;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += ws[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        chunk_base[S] = (unsigned)carry;
+        hdr->n_chunks = carry;
+        if (carry > (unsigned long long)cap_chunks) atomicOr(&hdr->flags, MG_FLAG_CAP_CHUNKS);
+    }
+}
+
+__device__ __forceinline__ int find_slice(const unsigned *chunk_base, int S, unsigned c)
+{
+    // largest k with chunk_base[k] <= c (chunk_base is non-decreasing, chunk_base[S] = total)
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (chunk_base[mid] <= c)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int BIN_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *slices, int S, const unsigned *slice_rs,
+                                                             const unsigned *chunk_base, const ushort4 *rect,
+                                                             unsigned *hist, int Tmax, long long cap_chunks)
+{
+    extern __shared__ unsigned smem_u[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned *hs = smem_u + w * Tmax;
+    unsigned n_chunks = chunk_base[S];
+    if ((long long)n_chunks > cap_chunks) n_chunks = (unsigned)cap_chunks;
+    for (unsigned c = blockIdx.x * BIN_WARPS + w; c < n_chunks; c += gridDim.x * BIN_WARPS) {
+        int k = find_slice(chunk_base, S, c);
+        const int TX = slices[k].TX, Tk = TX * slices[k].TY;
+        unsigned r0 = slice_rs[k] + (c - chunk_base[k]) * MG_CHUNK;
+        unsigned r1 = min(r0 + MG_CHUNK, slice_rs[k + 1]);
+        for (int t = lane; t < Tk; t += 32) hs[t] = 0;
+        __syncwarp();
+        for (unsigned r = r0 + lane; r < r1; r += 32) {
+            ushort4 rc = rect[r];
+            for (int ty = rc.y; ty <= rc.w; ++ty)
+                for (int tx = rc.x; tx <= rc.z; ++tx) atomicAdd(&hs[ty * TX + tx], 1u);
+        }
+        __syncwarp();
+        unsigned *hout = hist + (size_t)c * Tmax;
+        for (int t = lane; t < Tk; t += 32) hout[t] = hs[t];
+        __syncwarp();
+    }
+}
+
+// per (slice, tile): exclusive prefix over the slice's chunks; tile totals
+__global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chunk_base, unsigned *hist, int Tmax,
+                              long long cap_chunks, unsigned *tile_cnt)
+{
+    long long total = (long long)S * Tmax;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int k = (int)(idx / Tmax), t = (int)(idx % Tmax);
+        int Tk = slices[k].TX * slices[k].TY;
+        if (t >= Tk) continue;
+        unsigned c0 = chunk_base[k], c1 = chunk_base[k + 1];
+        if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
+        unsigned run = 0;
+        for (unsigned c = c0; c < c1; ++c) {
+            unsigned v = hist[(size_t)c * Tmax + t];
+            hist[(size_t)c * Tmax + t] = run;
+            run += v;
+        }
+        tile_cnt[slices[k].tile_base + t] = run;
+    }
+}
+
+__global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *slices, int S,
+                                                                const unsigned *slice_rs, const unsigned *chunk_base,
+                                                                const ushort4 *rect, const unsigned *hist, int Tmax,
+                                                                long long cap_chunks, const unsigned *tile_off,
+                                                                unsigned *entries, long long cap_entries)
+{
+    extern __shared__ unsigned smem_u[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned *cur = smem_u + w * Tmax;
+    unsigned n_chunks = chunk_base[S];
+    if ((long long)n_chunks > cap_chunks) n_chunks = (unsigned)cap_chunks;
+    const unsigned lt = lanemask_lt();
+    for (unsigned c = blockIdx.x * BIN_WARPS + w; c < n_chunks; c += gridDim.x * BIN_WARPS) {
+        int k = find_slice(chunk_base, S, c);
+        const int TX = slices[k].TX, Tk = TX * slices[k].TY, tb = slices[k].tile_base;
+        unsigned r0 = slice_rs[k] + (c - chunk_base[k]) * MG_CHUNK;
+        unsigned r1 = min(r0 + MG_CHUNK, slice_rs[k + 1]);
+        const unsigned *hin = hist + (size_t)c * Tmax;
+        for (int t = lane; t < Tk; t += 32) cur[t] = tile_off[tb + t] + hin[t];
+        __syncwarp();
+        for (unsigned base = r0; base < r1; base += 32) {
+            unsigned r = base + lane;
+            bool have = r < r1;
+            ushort4 rc = have ? rect[r] : make_ushort4(0, 0, 0, 0);
+            int wdt = rc.z - rc.x + 1;
+            int area = have ? wdt * (rc.w - rc.y + 1) : 0;
+            int maxa = __reduce_max_sync(0xffffffffu, area);
+            for (int j = 0; j < maxa; ++j) {
+                bool act = j < area;
+                unsigned t = 0xffffffffu;
+                if (act) t = (unsigned)((rc.y + j / wdt) * TX + rc.x + j % wdt);
+                unsigned peers = __match_any_sync(0xffffffffu, t);
+                unsigned before = peers & lt;
+                unsigned pos = 0;
+                if (act) pos = cur[t] + __popc(before);
+                __syncwarp();
+                if (act) {
+                    if ((long long)pos < cap_entries) entries[pos] = r;
+                    if (before == 0) cur[t] += __popc(peers);
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the whole record + binning pass
+// ---------------------------------------------------------------------------
+void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab, const float *mean,
+                   const float *quat, const float *scale, const float *alpha, long long n, float K, float f64_ratio,
+                   cudaStream_t st)
+{
+    WsHeader *hdr = (WsHeader *)(ws + L.hdr);
+    unsigned *cnt = (unsigned *)(ws + L.cnt);
+    unsigned long long *part = (unsigned long long *)(ws + L.scan_part);
+    Records rec;
+    rec.geo = (float4 *)(ws + L.rec_geo);
+    rec.geo2 = (float2 *)(ws + L.rec_geo2);
+    rec.gid = (int *)(ws + L.rec_gid);
+    rec.slice = (int *)(ws + L.rec_slice);
+    rec.rect = (ushort4 *)(ws + L.rec_rect);
+    rec.mom = (float *)(ws + L.rec_mom);
+    rec.cap = L.cap_records;
+    unsigned *chunk_base = (unsigned *)(ws + L.chunk_base);
+    unsigned *slice_rs = chunk_base + (L.S + 1);
+    unsigned *hist = (unsigned *)(ws + L.hist);
+    unsigned *tile_cnt = (unsigned *)(ws + L.tile_cnt);
+    unsigned *tile_off = (unsigned *)(ws + L.tile_off);
+    unsigned *entries = (unsigned *)(ws + L.entries);
+    const int S = (int)L.S, NB = (int)L.NB;
+    const float K2 = K * K;  // one FP32 multiply, rounded once (as in the predicate)
+
+    cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
+    dim3 g1((unsigned)NB, (unsigned)((S + K1_SG - 1) / K1_SG));
+    k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, cnt, NB, hdr);
+    mg_launch_scan_u32(cnt, cnt, (long long)S * NB, nullptr, part, &hdr->n_records, st);
+    k1_emit<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NB, rec);
+    k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, NB, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
+    const int Tmax = (int)L.max_tiles;
+    size_t smem = (size_t)BIN_WARPS * Tmax * sizeof(unsigned);
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_bin_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    long long want = (L.cap_chunks + BIN_WARPS - 1) / BIN_WARPS;
+    int gb = (int)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
+    k_bin_hist<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax, L.cap_chunks);
+    long long tot = (long long)S * Tmax;
+    int gc = (int)((tot + 255) / 256 < 148 * 32 ? (tot + 255) / 256 : 148 * 32);
+    k_bin_colscan<<<gc, 256, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt);
+    mg_launch_scan_u32(tile_cnt, tile_off, L.n_tiles, nullptr, part, &hdr->n_entries, st);
+    k_bin_scatter<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+                                                    L.cap_chunks, tile_off, entries, L.cap_entries);
+}

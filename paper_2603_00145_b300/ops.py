@@ -1,0 +1,319 @@
+"""Python binding of the mgauss C ABI over torch CUDA tensors.
+
+The functions ``mg_*`` below carry the names and arguments of include/mgauss.h
+and only marshal arguments (tensor -> device pointer, stream handle); every
+step of the computation runs in the library's CUDA kernels. PyTorch provides
+device memory, streams and autograd glue.
+
+``SliceRenderer`` owns a workspace and grows it when the device reports a
+capacity overflow; ``RenderSlices`` is the autograd Function whose backward
+is ``mg_render_bwd``.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import List, Sequence
+
+import torch
+
+from . import _lib as L
+
+_F32 = torch.float32
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype=_F32, numel=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _gauss(mean, quat, scale, alpha) -> L.MgGaussians:
+    n = mean.shape[0] if mean.dim() == 2 else mean.numel() // 3
+    return L.MgGaussians(n, _dev(mean, "mean", numel=3 * n), _dev(quat, "quat", numel=4 * n),
+                         _dev(scale, "scale", numel=3 * n), _dev(alpha, "alpha", numel=n))
+
+
+def _opts(cutoff_k=3.0, f64_ratio=100.0, cap_records=0, cap_entries=0) -> L.MgOpts:
+    return L.MgOpts(float(cutoff_k), float(f64_ratio), int(cap_records), int(cap_entries))
+
+
+class DeviceStacks:
+    """Stack geometry resident on the device (transforms uploaded once)."""
+
+    def __init__(self, stacks: Sequence, device="cuda"):
+        self.stacks = list(stacks)
+        self.xforms = [torch.as_tensor(s.xform, dtype=_F32).reshape(s.n_slices, 12).contiguous().to(device)
+                       for s in self.stacks]
+        arr = (L.MgStack * len(self.stacks))()
+        for i, (s, x) in enumerate(zip(self.stacks, self.xforms)):
+            arr[i] = L.MgStack(int(s.n_slices), int(s.H), int(s.W), float(s.dx), float(s.dy), float(s.thickness),
+                               x.data_ptr())
+        self.arr = arr
+        self.n = len(self.stacks)
+        self.n_vox = sum(int(s.n_slices) * int(s.H) * int(s.W) for s in self.stacks)
+        self.n_slices = sum(int(s.n_slices) for s in self.stacks)
+        self.n_tiles = sum(int(s.n_slices) * ((int(s.W) + 15) // 16) * ((int(s.H) + 15) // 16) for s in self.stacks)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+
+def mg_render_workspace_size(n: int, stacks: DeviceStacks, opts: L.MgOpts) -> int:
+    g = L.MgGaussians(int(n), None, None, None, None)
+    return int(L.lib().mg_render_workspace_size(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts)))
+
+
+def mg_render_fwd(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, out, ws, stream=None):
+    g = _gauss(mean, quat, scale, alpha)
+    _dev(out, "out", numel=stacks.n_vox)
+    _dev(ws, "ws", dtype=torch.uint8)
+    st = L.lib().mg_render_fwd(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts), out.data_ptr(),
+                               ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    L.check(st, "mg_render_fwd")
+
+
+def mg_render_bwd(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, grad_out, g_mean, g_quat,
+                  g_scale, g_alpha, ws, stream=None, raise_on_error=True) -> int:
+    g = _gauss(mean, quat, scale, alpha)
+    n = g.n
+    _dev(grad_out, "grad_out", numel=stacks.n_vox)
+    ptrs = [_dev(g_mean, "g_mean", numel=3 * n), _dev(g_quat, "g_quat", numel=4 * n),
+            _dev(g_scale, "g_scale", numel=3 * n), _dev(g_alpha, "g_alpha", numel=n)]
+    st = L.lib().mg_render_bwd(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts), grad_out.data_ptr(),
+                               *ptrs, ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    if raise_on_error:
+        L.check(st, "mg_render_bwd")
+    return st
+
+
+def mg_render_ws_layout(n: int, stacks: DeviceStacks, opts: L.MgOpts) -> dict:
+    g = L.MgGaussians(int(n), None, None, None, None)
+    lay = L.MgWsLayout()
+    L.check(L.lib().mg_render_ws_layout(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts), ctypes.byref(lay)),
+            "mg_render_ws_layout")
+    return {k: int(getattr(lay, k)) for k, _ in L.MgWsLayout._fields_}
+
+
+def mg_sample_ws_layout(n: int, G: int, opts: L.MgOpts) -> dict:
+    lay = L.MgWsLayout()
+    L.check(L.lib().mg_sample_ws_layout(int(n), int(G), ctypes.byref(opts), ctypes.byref(lay)), "mg_sample_ws_layout")
+    return {k: int(getattr(lay, k)) for k, _ in L.MgWsLayout._fields_}
+
+
+def read_bins(ws, layout: dict, n_records: int, n_tiles: int, n_entries: int):
+    """Copies of the records (gid, slice, rect) and tile bins from a workspace."""
+    def view(off, count, dtype, width=1):
+        nbytes = count * width * torch.tensor([], dtype=dtype).element_size()
+        return ws[off:off + nbytes].view(dtype).reshape(count, width).cpu()
+    gid = view(layout["rec_gid"], n_records, torch.int32)[:, 0]
+    sl = view(layout["rec_slice"], n_records, torch.int32)[:, 0]
+    rect = view(layout["rec_rect"], n_records, torch.int16, 4).to(torch.int32) & 0xFFFF
+    toff = view(layout["tile_off"], n_tiles + 1, torch.int32)[:, 0].to(torch.int64) & 0xFFFFFFFF
+    ent = view(layout["entries"], n_entries, torch.int32)[:, 0].to(torch.int64) & 0xFFFFFFFF
+    return gid, sl, rect, toff, ent
+
+
+def mg_render_stats_get(ws, stream=None) -> dict:
+    s = L.MgRenderStats()
+    st = L.lib().mg_render_stats_get(ws.data_ptr(), ws.numel(), ctypes.byref(s), _stream_handle(stream))
+    if st not in (L.MG_OK, L.MG_ERR_CAPACITY, L.MG_ERR_NOT_FINITE):
+        L.check(st, "mg_render_stats_get")
+    return {"records": s.records, "entries": s.entries, "tiles": s.tiles, "cap_records": s.cap_records,
+            "cap_entries": s.cap_entries, "status": s.status}
+
+
+def mg_sample_workspace_size(n: int, G: int, opts: L.MgOpts) -> int:
+    return int(L.lib().mg_sample_workspace_size(int(n), int(G), ctypes.byref(opts)))
+
+
+def mg_sample_volume(mean, quat, scale, alpha, centre, spacing: float, G: int, opts: L.MgOpts, out, ws, stream=None):
+    g = _gauss(mean, quat, scale, alpha)
+    _dev(out, "out", numel=G ** 3)
+    c = (ctypes.c_float * 3)(*[float(v) for v in centre])
+    st = L.lib().mg_sample_volume(ctypes.byref(g), c, float(spacing), int(G), ctypes.byref(opts), out.data_ptr(),
+                                  ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    L.check(st, "mg_sample_volume")
+
+
+def mg_reduce_workspace_size(n: int) -> int:
+    return int(L.lib().mg_reduce_workspace_size(int(n)))
+
+
+def mg_loss_l1l2(pred, target, grad, loss_out, ws, stream=None):
+    n = pred.numel()
+    _dev(target, "target", numel=n)
+    gp = _dev(grad, "grad", numel=n) if grad is not None else None
+    _dev(loss_out, "loss_out", dtype=torch.float64, numel=2)
+    st = L.lib().mg_loss_l1l2(_dev(pred, "pred"), target.data_ptr(), n, gp, loss_out.data_ptr(), ws.data_ptr(),
+                              ws.numel(), _stream_handle(stream))
+    L.check(st, "mg_loss_l1l2")
+
+
+def mg_sq_diff_sum(a, b, out, ws, stream=None):
+    n = a.numel()
+    _dev(b, "b", numel=n)
+    _dev(out, "out", dtype=torch.float64, numel=1)
+    st = L.lib().mg_sq_diff_sum(_dev(a, "a"), b.data_ptr(), n, out.data_ptr(), ws.data_ptr(), ws.numel(),
+                                _stream_handle(stream))
+    L.check(st, "mg_sq_diff_sum")
+
+
+def mg_version() -> str:
+    return L.lib().mg_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# workspace management and autograd
+# ---------------------------------------------------------------------------
+
+
+class SliceRenderer:
+    """Renders a fixed set of stacks; keeps the workspace between calls.
+
+    Capacity: starts from ``records_per_gaussian`` records per Gaussian (or the
+    exact bound n * slices when smaller) and 8 entries per record; when the
+    device reports an overflow the forward is repeated with 1.25x the
+    reported need. ``check`` reads the device counters after every forward
+    (one stream synchronisation)."""
+
+    def __init__(self, stacks: Sequence, device="cuda", cutoff_k: float = 3.0, f64_ratio: float = 100.0,
+                 records_per_gaussian: int = 32, entries_per_record: int = 8, check: bool = True):
+        self.dev = DeviceStacks(stacks, device)
+        self.device = device
+        self.K = cutoff_k
+        self.f64_ratio = f64_ratio
+        self.rpg = records_per_gaussian
+        self.epr = entries_per_record
+        self.check = check
+        self.caps = None
+        self.ws = None
+        self.last_stats = None
+        self._n = None
+
+    def opts(self) -> L.MgOpts:
+        return _opts(self.K, self.f64_ratio, self.caps[0], self.caps[1])
+
+    def _ensure(self, n: int):
+        if self.caps is None or self._n != n:
+            cr = max(1, min(n * self.dev.n_slices, self.rpg * n))
+            self.caps = (cr, self.epr * cr)
+            self._n = n
+        need = mg_render_workspace_size(n, self.dev, self.opts())
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = None
+            self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+
+    def set_capacity(self, records: int, entries: int, n: int):
+        self.caps = (max(1, int(records)), max(1, int(entries)))
+        self._n = n
+        self._ensure(n)
+
+    def forward(self, mean, quat, scale, alpha, out=None, stream=None):
+        n = int(mean.shape[0])
+        if out is None:
+            out = torch.empty(self.dev.n_vox, dtype=_F32, device=mean.device)
+        for _ in range(4):
+            self._ensure(n)
+            mg_render_fwd(mean, quat, scale, alpha, self.dev, self.opts(), out, self.ws, stream)
+            if not self.check:
+                return out
+            st = mg_render_stats_get(self.ws, stream)
+            self.last_stats = st
+            if st["status"] == L.MG_OK:
+                return out
+            if st["status"] == L.MG_ERR_NOT_FINITE:
+                raise L.MgError(L.MG_ERR_NOT_FINITE, "mg_render_fwd")
+            self.caps = (max(self.caps[0], int(st["records"] * 1.25) + 1),
+                         max(self.caps[1], int(st["entries"] * 1.25) + 1))
+        raise L.MgError(L.MG_ERR_CAPACITY, "mg_render_fwd (after growing the workspace)")
+
+    def stats(self, stream=None) -> dict:
+        return mg_render_stats_get(self.ws, stream)
+
+    def backward(self, mean, quat, scale, alpha, grad_out, stream=None):
+        n = int(mean.shape[0])
+        g = [torch.empty(n, 3, dtype=_F32, device=mean.device), torch.empty(n, 4, dtype=_F32, device=mean.device),
+             torch.empty(n, 3, dtype=_F32, device=mean.device), torch.empty(n, dtype=_F32, device=mean.device)]
+        st = mg_render_bwd(mean, quat, scale, alpha, self.dev, self.opts(), grad_out.contiguous(), *g, self.ws,
+                           stream, raise_on_error=False)
+        if st == L.MG_ERR_STALE_WORKSPACE:
+            # the workspace was reused by another forward: rebuild its bins
+            self.forward(mean, quat, scale, alpha)
+            st = mg_render_bwd(mean, quat, scale, alpha, self.dev, self.opts(), grad_out.contiguous(), *g, self.ws,
+                               stream, raise_on_error=False)
+        L.check(st, "mg_render_bwd")
+        return g
+
+
+class RenderSlices(torch.autograd.Function):
+    """Slices of all stacks from Gaussians (mean, unit quat, scale, alpha)."""
+
+    @staticmethod
+    def forward(ctx, renderer: SliceRenderer, mean, quat, scale, alpha):
+        mean, quat, scale, alpha = (t.detach().contiguous() for t in (mean, quat, scale, alpha))
+        out = renderer.forward(mean, quat, scale, alpha)
+        ctx.renderer = renderer
+        ctx.save_for_backward(mean, quat, scale, alpha)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        mean, quat, scale, alpha = ctx.saved_tensors
+        gm, gq, gs, ga = ctx.renderer.backward(mean, quat, scale, alpha, grad_out)
+        return None, gm, gq, gs, ga
+
+
+def render_slices(renderer: SliceRenderer, mean, quat_raw, log_scale, alpha):
+    """The paper's parameterisation (Sec. 3.2): unnormalised quaternion and
+    log-scale; normalisation and exp are taken in torch so autograd chains
+    through them."""
+    q = quat_raw / quat_raw.norm(dim=1, keepdim=True)
+    return RenderSlices.apply(renderer, mean, q, torch.exp(log_scale), alpha)
+
+
+class VolumeSampler:
+    """Inference sampling onto the isotropic G^3 grid (mg_sample_volume)."""
+
+    def __init__(self, G: int, spacing: float, centre=(0.0, 0.0, 0.0), device="cuda", cutoff_k: float = 3.0,
+                 f64_ratio: float = 100.0, records_per_gaussian: int = 64):
+        self.G, self.h, self.centre = int(G), float(spacing), tuple(float(c) for c in centre)
+        self.device, self.K, self.f64 = device, cutoff_k, f64_ratio
+        self.rpg = records_per_gaussian
+        self.caps = None
+        self.ws = None
+
+    def __call__(self, mean, quat, scale, alpha, out=None, stream=None):
+        n = int(mean.shape[0])
+        if out is None:
+            out = torch.empty(self.G ** 3, dtype=_F32, device=mean.device)
+        if self.caps is None:
+            cr = max(1, min(n * self.G, self.rpg * n))
+            self.caps = (cr, 8 * cr)
+        for _ in range(4):
+            o = _opts(self.K, self.f64, *self.caps)
+            need = mg_sample_workspace_size(n, self.G, o)
+            if self.ws is None or self.ws.numel() < need:
+                self.ws = None
+                self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+            mg_sample_volume(mean, quat, scale, alpha, self.centre, self.h, self.G, o, out, self.ws, stream)
+            st = mg_render_stats_get(self.ws, stream)
+            if st["status"] == L.MG_OK:
+                self.last_stats = st
+                return out.view(self.G, self.G, self.G)
+            if st["status"] == L.MG_ERR_NOT_FINITE:
+                raise L.MgError(L.MG_ERR_NOT_FINITE, "mg_sample_volume")
+            self.caps = (max(self.caps[0], int(st["records"] * 1.25) + 1),
+                         max(self.caps[1], int(st["entries"] * 1.25) + 1))
+        raise L.MgError(L.MG_ERR_CAPACITY, "mg_sample_volume (after growing the workspace)")

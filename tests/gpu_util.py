@@ -1,0 +1,71 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI on
+seeded inputs and put the oracle beside it."""
+import numpy as np
+import torch
+
+import mg_synth as ms
+
+TOL_REL_L2 = 1e-5        # relative L2 of a rendered slice set vs the FP64 oracle
+TOL_MAX_ABS = 1e-4       # maximum absolute error, as a fraction of the oracle's intensity range
+TOL_GRAD_REL = 1e-4      # relative L2 of each gradient group vs the oracle's analytic FP64 gradient
+
+
+def to_dev(G: ms.Gaussians, device="cuda"):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in (G.mean, G.quat, G.scale, G.alpha)]
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def assert_render_close(got, want, what=""):
+    got = np.asarray(got, np.float64).ravel()
+    want = np.asarray(want, np.float64).ravel()
+    rng = float(want.max() - want.min()) if want.size else 0.0
+    r = rel_l2(got, want)
+    m = float(np.max(np.abs(got - want))) if want.size else 0.0
+    assert r <= TOL_REL_L2, f"{what}: rel-L2 {r:.3e} > {TOL_REL_L2}"
+    assert m <= TOL_MAX_ABS * max(rng, 1e-30), f"{what}: max-abs {m:.3e} > {TOL_MAX_ABS} * range {rng:.3e}"
+    return r, m
+
+
+def render_gpu(G: ms.Gaussians, stacks, K=3.0, f64_ratio=100.0, caps=None, renderer=None):
+    from paper_2603_00145_b300 import SliceRenderer
+
+    R = renderer or SliceRenderer(stacks, cutoff_k=K, f64_ratio=f64_ratio)
+    if caps is not None:
+        R.set_capacity(caps[0], caps[1], G.n)
+    m, q, s, a = to_dev(G)
+    out = R.forward(m, q, s, a)
+    torch.cuda.synchronize()
+    return R, out, (m, q, s, a)
+
+
+def gpu_bins(R, n):
+    """Records and bins read back from the renderer's workspace."""
+    from paper_2603_00145_b300.ops import mg_render_ws_layout, read_bins
+
+    st = R.stats()
+    lay = mg_render_ws_layout(n, R.dev, R.opts())
+    return st, read_bins(R.ws, lay, st["records"], R.dev.n_tiles, st["entries"])
+
+
+def sub_stacks(stacks, picks):
+    """Stacks holding only the picked slices ((stack index, slice index) pairs)
+    in the same order; returns the new stacks and each pick's flat voxel slice
+    in the full concatenated output."""
+    out, ranges = [], []
+    base = 0
+    bases = []
+    for s in stacks:
+        bases.append(base)
+        base += s.n_vox
+    for si, k in picks:
+        s = stacks[si]
+        out.append(ms.Stack(1, s.H, s.W, s.dx, s.dy, s.thickness, s.xform[k:k + 1]))
+        o = bases[si] + k * s.H * s.W
+        ranges.append((o, o + s.H * s.W))
+    return out, ranges

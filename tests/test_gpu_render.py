@@ -1,0 +1,210 @@
+"""GPU parity of the slice renderer (C ABI) against the FP64 oracle.
+
+Records and tile bins must match the oracle bit for bit; rendered slices
+within relative L2 1e-5 and max-abs 1e-4 of the intensity range; the adjoint
+within relative L2 1e-4 per parameter group.
+"""
+import numpy as np
+import pytest
+import torch
+
+import mg_synth as ms
+import oracle as orc
+from gpu_util import (TOL_GRAD_REL, assert_render_close, gpu_bins, rel_l2, render_gpu, sub_stacks, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_case(seed, n=300, neg=0.1):
+    rng = np.random.default_rng(seed)
+    G = ms.random_gaussians(n, 200 + seed, box=(-22, 22), sigma=(0.6, 3.0), aniso=3.0, alpha=(0.1, 1.0),
+                            negative_frac=neg)
+    stacks = [ms.make_stack(ms.AXIAL, 9, 37, 50, 1.0, 1.1, 3.0, 3.0),
+              ms.make_stack(ms.random_rotations(1, rng)[0], 7, 48, 40, 0.9, 0.9, 2.0, 2.5, rng=rng,
+                            max_rot_deg=5.0, max_trans_mm=1.0),
+              ms.make_stack(ms.SAGITTAL, 5, 33, 17, 1.3, 1.2, 0.0, 4.0)]
+    return G, stacks
+
+
+def _check_bins(G, stacks, R, K=3.0):
+    rec = orc.records(G, stacks, K)
+    st, (gid, sl, rect, toff, ent) = gpu_bins(R, G.n)
+    assert st["status"] == 0
+    assert st["records"] == rec.n
+    assert np.array_equal(gid.numpy(), rec.gid) and np.array_equal(sl.numpy(), rec.slice)
+    assert np.array_equal(rect.numpy(), rec.rect)
+    counts, offs, ids = orc.tile_bins(rec, stacks)
+    assert st["entries"] == ids.size
+    assert np.array_equal(toff.numpy(), offs)
+    ent = ent.numpy()
+    for t in np.nonzero(counts)[0]:
+        assert np.array_equal(np.sort(ent[offs[t]:offs[t + 1]]), ids[offs[t]:offs[t + 1]]), t
+    return rec
+
+
+def test_tiny_workload_fwd_bwd():
+    """The 48^3 plain-method case: 3 orthogonal stacks of 16 slices, 48x48, 3 mm
+    profile, 2048 devoxelised Gaussians; one FP32 forward + backward."""
+    wl = ms.tiny_workload(0)
+    vol = wl.phantom.volume()
+    data = [ms.simulate_stack(vol, 1.0, s, seed=i, noise_sigma=wl.noise_sigma).numpy() for i, s in
+            enumerate(wl.stacks)]
+    G = ms.devoxelised_gaussians(wl.stacks, data, wl.n_gaussians, seed=0)
+    R, out, dev = render_gpu(G, wl.stacks)
+    rec = _check_bins(G, wl.stacks, R)
+    want = orc.render(G, wl.stacks, rec)
+    assert_render_close(out.cpu().numpy(), want, "tiny fwd")
+    rng = np.random.default_rng(1)
+    gout = rng.normal(size=want.size).astype(np.float32)
+    g = R.backward(*dev, torch.from_numpy(gout).cuda())
+    ref = orc.grad(G, wl.stacks, rec, gout.astype(np.float64))
+    for name, got in zip(("mean", "quat", "scale", "alpha"), g):
+        r = rel_l2(got.cpu().numpy(), ref[name])
+        assert r <= TOL_GRAD_REL, (name, r)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mixed_stacks_fwd_bwd(seed):
+    """Ragged sizes, an oblique stack with per-slice motion, a zero-thickness
+    stack, negative intensities."""
+    G, stacks = _mixed_case(seed)
+    R, out, dev = render_gpu(G, stacks)
+    rec = _check_bins(G, stacks, R)
+    want = orc.render(G, stacks, rec)
+    assert_render_close(out.cpu().numpy(), want, "mixed fwd")
+    gout = np.random.default_rng(seed).normal(size=want.size).astype(np.float32)
+    g = R.backward(*dev, torch.from_numpy(gout).cuda())
+    ref = orc.grad(G, stacks, rec, gout.astype(np.float64))
+    for name, got in zip(("mean", "quat", "scale", "alpha"), g):
+        r = rel_l2(got.cpu().numpy(), ref[name])
+        assert r <= TOL_GRAD_REL, (name, r)
+
+
+@pytest.mark.parametrize("K", [2.0, 4.5])
+def test_other_cutoffs(K):
+    G, stacks = _mixed_case(7, n=150, neg=0.0)
+    R, out, dev = render_gpu(G, stacks, K=K)
+    rec = _check_bins(G, stacks, R, K=K)
+    assert_render_close(out.cpu().numpy(), orc.render(G, stacks, rec), f"K={K}")
+
+
+def test_deterministic_and_repeatable():
+    G, stacks = _mixed_case(3)
+    R, out1, dev = render_gpu(G, stacks)
+    _, b1 = gpu_bins(R, G.n)
+    out2 = R.forward(*dev)
+    _, b2 = gpu_bins(R, G.n)
+    assert torch.equal(out1, out2)
+    for x, y in zip(b1, b2):
+        assert torch.equal(x, y)
+
+
+def test_capacity_overflow_then_growth():
+    from paper_2603_00145_b300 import SliceRenderer
+    from paper_2603_00145_b300.ops import mg_render_fwd, mg_render_stats_get
+
+    G, stacks = _mixed_case(4)
+    R = SliceRenderer(stacks, check=False)
+    R.set_capacity(7, 20, G.n)
+    m, q, s, a = to_dev(G)
+    out = torch.empty(R.dev.n_vox, device="cuda")
+    mg_render_fwd(m, q, s, a, R.dev, R.opts(), out, R.ws)
+    st = mg_render_stats_get(R.ws)
+    assert st["status"] == 3 and st["records"] > 7  # MG_ERR_CAPACITY with the need reported
+    R2 = SliceRenderer(stacks)
+    R2.set_capacity(7, 20, G.n)
+    out2 = R2.forward(m, q, s, a)  # grows and retries
+    assert_render_close(out2.cpu().numpy(), orc.render(G, stacks), "after growth")
+
+
+def test_empty_and_outside():
+    from paper_2603_00145_b300 import SliceRenderer
+
+    stacks = [ms.make_stack(ms.AXIAL, 3, 20, 21, 1.0, 1.0, 3.0, 3.0)]
+    R = SliceRenderer(stacks)
+    e = torch.empty(0, 3, device="cuda")
+    out = R.forward(e, torch.empty(0, 4, device="cuda"), e.clone(), torch.empty(0, device="cuda"))
+    assert out.numel() == 3 * 20 * 21 and float(out.abs().max()) == 0.0
+    G = ms.random_gaussians(50, 5, box=(200, 300))  # far outside the field of view
+    _, out, _ = render_gpu(G, stacks)
+    assert float(out.abs().max()) == 0.0
+
+
+def test_not_finite_reported():
+    from paper_2603_00145_b300 import SliceRenderer
+    from paper_2603_00145_b300.ops import mg_render_fwd, mg_render_stats_get
+
+    G, stacks = _mixed_case(5, n=40)
+    G.mean[3, 1] = np.nan
+    G.scale[7, 0] = 0.0
+    R = SliceRenderer(stacks, check=False)
+    R._ensure(G.n)
+    m, q, s, a = to_dev(G)
+    out = torch.empty(R.dev.n_vox, device="cuda")
+    mg_render_fwd(m, q, s, a, R.dev, R.opts(), out, R.ws)
+    assert mg_render_stats_get(R.ws)["status"] == 5  # MG_ERR_NOT_FINITE
+    # the remaining Gaussians still render exactly as without the bad ones
+    keep = np.setdiff1d(np.arange(G.n), [3, 7])
+    assert np.isfinite(out.cpu().numpy()).all()
+    want = orc.render(G.subset(keep), stacks)
+    assert_render_close(out.cpu().numpy(), want, "bad inputs skipped")
+
+
+def test_backward_requires_matching_forward():
+    from paper_2603_00145_b300 import SliceRenderer
+    from paper_2603_00145_b300 import _lib as L
+    from paper_2603_00145_b300.ops import mg_render_bwd
+
+    G, stacks = _mixed_case(6, n=30)
+    R = SliceRenderer(stacks)
+    R._ensure(G.n)
+    m, q, s, a = to_dev(G)
+    g = [torch.empty(G.n, 3, device="cuda"), torch.empty(G.n, 4, device="cuda"), torch.empty(G.n, 3, device="cuda"),
+         torch.empty(G.n, device="cuda")]
+    go = torch.zeros(R.dev.n_vox, device="cuda")
+    st = mg_render_bwd(m, q, s, a, R.dev, R.opts(), go, *g, R.ws, raise_on_error=False)
+    assert st == L.MG_ERR_STALE_WORKSPACE
+
+
+def test_degenerate_gaussians_fp64_geometry():
+    """Needle/pancake Gaussians (scale ratio up to 400) take the FP64 record
+    geometry; bins stay bit-exact and values stay within tolerance."""
+    rng = np.random.default_rng(9)
+    G = ms.random_gaussians(120, 77, box=(-15, 15), sigma=(0.5, 2.0), aniso=1.5)
+    sc = G.scale.copy()
+    for i in range(0, G.n, 2):
+        ax = rng.integers(3)
+        sc[i, ax] *= rng.uniform(20, 60)
+        sc[i, (ax + 1) % 3] /= rng.uniform(3, 8)
+    G = ms.Gaussians(G.mean, G.quat, sc, G.alpha)
+    stacks = [ms.make_stack(ms.AXIAL, 8, 40, 40, 0.8, 0.8, 2.0, 2.0),
+              ms.make_stack(ms.random_rotations(1, rng)[0], 6, 36, 44, 0.9, 0.9, 2.0, 3.0)]
+    R, out, dev = render_gpu(G, stacks)
+    rec = _check_bins(G, stacks, R)
+    assert_render_close(out.cpu().numpy(), orc.render(G, stacks, rec), "degenerate fwd")
+
+
+def test_bench_config_sampled_slices():
+    """The FeTA-shaped fit at full size (200k Gaussians; 3 x 64 slices of
+    256^2): the GPU renders everything; the oracle checks one slice per stack,
+    and the adjoint with dL/dI non-zero on those slices only."""
+    wl = ms.feta_workload(0)
+    G = ms.phantom_init_gaussians(wl, seed=0)
+    R, out, dev = render_gpu(G, wl.stacks)
+    picks = [(0, 20), (1, 33), (2, 47)]
+    sub, ranges = sub_stacks(wl.stacks, picks)
+    rec = orc.records(G, sub)
+    want = orc.render(G, sub, rec)
+    got = np.concatenate([out[a:b].cpu().numpy() for a, b in ranges])
+    assert_render_close(got, want, "feta slices")
+    gout_sub = np.random.default_rng(2).normal(size=want.size).astype(np.float32)
+    gout = torch.zeros(R.dev.n_vox, device="cuda")
+    o = 0
+    for a, b in ranges:
+        gout[a:b] = torch.from_numpy(gout_sub[o:o + b - a]).cuda()
+        o += b - a
+    g = R.backward(*dev, gout)
+    ref = orc.grad(G, sub, rec, gout_sub.astype(np.float64))
+    for name, got_g in zip(("mean", "quat", "scale", "alpha"), g):
+        r = rel_l2(got_g.cpu().numpy(), ref[name])
+        assert r <= TOL_GRAD_REL, (name, r)
