@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Throughput of the Magnetic Gaussian slice renderer on one B300.
+
+One step = one training iteration of the FeTA-shaped plain fit (256^3
+phantom at 0.5 mm; 3 orthogonal stacks of 64 slices of 256 x 256 at 0.5 mm,
+2 mm slice profile; 200k Gaussians): record pass + tile binning + forward
+render, the FP64 L1+L2 slice loss with its gradient, and the adjoint (moments
++ chain to the Gaussian parameters). All of it runs in this repository's
+CUDA kernels through the C ABI.
+
+metric: fwd+bwd Gaussian-voxel pairs/s = P / step time, P = (Gaussian record,
+slice voxel) pairs inside the K = 3 ellipsoid of the profile-convolved
+covariance, counted on the device by mg_render_pair_count for the step's
+input. The evaluated (tile-level) pair count is reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgauss|reference]
+Under torchrun each rank renders its own independent replica (seed = rank):
+weak scaling, no collective on the data path (the step does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+bwd Gaussian-voxel pairs/s"
+UNIT = "pairs/s"
+# kernels per library stage (the scans are three kernels each)
+KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 3, "k1_emit": 1, "chunks": 1, "bin_hist": 1,
+                     "bin_colscan": 1, "scan_tiles": 3, "bin_scatter": 1, "render_fwd": 1, "zero_moments": 1,
+                     "render_bwd": 1, "chain": 1, "loss": 2, "pair_count": 1, "nrf_fwd": 1, "nrf_bwd": 1}
+# Algorithmic per-pair work of the evaluation kernels (SIMT FP32 pipe ops,
+# MUFU ex2 ops): forward q (2 FMA) + accumulate (1 FMA) + 1 ex2; backward q
+# (2 FMA) + w = g 2^q (1 MUL) + three moment accumulations (3) + 1 ex2.
+PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (6, 1)}
+# B300 unit counts per SM and clock (sm_103: 148 SMs, 128 FP32 lanes and 16
+# MUFU lanes per SM per clock, 2032 MHz maximum SM clock).
+N_SM, FP32_LANES, MUFU_LANES, SM_MHZ = 148, 128, 16, 2032.0
+
+
+def alu_peak_pairs(kernel: str) -> float:
+    fp32, mufu = PAIR_OPS[kernel]
+    per_clk = min(FP32_LANES / fp32, MUFU_LANES / mufu)
+    return N_SM * per_clk * SM_MHZ * 1e6
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def build_workload(name: str, seed: int, device):
+    import torch
+
+    import mg_synth as ms
+
+    maker = {"feta": ms.feta_workload, "tiny": ms.tiny_workload, "motion": ms.motion_workload,
+             "stress": ms.stress_workload}[name]
+    wl = maker(seed)
+    vol = wl.phantom.volume_torch(device=str(device))
+    vs = wl.phantom.spacing
+    data = [ms.simulate_stack(vol, vs, s, seed=seed * 100 + i, noise_sigma=wl.noise_sigma, device=str(device))
+            for i, s in enumerate(wl.stacks)]
+    target = torch.cat([d.reshape(-1) for d in data]).contiguous()
+    del vol
+    if name == "tiny":
+        G = ms.devoxelised_gaussians(wl.stacks, [d.cpu().numpy() for d in data], wl.n_gaussians, seed=seed)
+    else:
+        G = ms.phantom_init_gaussians(wl, seed=seed)
+    return wl, G, target
+
+
+# ---------------------------------------------------------------------------
+# the mgauss arm
+# ---------------------------------------------------------------------------
+def run_mgauss(args, rank, world, local_rank):
+    import torch
+
+    from paper_2603_00145_b300 import SliceRenderer, mg_loss_l1l2, mg_reduce_workspace_size
+    from paper_2603_00145_b300.ops import mg_profile_enable, mg_profile_read
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    wl, G, target = build_workload(args.workload, args.seed + rank, dev)
+    m, q, s, a = (torch.from_numpy(x).to(dev) for x in (G.mean, G.quat, G.scale, G.alpha))
+    R = SliceRenderer(wl.stacks, device=dev, check=True)
+    out = R.forward(m, q, s, a)  # sizes the workspace (grows on overflow)
+    st = R.stats()
+    R.set_capacity(int(st["records"] * 1.1) + 64, int(st["entries"] * 1.1) + 256, G.n)
+    R.forward(m, q, s, a, out=out)
+    pairs_inside, pairs_eval = R.pair_count(m, q, s, a)
+    R.check = False
+    nv = target.numel()
+    grad = torch.empty(nv, dtype=torch.float32, device=dev)
+    loss = torch.empty(2, dtype=torch.float64, device=dev)
+    wsr = torch.empty(mg_reduce_workspace_size(nv), dtype=torch.uint8, device=dev)
+
+    def step(mm, qq, ss, aa):
+        R.forward(mm, qq, ss, aa, out=out)
+        mg_loss_l1l2(out, target, grad, loss, wsr)
+        return R.backward(mm, qq, ss, aa, grad)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+    for _ in range(args.warmup):
+        step(m, q, s, a)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    mg_profile_read(reset=True)
+    mg_profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        step(m, q, s, a)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    mg_profile_enable(False)
+    prof = mg_profile_read(reset=True)
+    clk = clocks.stop()
+    ms_total = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value_rank = pairs_inside / (ms_step / 1e3)
+    value = value_rank * world
+    st = R.stats()
+    assert st["status"] == 0, f"device status {st['status']} during the timed steps"
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs
+    # (Gaussian parameters and target slices) from pinned memory, the step,
+    # D2H of the loss and of the gradients
+    host_in = [torch.from_numpy(x).pin_memory() for x in (G.mean, G.quat, G.scale, G.alpha)]
+    host_tgt = target.cpu().pin_memory()
+    dev_in = [torch.empty_like(x, device=dev) for x in host_in]
+    host_out = [torch.empty((G.n, w), dtype=torch.float32).pin_memory() for w in (3, 4, 3)] + \
+        [torch.empty(G.n, dtype=torch.float32).pin_memory()]
+    host_loss = torch.empty(2, dtype=torch.float64).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in host_in) + host_tgt.numel() * 4
+    d2h = sum(x.numel() * x.element_size() for x in host_out) + 16
+    e2e_ms = 0.0
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d_, h_ in zip(dev_in, host_in):
+            d_.copy_(h_, non_blocking=True)
+        target.copy_(host_tgt, non_blocking=True)
+        gs = step(*dev_in)
+        for h_, g_ in zip(host_out, gs):
+            h_.copy_(g_, non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms += e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = pairs_inside * world / (e2e_ms / args.steps / 1e3)
+
+    # roofline of the dominant evaluation kernel, timed live with CUDA events
+    stages = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(("render_fwd", "render_bwd"), key=lambda k: stages.get(k, (0, 0))[0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    achieved = pairs_eval / (dom_ms / 1e3)
+    peak = alu_peak_pairs(dom)
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_basis": (f"{N_SM} SMs x min({FP32_LANES}/{PAIR_OPS[dom][0]} FP32, {MUFU_LANES}/{PAIR_OPS[dom][1]} "
+                           f"MUFU) pairs/clk x {SM_MHZ:.0f} MHz (nominal unit counts)"),
+            "units_per_launch": pairs_eval}
+    other = {}
+    for k in ("render_fwd", "render_bwd"):
+        if k in stages and k != dom:
+            t_ = stages[k][0] / stages[k][1]
+            other[k] = {"ms": t_, "Gpair_s": pairs_eval / (t_ / 1e3) / 1e9,
+                        "frac": pairs_eval / (t_ / 1e3) / alu_peak_pairs(k)}
+    roof["other"] = other
+    launches = sum(KERNELS_PER_STAGE.get(k, 1) * v[1] for k, v in stages.items())
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ellipsoid phantom, simulated stacks)",
+            "config": {"workload": wl.name, "gaussians": G.n, "stacks": len(wl.stacks),
+                       "slices": sum(s_.n_slices for s_ in wl.stacks), "voxels": nv, "cutoff_k": 3.0,
+                       "records": st["records"], "entries": st["entries"],
+                       "pairs_inside_per_step": pairs_inside, "pairs_evaluated_per_step": pairs_eval,
+                       "binning_efficiency": pairs_inside / max(pairs_eval, 1),
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": launches,
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(G, wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_step(G, wl, picks):
+    """Oracle forward + adjoint (with the L1+L2 loss gradient) on the picked
+    slices of the workload; returns the sub-stacks and their records."""
+    import mg_synth as ms
+    import oracle as orc
+    from oracle import metrics
+
+    sub, _ = ms.pick_slices(wl.stacks, picks)
+    rec = orc.records(G, sub)
+    S = orc.render(G, sub, rec)
+    _, g = metrics.l1_l2(S, np.zeros_like(S))
+    orc.grad(G, sub, rec, g)
+    return sub, rec
+
+
+def _sample_pairs(G, wl, picks):
+    import mg_synth as ms
+    import oracle as orc
+
+    tot = 0
+    for pk in picks:
+        sub, _ = ms.pick_slices(wl.stacks, [pk])
+        tot += orc.pair_counts(G, sub, orc.records(G, sub))[0]
+    return tot
+
+
+def cpu_baseline(G, wl, seconds: float):
+    """The oracle as it stands, on whole slices of the same workload (one slice
+    of each stack in turn) for about ``seconds`` of host time."""
+    n_sl = [s.n_slices for s in wl.stacks]
+    picks = []
+    t0 = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < seconds or i == 0:
+        pk = (i % len(n_sl), (i * 7 + 3) % n_sl[i % len(n_sl)])
+        oracle_sample_step(G, wl, [pk])
+        picks.append(pk)
+        i += 1
+    el = time.perf_counter() - t0
+    pairs = _sample_pairs(G, wl, picks)
+    return {"value": pairs / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(picks)} full slices (forward + adjoint, FP64, OpenMP) of the same workload in "
+                      f"{el:.1f} s; pairs counted by the oracle"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU FP64 oracle on the same workload and metric,
+    each step a bounded sample (one full slice, forward + adjoint)."""
+    if rank != 0:
+        return
+    import torch  # noqa: F401
+
+    import mg_synth as ms
+
+    wl = {"feta": ms.feta_workload, "tiny": ms.tiny_workload, "motion": ms.motion_workload,
+          "stress": ms.stress_workload}[args.workload](args.seed)
+    G = ms.phantom_init_gaussians(wl, seed=args.seed) if args.workload != "tiny" else None
+    if G is None:
+        vol = wl.phantom.volume()
+        data = [ms.simulate_stack(vol, 1.0, s, seed=i, noise_sigma=wl.noise_sigma).numpy()
+                for i, s in enumerate(wl.stacks)]
+        G = ms.devoxelised_gaussians(wl.stacks, data, wl.n_gaussians, seed=args.seed)
+    n_sl = [s.n_slices for s in wl.stacks]
+    picks = [(i % len(n_sl), (i * 7 + 3) % n_sl[i % len(n_sl)]) for i in range(args.warmup + args.steps)]
+    tt = 0.0
+    pairs = 0
+    for i, pk in enumerate(picks):
+        t0 = time.perf_counter()
+        oracle_sample_step(G, wl, [pk])
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            tt += el
+            pairs += _sample_pairs(G, wl, [pk])
+    value = pairs / tt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "gaussians": G.n, "sample_per_step": "one full slice, forward + adjoint"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} slices of the workload, one per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mgauss", "reference"], default="mgauss")
+    ap.add_argument("--workload", default="feta", choices=["feta", "tiny", "motion", "stress"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_mgauss(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,7 +145,10 @@ mg_status mg_render_fwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
  * Adjoint of mg_render_fwd (the paper trains by differentiable rendering,
  * Sec. 3.1): given grad_out = dL/d(out) (device, FP32, total voxels), writes
  * dL/dmean [n,3], dL/dquat [n,4] (derivative of the rotation formula above in
- * the four quaternion components, as given), dL/dscale [n,3] and dL/dalpha [n]
+ * the four quaternion components, projected on the tangent space of the unit
+ * sphere at quat: the component along quat is removed, as the normalisation
+ * quat = q_raw/|q_raw| does; the rotation formula is a rotation only for unit
+ * quat), dL/dscale [n,3] and dL/dalpha [n]
  * (device, FP32, overwritten). The records are held fixed (the sum is
  * piecewise constant in them). Must follow mg_render_fwd on the same
  * workspace with the same arguments (else MG_ERR_STALE_WORKSPACE); the
@@ -203,6 +206,30 @@ mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float 
  * double [1] = sum (a-b)^2, fixed-order FP64 accumulation. */
 mg_status mg_sq_diff_sum(const float *a, const float *b, int64_t n, double *out, void *ws, size_t ws_bytes,
                          mg_stream_t stream);
+
+/*
+ * Pair statistics of the last forward on this workspace (same arguments as
+ * that forward): counts[0] = (record, in-image voxel) pairs inside the
+ * record's K-sigma ellipsoid of the profile-convolved covariance (FP32 test
+ * of the voxel's quadratic form against K^2 - w0^2/Sww), counts[1] = all
+ * evaluated pairs (records x in-image voxels of their listed tiles).
+ * counts: HOST int64[2]. Synchronises `stream`.
+ */
+mg_status mg_render_pair_count(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                               void *ws, size_t ws_bytes, int64_t counts[2], mg_stream_t stream);
+
+/*
+ * Per-stage GPU timing with CUDA events. While enabled, every kernel stage
+ * this library launches is bracketed by two events on its stream;
+ * mg_profile_read waits for them and returns the accumulated milliseconds
+ * and call counts per stage (arrays of mg_profile_stage_count() entries,
+ * host memory; either may be NULL), optionally resetting them. Off by
+ * default; enabling affects all threads of the process.
+ */
+mg_status mg_profile_enable(int on);
+int mg_profile_stage_count(void);
+const char *mg_profile_stage_name(int stage);
+mg_status mg_profile_read(double *ms, int64_t *calls, int reset);
 
 const char *mg_status_string(mg_status s);
 const char *mg_last_error(void);

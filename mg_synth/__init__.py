@@ -238,6 +238,34 @@ class Phantom:
             np.clip(out, 0.0, 1.0, out=out)
         return out
 
+    def volume_torch(self, G: int | None = None, spacing: float | None = None, device: str = "cpu"):
+        """Same as ``volume`` evaluated with torch on ``device`` (float32
+        coordinates; returns a float32 tensor [z,y,x])."""
+        import torch
+
+        h = self.spacing if spacing is None else spacing
+        G = int(round(self.fov_mm / h)) if G is None else G
+        ax = (torch.arange(G, device=device, dtype=torch.float32) - (G - 1) / 2.0) * h
+        out = torch.zeros(G, G, G, device=device, dtype=torch.float32)
+        zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
+        for c, a, R, v in zip(self.centres, self.axes, self.rots, self.values):
+            Rt = torch.as_tensor(R, dtype=torch.float32, device=device)
+            ct = torch.as_tensor(c, dtype=torch.float32, device=device)
+            at = torch.as_tensor(a, dtype=torch.float32, device=device)
+            d0, d1, d2 = xx - ct[0], yy - ct[1], zz - ct[2]
+            r = torch.zeros_like(out)
+            for j in range(3):  # coordinates in the ellipsoid frame: (x - c) @ R
+                l = d0 * Rt[0, j] + d1 * Rt[1, j] + d2 * Rt[2, j]
+                r += (l / at[j]) ** 2
+            inside = r <= 1.0
+            if self.mode == "sum":
+                out += inside.to(out.dtype) * float(v)
+            else:
+                out = torch.where(inside, torch.full_like(out, float(v)), out)
+        if self.mode == "sum":
+            out.clamp_(0.0, 1.0)
+        return out
+
     def volume(self, G: int | None = None, spacing: float | None = None) -> np.ndarray:
         """Phantom sampled at voxel centres of a G^3 grid centred on the origin,
         stored [z,y,x]."""
@@ -326,23 +354,39 @@ def simulate_stack(vol: np.ndarray, vol_spacing: float, stack: Stack, seed: int,
     v = (j - (stack.H - 1) / 2.0) * stack.dy
     vv, uu = torch.meshgrid(v, u, indexing="ij")
     out = torch.zeros(stack.n_slices, stack.H, stack.W, dtype=torch.float32, device=dev)
+    tq = torch.as_tensor(ts, dtype=torch.float64, device=dev)
+    wq = torch.as_tensor(w, dtype=torch.float64, device=dev)
     for k in range(stack.n_slices):
         R = xf[k, :9].reshape(3, 3)
         t = xf[k, 9:]
         base = uu[..., None] * R[:, 0] + vv[..., None] * R[:, 1] + t
-        acc = torch.zeros(stack.H, stack.W, dtype=torch.float64, device=dev)
-        for tq, wq in zip(ts, w):
-            p = base + float(tq) * R[:, 2]
-            g = (p / half_extent).to(torch.float32)[None, None]  # grid_sample order is (x,y,z)
-            s = F.grid_sample(V, g, mode="bilinear", padding_mode="zeros", align_corners=True)
-            acc += float(wq) * s[0, 0, 0].to(torch.float64)
-        out[k] = acc.to(torch.float32)
+        p = base[None] + tq[:, None, None, None] * R[:, 2]  # [n_quad, H, W, 3]
+        g = (p / half_extent).to(torch.float32)[None]  # grid_sample order is (x,y,z)
+        s = F.grid_sample(V, g, mode="bilinear", padding_mode="zeros", align_corners=True)[0, 0]
+        out[k] = (s.to(torch.float64) * wq[:, None, None]).sum(0).to(torch.float32)
     if noise_sigma > 0:
         gen = torch.Generator(device="cpu").manual_seed(int(seed))
         n1 = torch.randn(out.shape, generator=gen, dtype=torch.float32).to(dev) * noise_sigma
         n2 = torch.randn(out.shape, generator=gen, dtype=torch.float32).to(dev) * noise_sigma
         out = torch.sqrt((out + n1) ** 2 + n2 ** 2)
     return out
+
+
+def pick_slices(stacks: Sequence[Stack], picks):
+    """Stacks holding only the picked slices ((stack index, slice index) pairs),
+    in order, and each pick's [start, end) range in the flat output of the
+    full stacks."""
+    bases, base = [], 0
+    for s in stacks:
+        bases.append(base)
+        base += s.n_vox
+    out, ranges = [], []
+    for si, k in picks:
+        s = stacks[si]
+        out.append(Stack(1, s.H, s.W, s.dx, s.dy, s.thickness, s.xform[k:k + 1]))
+        o = bases[si] + k * s.H * s.W
+        ranges.append((o, o + s.H * s.W))
+    return out, ranges
 
 
 def devoxelised_gaussians(stacks: Sequence[Stack], data: Sequence[np.ndarray], n: int, seed: int,

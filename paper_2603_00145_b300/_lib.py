@@ -58,6 +58,12 @@ SIGNATURES = {
     "mg_reduce_workspace_size": (c_sz, [c_i64]),
     "mg_loss_l1l2": (ctypes.c_int, [c_p, c_p, c_i64, c_p, c_p, c_p, c_sz, c_p]),
     "mg_sq_diff_sum": (ctypes.c_int, [c_p, c_p, c_i64, c_p, c_p, c_sz, c_p]),
+    "mg_render_pair_count": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
+                                            ctypes.POINTER(MgOpts), c_p, c_sz, ctypes.POINTER(c_i64), c_p]),
+    "mg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mg_profile_stage_count": (ctypes.c_int, []),
+    "mg_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "mg_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_i64), ctypes.c_int]),
     "mg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_version": (ctypes.c_char_p, []),

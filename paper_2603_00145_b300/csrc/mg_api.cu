@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -16,6 +17,58 @@ int mg_reduce_blocks(long long n);
 void mg_launch_loss_l1l2(const float *pred, const float *target, long long n, float *grad, double *out,
                          double *part, cudaStream_t st);
 void mg_launch_sq_diff(const float *a, const float *b, long long n, double *out, double *part, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// per-stage CUDA-event timing
+// ---------------------------------------------------------------------------
+namespace prof {
+std::atomic<bool> on{false};
+std::mutex mu;
+struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+};
+std::vector<Pending> pending;
+std::vector<cudaEvent_t> pool;
+double ms[MG_NSTAGES];
+long long calls[MG_NSTAGES];
+thread_local cudaEvent_t open_ev[MG_NSTAGES];
+const char *names[MG_NSTAGES] = {"slices",      "k1_count",   "scan_records", "k1_emit",    "chunks",
+                                 "bin_hist",    "bin_colscan", "scan_tiles",   "bin_scatter", "render_fwd",
+                                 "zero_moments", "render_bwd", "chain",        "loss",       "pair_count",
+                                 "nrf_fwd",     "nrf_bwd"};
+
+cudaEvent_t get_event()
+{
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace prof
+
+void mg_prof_begin(int stage, cudaStream_t st)
+{
+    if (!prof::on.load(std::memory_order_relaxed)) return;
+    cudaEvent_t e = prof::get_event();
+    cudaEventRecord(e, st);
+    prof::open_ev[stage] = e;
+}
+
+void mg_prof_end(int stage, cudaStream_t st)
+{
+    if (!prof::on.load(std::memory_order_relaxed) || !prof::open_ev[stage]) return;
+    cudaEvent_t e = prof::get_event();
+    cudaEventRecord(e, st);
+    std::lock_guard<std::mutex> lk(prof::mu);
+    prof::pending.push_back({stage, prof::open_ev[stage], e});
+    prof::open_ev[stage] = nullptr;
+}
 
 namespace {
 
@@ -118,6 +171,7 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.rec_slice = take(4 * (size_t)L.cap_records);
     L.rec_rect = take(8 * (size_t)L.cap_records);
     L.rec_mom = take(32 * (size_t)L.cap_records);
+    L.rec_thr = take(4 * (size_t)L.cap_records);
     L.chunk_base = take(sizeof(unsigned) * 2 * (size_t)(S + 1));
     L.hist = take(sizeof(unsigned) * (size_t)L.cap_chunks * (size_t)tmax);
     L.tile_cnt = take(sizeof(unsigned) * (size_t)tiles);
@@ -464,8 +518,81 @@ mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float 
     if (n < 0 || (n > 0 && (!pred || !target)) || !loss_out || !ws)
         return fail(MG_ERR_INVALID_ARG, "bad pointer or size");
     if (ws_bytes < mg_reduce_workspace_size(n)) return fail(MG_ERR_INVALID_ARG, "workspace too small");
-    mg_launch_loss_l1l2(pred, target, n, grad, loss_out, (double *)ws, (cudaStream_t)stream);
+    {
+        MG_PROF(MG_ST_LOSS, (cudaStream_t)stream);
+        mg_launch_loss_l1l2(pred, target, n, grad, loss_out, (double *)ws, (cudaStream_t)stream);
+    }
     return check_cuda("mg_loss_l1l2");
+}
+
+mg_status mg_render_pair_count(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                               void *ws, size_t ws_bytes, int64_t counts[2], mg_stream_t stream)
+{
+    std::string why;
+    if (!counts || !ws || !valid_gauss(g, why, false)) return fail(MG_ERR_INVALID_ARG, "bad arguments");
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (!valid_stacks(st, false, why)) return fail(MG_ERR_INVALID_ARG, why);
+    long long S = 0;
+    for (const StackDesc &d : st) S += d.n_slices;
+    mg_opts o = resolve_opts(opts, g->n, S);
+    WsLayout L = make_layout(g->n, st, o);
+    if (ws_bytes < L.total) return fail(MG_ERR_INVALID_ARG, "workspace too small");
+    {
+        std::lock_guard<std::mutex> lk(g_tag_mu);
+        if (g_tags.find(ws) == g_tags.end()) return fail(MG_ERR_STALE_WORKSPACE, "no forward on this workspace");
+    }
+    mg_launch_pair_count(L, (char *)ws, make_table(st), (cudaStream_t)stream);
+    mg_status s = check_cuda("mg_render_pair_count");
+    if (s != MG_OK) return s;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return check_cuda("mg_render_pair_count");
+    WsHeader h;
+    if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return check_cuda("mg_render_pair_count");
+    counts[0] = (int64_t)h.pairs_inside;
+    counts[1] = (int64_t)h.pairs_evaluated;
+    return MG_OK;
+}
+
+mg_status mg_profile_enable(int on)
+{
+    prof::on.store(on != 0);
+    return MG_OK;
+}
+
+int mg_profile_stage_count(void) { return MG_NSTAGES; }
+
+const char *mg_profile_stage_name(int stage)
+{
+    return (stage >= 0 && stage < MG_NSTAGES) ? prof::names[stage] : "";
+}
+
+mg_status mg_profile_read(double *ms, int64_t *calls, int reset)
+{
+    std::vector<prof::Pending> todo;
+    {
+        std::lock_guard<std::mutex> lk(prof::mu);
+        todo.swap(prof::pending);
+    }
+    for (const prof::Pending &p : todo) {
+        float f = 0.f;
+        if (cudaEventSynchronize(p.b) != cudaSuccess) return check_cuda("mg_profile_read");
+        cudaEventElapsedTime(&f, p.a, p.b);
+        std::lock_guard<std::mutex> lk(prof::mu);
+        prof::ms[p.stage] += f;
+        prof::calls[p.stage] += 1;
+        prof::pool.push_back(p.a);
+        prof::pool.push_back(p.b);
+    }
+    std::lock_guard<std::mutex> lk(prof::mu);
+    for (int i = 0; i < MG_NSTAGES; ++i) {
+        if (ms) ms[i] = prof::ms[i];
+        if (calls) calls[i] = prof::calls[i];
+        if (reset) {
+            prof::ms[i] = 0.0;
+            prof::calls[i] = 0;
+        }
+    }
+    return check_cuda("mg_profile_read");
 }
 
 mg_status mg_sq_diff_sum(const float *a, const float *b, int64_t n, double *out, void *ws, size_t ws_bytes,

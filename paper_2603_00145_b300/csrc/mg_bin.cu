@@ -62,6 +62,7 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
 
 void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_t st)
 {
+    MG_PROF(MG_ST_SLICES, st);
     k_build_slices<<<(S + 127) / 128, 128, 0, st>>>(in, out, S);
 }
 
@@ -296,7 +297,7 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RecGeomT {
-    T pcx, pcy, A, B2, C, amp;
+    T pcx, pcy, A, B2, C, amp, thr;
 };
 
 template <typename T>
@@ -315,7 +316,7 @@ __device__ __forceinline__ double t_rsqrt<double>(double x) { return 1.0 / sqrt(
 
 template <typename T>
 __device__ void record_geometry(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
-                                RecGeomT<T> &o)
+                                float K2, RecGeomT<T> &o)
 {
     T w = q[0], x = q[1], y = q[2], z = q[3];
     T R[3][3];
@@ -372,6 +373,8 @@ __device__ void record_geometry(const float *mu, const float *q, const float *s,
     o.B2 = 2 * kap * Kuv * dx * dy;
     o.C = kap * Kvv * dy * dy;
     o.amp = (T)alpha * t_rsqrt<T>(D) * t_exp<T>((T)(-0.5) * w0 * w0 / Sww);
+    T r2 = (T)K2 - w0 * w0 / Sww;  // the cut ellipse is q <= r2 (natural units)
+    o.thr = kap * (r2 > 0 ? r2 : (T)0);
 }
 
 __device__ __forceinline__ bool is_degenerate(const float *s, float ratio)
@@ -456,14 +459,16 @@ __global__ void __launch_bounds__(K1_NT) k1_emit(const SliceDev *slices, int S, 
                 float2 geo2;
                 if (degen) {
                     RecGeomT<double> r;
-                    record_geometry<double>(G.mu, qv, sc, av, Sd, r);
+                    record_geometry<double>(G.mu, qv, sc, av, Sd, K2, r);
                     geo = make_float4((float)r.pcx, (float)r.pcy, (float)r.A, (float)r.B2);
                     geo2 = make_float2((float)r.C, (float)r.amp);
+                    rec.thr[pos] = (float)r.thr;
                 } else {
                     RecGeomT<float> r;
-                    record_geometry<float>(G.mu, qv, sc, av, Sd, r);
+                    record_geometry<float>(G.mu, qv, sc, av, Sd, K2, r);
                     geo = make_float4(r.pcx, r.pcy, r.A, r.B2);
                     geo2 = make_float2(r.C, r.amp);
+                    rec.thr[pos] = r.thr;
                 }
                 rec.geo[pos] = geo;
                 rec.geo2[pos] = geo2;
@@ -662,6 +667,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     rec.slice = (int *)(ws + L.rec_slice);
     rec.rect = (ushort4 *)(ws + L.rec_rect);
     rec.mom = (float *)(ws + L.rec_mom);
+    rec.thr = (float *)(ws + L.rec_thr);
     rec.cap = L.cap_records;
     unsigned *chunk_base = (unsigned *)(ws + L.chunk_base);
     unsigned *slice_rs = chunk_base + (L.S + 1);
@@ -674,10 +680,22 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
 
     cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
     dim3 g1((unsigned)NB, (unsigned)((S + K1_SG - 1) / K1_SG));
-    k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, cnt, NB, hdr);
-    mg_launch_scan_u32(cnt, cnt, (long long)S * NB, nullptr, part, &hdr->n_records, st);
-    k1_emit<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NB, rec);
-    k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, NB, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
+    {
+        MG_PROF(MG_ST_K1_COUNT, st);
+        k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, cnt, NB, hdr);
+    }
+    {
+        MG_PROF(MG_ST_SCAN_REC, st);
+        mg_launch_scan_u32(cnt, cnt, (long long)S * NB, nullptr, part, &hdr->n_records, st);
+    }
+    {
+        MG_PROF(MG_ST_K1_EMIT, st);
+        k1_emit<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NB, rec);
+    }
+    {
+        MG_PROF(MG_ST_CHUNKS, st);
+        k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, NB, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
+    }
     const int Tmax = (int)L.max_tiles;
     size_t smem = (size_t)BIN_WARPS * Tmax * sizeof(unsigned);
     if (smem > 48 * 1024) {
@@ -686,11 +704,24 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     long long want = (L.cap_chunks + BIN_WARPS - 1) / BIN_WARPS;
     int gb = (int)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
-    k_bin_hist<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax, L.cap_chunks);
+    {
+        MG_PROF(MG_ST_BIN_HIST, st);
+        k_bin_hist<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+                                                     L.cap_chunks);
+    }
     long long tot = (long long)S * Tmax;
     int gc = (int)((tot + 255) / 256 < 148 * 32 ? (tot + 255) / 256 : 148 * 32);
-    k_bin_colscan<<<gc, 256, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt);
-    mg_launch_scan_u32(tile_cnt, tile_off, L.n_tiles, nullptr, part, &hdr->n_entries, st);
-    k_bin_scatter<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
-                                                    L.cap_chunks, tile_off, entries, L.cap_entries);
+    {
+        MG_PROF(MG_ST_BIN_COLSCAN, st);
+        k_bin_colscan<<<gc, 256, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt);
+    }
+    {
+        MG_PROF(MG_ST_SCAN_TILES, st);
+        mg_launch_scan_u32(tile_cnt, tile_off, L.n_tiles, nullptr, part, &hdr->n_entries, st);
+    }
+    {
+        MG_PROF(MG_ST_BIN_SCATTER, st);
+        k_bin_scatter<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+                                                        L.cap_chunks, tile_off, entries, L.cap_entries);
+    }
 }

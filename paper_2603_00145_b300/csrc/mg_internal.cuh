@@ -63,7 +63,9 @@ struct WsHeader {
     unsigned long long n_entries;
     unsigned long long n_chunks;
     unsigned long long scan_total;
-    unsigned long long reserved[27];
+    unsigned long long pairs_inside;     // mg_render_pair_count
+    unsigned long long pairs_evaluated;
+    unsigned long long reserved[25];
 };
 
 // Records are stored as structure-of-arrays.
@@ -74,13 +76,14 @@ struct Records {
     int *slice;         // global slice id
     ushort4 *rect;      // tile rectangle (tx0, ty0, tx1, ty1)
     float *mom;         // [cap][8] backward moments (6 used)
+    float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
     long long cap;
 };
 
 // Workspace layout, computed identically on the host for fwd, bwd and the
 // size query.
 struct WsLayout {
-    size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom;
+    size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom, rec_thr;
     size_t chunk_base, hist, tile_cnt, tile_off, entries, total;
     long long S, NB, NG, SG, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
@@ -102,7 +105,39 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// per-stage CUDA-event timing (mg_profile_*); no-ops unless enabled
+enum MgStage {
+    MG_ST_SLICES = 0,
+    MG_ST_K1_COUNT,
+    MG_ST_SCAN_REC,
+    MG_ST_K1_EMIT,
+    MG_ST_CHUNKS,
+    MG_ST_BIN_HIST,
+    MG_ST_BIN_COLSCAN,
+    MG_ST_SCAN_TILES,
+    MG_ST_BIN_SCATTER,
+    MG_ST_RENDER_FWD,
+    MG_ST_ZERO,
+    MG_ST_RENDER_BWD,
+    MG_ST_CHAIN,
+    MG_ST_LOSS,
+    MG_ST_PAIRS,
+    MG_ST_NRF_FWD,
+    MG_ST_NRF_BWD,
+    MG_NSTAGES
+};
+void mg_prof_begin(int stage, cudaStream_t st);
+void mg_prof_end(int stage, cudaStream_t st);
+struct MgProfScope {
+    int s;
+    cudaStream_t st;
+    MgProfScope(int stage, cudaStream_t stream) : s(stage), st(stream) { mg_prof_begin(s, st); }
+    ~MgProfScope() { mg_prof_end(s, st); }
+};
+#define MG_PROF(stage, stream) MgProfScope mg_prof_scope_##stage(stage, stream)
+
 // host-side launch helpers (defined in the .cu files)
+void mg_launch_pair_count(const WsLayout &L, char *ws, const StackTable &tab, cudaStream_t st);
 void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_t st);
 void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab, const float *mean,
                    const float *quat, const float *scale, const float *alpha, long long n, float K, float f64_ratio,

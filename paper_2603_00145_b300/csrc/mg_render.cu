@@ -216,6 +216,55 @@ __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const un
     }
 }
 
+// Pair statistics over the bins: evaluated (record, in-image voxel) pairs and
+// those inside the record's K-sigma ellipsoid (q >= thr in log2 units).
+__global__ void __launch_bounds__(32 * RW) k_pair_count(StackTable tab, const unsigned *__restrict__ tile_off,
+                                                        const unsigned *__restrict__ entries, long long cap_entries,
+                                                        long long cap_records, const float4 *__restrict__ geo,
+                                                        const float2 *__restrict__ geo2,
+                                                        const float *__restrict__ thr, WsHeader *hdr)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * RW + w;
+    if (t >= tab.n_tiles_total) return;
+    TileLoc L = locate_tile(tab, t, lane);
+    const float fpx = (float)L.px, fpy0 = (float)L.py0;
+    unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
+    if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
+    if (e0 > e1) e0 = e1;
+    unsigned long long inside = 0, evald = 0;
+    int nvalid = 0;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) nvalid += (L.px < L.W && L.py0 + v < L.H);
+    for (unsigned e = e0; e < e1; ++e) {
+        unsigned r = entries[e];
+        if ((long long)r >= cap_records) continue;
+        const float4 a = geo[r];
+        const float C = geo2[r].x;
+        const float th = thr[r];
+        const float dx = fpx - a.x;
+        const float dy0 = fpy0 - a.y;
+        const float cdy = C * dy0;
+        const float a1 = fmaf(a.w, dx, cdy + cdy);
+        const float a0 = fmaf(fmaf(a.z, dx, a.w * dy0), dx, cdy * dy0);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const float q = fmaf(fmaf(C, (float)v, a1), (float)v, a0);
+            inside += (L.px < L.W && L.py0 + v < L.H && q >= th);
+        }
+        evald += nvalid;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        inside += __shfl_xor_sync(0xffffffffu, inside, o);
+        evald += __shfl_xor_sync(0xffffffffu, evald, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&hdr->pairs_inside, inside);
+        atomicAdd(&hdr->pairs_evaluated, evald);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K6: chain the per-record moments to the Gaussian parameters
 // ---------------------------------------------------------------------------
@@ -368,6 +417,14 @@ __global__ void k_chain(const WsHeader *hdr, long long cap_records, const float4
         } else {
             geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, gamp, gm, gq, gs, ga);
         }
+        // gradient on the unit sphere: drop the component along q (the
+        // normalisation q = q_raw/|q_raw| removes it, and the rotation formula
+        // is only a rotation for unit q)
+        {
+            float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+            float rad = (gq[0] * qv[0] + gq[1] * qv[1] + gq[2] * qv[2] + gq[3] * qv[3]) / qq;
+            for (int i = 0; i < 4; ++i) gq[i] -= rad * qv[i];
+        }
         atomicAdd(&g_mean[3 * g], gm[0]);
         atomicAdd(&g_mean[3 * g + 1], gm[1]);
         atomicAdd(&g_mean[3 * g + 2], gm[2]);
@@ -385,10 +442,23 @@ __global__ void k_chain(const WsHeader *hdr, long long cap_records, const float4
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+void mg_launch_pair_count(const WsLayout &L, char *ws, const StackTable &tab, cudaStream_t st)
+{
+    WsHeader *hdr = (WsHeader *)(ws + L.hdr);
+    cudaMemsetAsync(&hdr->pairs_inside, 0, 2 * sizeof(unsigned long long), st);
+    int nt = tab.n_tiles_total;
+    if (nt <= 0) return;
+    MG_PROF(MG_ST_PAIRS, st);
+    k_pair_count<<<(nt + RW - 1) / RW, 32 * RW, 0, st>>>(
+        tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
+        (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), (const float *)(ws + L.rec_thr), hdr);
+}
+
 void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, float *out, cudaStream_t st)
 {
     int nt = tab.n_tiles_total;
     if (nt <= 0) return;
+    MG_PROF(MG_ST_RENDER_FWD, st);
     k_render_fwd<<<(nt + RW - 1) / RW, 32 * RW, 0, st>>>(
         tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
         (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), out);
@@ -407,15 +477,22 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     long long capv = L.cap_records * 2;
     int gz = (int)((capv + 255) / 256 < 148 * 16 ? (capv + 255) / 256 : 148 * 16);
     if (gz < 1) gz = 1;
-    k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), hdr, L.cap_records);
+    {
+        MG_PROF(MG_ST_ZERO, st);
+        k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), hdr, L.cap_records);
+    }
     int nt = tab.n_tiles_total;
-    if (nt > 0)
-        k_render_bwd<<<(nt + RW - 1) / RW, 32 * RW, 0, st>>>(
-            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
-            L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), grad_out,
-            (float *)(ws + L.rec_mom));
+    {
+        MG_PROF(MG_ST_RENDER_BWD, st);
+        if (nt > 0)
+            k_render_bwd<<<(nt + RW - 1) / RW, 32 * RW, 0, st>>>(
+                tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
+                L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), grad_out,
+                (float *)(ws + L.rec_mom));
+    }
     int gc = (int)((L.cap_records + 255) / 256 < 148 * 16 ? (L.cap_records + 255) / 256 : 148 * 16);
     if (gc < 1) gc = 1;
+    MG_PROF(MG_ST_CHAIN, st);
     k_chain<<<gc, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2),
                                 (const int *)(ws + L.rec_gid), (const int *)(ws + L.rec_slice),
                                 (const float *)(ws + L.rec_mom), slices, mean, quat, scale, alpha, f64_ratio, g_mean,

@@ -170,6 +170,28 @@ def mg_sq_diff_sum(a, b, out, ws, stream=None):
     L.check(st, "mg_sq_diff_sum")
 
 
+def mg_render_pair_count(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, ws, stream=None):
+    g = _gauss(mean, quat, scale, alpha)
+    c = (ctypes.c_int64 * 2)()
+    L.check(L.lib().mg_render_pair_count(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts), ws.data_ptr(),
+                                         ws.numel(), c, _stream_handle(stream)), "mg_render_pair_count")
+    return int(c[0]), int(c[1])
+
+
+def mg_profile_enable(on: bool = True):
+    L.check(L.lib().mg_profile_enable(1 if on else 0), "mg_profile_enable")
+
+
+def mg_profile_read(reset: bool = True) -> dict:
+    """{stage name: (milliseconds, calls)} accumulated since the last reset."""
+    lib = L.lib()
+    n = lib.mg_profile_stage_count()
+    ms = (ctypes.c_double * n)()
+    calls = (ctypes.c_int64 * n)()
+    L.check(lib.mg_profile_read(ms, calls, 1 if reset else 0), "mg_profile_read")
+    return {lib.mg_profile_stage_name(i).decode(): (ms[i], int(calls[i])) for i in range(n)}
+
+
 def mg_version() -> str:
     return L.lib().mg_version().decode()
 
@@ -241,6 +263,10 @@ class SliceRenderer:
 
     def stats(self, stream=None) -> dict:
         return mg_render_stats_get(self.ws, stream)
+
+    def pair_count(self, mean, quat, scale, alpha, stream=None):
+        """(pairs inside the K-sigma ellipsoid, evaluated pairs) of the last forward."""
+        return mg_render_pair_count(mean, quat, scale, alpha, self.dev, self.opts(), self.ws, stream)
 
     def backward(self, mean, quat, scale, alpha, grad_out, stream=None):
         n = int(mean.shape[0])

@@ -32,6 +32,28 @@ def assert_render_close(got, want, what=""):
     return r, m
 
 
+def tangent(gq, quat):
+    """Remove the component of a quaternion gradient along the quaternion."""
+    q = np.asarray(quat, np.float64)
+    g = np.asarray(gq, np.float64)
+    return g - (np.sum(g * q, axis=1) / np.sum(q * q, axis=1))[:, None] * q
+
+
+def assert_grads_close(got, ref, G, what=""):
+    """got: the library's (mean, quat, scale, alpha) gradients; ref: the
+    oracle's dict. The quaternion gradient is compared on the tangent space."""
+    out = {}
+    for name, x in zip(("mean", "quat", "scale", "alpha"), got):
+        x = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+        want = ref[name]
+        if name == "quat":
+            want = tangent(want, G.quat)
+        r = rel_l2(x, want)
+        out[name] = r
+        assert r <= TOL_GRAD_REL, f"{what}: grad {name} rel-L2 {r:.3e} > {TOL_GRAD_REL}"
+    return out
+
+
 def render_gpu(G: ms.Gaussians, stacks, K=3.0, f64_ratio=100.0, caps=None, renderer=None):
     from paper_2603_00145_b300 import SliceRenderer
 
@@ -54,18 +76,4 @@ def gpu_bins(R, n):
 
 
 def sub_stacks(stacks, picks):
-    """Stacks holding only the picked slices ((stack index, slice index) pairs)
-    in the same order; returns the new stacks and each pick's flat voxel slice
-    in the full concatenated output."""
-    out, ranges = [], []
-    base = 0
-    bases = []
-    for s in stacks:
-        bases.append(base)
-        base += s.n_vox
-    for si, k in picks:
-        s = stacks[si]
-        out.append(ms.Stack(1, s.H, s.W, s.dx, s.dy, s.thickness, s.xform[k:k + 1]))
-        o = bases[si] + k * s.H * s.W
-        ranges.append((o, o + s.H * s.W))
-    return out, ranges
+    return ms.pick_slices(stacks, picks)

@@ -10,7 +10,7 @@ import torch
 
 import mg_synth as ms
 import oracle as orc
-from gpu_util import (TOL_GRAD_REL, assert_render_close, gpu_bins, rel_l2, render_gpu, sub_stacks, to_dev)
+from gpu_util import (assert_grads_close, assert_render_close, gpu_bins, render_gpu, sub_stacks, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -58,9 +58,7 @@ def test_tiny_workload_fwd_bwd():
     gout = rng.normal(size=want.size).astype(np.float32)
     g = R.backward(*dev, torch.from_numpy(gout).cuda())
     ref = orc.grad(G, wl.stacks, rec, gout.astype(np.float64))
-    for name, got in zip(("mean", "quat", "scale", "alpha"), g):
-        r = rel_l2(got.cpu().numpy(), ref[name])
-        assert r <= TOL_GRAD_REL, (name, r)
+    assert_grads_close(g, ref, G, "tiny")
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -75,9 +73,7 @@ def test_mixed_stacks_fwd_bwd(seed):
     gout = np.random.default_rng(seed).normal(size=want.size).astype(np.float32)
     g = R.backward(*dev, torch.from_numpy(gout).cuda())
     ref = orc.grad(G, stacks, rec, gout.astype(np.float64))
-    for name, got in zip(("mean", "quat", "scale", "alpha"), g):
-        r = rel_l2(got.cpu().numpy(), ref[name])
-        assert r <= TOL_GRAD_REL, (name, r)
+    assert_grads_close(g, ref, G, "mixed")
 
 
 @pytest.mark.parametrize("K", [2.0, 4.5])
@@ -205,6 +201,4 @@ def test_bench_config_sampled_slices():
         o += b - a
     g = R.backward(*dev, gout)
     ref = orc.grad(G, sub, rec, gout_sub.astype(np.float64))
-    for name, got_g in zip(("mean", "quat", "scale", "alpha"), g):
-        r = rel_l2(got_g.cpu().numpy(), ref[name])
-        assert r <= TOL_GRAD_REL, (name, r)
+    assert_grads_close(g, ref, G, "feta slices")
