@@ -202,3 +202,16 @@ def test_bench_config_sampled_slices():
     g = R.backward(*dev, gout)
     ref = orc.grad(G, sub, rec, gout_sub.astype(np.float64))
     assert_grads_close(g, ref, G, "feta slices")
+
+
+def test_pair_counts_vs_oracle():
+    """Evaluated pairs are an exact integer function of the bins; pairs inside
+    the K-sigma ellipsoid agree up to FP32-vs-FP64 boundary decisions."""
+    G, stacks = _mixed_case(8)
+    R, out, dev = render_gpu(G, stacks)
+    inside, evald = R.pair_count(*dev)
+    rec = orc.records(G, stacks)
+    o_in, o_ev = orc.pair_counts(G, stacks, rec)
+    assert evald == o_ev
+    assert abs(inside - o_in) <= max(2, 1e-4 * o_in), (inside, o_in)
+    assert 0 < inside < evald
