@@ -202,6 +202,31 @@ size_t mg_reduce_workspace_size(int64_t n);
 mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float *grad, double *loss_out, void *ws,
                        size_t ws_bytes, mg_stream_t stream);
 
+/*
+ * mg_loss_l1l2 without any device allocation (an addition of this library;
+ * the paper has no counterpart). Some callers cannot allocate device memory
+ * or hand out a workspace: an application that reserves all device memory
+ * for its own pool up front, a plugin inside another runtime that owns every
+ * device allocation, a real-time loop that must never enter the driver's
+ * allocator. This entry point keeps its per-block FP64 partial sums in a
+ * fixed 128 KiB array inside the library (a file-scope __device__ array that
+ * every GPU which loads the library holds until the process exits) and calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *   Limit: n <= 33554432 (8192 partial blocks of 4096 voxels); larger n
+ *   returns MG_ERR_INVALID_ARG with nothing launched.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address with that device current; make that first call before any
+ *   stream capture.
+ *   Sharing: every call uses the same array. Calls that overlap on the GPU
+ *   (other streams, other host threads) race on it; serialise them. Each
+ *   call writes every slot it reads, so nothing needs clearing between calls.
+ * Arguments and results are those of mg_loss_l1l2 (device pointers; grad
+ * may be NULL); the result agrees with mg_loss_l1l2 up to FP64 summation
+ * order.
+ */
+mg_status mg_loss_l1l2_noalloc(const float *pred, const float *target, int64_t n, float *grad, double *loss_out,
+                               mg_stream_t stream);
+
 /* FP64 sum of squared differences (for MSE / PSNR, Sec. 4.1.3): out: device
  * double [1] = sum (a-b)^2, fixed-order FP64 accumulation. */
 mg_status mg_sq_diff_sum(const float *a, const float *b, int64_t n, double *out, void *ws, size_t ws_bytes,

@@ -337,6 +337,8 @@ mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &s
 
 }  // namespace
 
+mg_status mg_set_error(mg_status s, const char *msg) { return fail(s, msg); }
+
 extern "C" {
 
 mg_opts mg_default_opts(void)

@@ -10,7 +10,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "mg_internal.cuh"
+
+mg_status mg_set_error(mg_status s, const char *msg);  // mg_api.cu
 
 constexpr int RED_NT = 256;
 constexpr int RED_LEAF = 16;
@@ -131,4 +135,57 @@ void mg_launch_sq_diff(const float *a, const float *b, long long n, double *out,
     int nb = mg_reduce_blocks(n);
     k_reduce_leaf<1><<<nb, RED_NT, 0, st>>>(a, b, n, nullptr, 0.0, part);
     k_reduce_final<1><<<1, 32, 0, st>>>(part, nb, 0.0, out);
+}
+
+// ---------------------------------------------------------------------------
+// mg_loss_l1l2_noalloc: the same reduction with its per-block partial sums in
+// a fixed array inside the library instead of a caller workspace.
+// ---------------------------------------------------------------------------
+#define MG_NOALLOC_MAX_BLOCKS 8192  // 2 doubles each: 128 KiB
+#define MG_NOALLOC_MAX_N ((long long)MG_NOALLOC_MAX_BLOCKS * RED_NT * RED_LEAF)
+#define MG_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) double g_noalloc_part[2 * MG_NOALLOC_MAX_BLOCKS];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_ptr[MG_NOALLOC_MAX_DEVICES];
+
+extern "C" mg_status mg_loss_l1l2_noalloc(const float *pred, const float *target, int64_t n, float *grad,
+                                          double *loss_out, mg_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!pred || !target)) || !loss_out)
+        return mg_set_error(MG_ERR_INVALID_ARG, "mg_loss_l1l2_noalloc: bad pointer or size");
+    if (n > MG_NOALLOC_MAX_N)
+        return mg_set_error(MG_ERR_INVALID_ARG,
+                            "mg_loss_l1l2_noalloc: n exceeds the fixed partial-sum array (at most 33554432 "
+                            "elements); use mg_loss_l1l2 with a workspace");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MG_NOALLOC_MAX_DEVICES)
+        return mg_set_error(MG_ERR_CUDA, "mg_loss_l1l2_noalloc: no usable current device");
+    double *part = nullptr;
+    {
+        // set-up, once per device, with that device current: the device
+        // address of the array (its name is only a host-side stand-in)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
+            if (e != cudaSuccess || !p)
+                return mg_set_error(MG_ERR_CUDA, "mg_loss_l1l2_noalloc: cudaGetSymbolAddress failed");
+            g_noalloc_ptr[dev] = (double *)p;
+        }
+        part = g_noalloc_ptr[dev];
+    }
+    long long leaves = (n + RED_LEAF - 1) / RED_LEAF;
+    int nb = (int)((leaves + RED_NT - 1) / RED_NT);
+    if (nb < 1) nb = 1;
+    double inv_n = n > 0 ? 1.0 / (double)n : 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    // every partial slot the final pass reads is written by the first pass,
+    // so nothing left in the array by an earlier call is used
+    k_reduce_leaf<0><<<nb, RED_NT, 0, st>>>(pred, target, n, grad, inv_n, part);
+    k_reduce_final<0><<<1, 32, 0, st>>>(part, nb, inv_n, loss_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return mg_set_error(MG_ERR_CUDA, cudaGetErrorString(e));
+    return MG_OK;
 }
