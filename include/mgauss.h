@@ -41,14 +41,16 @@
  *   Lww = e_n.(Sigma e_n), Luw = e_u.(Sigma e_n), Lvw = e_v.(Sigma e_n),
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v);  Sww = Lww + sig2;  K2 = K*K;
  *   sig2 = (float)(thickness^2 * 0.18033688011112042) (computed in double);
- *   the record exists iff  w0*w0 <= K2*Sww  and its pixel box below is non-empty:
+ *   the record exists iff  w0*w0 <= K2*Sww  (the K-sigma slab test); its pixel box:
  *   r2 = max(K2 - (w0*w0)/Sww, 0);  Cuu = max(Luu - (Luw*Luw)/Sww, 0);
  *   Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0);  cu = u0 - (Luw*w0)/Sww;  cv = v0 - (Lvw*w0)/Sww;
  *   ru = sqrt(r2*Cuu), rv = sqrt(r2*Cvv);  hx = 0.5*(W-1), hy = 0.5*(H-1);
  *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx),
  *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy);
- *   non-empty iff il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0 (NaN: empty);
- *   clamp il,jl up to 0 and ih,jh down to W-1,H-1; tiles [il/16, ih/16] x [jl/16, jh/16].
+ *   the box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0 (NaN: empty);
+ *   a non-empty box is clamped (il,jl up to 0, ih,jh down to W-1,H-1) and lists the
+ *   tiles [il/16, ih/16] x [jl/16, jh/16]; an empty box lists no tile (stored as the
+ *   tile rectangle (1,1,0,0)).
  *   Tile (tx,ty) of a slice covers pixels 16tx..16tx+15 x 16ty..16ty+15.
  *   The count of records and of (record, tile) entries is therefore exact
  *   and reproducible bit for bit by any IEEE FP32 implementation.

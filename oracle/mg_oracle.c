@@ -37,16 +37,17 @@
  *   Lww = e_n.(Sigma e_n), Luw = e_u.(Sigma e_n), Lvw = e_v.(Sigma e_n),
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v), (Sigma a)_r = (S_r0 a0 + S_r1 a1) + S_r2 a2
  *   Sww = Lww + sig2;  K2 = K*K
- *   record exists only if  w0*w0 <= K2*Sww  (the K-sigma slab test)
+ *   the record exists iff  w0*w0 <= K2*Sww  (the K-sigma slab test)
  *   r2 = max(K2 - (w0*w0)/Sww, 0)
  *   Cuu = max(Luu - (Luw*Luw)/Sww, 0),  Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0)
  *   cu = u0 - (Luw*w0)/Sww,  cv = v0 - (Lvw*w0)/Sww
  *   ru = sqrt(r2*Cuu),  rv = sqrt(r2*Cvv)
  *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx), hx = 0.5*(W-1)
  *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy), hy = 0.5*(H-1)
- *   the record also needs il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0
- *   (false for NaN); then il,jl are clamped up to 0 and ih,jh down to W-1,H-1
- *   tiles: [il/16, ih/16] x [jl/16, jh/16]  (integer division)
+ *   the pixel box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1,
+ *   jh>=0 (false for NaN); a non-empty box has il,jl clamped up to 0 and ih,jh
+ *   down to W-1,H-1 and lists the tiles [il/16, ih/16] x [jl/16, jh/16]
+ *   (integer division); an empty box lists none (rectangle (1,1,0,0))
  *   sig2 = (float)(thickness^2 * 0.18033688011112042) computed in double.
  * (u,v) bounds of the ellipse {y : y^T Sigma'^-1 y <= K^2} cut by the plane
  * w = 0 are cu +- ru, cv +- rv: the in-plane conditional covariance of Sigma'
@@ -183,7 +184,10 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     float jl = ceilf((cv - rv) / sl->dy + hy);
     float jh = floorf((cv + rv) / sl->dy + hy);
     float Wm1 = (float)(sl->W - 1), Hm1 = (float)(sl->H - 1);
-    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) return 0;
+    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
+        rect[0] = 1; rect[1] = 1; rect[2] = 0; rect[3] = 0; /* record without tiles */
+        return 1;
+    }
     if (il < 0.0f) il = 0.0f;
     if (jl < 0.0f) jl = 0.0f;
     if (ih > Wm1) ih = Wm1;

@@ -36,7 +36,7 @@ thread_local cudaEvent_t open_ev[MG_NSTAGES];
 const char *names[MG_NSTAGES] = {"slices",      "k1_count",   "scan_records", "k1_emit",    "chunks",
                                  "bin_hist",    "bin_colscan", "scan_tiles",   "bin_scatter", "render_fwd",
                                  "zero_moments", "render_bwd", "chain",        "loss",       "pair_count",
-                                 "nrf_fwd",     "nrf_bwd"};
+                                 "nrf_fwd",     "nrf_bwd",     "rec_geom"};
 
 cudaEvent_t get_event()
 {
@@ -150,6 +150,8 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     }
     L.S = S;
     L.NB = (n + 255) / 256;
+    L.NW = (n + 31) / 32;
+    L.SW = (S + 31) / 32;
     L.cap_records = o.cap_records;
     L.cap_entries = o.cap_entries;
     L.cap_chunks = o.cap_records / MG_CHUNK + S + 1;
@@ -163,7 +165,9 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     };
     L.hdr = take(sizeof(WsHeader));
     L.slices = take(sizeof(SliceDev) * (size_t)S);
-    L.cnt = take(sizeof(unsigned) * (size_t)(S * L.NB + 1));
+    L.cnt = take(sizeof(unsigned) * (size_t)(S * L.NW + 1));
+    L.gcnt = take(sizeof(unsigned) * (size_t)(n + 1));
+    L.bits = take(sizeof(unsigned) * (size_t)(L.SW * n + 1));
     L.scan_part = take(sizeof(unsigned long long) * MG_SCAN_BLOCKS);
     L.rec_geo = take(16 * (size_t)L.cap_records);
     L.rec_geo2 = take(8 * (size_t)L.cap_records);
@@ -177,6 +181,8 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.tile_cnt = take(sizeof(unsigned) * (size_t)tiles);
     L.tile_off = take(sizeof(unsigned) * (size_t)(tiles + 1));
     L.entries = take(sizeof(unsigned) * (size_t)L.cap_entries);
+    L.gmap = take(sizeof(unsigned) * (size_t)L.cap_records);
+    L.rec_grad = take(48 * (size_t)L.cap_records);
     L.total = off;
     return L;
 }

@@ -46,7 +46,9 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
     d.sig2 = in.sig2[s];
     d.hx = 0.5f * (float)(d.W - 1);
     d.hy = 0.5f * (float)(d.H - 1);
+    d.same_frame = 0;
     if (in.planes) {
+        d.same_frame = kk > 0;
         for (int i = 0; i < 9; ++i) d.Q[i] = (i % 4 == 0) ? 1.0f : 0.0f;
         d.t[0] = in.cx;
         d.t[1] = in.cy;
@@ -56,6 +58,12 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
         const float *x = in.xform[s] + (size_t)kk * 12;
         for (int i = 0; i < 9; ++i) d.Q[i] = x[i];
         for (int i = 0; i < 3; ++i) d.t[i] = x[9 + i];
+        if (kk > 0) {
+            const unsigned *a = (const unsigned *)x, *b = (const unsigned *)(x - 12);
+            int same = 1;
+            for (int i = 0; i < 9; ++i) same &= (a[i] == b[i]);
+            d.same_frame = same;
+        }
     }
     out[k] = d;
 }
@@ -223,46 +231,80 @@ __device__ bool load_gauss_pred(const float *mean, const float *quat, const floa
 }
 
 struct PredOut {
-    float w0, u0, v0, Sww, Luw, Lvw;
     int il, ih, jl, jh;  // clamped pixel box
 };
 
-// slab test only (cheap prefilter) then the full predicate; returns existence
-__device__ __forceinline__ bool record_predicate(const GaussPred &G, const SliceDev &S, float K2, PredOut &o)
+// The terms of the predicate that depend on the Gaussian's covariance and the
+// slice's rotation only (reused across the slices of a stack without motion).
+struct FrameTerms {
+    float Lww;
+    float Luw, Lvw, Luu, Lvv;
+    bool full;  // Luw..Lvv computed
+};
+
+__device__ __forceinline__ void frame_slab(const GaussPred &G, const float *Q, FrameTerms &f)
 {
-    const float *Q = S.Q;
-    float p0 = __fsub_rn(G.mu[0], S.t[0]), p1 = __fsub_rn(G.mu[1], S.t[1]), p2 = __fsub_rn(G.mu[2], S.t[2]);
     float en0 = Q[2], en1 = Q[5], en2 = Q[8];
-    float w0 = dot3_rn(en0, en1, en2, p0, p1, p2);
     float sn0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], en0, en1, en2);
     float sn1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], en0, en1, en2);
     float sn2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], en0, en1, en2);
-    float Lww = dot3_rn(en0, en1, en2, sn0, sn1, sn2);
-    float Sww = __fadd_rn(Lww, S.sig2);
-    float ww = __fmul_rn(w0, w0);
-    if (!(ww <= __fmul_rn(K2, Sww))) return false;
+    f.Lww = dot3_rn(en0, en1, en2, sn0, sn1, sn2);
+    f.full = false;
+}
+
+__device__ __forceinline__ void frame_full(const GaussPred &G, const float *Q, FrameTerms &f)
+{
+    float en0 = Q[2], en1 = Q[5], en2 = Q[8];
     float eu0 = Q[0], eu1 = Q[3], eu2 = Q[6];
     float ev0 = Q[1], ev1 = Q[4], ev2 = Q[7];
-    float u0 = dot3_rn(eu0, eu1, eu2, p0, p1, p2);
-    float v0 = dot3_rn(ev0, ev1, ev2, p0, p1, p2);
-    float Luw = dot3_rn(eu0, eu1, eu2, sn0, sn1, sn2);
-    float Lvw = dot3_rn(ev0, ev1, ev2, sn0, sn1, sn2);
+    float sn0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], en0, en1, en2);
+    float sn1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], en0, en1, en2);
+    float sn2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], en0, en1, en2);
+    f.Luw = dot3_rn(eu0, eu1, eu2, sn0, sn1, sn2);
+    f.Lvw = dot3_rn(ev0, ev1, ev2, sn0, sn1, sn2);
     float su0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], eu0, eu1, eu2);
     float su1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], eu0, eu1, eu2);
     float su2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], eu0, eu1, eu2);
-    float Luu = dot3_rn(eu0, eu1, eu2, su0, su1, su2);
+    f.Luu = dot3_rn(eu0, eu1, eu2, su0, su1, su2);
     float sv0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], ev0, ev1, ev2);
     float sv1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], ev0, ev1, ev2);
     float sv2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], ev0, ev1, ev2);
-    float Lvv = dot3_rn(ev0, ev1, ev2, sv0, sv1, sv2);
+    f.Lvv = dot3_rn(ev0, ev1, ev2, sv0, sv1, sv2);
+    f.full = true;
+}
+
+// The record-existence part of the predicate: the K-sigma slab test.
+__device__ __forceinline__ bool slab_test(const GaussPred &G, const SliceDev &S, float K2, float Lww)
+{
+    const float *Q = S.Q;
+    float p0 = __fsub_rn(G.mu[0], S.t[0]), p1 = __fsub_rn(G.mu[1], S.t[1]), p2 = __fsub_rn(G.mu[2], S.t[2]);
+    float w0 = dot3_rn(Q[2], Q[5], Q[8], p0, p1, p2);
+    float Sww = __fadd_rn(Lww, S.sig2);
+    return __fmul_rn(w0, w0) <= __fmul_rn(K2, Sww);
+}
+
+// The record predicate of mgauss.h given the frame terms (computed here when
+// missing). Returns existence and the clamped pixel box.
+__device__ __forceinline__ bool record_predicate(const GaussPred &G, const SliceDev &S, float K2, FrameTerms &f,
+                                                 PredOut &o)
+{
+    const float *Q = S.Q;
+    float p0 = __fsub_rn(G.mu[0], S.t[0]), p1 = __fsub_rn(G.mu[1], S.t[1]), p2 = __fsub_rn(G.mu[2], S.t[2]);
+    float w0 = dot3_rn(Q[2], Q[5], Q[8], p0, p1, p2);
+    float Sww = __fadd_rn(f.Lww, S.sig2);
+    float ww = __fmul_rn(w0, w0);
+    if (!(ww <= __fmul_rn(K2, Sww))) return false;
+    if (!f.full) frame_full(G, Q, f);
+    float u0 = dot3_rn(Q[0], Q[3], Q[6], p0, p1, p2);
+    float v0 = dot3_rn(Q[1], Q[4], Q[7], p0, p1, p2);
     float r2 = __fsub_rn(K2, __fdiv_rn(ww, Sww));
     if (r2 < 0.0f) r2 = 0.0f;
-    float Cuu = __fsub_rn(Luu, __fdiv_rn(__fmul_rn(Luw, Luw), Sww));
+    float Cuu = __fsub_rn(f.Luu, __fdiv_rn(__fmul_rn(f.Luw, f.Luw), Sww));
     if (Cuu < 0.0f) Cuu = 0.0f;
-    float Cvv = __fsub_rn(Lvv, __fdiv_rn(__fmul_rn(Lvw, Lvw), Sww));
+    float Cvv = __fsub_rn(f.Lvv, __fdiv_rn(__fmul_rn(f.Lvw, f.Lvw), Sww));
     if (Cvv < 0.0f) Cvv = 0.0f;
-    float cu = __fsub_rn(u0, __fdiv_rn(__fmul_rn(Luw, w0), Sww));
-    float cv = __fsub_rn(v0, __fdiv_rn(__fmul_rn(Lvw, w0), Sww));
+    float cu = __fsub_rn(u0, __fdiv_rn(__fmul_rn(f.Luw, w0), Sww));
+    float cv = __fsub_rn(v0, __fdiv_rn(__fmul_rn(f.Lvw, w0), Sww));
     float ru = __fsqrt_rn(__fmul_rn(r2, Cuu));
     float rv = __fsqrt_rn(__fmul_rn(r2, Cvv));
     float il = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cu, ru), S.dx), S.hx));
@@ -270,7 +312,11 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     float jl = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cv, rv), S.dy), S.hy));
     float jh = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(cv, rv), S.dy), S.hy));
     float Wm1 = (float)(S.W - 1), Hm1 = (float)(S.H - 1);
-    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) return false;
+    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
+        o.il = o.jl = MG_TILE;  // empty box: tile rectangle (1,1,0,0)
+        o.ih = o.jh = 0;
+        return true;
+    }
     if (il < 0.0f) il = 0.0f;
     if (jl < 0.0f) jl = 0.0f;
     if (ih > Wm1) ih = Wm1;
@@ -279,12 +325,6 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     o.ih = (int)ih;
     o.jl = (int)jl;
     o.jh = (int)jh;
-    o.w0 = w0;
-    o.u0 = u0;
-    o.v0 = v0;
-    o.Sww = Sww;
-    o.Luw = Luw;
-    o.Lvw = Lvw;
     return true;
 }
 
@@ -315,6 +355,13 @@ template <>
 __device__ __forceinline__ double t_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
 
 template <typename T>
+__device__ __forceinline__ T t_rcp(T x);
+template <>
+__device__ __forceinline__ float t_rcp<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double t_rcp<double>(double x) { return 1.0 / x; }
+
+template <typename T>
 __device__ void record_geometry(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
                                 float K2, RecGeomT<T> &o)
 {
@@ -330,6 +377,7 @@ __device__ void record_geometry(const float *mu, const float *q, const float *s,
     R[2][1] = 2 * (y * z + w * x);
     R[2][2] = 1 - 2 * (x * x + y * y);
     T sc[3] = {s[0], s[1], s[2]};
+    T isc[3] = {t_rcp<T>(sc[0]), t_rcp<T>(sc[1]), t_rcp<T>(sc[2])};
     T P[3][3];  // P[a][c] = e_a . R_c,  a in (u, v, w)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -345,7 +393,7 @@ __device__ void record_geometry(const float *mu, const float *q, const float *s,
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            g[a][c] = P[a][c] / sc[c];
+            g[a][c] = P[a][c] * isc[c];
             L[a][c] = P[a][c] * sc[c];
         }
     T Huu = g[0][0] * g[0][0] + g[0][1] * g[0][1] + g[0][2] * g[0][2];
@@ -357,23 +405,26 @@ __device__ void record_geometry(const float *mu, const float *q, const float *s,
     T Suw = L[0][0] * L[2][0] + L[0][1] * L[2][1] + L[0][2] * L[2][2];
     T Svw = L[1][0] * L[2][0] + L[1][1] * L[2][1] + L[1][2] * L[2][2];
     T Sww = L[2][0] * L[2][0] + L[2][1] * L[2][1] + L[2][2] * L[2][2] + (T)S.sig2;
+    T iSww = t_rcp<T>(Sww);
     T sig2 = (T)S.sig2;
     T D = 1 + sig2 * Hww;
-    T f = sig2 / D;
+    T rD = t_rsqrt<T>(D);
+    T f = sig2 * rD * rD;  // sig2 / D
     T Kuu = Huu - f * Huw * Huw;
     T Kuv = Huv - f * Huw * Hvw;
     T Kvv = Hvv - f * Hvw * Hvw;
-    T cu = du - Suw * w0 / Sww;
-    T cv = dv - Svw * w0 / Sww;
+    T wS = w0 * iSww;
+    T cu = du - Suw * wS;
+    T cv = dv - Svw * wS;
     const T kap = (T)(-0.72134752044448170368);  // -log2(e)/2
     T dx = S.dx, dy = S.dy;
-    o.pcx = cu / dx + (T)S.hx;
-    o.pcy = cv / dy + (T)S.hy;
+    o.pcx = cu * t_rcp<T>(dx) + (T)S.hx;
+    o.pcy = cv * t_rcp<T>(dy) + (T)S.hy;
     o.A = kap * Kuu * dx * dx;
     o.B2 = 2 * kap * Kuv * dx * dy;
     o.C = kap * Kvv * dy * dy;
-    o.amp = (T)alpha * t_rsqrt<T>(D) * t_exp<T>((T)(-0.5) * w0 * w0 / Sww);
-    T r2 = (T)K2 - w0 * w0 / Sww;  // the cut ellipse is q <= r2 (natural units)
+    o.amp = (T)alpha * rD * t_exp<T>((T)(-0.5) * w0 * wS);
+    T r2 = (T)K2 - w0 * wS;  // the cut ellipse is q <= r2 (natural units)
     o.thr = kap * (r2 > 0 ? r2 : (T)0);
 }
 
@@ -386,97 +437,150 @@ __device__ __forceinline__ bool is_degenerate(const float *s, float ratio)
 }
 
 // ---------------------------------------------------------------------------
-// K1: count and emit records, grid (Gaussian blocks of 256, slice groups)
+// K1: count, emit and geometry passes
+//   k1_count : one thread per Gaussian sweeps every slice (frame terms reused
+//              while the rotation is unchanged); writes a bit per (Gaussian,
+//              slice) record, per-(slice, warp) record counts and per-Gaussian
+//              counts.
+//   k1_emit  : revisits only the set bits; the exclusive scan of the
+//              (slice, warp) counts gives slice-major, Gaussian-ascending
+//              record positions; writes record identity, tile rectangle and
+//              the Gaussian-major record list used by the chain.
+//   k_rec_geom : one thread per record, evaluation geometry.
 // ---------------------------------------------------------------------------
 constexpr int K1_NT = 256;
-constexpr int K1_SG = 16;  // slices per group
+constexpr int K1_SMEM_SLICES = 256;  // slices staged in shared memory at a time
 
-__global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *slices, int S, const float *mean,
-                                                  const float *quat, const float *scale, const float *alpha,
-                                                  long long n, float K2, unsigned *cnt, int NB, WsHeader *hdr)
+__global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ slices, int S,
+                                                  const float *mean, const float *quat, const float *scale,
+                                                  const float *alpha, long long n, float K2, float f64_ratio,
+                                                  unsigned *cnt, long long NW, unsigned *gcnt, unsigned *bits,
+                                                  WsHeader *hdr)
 {
-    __shared__ SliceDev ssl[K1_SG];
-    const int k0 = blockIdx.y * K1_SG;
-    const int nk = min(K1_SG, S - k0);
-    for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
-    __syncthreads();
-    long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    __shared__ SliceDev ssl[K1_SMEM_SLICES];
+    const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    const long long wg = g >> 5;
+    const int lane = threadIdx.x & 31;
     GaussPred G;
     bool valid = false;
     if (g < n) {
         valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
-        if (!valid && blockIdx.y == 0) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
+        if (!valid) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        if (valid && is_degenerate(sc, f64_ratio)) atomicOr(&hdr->flags, MG_FLAG_DEGENERATE);
     }
-    for (int kk = 0; kk < nk; ++kk) {
-        PredOut po;
-        int f = valid ? (int)record_predicate(G, ssl[kk], K2, po) : 0;
-        int c = __syncthreads_count(f);
-        if (threadIdx.x == 0) cnt[(long long)(k0 + kk) * NB + blockIdx.x] = (unsigned)c;
+    FrameTerms f;
+    f.full = false;
+    f.Lww = 0.f;
+    unsigned word = 0, mine = 0;
+    for (int k0 = 0; k0 < S; k0 += K1_SMEM_SLICES) {
+        const int nk = min(K1_SMEM_SLICES, S - k0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
+        __syncthreads();
+        for (int kk = 0; kk < nk; ++kk) {
+            const int k = k0 + kk;
+            const SliceDev &Sd = ssl[kk];
+            bool ex = false;
+            if (valid) {
+                if (!Sd.same_frame || k == 0) frame_slab(G, Sd.Q, f);
+                ex = slab_test(G, Sd, K2, f.Lww);
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, ex);
+            if (lane == 0 && wg < NW) cnt[(long long)k * NW + wg] = __popc(bal);
+            word |= (unsigned)ex << (k & 31);
+            mine += ex;
+            if ((k & 31) == 31 || k == S - 1) {
+                if (g < n) bits[(long long)(k >> 5) * n + g] = word;
+                word = 0;
+            }
+        }
     }
+    if (g < n) gcnt[g] = mine;
 }
 
-__global__ void __launch_bounds__(K1_NT) k1_emit(const SliceDev *slices, int S, const float *mean, const float *quat,
-                                                 const float *scale, const float *alpha, long long n, float K2,
-                                                 float f64_ratio, const unsigned *off, int NB, Records rec)
+__global__ void __launch_bounds__(K1_NT) k1_emit(const SliceDev *__restrict__ slices, int S, const float *mean,
+                                                 const float *quat, const float *scale, const float *alpha,
+                                                 long long n, float K2, float f64_ratio,
+                                                 const unsigned *__restrict__ bits, const unsigned *__restrict__ off,
+                                                 long long NW, const unsigned *__restrict__ goff, Records rec,
+                                                 unsigned *gmap)
 {
-    __shared__ SliceDev ssl[K1_SG];
-    __shared__ unsigned wc[2][K1_NT / 32];
-    const int k0 = blockIdx.y * K1_SG;
-    const int nk = min(K1_SG, S - k0);
-    for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
-    __syncthreads();
-    long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    const long long wg = g >> 5;
     GaussPred G;
-    bool valid = false;
-    bool degen = false;
-    float sc[3] = {1.f, 1.f, 1.f}, qv[4] = {1.f, 0.f, 0.f, 0.f}, av = 0.f;
+    bool valid = false, degen = false;
+    float qv[4] = {1.f, 0.f, 0.f, 0.f}, sc[3] = {1.f, 1.f, 1.f}, av = 0.f;
     if (g < n) {
         valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
-        sc[0] = scale[3 * g];
-        sc[1] = scale[3 * g + 1];
-        sc[2] = scale[3 * g + 2];
-        qv[0] = quat[4 * g];
-        qv[1] = quat[4 * g + 1];
-        qv[2] = quat[4 * g + 2];
-        qv[3] = quat[4 * g + 3];
+        for (int i = 0; i < 4; ++i) qv[i] = quat[4 * g + i];
+        for (int i = 0; i < 3; ++i) sc[i] = scale[3 * g + i];
         av = alpha[g];
         degen = is_degenerate(sc, f64_ratio);
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int kk = 0; kk < nk; ++kk) {
-        PredOut po;
-        bool f = valid && record_predicate(G, ssl[kk], K2, po);
-        unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wc[kk & 1][w] = __popc(bal);
-        __syncthreads();
-        if (f) {
-            unsigned long long pos = off[(long long)(k0 + kk) * NB + blockIdx.x];
-            for (int u = 0; u < w; ++u) pos += wc[kk & 1][u];
-            pos += __popc(bal & lanemask_lt());
-            if ((long long)pos < rec.cap) {
-                const SliceDev &Sd = ssl[kk];
-                float4 geo;
-                float2 geo2;
-                if (degen) {
-                    RecGeomT<double> r;
-                    record_geometry<double>(G.mu, qv, sc, av, Sd, K2, r);
-                    geo = make_float4((float)r.pcx, (float)r.pcy, (float)r.A, (float)r.B2);
-                    geo2 = make_float2((float)r.C, (float)r.amp);
-                    rec.thr[pos] = (float)r.thr;
-                } else {
-                    RecGeomT<float> r;
-                    record_geometry<float>(G.mu, qv, sc, av, Sd, K2, r);
-                    geo = make_float4(r.pcx, r.pcy, r.A, r.B2);
-                    geo2 = make_float2(r.C, r.amp);
-                    rec.thr[pos] = r.thr;
+    const unsigned lt = lanemask_lt();
+    unsigned long long gpos = valid ? goff[g] : 0;
+    const int SW = (S + 31) >> 5;
+    for (int wd = 0; wd < SW; ++wd) {
+        unsigned word = valid ? bits[(long long)wd * n + g] : 0u;
+        unsigned uni = __reduce_or_sync(0xffffffffu, word);
+        while (uni) {
+            const int b = __ffs(uni) - 1;
+            uni &= uni - 1;
+            const int k = wd * 32 + b;
+            const bool f = (word >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) {
+                unsigned long long pos = (unsigned long long)off[(long long)k * NW + wg] + __popc(bal & lt);
+                const SliceDev Sd = slices[k];
+                FrameTerms ft;
+                frame_slab(G, Sd.Q, ft);
+                PredOut po;
+                record_predicate(G, Sd, K2, ft, po);  // true: same inputs as the count pass
+                if ((long long)pos < rec.cap) {
+                    rec.gid[pos] = (int)g;
+                    rec.slice[pos] = k;
+                    rec.rect[pos] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
+                                                 (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+                    if (!degen) {  // near-degenerate Gaussians: FP64 geometry in k_rec_geom_f64
+                        RecGeomT<float> o;
+                        record_geometry<float>(G.mu, qv, sc, av, Sd, K2, o);
+                        rec.geo[pos] = make_float4(o.pcx, o.pcy, o.A, o.B2);
+                        rec.geo2[pos] = make_float2(o.C, o.amp);
+                        rec.thr[pos] = o.thr;
+                    }
                 }
-                rec.geo[pos] = geo;
-                rec.geo2[pos] = geo2;
-                rec.gid[pos] = (int)g;
-                rec.slice[pos] = k0 + kk;
-                rec.rect[pos] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
-                                             (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+                if ((long long)gpos < rec.cap) gmap[gpos] = (unsigned)pos;
+                ++gpos;
             }
+        }
+    }
+}
+
+// FP64 record geometry for near-degenerate Gaussians (scale ratio above
+// f64_ratio), one thread per Gaussian over its records
+__global__ void k_rec_geom_f64(const WsHeader *hdr, long long n, const SliceDev *__restrict__ slices,
+                               const float *mean, const float *quat, const float *scale, const float *alpha, float K2,
+                               float f64_ratio, const unsigned *__restrict__ goff, const unsigned *__restrict__ gmap,
+                               Records rec)
+{
+    if (!(hdr->flags & MG_FLAG_DEGENERATE)) return;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        if (!is_degenerate(sc, f64_ratio)) continue;
+        float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
+        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
+        float av = alpha[g];
+        unsigned long long j1 = goff[g + 1];
+        if ((long long)j1 > rec.cap) j1 = rec.cap;
+        for (unsigned long long j = goff[g]; j < j1; ++j) {
+            const unsigned r = gmap[j];
+            if ((long long)r >= rec.cap) continue;
+            RecGeomT<double> o;
+            record_geometry<double>(mu, qv, sc, av, slices[rec.slice[r]], K2, o);
+            rec.geo[r] = make_float4((float)o.pcx, (float)o.pcy, (float)o.A, (float)o.B2);
+            rec.geo2[r] = make_float2((float)o.C, (float)o.amp);
+            rec.thr[r] = (float)o.thr;
         }
     }
 }
@@ -675,26 +779,38 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     unsigned *tile_cnt = (unsigned *)(ws + L.tile_cnt);
     unsigned *tile_off = (unsigned *)(ws + L.tile_off);
     unsigned *entries = (unsigned *)(ws + L.entries);
-    const int S = (int)L.S, NB = (int)L.NB;
+    const int S = (int)L.S;
     const float K2 = K * K;  // one FP32 multiply, rounded once (as in the predicate)
 
     cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
-    dim3 g1((unsigned)NB, (unsigned)((S + K1_SG - 1) / K1_SG));
+    unsigned *gcnt = (unsigned *)(ws + L.gcnt);
+    unsigned *bits = (unsigned *)(ws + L.bits);
+    unsigned *gmap = (unsigned *)(ws + L.gmap);
+    const long long NW = L.NW;
+    const unsigned g1 = (unsigned)L.NB;
     {
         MG_PROF(MG_ST_K1_COUNT, st);
-        k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, cnt, NB, hdr);
+        k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NW, gcnt, bits,
+                                       hdr);
     }
     {
         MG_PROF(MG_ST_SCAN_REC, st);
-        mg_launch_scan_u32(cnt, cnt, (long long)S * NB, nullptr, part, &hdr->n_records, st);
+        mg_launch_scan_u32(cnt, cnt, (long long)S * NW, nullptr, part, &hdr->n_records, st);
+        mg_launch_scan_u32(gcnt, gcnt, n, nullptr, part, &hdr->scan_total, st);
     }
     {
         MG_PROF(MG_ST_K1_EMIT, st);
-        k1_emit<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NB, rec);
+        k1_emit<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, bits, cnt, NW, gcnt,
+                                      rec, gmap);
+    }
+    if (f64_ratio > 0.f) {
+        MG_PROF(MG_ST_REC_GEOM, st);
+        int gg = (int)((n + 255) / 256 < 148 * 8 ? (n + 255) / 256 : 148 * 8);
+        k_rec_geom_f64<<<gg, 256, 0, st>>>(hdr, n, slices, mean, quat, scale, alpha, K2, f64_ratio, gcnt, gmap, rec);
     }
     {
         MG_PROF(MG_ST_CHUNKS, st);
-        k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, NB, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
+        k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, (int)NW, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
     }
     const int Tmax = (int)L.max_tiles;
     size_t smem = (size_t)BIN_WARPS * Tmax * sizeof(unsigned);

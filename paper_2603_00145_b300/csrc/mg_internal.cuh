@@ -17,6 +17,7 @@
 #define MG_FLAG_CAP_ENTRIES 2u
 #define MG_FLAG_CAP_CHUNKS 4u
 #define MG_FLAG_NOT_FINITE 8u
+#define MG_FLAG_DEGENERATE 16u  // some Gaussian takes the FP64 geometry
 
 // One slice as the kernels see it (built on the device from the stacks).
 struct SliceDev {
@@ -27,6 +28,7 @@ struct SliceDev {
     int W, H, TX, TY;
     int tile_base;  // global index of tile (0,0)
     int stack;
+    int same_frame;  // 1: rotation and profile bitwise equal to the previous slice's
     long long pix_base;  // offset of pixel (0,0) in the output
 };
 
@@ -84,8 +86,8 @@ struct Records {
 // size query.
 struct WsLayout {
     size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom, rec_thr;
-    size_t chunk_base, hist, tile_cnt, tile_off, entries, total;
-    long long S, NB, NG, SG, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
+    size_t chunk_base, hist, tile_cnt, tile_off, entries, gcnt, bits, gmap, rec_grad, total;
+    long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
 
 // -------------------------------------------------------------------------
@@ -124,6 +126,7 @@ enum MgStage {
     MG_ST_PAIRS,
     MG_ST_NRF_FWD,
     MG_ST_NRF_BWD,
+    MG_ST_REC_GEOM,
     MG_NSTAGES
 };
 void mg_prof_begin(int stage, cudaStream_t st);
@@ -147,5 +150,8 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
                           const float *grad_out, const float *mean, const float *quat, const float *scale,
                           const float *alpha, long long n, float f64_ratio, float *g_mean, float *g_quat,
                           float *g_scale, float *g_alpha, cudaStream_t st);
+// record geometry pass (one thread per record)
+void mg_launch_rec_geom(const WsLayout &L, char *ws, const SliceDev *slices, const float *mean, const float *quat,
+                        const float *scale, const float *alpha, float K, float f64_ratio, cudaStream_t st);
 void mg_launch_scan_u32(const unsigned *in, unsigned *out, long long n_host, const unsigned long long *n_dev,
                         unsigned long long *part, unsigned long long *total_out, cudaStream_t st);

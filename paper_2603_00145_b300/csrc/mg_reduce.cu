@@ -104,20 +104,26 @@ __global__ void __launch_bounds__(RED_NT) k_reduce_leaf(const float *__restrict_
     }
 }
 
+// one block: thread i adds partials i, i+256, ... in index order, then a
+// fixed shuffle tree; the same bits on every run
 template <int MODE>
-__global__ void k_reduce_final(const double *__restrict__ part, int nb, double inv_n, double *__restrict__ out)
+__global__ void __launch_bounds__(RED_NT) k_reduce_final(const double *__restrict__ part, int nb, double inv_n,
+                                                         double *__restrict__ out)
 {
-    if (threadIdx.x != 0) return;
     double s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i < nb; ++i) {
+    for (int i = threadIdx.x; i < nb; i += RED_NT) {
         s1 += part[2 * i];
         s2 += part[2 * i + 1];
     }
-    if (MODE == 0) {
-        out[0] = s1 * inv_n + s2 * inv_n;
-        out[1] = s2;
-    } else {
-        out[0] = s2;
+    double t1 = block_sum_d(s1);
+    double t2 = block_sum_d(s2);
+    if (threadIdx.x == 0) {
+        if (MODE == 0) {
+            out[0] = t1 * inv_n + t2 * inv_n;
+            out[1] = t2;
+        } else {
+            out[0] = t2;
+        }
     }
 }
 
@@ -127,14 +133,14 @@ void mg_launch_loss_l1l2(const float *pred, const float *target, long long n, fl
     int nb = mg_reduce_blocks(n);
     double inv_n = n > 0 ? 1.0 / (double)n : 0.0;
     k_reduce_leaf<0><<<nb, RED_NT, 0, st>>>(pred, target, n, grad, inv_n, part);
-    k_reduce_final<0><<<1, 32, 0, st>>>(part, nb, inv_n, out);
+    k_reduce_final<0><<<1, RED_NT, 0, st>>>(part, nb, inv_n, out);
 }
 
 void mg_launch_sq_diff(const float *a, const float *b, long long n, double *out, double *part, cudaStream_t st)
 {
     int nb = mg_reduce_blocks(n);
     k_reduce_leaf<1><<<nb, RED_NT, 0, st>>>(a, b, n, nullptr, 0.0, part);
-    k_reduce_final<1><<<1, 32, 0, st>>>(part, nb, 0.0, out);
+    k_reduce_final<1><<<1, RED_NT, 0, st>>>(part, nb, 0.0, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,7 +190,7 @@ extern "C" mg_status mg_loss_l1l2_noalloc(const float *pred, const float *target
     // every partial slot the final pass reads is written by the first pass,
     // so nothing left in the array by an earlier call is used
     k_reduce_leaf<0><<<nb, RED_NT, 0, st>>>(pred, target, n, grad, inv_n, part);
-    k_reduce_final<0><<<1, 32, 0, st>>>(part, nb, inv_n, loss_out);
+    k_reduce_final<0><<<1, RED_NT, 0, st>>>(part, nb, inv_n, loss_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return mg_set_error(MG_ERR_CUDA, cudaGetErrorString(e));
     return MG_OK;

@@ -44,6 +44,13 @@ __device__ __forceinline__ TileLoc locate_tile(const StackTable &tab, int t, int
     return L;
 }
 
+// K4: one warp per 16x16 tile. The two half-warps take alternate records of
+// the tile's list; lane c of a half-warp owns pixel column c of the tile (16
+// rows), so the per-record set-up is shared by 16 voxels. Records are staged
+// 32 at a time in shared memory (software-pipelined global loads) and read by
+// broadcast. Per (record, voxel pair): q from two packed FMAs, two ex2, one
+// packed FMA into the accumulators. At the end the half-warps exchange and
+// add their halves of the column (8 shuffles) and each writes 8 rows.
 __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                         const unsigned *__restrict__ entries, long long cap_entries,
                                                         long long cap_records, const float4 *__restrict__ geo,
@@ -54,15 +61,25 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * RW + w;
     if (t >= tab.n_tiles_total) return;  // whole warp
-    TileLoc L = locate_tile(tab, t, lane);
-    const float fpx = (float)L.px, fpy0 = (float)L.py0;
+    int s = 0;
+    while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
+    const int TX = tab.TX[s], T = TX * tab.TY[s];
+    const int local = t - tab.tile_base[s];
+    const int kk = local / T, within = local - kk * T;
+    const int ty = within / TX, tx = within - ty * TX;
+    const int W = tab.W[s], H = tab.H[s];
+    const long long pixbase = tab.pix_base[s] + (long long)kk * H * W;
+    const int half = lane >> 4, col = lane & 15;
+    const int px = tx * MG_TILE + col, py0 = ty * MG_TILE;
+    // rows are addressed relative to the tile's middle row (offsets +-7.5) to
+    // keep the terms of the expanded quadratic small
+    const float fpx = (float)px, fpyc = (float)py0 + 7.5f;
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 > e1) e0 = e1;
-    float acc[VPT];
+    float2 acc[MG_TILE / 2];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) acc[v] = 0.f;
-    // software pipeline: fetch the next chunk's records while evaluating
+    for (int v = 0; v < MG_TILE / 2; ++v) acc[v] = make_float2(0.f, 0.f);
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     if (e0 + lane < e1) {
@@ -76,7 +93,7 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
         sg[w][lane] = na;
         sg2[w][lane] = nb;
         __syncwarp();
-        unsigned nxt = base + 32 + lane;
+        const unsigned nxt = base + 32 + lane;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
         nb = make_float2(0.f, 0.f);
         if (nxt < e1) {
@@ -87,82 +104,86 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
             }
         }
         const int m = (int)min(32u, e1 - base);
-        for (int j = 0; j < m; ++j) {
-            const float4 a = sg[w][j];
-            const float2 b = sg2[w][j];
+        for (int j2 = 0; j2 < m; j2 += 2) {
+            const int j = j2 + half;  // this half-warp's record (zero record past the end)
+            float4 a = sg[w][j & 31];
+            float2 b = sg2[w][j & 31];
+            if (j >= m) b.y = 0.f;
             const float dx = fpx - a.x;
-            const float dy0 = fpy0 - a.y;
+            const float dyc = fpyc - a.y;
             const float C = b.x, amp = b.y;
-            const float cdy = C * dy0;
+            const float cdy = C * dyc;
             const float a1 = fmaf(a.w, dx, cdy + cdy);
-            const float a0 = fmaf(fmaf(a.z, dx, a.w * dy0), dx, cdy * dy0);
+            const float a0 = fmaf(fmaf(a.z, dx, a.w * dyc), dx, cdy * dyc);
+            const float2 C2 = make_float2(C, C), a12 = make_float2(a1, a1), a02 = make_float2(a0, a0);
+            const float2 amp2 = make_float2(amp, amp);
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const float q = fmaf(fmaf(C, (float)v, a1), (float)v, a0);
-                acc[v] = fmaf(amp, ex2_approx(q), acc[v]);
+            for (int p = 0; p < MG_TILE / 2; ++p) {
+                const float2 vp = make_float2((float)(2 * p) - 7.5f, (float)(2 * p + 1) - 7.5f);
+                const float2 q = __ffma2_rn(__ffma2_rn(C2, vp, a12), vp, a02);
+                const float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                acc[p] = __ffma2_rn(amp2, e, acc[p]);
             }
         }
         __syncwarp();
     }
-    if (L.px < L.W) {
+    // half 0 keeps rows 0..7 and half 1 rows 8..15 of the column
 #pragma unroll
-        for (int v = 0; v < VPT; ++v)
-            if (L.py0 + v < L.H) out[L.pixbase + (long long)(L.py0 + v) * L.W + L.px] = acc[v];
+    for (int p = 0; p < MG_TILE / 4; ++p) {
+        const float2 send = half ? acc[p] : acc[p + MG_TILE / 4];
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+        const float2 keep = half ? acc[p + MG_TILE / 4] : acc[p];
+        acc[p] = make_float2(keep.x + recv.x, keep.y + recv.y);
+    }
+    if (px < W) {
+        const int r0 = py0 + half * (MG_TILE / 2);
+#pragma unroll
+        for (int p = 0; p < MG_TILE / 4; ++p) {
+            if (r0 + 2 * p < H) out[pixbase + (long long)(r0 + 2 * p) * W + px] = acc[p].x;
+            if (r0 + 2 * p + 1 < H) out[pixbase + (long long)(r0 + 2 * p + 1) * W + px] = acc[p].y;
+        }
     }
 }
 
-// reduce-scatter of six per-lane values over the warp (8 shuffles); lanes
-// 0,4,8 hold the sums of v0,v1,v2 and lanes 16,20,24 those of v3,v4,v5.
-__device__ __forceinline__ float warp_reduce6(const float v[6], int lane, int &idx)
-{
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    float k[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        float send = b4 ? v[i] : v[3 + i];
-        float recv = __shfl_xor_sync(0xffffffffu, send, 16);
-        k[i] = (b4 ? v[3 + i] : v[i]) + recv;
-    }
-    float s0 = b3 ? k[0] : k[2];
-    float r0 = __shfl_xor_sync(0xffffffffu, s0, 8);
-    float s1 = b3 ? k[1] : 0.f;
-    float r1 = __shfl_xor_sync(0xffffffffu, s1, 8);
-    float m0 = (b3 ? k[2] : k[0]) + r0;
-    float m1 = b3 ? 0.f : (k[1] + r1);
-    float s2 = b2 ? m0 : m1;
-    float r2 = __shfl_xor_sync(0xffffffffu, s2, 4);
-    float n = (b2 ? m1 : m0) + r2;
-    n += __shfl_xor_sync(0xffffffffu, n, 2);
-    n += __shfl_xor_sync(0xffffffffu, n, 1);
-    int base = b4 ? 3 : 0;
-    idx = b3 ? (b2 ? -1 : base + 2) : base + (b2 ? 1 : 0);
-    if (lane & 3) idx = -1;
-    return n;
-}
-
+// K5, "one lane per record": lane l takes record l of the tile's next 32
+// entries and sweeps all 256 voxels of the tile, reading dL/dI from shared
+// memory by broadcast. Per voxel: q from two FMAs (quadratic in the column
+// offset), w = g 2^q, and three row sums (w, i w, i^2 w); per row the row
+// sums fold into six moment accumulators with the row offset. Moments are
+// taken about the tile centre and moved to the record centre at the end, so
+// no cross-lane reduction is needed; each lane then adds its record's six
+// moments with six atomics.
 __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                         const unsigned *__restrict__ entries, long long cap_entries,
                                                         long long cap_records, const float4 *__restrict__ geo,
                                                         const float2 *__restrict__ geo2,
                                                         const float *__restrict__ grad_out, float *__restrict__ mom)
 {
-    __shared__ float4 sg[RW][32];
-    __shared__ float2 sg2[RW][32];
-    __shared__ unsigned sr[RW][32];
+    __shared__ __align__(16) float sgv[RW][MG_TILE * MG_TILE];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * RW + w;
     if (t >= tab.n_tiles_total) return;
-    TileLoc L = locate_tile(tab, t, lane);
-    const float fpx = (float)L.px, fpy0 = (float)L.py0;
+    int s = 0;
+    while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
+    const int TX = tab.TX[s], T = TX * tab.TY[s];
+    const int local = t - tab.tile_base[s];
+    const int kk = local / T, within = local - kk * T;
+    const int ty = within / TX, tx = within - ty * TX;
+    const int W = tab.W[s], H = tab.H[s];
+    const long long pixbase = tab.pix_base[s] + (long long)kk * H * W;
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
-    if (e0 > e1) e0 = e1;
-    float gv[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v)
-        gv[v] = (L.px < L.W && L.py0 + v < L.H) ? grad_out[L.pixbase + (long long)(L.py0 + v) * L.W + L.px] : 0.f;
+    if (e0 >= e1) return;
+    for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
+        const int px = tx * MG_TILE + (i & 15), py = ty * MG_TILE + (i >> 4);
+        sgv[w][i] = (px < W && py < H) ? grad_out[pixbase + (long long)py * W + px] : 0.f;
+    }
+    __syncwarp();
+    const float x0c = (float)(tx * MG_TILE) + 7.5f, y0c = (float)(ty * MG_TILE) + 7.5f;
     for (unsigned base = e0; base < e1; base += 32) {
-        unsigned e = base + lane;
+        const unsigned e = base + lane;
         unsigned r = 0xffffffffu;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 b = make_float2(0.f, 0.f);
@@ -175,44 +196,56 @@ __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const un
                 r = 0xffffffffu;
             }
         }
-        sg[w][lane] = a;
-        sg2[w][lane] = b;
-        sr[w][lane] = r;
-        __syncwarp();
-        const int m = (int)min(32u, e1 - base);
-        for (int j = 0; j < m; ++j) {
-            const float4 aa = sg[w][j];
-            const float2 bb = sg2[w][j];
-            const float dx = fpx - aa.x;
-            const float dy0 = fpy0 - aa.y;
-            const float C = bb.x;
-            const float cdy = C * dy0;
-            const float a1 = fmaf(aa.w, dx, cdy + cdy);
-            const float a0 = fmaf(fmaf(aa.z, dx, aa.w * dy0), dx, cdy * dy0);
-            float W0 = 0.f, M1 = 0.f, M2 = 0.f;
+        const float A = a.z, B2 = a.w, C = b.x;
+        const float dxc = x0c - a.x;   // column offset of the tile centre from the record centre
+        const float dyc = y0c - a.y;   // row offset of the tile centre
+        const float A2x = 2.f * A * dxc, Ax = A * dxc;
+        const float2 A2 = make_float2(A, A);
+        float T0 = 0.f, T1 = 0.f, T2 = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
+        float jc = -7.5f;
+#pragma unroll 1
+        for (int j = 0; j < MG_TILE; ++j, jc += 1.f) {
+            const float dy = dyc + jc;
+            const float u = B2 * dy;
+            const float b1 = A2x + u;
+            const float b0 = fmaf(Ax + u, dxc, (C * dy) * dy);
+            const float4 *gr = (const float4 *)&sgv[w][j * MG_TILE];
+            // column pairs (i, i+1) with packed FP32x2 arithmetic
+            const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
+            float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const float q = fmaf(fmaf(C, (float)v, a1), (float)v, a0);
-                const float wv = gv[v] * ex2_approx(q);
-                const float jc = (float)v - 0.5f * (VPT - 1);
-                W0 += wv;
-                M1 = fmaf(jc, wv, M1);
-                M2 = fmaf(jc * jc, wv, M2);
+            for (int i4 = 0; i4 < 4; ++i4) {
+                const float4 g4 = gr[i4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float i0 = (float)(i4 * 4 + 2 * h) - 7.5f;
+                    const float2 ic = make_float2(i0, i0 + 1.f);
+                    const float2 ic2 = make_float2(i0 * i0, (i0 + 1.f) * (i0 + 1.f));
+                    const float2 gp = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
+                    const float2 q = __ffma2_rn(__ffma2_rn(A2, ic, b12), ic, b02);
+                    const float2 wv = __fmul2_rn(gp, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
+                    P0 = __fadd2_rn(P0, wv);
+                    P1 = __ffma2_rn(ic, wv, P1);
+                    P2 = __ffma2_rn(ic2, wv, P2);
+                }
             }
-            const float dyc = dy0 + 0.5f * (VPT - 1);
-            float mv[6];
-            mv[0] = W0;
-            mv[1] = dx * W0;
-            mv[2] = fmaf(dyc, W0, M1);
-            mv[3] = dx * mv[1];
-            mv[4] = dx * mv[2];
-            mv[5] = fmaf(dyc, fmaf(dyc, W0, M1 + M1), M2);
-            int idx;
-            float s = warp_reduce6(mv, lane, idx);
-            const unsigned rr = sr[w][j];
-            if (idx >= 0 && rr != 0xffffffffu) atomicAdd(&mom[(size_t)rr * 8 + idx], s);
+            const float R0 = P0.x + P0.y, R1 = P1.x + P1.y, R2 = P2.x + P2.y;
+            T0 += R0;
+            T1 += R1;
+            T2 += R2;
+            Y0 = fmaf(jc, R0, Y0);
+            Y1 = fmaf(jc, R1, Y1);
+            Y2 = fmaf(jc * jc, R0, Y2);
         }
-        __syncwarp();
+        if (r != 0xffffffffu) {
+            float *mr = mom + (size_t)r * 8;
+            atomicAdd(mr + 0, T0);
+            atomicAdd(mr + 1, fmaf(dxc, T0, T1));
+            atomicAdd(mr + 2, fmaf(dyc, T0, Y0));
+            atomicAdd(mr + 3, fmaf(dxc, fmaf(dxc, T0, T1 + T1), T2));
+            atomicAdd(mr + 4, fmaf(dxc, fmaf(dyc, T0, Y0), fmaf(dyc, T1, Y1)));
+            atomicAdd(mr + 5, fmaf(dyc, fmaf(dyc, T0, Y0 + Y0), Y2));
+        }
     }
 }
 
@@ -278,6 +311,21 @@ __device__ __forceinline__ double c_exp<double>(double x) { return exp(x); }
 // Adjoint of the record geometry: (centre, conic, amp) of the record of a
 // Gaussian on a slice, given dL/d(pcx, pcy, A, B2, C, amp).
 template <typename T>
+__device__ __forceinline__ T c_rcp(T x);
+template <>
+__device__ __forceinline__ float c_rcp<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double c_rcp<double>(double x) { return 1.0 / x; }
+template <typename T>
+__device__ __forceinline__ T c_rsqrt(T x);
+template <>
+__device__ __forceinline__ float c_rsqrt<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double c_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
+
+// Adjoint of the record geometry: (centre, conic, amp) of the record of a
+// Gaussian on a slice, given dL/d(pcx, pcy, A, B2, C, amp).
+template <typename T>
 __device__ void geometry_adjoint(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
                                  T gA, T gB2, T gC, T gpx, T gpy, T gamp, T gmu[3], T gq[4], T gs[3], T &galpha)
 {
@@ -294,17 +342,21 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     R[2][1] = 2 * (y * z + w * x);
     R[2][2] = 1 - 2 * (x * x + y * y);
     T sc[3] = {s[0], s[1], s[2]};
+    T isc[3] = {c_rcp<T>(sc[0]), c_rcp<T>(sc[1]), c_rcp<T>(sc[2])};
+    T Q[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Q[i] = (T)S.Q[i];
     T P[3][3], g[3][3], Lm[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            P[a][c] = (T)S.Q[a] * R[0][c] + (T)S.Q[3 + a] * R[1][c] + (T)S.Q[6 + a] * R[2][c];
-            g[a][c] = P[a][c] / sc[c];
+            P[a][c] = Q[a] * R[0][c] + Q[3 + a] * R[1][c] + Q[6 + a] * R[2][c];
+            g[a][c] = P[a][c] * isc[c];
             Lm[a][c] = P[a][c] * sc[c];
         }
     T p0 = (T)mu[0] - (T)S.t[0], p1 = (T)mu[1] - (T)S.t[1], p2 = (T)mu[2] - (T)S.t[2];
-    T w0 = (T)S.Q[2] * p0 + (T)S.Q[5] * p1 + (T)S.Q[8] * p2;
+    T w0 = Q[2] * p0 + Q[5] * p1 + Q[8] * p2;
     T Huw = g[0][0] * g[2][0] + g[0][1] * g[2][1] + g[0][2] * g[2][2];
     T Hvw = g[1][0] * g[2][0] + g[1][1] * g[2][1] + g[1][2] * g[2][2];
     T Hww = g[2][0] * g[2][0] + g[2][1] * g[2][1] + g[2][2] * g[2][2];
@@ -312,10 +364,13 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     T Svw = Lm[1][0] * Lm[2][0] + Lm[1][1] * Lm[2][1] + Lm[1][2] * Lm[2][2];
     T sig2 = (T)S.sig2;
     T Sww = Lm[2][0] * Lm[2][0] + Lm[2][1] * Lm[2][1] + Lm[2][2] * Lm[2][2] + sig2;
+    T iSww = c_rcp<T>(Sww);
     T D = 1 + sig2 * Hww;
-    T f = sig2 / D;
-    T rD = (T)1 / sqrt(D);
-    T E = c_exp<T>((T)(-0.5) * w0 * w0 / Sww);
+    T rD = c_rsqrt<T>(D);
+    T iD = rD * rD;
+    T f = sig2 * iD;
+    T wS = w0 * iSww;
+    T E = c_exp<T>((T)(-0.5) * w0 * wS);
     T amp = (T)alpha * rD * E;
     const T kap = (T)(-0.72134752044448170368);
     T dx = S.dx, dy = S.dy;
@@ -323,27 +378,24 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     T gKuu = gA * kap * dx * dx;
     T gKuv = gB2 * 2 * kap * dx * dy;
     T gKvv = gC * kap * dy * dy;
-    T gcu = gpx / dx, gcv = gpy / dy;
+    T gcu = gpx * c_rcp<T>(dx), gcv = gpy * c_rcp<T>(dy);
     galpha = gamp * rD * E;
-    T gD = gamp * amp * (T)(-0.5) / D;
-    T gw0 = -gamp * amp * w0 / Sww;
-    T gSww = gamp * amp * (T)0.5 * w0 * w0 / (Sww * Sww);
+    T ga = gamp * amp;
+    T gD = (T)(-0.5) * ga * iD;
+    T gw0 = -ga * wS;
+    T gSww = (T)0.5 * ga * wS * wS;
     T gdu = gcu, gdv = gcv;
-    T gSuw = -gcu * w0 / Sww;
-    T gSvw = -gcv * w0 / Sww;
+    T gSuw = -gcu * wS;
+    T gSvw = -gcv * wS;
     T cs = gcu * Suw + gcv * Svw;
-    gw0 -= cs / Sww;
-    gSww += cs * w0 / (Sww * Sww);
+    gw0 -= cs * iSww;
+    gSww += cs * wS * iSww;
     T gHuu = gKuu, gHvv = gKvv, gHuv = gKuv;
     T gHuw = -f * (2 * gKuu * Huw + gKuv * Hvw);
     T gHvw = -f * (2 * gKvv * Hvw + gKuv * Huw);
-    gD += sig2 / (D * D) * (gKuu * Huw * Huw + gKuv * Huw * Hvw + gKvv * Hvw * Hvw);
+    gD += f * iD * (gKuu * Huw * Huw + gKuv * Huw * Hvw + gKvv * Hvw * Hvw);
     T gHww = sig2 * gD;
     T gR[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gR[r][c] = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         T gg0 = 2 * gHuu * g[0][c] + gHuv * g[1][c] + gHuw * g[2][c];
@@ -352,16 +404,16 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
         T gL0 = gSuw * Lm[2][c];
         T gL1 = gSvw * Lm[2][c];
         T gL2 = gSuw * Lm[0][c] + gSvw * Lm[1][c] + 2 * gSww * Lm[2][c];
-        T gP0 = gg0 / sc[c] + gL0 * sc[c];
-        T gP1 = gg1 / sc[c] + gL1 * sc[c];
-        T gP2 = gg2 / sc[c] + gL2 * sc[c];
-        gs[c] = -(gg0 * P[0][c] + gg1 * P[1][c] + gg2 * P[2][c]) / (sc[c] * sc[c]) +
+        T gP0 = gg0 * isc[c] + gL0 * sc[c];
+        T gP1 = gg1 * isc[c] + gL1 * sc[c];
+        T gP2 = gg2 * isc[c] + gL2 * sc[c];
+        gs[c] = -(gg0 * g[0][c] + gg1 * g[1][c] + gg2 * g[2][c]) * isc[c] +
                 (gL0 * P[0][c] + gL1 * P[1][c] + gL2 * P[2][c]);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) gR[r][c] = (T)S.Q[3 * r] * gP0 + (T)S.Q[3 * r + 1] * gP1 + (T)S.Q[3 * r + 2] * gP2;
+        for (int r = 0; r < 3; ++r) gR[r][c] = Q[3 * r] * gP0 + Q[3 * r + 1] * gP1 + Q[3 * r + 2] * gP2;
     }
 #pragma unroll
-    for (int r = 0; r < 3; ++r) gmu[r] = (T)S.Q[3 * r] * gdu + (T)S.Q[3 * r + 1] * gdv + (T)S.Q[3 * r + 2] * gw0;
+    for (int r = 0; r < 3; ++r) gmu[r] = Q[3 * r] * gdu + Q[3 * r + 1] * gdv + Q[3 * r + 2] * gw0;
     gq[0] = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
     gq[1] = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] +
                  w * gR[2][1] - 2 * x * gR[2][2]);
@@ -380,17 +432,32 @@ __global__ void k_zero_mom(float4 *mom, const WsHeader *hdr, long long cap_recor
         mom[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void k_chain(const WsHeader *hdr, long long cap_records, const float4 *__restrict__ geo,
-                        const float2 *__restrict__ geo2, const int *__restrict__ gid, const int *__restrict__ rslice,
-                        const float *__restrict__ mom, const SliceDev *__restrict__ slices, const float *mean,
-                        const float *quat, const float *scale, const float *alpha, float f64_ratio, float *g_mean,
-                        float *g_quat, float *g_scale, float *g_alpha)
+// K6a: one thread per record: moments -> dL/d(centre, conic, amp) -> adjoint
+// of the record geometry -> the record's share of dL/d(mean, quat, scale,
+// alpha), written to its own 12-float slot (FP32 geometry; DBL: only the
+// records of near-degenerate Gaussians, in FP64)
+template <bool DBL>
+__global__ void k_chain_rec(const WsHeader *hdr, long long cap_records, const float4 *__restrict__ geo,
+                            const float2 *__restrict__ geo2, const int *__restrict__ gid,
+                            const int *__restrict__ rslice, const float *__restrict__ mom,
+                            const SliceDev *__restrict__ slices, const float *__restrict__ mean,
+                            const float *__restrict__ quat, const float *__restrict__ scale,
+                            const float *__restrict__ alpha, float f64_ratio, float4 *__restrict__ rg)
 {
-    long long n = (long long)hdr->n_records;
-    if (n > cap_records) n = cap_records;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        const float4 m0 = *(const float4 *)(mom + r * 8);
-        const float2 m1 = *(const float2 *)(mom + r * 8 + 4);
+    if (DBL && !(hdr->flags & MG_FLAG_DEGENERATE)) return;
+    long long nr = (long long)hdr->n_records;
+    if (nr > cap_records) nr = cap_records;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
+        const long long g = gid[r];
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        float mx = fmaxf(fmaxf(sc[0], sc[1]), sc[2]), mn = fminf(fminf(sc[0], sc[1]), sc[2]);
+        const bool dbl = f64_ratio > 0.f && mx > f64_ratio * mn;
+        if (dbl != DBL) continue;  // the other instance handles this record
+        float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
+        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
+        float al = alpha[g];
+        const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
+        const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
         const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
         const float4 a = geo[r];
         const float2 b = geo2[r];
@@ -399,43 +466,61 @@ __global__ void k_chain(const WsHeader *hdr, long long cap_records, const float4
         const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
         const float gpx = -la * (2.f * A * Sx + B2 * Sy);
         const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
-        const float gamp = S0;
-        const long long g = gid[r];
-        const SliceDev Sd = slices[rslice[r]];
-        float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
-        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
-        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
-        float al = alpha[g];
-        float mx = fmaxf(fmaxf(sc[0], sc[1]), sc[2]), mn = fminf(fminf(sc[0], sc[1]), sc[2]);
-        float gm[3], gq[4], gs[3], ga;
-        if (f64_ratio > 0.f && mx > f64_ratio * mn) {
+        const SliceDev &Sd = slices[rslice[r]];
+        float o[12];
+        if (DBL) {
             double dm[3], dq[4], ds[3], da;
-            geometry_adjoint<double>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, gamp, dm, dq, ds, da);
-            for (int i = 0; i < 3; ++i) gm[i] = (float)dm[i], gs[i] = (float)ds[i];
-            for (int i = 0; i < 4; ++i) gq[i] = (float)dq[i];
-            ga = (float)da;
+            geometry_adjoint<double>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, dm, dq, ds, da);
+            for (int i = 0; i < 3; ++i) o[i] = (float)dm[i], o[7 + i] = (float)ds[i];
+            for (int i = 0; i < 4; ++i) o[3 + i] = (float)dq[i];
+            o[10] = (float)da;
         } else {
-            geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, gamp, gm, gq, gs, ga);
+            float gm[3], gq[4], gs[3], ga;
+            geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga);
+            for (int i = 0; i < 3; ++i) o[i] = gm[i], o[7 + i] = gs[i];
+            for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
+            o[10] = ga;
+        }
+        o[11] = 0.f;
+        rg[3 * r] = make_float4(o[0], o[1], o[2], o[3]);
+        rg[3 * r + 1] = make_float4(o[4], o[5], o[6], o[7]);
+        rg[3 * r + 2] = make_float4(o[8], o[9], o[10], o[11]);
+    }
+}
+
+// K6b: one thread per Gaussian sums its records' shares in slice order (fixed
+// order, no atomics) and writes every gradient once
+__global__ void k_chain_sum(long long n, const unsigned *__restrict__ goff, const unsigned *__restrict__ gmap,
+                            long long cap_records, const float4 *__restrict__ rg, const float *__restrict__ quat,
+                            float *g_mean, float *g_quat, float *g_scale, float *g_alpha)
+{
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        unsigned long long j0 = goff[g], j1 = goff[g + 1];
+        if ((long long)j1 > cap_records) j1 = cap_records;
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
+        for (unsigned long long j = j0; j < j1; ++j) {
+            const unsigned r = gmap[j];
+            if ((long long)r >= cap_records) continue;
+            const float4 a = rg[3 * (size_t)r], b = rg[3 * (size_t)r + 1], c = rg[3 * (size_t)r + 2];
+            s0.x += a.x, s0.y += a.y, s0.z += a.z, s0.w += a.w;
+            s1.x += b.x, s1.y += b.y, s1.z += b.z, s1.w += b.w;
+            s2.x += c.x, s2.y += c.y, s2.z += c.z;
         }
         // gradient on the unit sphere: drop the component along q (the
         // normalisation q = q_raw/|q_raw| removes it, and the rotation formula
         // is only a rotation for unit q)
-        {
-            float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-            float rad = (gq[0] * qv[0] + gq[1] * qv[1] + gq[2] * qv[2] + gq[3] * qv[3]) / qq;
-            for (int i = 0; i < 4; ++i) gq[i] -= rad * qv[i];
-        }
-        atomicAdd(&g_mean[3 * g], gm[0]);
-        atomicAdd(&g_mean[3 * g + 1], gm[1]);
-        atomicAdd(&g_mean[3 * g + 2], gm[2]);
-        atomicAdd(&g_quat[4 * g], gq[0]);
-        atomicAdd(&g_quat[4 * g + 1], gq[1]);
-        atomicAdd(&g_quat[4 * g + 2], gq[2]);
-        atomicAdd(&g_quat[4 * g + 3], gq[3]);
-        atomicAdd(&g_scale[3 * g], gs[0]);
-        atomicAdd(&g_scale[3 * g + 1], gs[1]);
-        atomicAdd(&g_scale[3 * g + 2], gs[2]);
-        atomicAdd(&g_alpha[g], ga);
+        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
+        float aq[4] = {s0.w, s1.x, s1.y, s1.z};
+        float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+        float rad = qq > 0.f ? (aq[0] * qv[0] + aq[1] * qv[1] + aq[2] * qv[2] + aq[3] * qv[3]) / qq : 0.f;
+        g_mean[3 * g] = s0.x;
+        g_mean[3 * g + 1] = s0.y;
+        g_mean[3 * g + 2] = s0.z;
+        for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = aq[i] - rad * qv[i];
+        g_scale[3 * g] = s1.w;
+        g_scale[3 * g + 1] = s2.x;
+        g_scale[3 * g + 2] = s2.y;
+        g_alpha[g] = s2.z;
     }
 }
 
@@ -470,10 +555,6 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
                           float *g_scale, float *g_alpha, cudaStream_t st)
 {
     const WsHeader *hdr = (const WsHeader *)(ws + L.hdr);
-    cudaMemsetAsync(g_mean, 0, sizeof(float) * 3 * n, st);
-    cudaMemsetAsync(g_quat, 0, sizeof(float) * 4 * n, st);
-    cudaMemsetAsync(g_scale, 0, sizeof(float) * 3 * n, st);
-    cudaMemsetAsync(g_alpha, 0, sizeof(float) * n, st);
     long long capv = L.cap_records * 2;
     int gz = (int)((capv + 255) / 256 < 148 * 16 ? (capv + 255) / 256 : 148 * 16);
     if (gz < 1) gz = 1;
@@ -490,11 +571,21 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), grad_out,
                 (float *)(ws + L.rec_mom));
     }
-    int gc = (int)((L.cap_records + 255) / 256 < 148 * 16 ? (L.cap_records + 255) / 256 : 148 * 16);
-    if (gc < 1) gc = 1;
     MG_PROF(MG_ST_CHAIN, st);
-    k_chain<<<gc, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2),
-                                (const int *)(ws + L.rec_gid), (const int *)(ws + L.rec_slice),
-                                (const float *)(ws + L.rec_mom), slices, mean, quat, scale, alpha, f64_ratio, g_mean,
-                                g_quat, g_scale, g_alpha);
+    float4 *rg = (float4 *)(ws + L.rec_grad);
+    long long wr = (L.cap_records + 255) / 256;
+    int gr = (int)(wr < 148 * 16 ? (wr > 0 ? wr : 1) : 148 * 16);
+    k_chain_rec<false><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
+                                           (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
+                                           (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom), slices,
+                                           mean, quat, scale, alpha, f64_ratio, rg);
+    if (f64_ratio > 0.f)
+        k_chain_rec<true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
+                                              (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
+                                              (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
+                                              slices, mean, quat, scale, alpha, f64_ratio, rg);
+    int gc = (int)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
+    if (gc < 1) gc = 1;
+    k_chain_sum<<<gc, 256, 0, st>>>(n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
+                                    L.cap_records, rg, quat, g_mean, g_quat, g_scale, g_alpha);
 }

@@ -8,7 +8,8 @@ tile rectangle of the cut ellipse) against brute force in FP64.
   of the cut ellipse, found here by an eigen-decomposition of the in-plane
   quadratic form (a different route from the Schur complement the predicate
   uses), up to an FP32 margin;
-* existence: a record exists exactly when that FP64 rectangle meets the image.
+* existence: a record exists exactly when the K-sigma slab test passes; its
+  tile rectangle is empty when the cut ellipse misses the image.
 """
 import numpy as np
 import pytest
@@ -60,6 +61,10 @@ def _fp64_tile_rect(A, b, c, K, st, margin_px):
 
 
 def _contains(outer, inner):
+    if inner is not None and (inner[0] > inner[2] or inner[1] > inner[3]):
+        inner = None  # a record whose pixel box is empty lists no tile
+    if outer is not None and (outer[0] > outer[2] or outer[1] > outer[3]):
+        outer = None
     if inner is None:
         return True
     if outer is None:
@@ -99,6 +104,13 @@ def test_records_vs_brute_force(seed, K):
                     jin, iin = np.nonzero(inside)
                     tx, ty = iin // TILE, jin // TILE
                     assert got[0] <= tx.min() and got[2] >= tx.max() and got[1] <= ty.min() and got[3] >= ty.max()
+                # slab test in FP64: w0^2 / Sww vs K^2 (margin for FP32 rounding)
+                q_min = c - b @ np.linalg.solve(A, b)  # min over the plane of q
+                # q_min is w0^2/Sww (the plane minimum of the convolved form)
+                if q_min < K * K * (1 - 1e-5):
+                    assert got is not None, ("slab record missing", k, g)
+                elif q_min > K * K * (1 + 1e-5):
+                    assert got is None, ("record outside the slab", k, g)
                 lo = _fp64_tile_rect(A, b, c, K * (1 - 1e-5), st, -1e-3)
                 hi = _fp64_tile_rect(A, b, c, K * (1 + 1e-5), st, 1e-3)
                 assert _contains(got, lo), (k, g, got, lo)
