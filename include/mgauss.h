@@ -258,6 +258,46 @@ int mg_profile_stage_count(void);
 const char *mg_profile_stage_name(int stage);
 mg_status mg_profile_read(double *ms, int64_t *calls, int reset);
 
+/*
+ * Neural residual field (Sec. 3.4, Eq. E8): r(x) = out_scale * tanh(MLP(enc(x)))
+ * for coordinates x in the canonical cube [-1,1]^3, added to the Gaussian
+ * intensity (I_final = I + r). Two encodings:
+ *   MG_NRF_FOURIER (the paper's): enc(x) = [x, sin(2^j pi x), cos(2^j pi x)],
+ *     j = 0..5 (per band: sin of x0,x1,x2 then cos of x0,x1,x2; 39 features),
+ *     4 hidden layers of 64 SiLU units;
+ *   MG_NRF_GRID: 16-level multiresolution hash grid, 2 features per level
+ *     (resolution floor(n_min * b^l), b = exp((ln n_max - ln n_min)/15);
+ *     p = clamp((x+1)/2, 0, 1); cell min(floor(p N), N-1); corners looked up
+ *     densely when (N+1)^3 <= 2^log2_table, else by the spatial hash
+ *     (x * 1) ^ (y * 2654435761) ^ (z * 805459861) mod 2^log2_table;
+ *     trilinear weights), 2 hidden layers of 64 ReLU units.
+ * Precision MG_NRF_BF16: weights and activations rounded to BF16, hidden
+ * layers on the tensor cores (mma.sync BF16, FP32 accumulation);
+ * MG_NRF_FP32: FP32 throughout (SIMT).
+ * params (device, FP32): for each hidden layer W[64][in] row-major then
+ * b[64]; then w_out[64], b_out (mg_nrf_param_count floats).
+ */
+typedef enum { MG_NRF_FOURIER = 0, MG_NRF_GRID = 1 } mg_nrf_encoding;
+typedef enum { MG_NRF_BF16 = 0, MG_NRF_FP32 = 1 } mg_nrf_precision;
+typedef struct {
+    int32_t encoding;   /* mg_nrf_encoding */
+    int32_t precision;  /* mg_nrf_precision */
+    const float *params;
+    const float *table; /* MG_NRF_GRID: device FP32 [16][2^log2_table][2]; else unused */
+    int32_t log2_table, n_min, n_max; /* MG_NRF_GRID geometry; 0 = 19, 16, 512 */
+    float out_scale;    /* bound of |r|; the paper's 0.1 */
+} mg_nrf;
+
+/* Number of FP32 parameters of an encoding's MLP (-1 for an unknown one). */
+int64_t mg_nrf_param_count(int32_t encoding);
+/* out[i] = r(xyz[i]) for n points (device xyz [n,3], out [n]). */
+mg_status mg_nrf_fwd(const mg_nrf *net, const float *xyz, int64_t n, float *out, mg_stream_t stream);
+/* Gradients of sum_i grad_out[i] r(xyz[i]): g_params (device, param_count
+ * floats) and, for MG_NRF_GRID, g_table (device, same shape as table) are
+ * overwritten. Accumulated with atomics (FP32 summation order varies). */
+mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float *grad_out, float *g_params,
+                     float *g_table, mg_stream_t stream);
+
 const char *mg_status_string(mg_status s);
 const char *mg_last_error(void);
 /* Library version string. */

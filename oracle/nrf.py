@@ -147,10 +147,14 @@ def encode(P: NRFParams, x):
     return fourier_encode(x) if P.preset == "paper" else grid_encode(x, P.table, P.spec)
 
 
-def forward(P: NRFParams, x, return_cache: bool = False):
-    """r(x) = out_scale * tanh(MLP(enc(x))) in FP64. Returns [n]."""
+def forward(P: NRFParams, x, return_cache: bool = False, round_fn=None):
+    """r(x) = out_scale * tanh(MLP(enc(x))) in FP64. Returns [n].
+    ``round_fn`` (optional) is applied to the encoding and to every hidden
+    activation, to model a lower-precision storage of activations."""
     act, _ = _act(P.preset)
     h = encode(P, x)
+    if round_fn is not None:
+        h = round_fn(h)
     cache = [h]
     zs = []
     nl = len(P.weights)
@@ -160,6 +164,8 @@ def forward(P: NRFParams, x, return_cache: bool = False):
         z = h @ W.T + b
         zs.append(z)
         h = act(z) if l < nl - 1 else z
+        if round_fn is not None and l < nl - 1:
+            h = round_fn(h)
         cache.append(h)
     y = P.out_scale * np.tanh(h[:, 0])
     if return_cache:

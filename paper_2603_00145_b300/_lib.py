@@ -36,6 +36,14 @@ class MgWsLayout(ctypes.Structure):
                 ("tile_off", ctypes.c_uint64), ("entries", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
 
 
+class MgNrf(ctypes.Structure):
+    _fields_ = [("encoding", c_i32), ("precision", c_i32), ("params", c_p), ("table", c_p), ("log2_table", c_i32),
+                ("n_min", c_i32), ("n_max", c_i32), ("out_scale", c_f32)]
+
+
+MG_NRF_FOURIER, MG_NRF_GRID = 0, 1
+MG_NRF_BF16, MG_NRF_FP32 = 0, 1
+
 MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_CAPACITY, MG_ERR_DEVICE_TIMEOUT, MG_ERR_NOT_FINITE, \
     MG_ERR_STALE_WORKSPACE = range(7)
 
@@ -61,6 +69,9 @@ SIGNATURES = {
     "mg_sq_diff_sum": (ctypes.c_int, [c_p, c_p, c_i64, c_p, c_p, c_sz, c_p]),
     "mg_render_pair_count": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                             ctypes.POINTER(MgOpts), c_p, c_sz, ctypes.POINTER(c_i64), c_p]),
+    "mg_nrf_param_count": (c_i64, [c_i32]),
+    "mg_nrf_fwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p]),
+    "mg_nrf_bwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p, c_p, c_p]),
     "mg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mg_profile_stage_count": (ctypes.c_int, []),
     "mg_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),

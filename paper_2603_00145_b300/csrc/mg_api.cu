@@ -561,6 +561,77 @@ mg_status mg_render_pair_count(const mg_gaussians *g, const mg_stack *stacks, in
     return MG_OK;
 }
 
+int64_t mg_nrf_param_count(int32_t encoding) { return mg_nrf_param_count_impl(encoding); }
+
+static bool valid_nrf(const mg_nrf *net, std::string &why)
+{
+    if (!net) {
+        why = "net is NULL";
+        return false;
+    }
+    if (net->encoding != MG_NRF_FOURIER && net->encoding != MG_NRF_GRID) {
+        why = "unknown encoding";
+        return false;
+    }
+    if (net->precision != MG_NRF_BF16 && net->precision != MG_NRF_FP32) {
+        why = "unknown precision";
+        return false;
+    }
+    if (!net->params) {
+        why = "params is NULL";
+        return false;
+    }
+    if (net->encoding == MG_NRF_GRID) {
+        if (!net->table) {
+            why = "grid encoding needs a table";
+            return false;
+        }
+        if (net->log2_table < 0 || net->log2_table > 24 || net->n_min < 0 || net->n_max < 0 ||
+            (net->n_min > 0 && net->n_max > 0 && net->n_max < net->n_min)) {
+            why = "bad grid geometry";
+            return false;
+        }
+    }
+    if (!(net->out_scale > 0.f) || !isfinite(net->out_scale)) {
+        why = "out_scale must be positive";
+        return false;
+    }
+    return true;
+}
+
+mg_status mg_nrf_fwd(const mg_nrf *net, const float *xyz, int64_t n, float *out, mg_stream_t stream)
+{
+    std::string why;
+    if (!valid_nrf(net, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (n < 0 || (n > 0 && (!xyz || !out))) return fail(MG_ERR_INVALID_ARG, "bad xyz/out or n");
+    if (n == 0) return MG_OK;
+    MG_PROF(MG_ST_NRF_FWD, (cudaStream_t)stream);
+    cudaError_t e = mg_launch_nrf(net, xyz, n, nullptr, out, nullptr, nullptr, false, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("mg_nrf_fwd: ") + cudaGetErrorString(e));
+    return MG_OK;
+}
+
+mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float *grad_out, float *g_params,
+                     float *g_table, mg_stream_t stream)
+{
+    std::string why;
+    if (!valid_nrf(net, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (n < 0 || (n > 0 && (!xyz || !grad_out)) || !g_params) return fail(MG_ERR_INVALID_ARG, "bad pointers or n");
+    if (net->encoding == MG_NRF_GRID && !g_table) return fail(MG_ERR_INVALID_ARG, "grid encoding needs g_table");
+    cudaStream_t st = (cudaStream_t)stream;
+    MG_PROF(MG_ST_NRF_BWD, st);
+    cudaMemsetAsync(g_params, 0, sizeof(float) * (size_t)mg_nrf_param_count_impl(net->encoding), st);
+    if (net->encoding == MG_NRF_GRID) {
+        int lt = net->log2_table > 0 ? net->log2_table : 19;
+        cudaMemsetAsync(g_table, 0, sizeof(float) * 2 * 16 * ((size_t)1 << lt), st);
+    }
+    if (n > 0) {
+        cudaError_t e = mg_launch_nrf(net, xyz, n, grad_out, nullptr, g_params, g_table, true, st);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("mg_nrf_bwd: ") + cudaGetErrorString(e));
+    }
+    return check_cuda("mg_nrf_bwd");
+}
+
 mg_status mg_profile_enable(int on)
 {
     prof::on.store(on != 0);

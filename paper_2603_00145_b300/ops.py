@@ -343,3 +343,88 @@ class VolumeSampler:
             self.caps = (max(self.caps[0], int(st["records"] * 1.25) + 1),
                          max(self.caps[1], int(st["entries"] * 1.25) + 1))
         raise L.MgError(L.MG_ERR_CAPACITY, "mg_sample_volume (after growing the workspace)")
+
+
+# ---------------------------------------------------------------------------
+# neural residual field
+# ---------------------------------------------------------------------------
+ENCODINGS = {"paper": L.MG_NRF_FOURIER, "grid": L.MG_NRF_GRID}
+PRECISIONS = {"bf16": L.MG_NRF_BF16, "fp32": L.MG_NRF_FP32}
+
+
+def mg_nrf_param_count(encoding: str) -> int:
+    return int(L.lib().mg_nrf_param_count(ENCODINGS[encoding]))
+
+
+class NRF:
+    """Device parameters of a neural residual field (FP32 master copies) and
+    the C-ABI calls on them. ``encoding``: "paper" (Fourier, 4 x 64 SiLU) or
+    "grid" (hash grid, 2 x 64 ReLU); ``precision``: "bf16" or "fp32"."""
+
+    def __init__(self, encoding: str, precision: str, weights, biases, table=None, device="cuda",
+                 log2_table: int = 19, n_min: int = 16, n_max: int = 512, out_scale: float = 0.1):
+        self.encoding, self.precision = encoding, precision
+        flat = []
+        for W, b in zip(weights, biases):
+            flat.append(torch.as_tensor(W, dtype=_F32).reshape(-1))
+            flat.append(torch.as_tensor(b, dtype=_F32).reshape(-1))
+        self.params = torch.cat(flat).to(device).contiguous()
+        if self.params.numel() != mg_nrf_param_count(encoding):
+            raise ValueError(f"{encoding}: {self.params.numel()} parameters, expected {mg_nrf_param_count(encoding)}")
+        self.table = None
+        if encoding == "grid":
+            self.table = torch.as_tensor(table, dtype=_F32).to(device).contiguous()
+            if self.table.numel() != 16 * 2 * (1 << log2_table):
+                raise ValueError("table must be [16, 2^log2_table, 2]")
+        self.log2_table, self.n_min, self.n_max, self.out_scale = log2_table, n_min, n_max, out_scale
+
+    def struct(self, params=None, table=None) -> L.MgNrf:
+        p = self.params if params is None else params
+        t = self.table if table is None else table
+        return L.MgNrf(ENCODINGS[self.encoding], PRECISIONS[self.precision], _dev(p, "params"),
+                       _dev(t, "table") if t is not None else None, self.log2_table, self.n_min, self.n_max,
+                       float(self.out_scale))
+
+
+def mg_nrf_fwd(net: NRF, xyz, out, params=None, table=None, stream=None):
+    n = xyz.numel() // 3
+    _dev(xyz, "xyz", numel=3 * n)
+    _dev(out, "out", numel=n)
+    s = net.struct(params, table)
+    L.check(L.lib().mg_nrf_fwd(ctypes.byref(s), xyz.data_ptr(), n, out.data_ptr(), _stream_handle(stream)),
+            "mg_nrf_fwd")
+
+
+def mg_nrf_bwd(net: NRF, xyz, grad_out, g_params, g_table=None, params=None, table=None, stream=None):
+    n = xyz.numel() // 3
+    _dev(xyz, "xyz", numel=3 * n)
+    _dev(grad_out, "grad_out", numel=n)
+    gp = _dev(g_params, "g_params", numel=mg_nrf_param_count(net.encoding))
+    gt = _dev(g_table, "g_table") if g_table is not None else None
+    s = net.struct(params, table)
+    L.check(L.lib().mg_nrf_bwd(ctypes.byref(s), xyz.data_ptr(), n, grad_out.data_ptr(), gp, gt,
+                               _stream_handle(stream)), "mg_nrf_bwd")
+
+
+class NRFFunction(torch.autograd.Function):
+    """r = NRF(xyz) with gradients for the parameter vector (and grid table)."""
+
+    @staticmethod
+    def forward(ctx, net: NRF, xyz, params, table):
+        xyz = xyz.detach().contiguous()
+        out = torch.empty(xyz.numel() // 3, dtype=_F32, device=xyz.device)
+        mg_nrf_fwd(net, xyz, out, params.detach(), None if table is None else table.detach())
+        ctx.net = net
+        ctx.save_for_backward(xyz, params, table if table is not None else torch.empty(0, device=xyz.device))
+        ctx.has_table = table is not None
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        xyz, params, table = ctx.saved_tensors
+        table = table if ctx.has_table else None
+        gp = torch.empty_like(params)
+        gt = torch.empty_like(table) if table is not None else None
+        mg_nrf_bwd(ctx.net, xyz, grad_out.contiguous(), gp, gt, params.detach(),
+                   None if table is None else table.detach())
+        return None, None, gp, gt
