@@ -36,7 +36,7 @@ thread_local cudaEvent_t open_ev[MG_NSTAGES];
 const char *names[MG_NSTAGES] = {"slices",      "k1_count",   "scan_records", "k1_emit",    "chunks",
                                  "bin_hist",    "bin_colscan", "scan_tiles",   "bin_scatter", "render_fwd",
                                  "zero_moments", "render_bwd", "chain",        "loss",       "pair_count",
-                                 "nrf_fwd",     "nrf_bwd",     "rec_geom"};
+                                 "nrf_fwd",     "nrf_bwd",     "rec_geom",   "rec_fill"};
 
 cudaEvent_t get_event()
 {

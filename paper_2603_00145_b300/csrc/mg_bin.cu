@@ -499,25 +499,13 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
     if (g < n) gcnt[g] = mine;
 }
 
-__global__ void __launch_bounds__(K1_NT) k1_emit(const SliceDev *__restrict__ slices, int S, const float *mean,
-                                                 const float *quat, const float *scale, const float *alpha,
-                                                 long long n, float K2, float f64_ratio,
-                                                 const unsigned *__restrict__ bits, const unsigned *__restrict__ off,
-                                                 long long NW, const unsigned *__restrict__ goff, Records rec,
-                                                 unsigned *gmap)
+__global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsigned *__restrict__ bits,
+                                                 const unsigned *__restrict__ off, long long NW,
+                                                 const unsigned *__restrict__ goff, Records rec, unsigned *gmap)
 {
     const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
     const long long wg = g >> 5;
-    GaussPred G;
-    bool valid = false, degen = false;
-    float qv[4] = {1.f, 0.f, 0.f, 0.f}, sc[3] = {1.f, 1.f, 1.f}, av = 0.f;
-    if (g < n) {
-        valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
-        for (int i = 0; i < 4; ++i) qv[i] = quat[4 * g + i];
-        for (int i = 0; i < 3; ++i) sc[i] = scale[3 * g + i];
-        av = alpha[g];
-        degen = is_degenerate(sc, f64_ratio);
-    }
+    const bool valid = g < n;
     const unsigned lt = lanemask_lt();
     unsigned long long gpos = valid ? goff[g] : 0;
     const int SW = (S + 31) >> 5;
@@ -531,29 +519,46 @@ __global__ void __launch_bounds__(K1_NT) k1_emit(const SliceDev *__restrict__ sl
             const bool f = (word >> b) & 1u;
             const unsigned bal = __ballot_sync(0xffffffffu, f);
             if (f) {
-                unsigned long long pos = (unsigned long long)off[(long long)k * NW + wg] + __popc(bal & lt);
-                const SliceDev Sd = slices[k];
-                FrameTerms ft;
-                frame_slab(G, Sd.Q, ft);
-                PredOut po;
-                record_predicate(G, Sd, K2, ft, po);  // true: same inputs as the count pass
+                const unsigned long long pos = (unsigned long long)off[(long long)k * NW + wg] + __popc(bal & lt);
                 if ((long long)pos < rec.cap) {
                     rec.gid[pos] = (int)g;
                     rec.slice[pos] = k;
-                    rec.rect[pos] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
-                                                 (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
-                    if (!degen) {  // near-degenerate Gaussians: FP64 geometry in k_rec_geom_f64
-                        RecGeomT<float> o;
-                        record_geometry<float>(G.mu, qv, sc, av, Sd, K2, o);
-                        rec.geo[pos] = make_float4(o.pcx, o.pcy, o.A, o.B2);
-                        rec.geo2[pos] = make_float2(o.C, o.amp);
-                        rec.thr[pos] = o.thr;
-                    }
                 }
                 if ((long long)gpos < rec.cap) gmap[gpos] = (unsigned)pos;
                 ++gpos;
             }
         }
+    }
+}
+
+// one thread per record: the tile rectangle (rest of the FP32 predicate; the
+// slab test passed in k1_count) and the FP32 evaluation geometry (FP64 for
+// near-degenerate Gaussians in k_rec_geom_f64)
+__global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ slices, const float *mean,
+                           const float *quat, const float *scale, const float *alpha, float K2, float f64_ratio,
+                           Records rec)
+{
+    long long nr = (long long)hdr->n_records;
+    if (nr > rec.cap) nr = rec.cap;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
+        const long long g = rec.gid[r];
+        const SliceDev &Sd = slices[rec.slice[r]];
+        GaussPred G;
+        load_gauss_pred(mean, quat, scale, alpha, g, G);
+        FrameTerms ft;
+        frame_slab(G, Sd.Q, ft);
+        PredOut po;
+        record_predicate(G, Sd, K2, ft, po);  // true: the slab test of k1_count
+        rec.rect[r] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
+                                   (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        if (is_degenerate(sc, f64_ratio)) continue;
+        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
+        RecGeomT<float> o;
+        record_geometry<float>(G.mu, qv, sc, alpha[g], Sd, K2, o);
+        rec.geo[r] = make_float4(o.pcx, o.pcy, o.A, o.B2);
+        rec.geo2[r] = make_float2(o.C, o.amp);
+        rec.thr[r] = o.thr;
     }
 }
 
@@ -800,8 +805,13 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_K1_EMIT, st);
-        k1_emit<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, bits, cnt, NW, gcnt,
-                                      rec, gmap);
+        k1_emit<<<g1, K1_NT, 0, st>>>(S, n, bits, cnt, NW, gcnt, rec, gmap);
+    }
+    {
+        MG_PROF(MG_ST_REC_FILL, st);
+        long long want_r = (L.cap_records + 255) / 256;
+        int gr = (int)(want_r < 148 * 16 ? (want_r > 0 ? want_r : 1) : 148 * 16);
+        k_rec_fill<<<gr, 256, 0, st>>>(hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, rec);
     }
     if (f64_ratio > 0.f) {
         MG_PROF(MG_ST_REC_GEOM, st);

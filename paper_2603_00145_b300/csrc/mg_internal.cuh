@@ -67,7 +67,8 @@ struct WsHeader {
     unsigned long long scan_total;
     unsigned long long pairs_inside;     // mg_render_pair_count
     unsigned long long pairs_evaluated;
-    unsigned long long reserved[25];
+    unsigned int tile_ctr[2];  // work counters of the persistent render kernels
+    unsigned long long reserved[24];
 };
 
 // Records are stored as structure-of-arrays.
@@ -127,6 +128,7 @@ enum MgStage {
     MG_ST_NRF_FWD,
     MG_ST_NRF_BWD,
     MG_ST_REC_GEOM,
+    MG_ST_REC_FILL,
     MG_NSTAGES
 };
 void mg_prof_begin(int stage, cudaStream_t st);

@@ -51,16 +51,12 @@ __device__ __forceinline__ TileLoc locate_tile(const StackTable &tab, int t, int
 // broadcast. Per (record, voxel pair): q from two packed FMAs, two ex2, one
 // packed FMA into the accumulators. At the end the half-warps exchange and
 // add their halves of the column (8 shuffles) and each writes 8 rows.
-__global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
-                                                        const unsigned *__restrict__ entries, long long cap_entries,
-                                                        long long cap_records, const float4 *__restrict__ geo,
-                                                        const float2 *__restrict__ geo2, float *__restrict__ out)
+__device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, float4 *sgw, float2 *sg2w,
+                                         const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
+                                         long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
+                                         const float2 *__restrict__ geo2, float *__restrict__ out)
 {
-    __shared__ float4 sg[RW][32];
-    __shared__ float2 sg2[RW][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * RW + w;
-    if (t >= tab.n_tiles_total) return;  // whole warp
+
     int s = 0;
     while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
     const int TX = tab.TX[s], T = TX * tab.TY[s];
@@ -90,8 +86,8 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
         }
     }
     for (unsigned base = e0; base < e1; base += 32) {
-        sg[w][lane] = na;
-        sg2[w][lane] = nb;
+        sgw[lane] = na;
+        sg2w[lane] = nb;
         __syncwarp();
         const unsigned nxt = base + 32 + lane;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -106,8 +102,8 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
         const int m = (int)min(32u, e1 - base);
         for (int j2 = 0; j2 < m; j2 += 2) {
             const int j = j2 + half;  // this half-warp's record (zero record past the end)
-            float4 a = sg[w][j & 31];
-            float2 b = sg2[w][j & 31];
+            float4 a = sgw[j & 31];
+            float2 b = sg2w[j & 31];
             if (j >= m) b.y = 0.f;
             const float dx = fpx - a.x;
             const float dyc = fpyc - a.y;
@@ -147,6 +143,27 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
     }
 }
 
+// persistent warps pull tiles from a counter (tiles carry very different
+// numbers of records)
+__global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
+                                                          const unsigned *__restrict__ entries, long long cap_entries,
+                                                          long long cap_records, const float4 *__restrict__ geo,
+                                                          const float2 *__restrict__ geo2, float *__restrict__ out,
+                                                          unsigned *counter)
+{
+    __shared__ float4 sg[RW][32];
+    __shared__ float2 sg2[RW][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int)t >= tab.n_tiles_total) break;
+        fwd_tile(tab, (int)t, lane, sg[w], sg2[w], tile_off, entries, cap_entries, cap_records, geo, geo2, out);
+        __syncwarp();
+    }
+}
+
 // K5, "one lane per record": lane l takes record l of the tile's next 32
 // entries and sweeps all 256 voxels of the tile, reading dL/dI from shared
 // memory by broadcast. Per voxel: q from two FMAs (quadratic in the column
@@ -155,16 +172,13 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
 // taken about the tile centre and moved to the record centre at the end, so
 // no cross-lane reduction is needed; each lane then adds its record's six
 // moments with six atomics.
-__global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
-                                                        const unsigned *__restrict__ entries, long long cap_entries,
-                                                        long long cap_records, const float4 *__restrict__ geo,
-                                                        const float2 *__restrict__ geo2,
-                                                        const float *__restrict__ grad_out, float *__restrict__ mom)
+__device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane, float *sgvw,
+                                         const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
+                                         long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
+                                         const float2 *__restrict__ geo2, const float *__restrict__ grad_out,
+                                         float *__restrict__ mom)
 {
-    __shared__ __align__(16) float sgv[RW][MG_TILE * MG_TILE];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * RW + w;
-    if (t >= tab.n_tiles_total) return;
+
     int s = 0;
     while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
     const int TX = tab.TX[s], T = TX * tab.TY[s];
@@ -176,9 +190,15 @@ __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const un
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 >= e1) return;
+    // dL/dI of the tile and its products with the column offset ic and ic^2
+    // (shared by all records of the tile)
     for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
         const int px = tx * MG_TILE + (i & 15), py = ty * MG_TILE + (i >> 4);
-        sgv[w][i] = (px < W && py < H) ? grad_out[pixbase + (long long)py * W + px] : 0.f;
+        const float gval = (px < W && py < H) ? grad_out[pixbase + (long long)py * W + px] : 0.f;
+        const float ic = (float)(i & 15) - 7.5f;
+        sgvw[i] = gval;
+        sgvw[MG_TILE * MG_TILE + i] = gval * ic;
+        sgvw[2 * MG_TILE * MG_TILE + i] = gval * ic * ic;
     }
     __syncwarp();
     const float x0c = (float)(tx * MG_TILE) + 7.5f, y0c = (float)(ty * MG_TILE) + 7.5f;
@@ -209,24 +229,25 @@ __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const un
             const float u = B2 * dy;
             const float b1 = A2x + u;
             const float b0 = fmaf(Ax + u, dxc, (C * dy) * dy);
-            const float4 *gr = (const float4 *)&sgv[w][j * MG_TILE];
-            // column pairs (i, i+1) with packed FP32x2 arithmetic
+            const float4 *g0r = (const float4 *)&sgvw[j * MG_TILE];
+            const float4 *g1r = g0r + MG_TILE * MG_TILE / 4;
+            const float4 *g2r = g1r + MG_TILE * MG_TILE / 4;
+            // column pairs (i, i+1) with packed FP32x2 arithmetic:
+            // P0 += g e, P1 += (g ic) e, P2 += (g ic^2) e
             const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
             float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
             for (int i4 = 0; i4 < 4; ++i4) {
-                const float4 g4 = gr[i4];
+                const float4 u0 = g0r[i4], u1 = g1r[i4], u2 = g2r[i4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float i0 = (float)(i4 * 4 + 2 * h) - 7.5f;
                     const float2 ic = make_float2(i0, i0 + 1.f);
-                    const float2 ic2 = make_float2(i0 * i0, (i0 + 1.f) * (i0 + 1.f));
-                    const float2 gp = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
                     const float2 q = __ffma2_rn(__ffma2_rn(A2, ic, b12), ic, b02);
-                    const float2 wv = __fmul2_rn(gp, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
-                    P0 = __fadd2_rn(P0, wv);
-                    P1 = __ffma2_rn(ic, wv, P1);
-                    P2 = __ffma2_rn(ic2, wv, P2);
+                    const float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                    P0 = __ffma2_rn(h ? make_float2(u0.z, u0.w) : make_float2(u0.x, u0.y), e, P0);
+                    P1 = __ffma2_rn(h ? make_float2(u1.z, u1.w) : make_float2(u1.x, u1.y), e, P1);
+                    P2 = __ffma2_rn(h ? make_float2(u2.z, u2.w) : make_float2(u2.x, u2.y), e, P2);
                 }
             }
             const float R0 = P0.x + P0.y, R1 = P1.x + P1.y, R2 = P2.x + P2.y;
@@ -246,6 +267,25 @@ __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const un
             atomicAdd(mr + 4, fmaf(dxc, fmaf(dyc, T0, Y0), fmaf(dyc, T1, Y1)));
             atomicAdd(mr + 5, fmaf(dyc, fmaf(dyc, T0, Y0 + Y0), Y2));
         }
+    }
+}
+
+__global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
+                                                          const unsigned *__restrict__ entries, long long cap_entries,
+                                                          long long cap_records, const float4 *__restrict__ geo,
+                                                          const float2 *__restrict__ geo2,
+                                                          const float *__restrict__ grad_out, float *__restrict__ mom,
+                                                          unsigned *counter)
+{
+    __shared__ __align__(16) float sgv[RW][3 * MG_TILE * MG_TILE];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int)t >= tab.n_tiles_total) break;
+        bwd_tile(tab, (int)t, lane, sgv[w], tile_off, entries, cap_entries, cap_records, geo, geo2, grad_out, mom);
+        __syncwarp();
     }
 }
 
@@ -539,14 +579,28 @@ void mg_launch_pair_count(const WsLayout &L, char *ws, const StackTable &tab, cu
         (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), (const float *)(ws + L.rec_thr), hdr);
 }
 
+static int resident_grid(const void *kern, int threads)
+{
+    int dev = 0, sms = 148, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
+    return sms * (per > 0 ? per : 1);
+}
+
 void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, float *out, cudaStream_t st)
 {
     int nt = tab.n_tiles_total;
     if (nt <= 0) return;
+    WsHeader *hdr = (WsHeader *)(ws + L.hdr);
+    cudaMemsetAsync(&hdr->tile_ctr[0], 0, sizeof(unsigned), st);
     MG_PROF(MG_ST_RENDER_FWD, st);
-    k_render_fwd<<<(nt + RW - 1) / RW, 32 * RW, 0, st>>>(
-        tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
-        (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), out);
+    int grid = resident_grid((const void *)k_render_fwd, 32 * RW);
+    if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
+    k_render_fwd<<<grid, 32 * RW, 0, st>>>(tab, (const unsigned *)(ws + L.tile_off),
+                                             (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
+                                             (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), out,
+                                             &hdr->tile_ctr[0]);
 }
 
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,
@@ -563,13 +617,15 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
         k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), hdr, L.cap_records);
     }
     int nt = tab.n_tiles_total;
-    {
+    if (nt > 0) {
+        cudaMemsetAsync((void *)&hdr->tile_ctr[1], 0, sizeof(unsigned), st);
         MG_PROF(MG_ST_RENDER_BWD, st);
-        if (nt > 0)
-            k_render_bwd<<<(nt + RW - 1) / RW, 32 * RW, 0, st>>>(
-                tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
-                L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), grad_out,
-                (float *)(ws + L.rec_mom));
+        int grid = resident_grid((const void *)k_render_bwd, 32 * RW);
+        if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
+        k_render_bwd<<<grid, 32 * RW, 0, st>>>(
+            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
+            L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), grad_out,
+            (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
     }
     MG_PROF(MG_ST_CHAIN, st);
     float4 *rg = (float4 *)(ws + L.rec_grad);
