@@ -116,7 +116,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def build_workload(name: str, seed: int, device):
+def build_workload(name: str, seed: int, device, keep_volume: bool = False):
     import torch
 
     import mg_synth as ms
@@ -129,11 +129,15 @@ def build_workload(name: str, seed: int, device):
     data = [ms.simulate_stack(vol, vs, s, seed=seed * 100 + i, noise_sigma=wl.noise_sigma, device=str(device))
             for i, s in enumerate(wl.stacks)]
     target = torch.cat([d.reshape(-1) for d in data]).contiguous()
-    del vol
+    if not keep_volume:
+        del vol
+        vol = None
     if name == "tiny":
         G = ms.devoxelised_gaussians(wl.stacks, [d.cpu().numpy() for d in data], wl.n_gaussians, seed=seed)
     else:
         G = ms.phantom_init_gaussians(wl, seed=seed)
+    if keep_volume:
+        return wl, G, target, vol
     return wl, G, target
 
 
@@ -274,12 +278,88 @@ def run_mgauss(args, rank, world, local_rank):
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(G, wl, args.cpu_seconds)
+    if rank == 0 and world == 1 and args.recon_iters > 0:
+        del R, out, grad, flush
+        torch.cuda.empty_cache()
+        line["recon"] = run_recon(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
+
+
+# ---------------------------------------------------------------------------
+# reconstruction time at equal PSNR (the second half of the metric)
+# ---------------------------------------------------------------------------
+RECON_FORMS = {
+    "gaussians_fp32": {},
+    "nrf_grid_fp32": {"nrf": "grid", "nrf_precision": "fp32"},
+    "nrf_grid_bf16": {"nrf": "grid", "nrf_precision": "bf16"},
+}
+
+
+def run_recon(args, dev):
+    """Full reconstructions of the workload: ``--recon-iters`` Adam iterations
+    of the L1+L2 slice loss (CUDA-graph replay of the whole iteration) plus
+    inference sampling onto the phantom's isotropic grid; wall seconds and
+    volume PSNR (FP64) against the phantom for the Gaussians alone (FP32) and
+    with the hash-grid NRF (switched on at half of the iterations, 2^20-voxel
+    batches) in FP32 and in BF16."""
+    import torch
+
+    from paper_2603_00145_b300 import recon
+    from paper_2603_00145_b300.ops import NRF, mg_nrf_bwd, mg_nrf_fwd
+
+    wl, G, target, vol = build_workload(args.workload, args.seed, dev, keep_volume=True)
+    gd = vol.shape[0]
+    half = wl.phantom.fov_mm / 2
+    forms = {}
+    for name, kw in RECON_FORMS.items():
+        cfg = recon.FitConfig(iterations=args.recon_iters, nrf_start=args.recon_iters // 2, nrf_batch=1 << 20,
+                              log_every=0, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model, nrf, st = recon.fit(wl.stacks, target, G, (0.0, 0.0, 0.0), half, cfg, device=dev)
+        V = recon.sample(model, nrf, gd, wl.phantom.spacing)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        forms[name] = {"seconds": sec, "fit_seconds": st["seconds"], "psnr_db": recon.psnr(V, vol),
+                       "final_loss": st["final_loss"], "iterations": st["iterations"],
+                       "graph_captures": st["graph_captures"]}
+        del model, nrf, V
+        torch.cuda.empty_cache()
+    # the NRF pass alone: forward + backward of one 2^20-point batch, CUDA events
+    import mg_synth as ms
+
+    nrf_ms = {}
+    xyz = torch.rand(1 << 20, 3, device=dev) * 2 - 1
+    gout = torch.randn(1 << 20, device=dev)
+    out = torch.empty(1 << 20, device=dev)
+    for prec in ("fp32", "bf16"):
+        W, b, t = ms.nrf_init("grid", 0, bf16=(prec == "bf16"), last_gain=0.1)
+        net = NRF("grid", prec, W, b, t, device=dev)
+        gp, gt = torch.empty_like(net.params), torch.empty_like(net.table)
+        for _ in range(3):
+            mg_nrf_fwd(net, xyz, out)
+            mg_nrf_bwd(net, xyz, gout, gp, gt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            mg_nrf_fwd(net, xyz, out)
+            mg_nrf_bwd(net, xyz, gout, gp, gt)
+        e1.record()
+        torch.cuda.synchronize()
+        nrf_ms[prec] = e0.elapsed_time(e1) / 20
+    f32, b16 = forms["nrf_grid_fp32"], forms["nrf_grid_bf16"]
+    return {"workload": wl.name, "iterations": args.recon_iters, "sampling": f"{gd}^3 at {wl.phantom.spacing} mm",
+            "loss": "mean|r| + mean r^2 (FP64)", "nrf": "hash grid 16x2, 2x64 ReLU, on at half, 2^20 voxels/iter",
+            "forms": forms,
+            "bf16_minus_fp32_psnr_db": b16["psnr_db"] - f32["psnr_db"],
+            "bf16_speedup_vs_fp32": f32["seconds"] / b16["seconds"],
+            "nrf_minus_gaussians_psnr_db": b16["psnr_db"] - forms["gaussians_fp32"]["psnr_db"],
+            "nrf_fwd_bwd_ms_per_2^20_points": nrf_ms}
 
 # ---------------------------------------------------------------------------
 # the CPU oracle (baseline leg and the reference arm)
@@ -379,6 +459,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--recon-iters", type=int, default=2000,
+                    help="iterations of each timed full reconstruction (0: skip the reconstruction timing)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -298,6 +298,48 @@ mg_status mg_nrf_fwd(const mg_nrf *net, const float *xyz, int64_t n, float *out,
 mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float *grad_out, float *g_params,
                      float *g_table, mg_stream_t stream);
 
+/*
+ * Device status word of a render workspace. The first 32-bit word of a
+ * workspace filled by mg_render_fwd / mg_sample_volume holds the forward's
+ * status bits; a bit of MG_WS_FAIL_BITS set means the forward failed (bins
+ * over capacity, or a non-finite input) and its output is incomplete. It is
+ * written by the device during the forward, so stream-ordered kernels (such
+ * as mg_adam_step below) can read it without a host round trip.
+ */
+#define MG_WS_FAIL_BITS 0x0Fu
+
+/*
+ * Optimiser step of the fit (Sec. 4.1.4: Adam, one learning rate per
+ * parameter group), all groups in one launch. Per element, with t = *step + 1:
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   p <- p - lr/(1-b1^t) * m / (sqrt(v)/sqrt(1-b2^t) + eps)
+ * (Kingma & Ba 2015, Algorithm 1, eps added after the bias correction of v),
+ * then p is clamped to [clamp_lo, clamp_hi] when clamp_lo <= clamp_hi (the
+ * alpha range [0, 1] of Sec. 3.2; pass lo > hi for no clamp). *step (device
+ * int32) is incremented after the update.
+ * Predication: when `status` (device, may be NULL) is given and
+ * (*status & status_mask) != 0 at the time the step runs, nothing is changed:
+ * no parameter, moment or step. With status = a render workspace's status word
+ * and status_mask = MG_WS_FAIL_BITS, an iteration whose forward failed is a
+ * no-op, so a fit can be replayed without host checks and detect failures
+ * later from *step. The paper has no counterpart of the predicate.
+ * All group pointers are device FP32 arrays of n elements; m and v are the
+ * caller's moment buffers (zero before the first step). 1 <= n_groups <= 8.
+ * Errors: MG_ERR_INVALID_ARG (NULL pointers, betas outside [0,1), eps <= 0,
+ * negative or non-finite lr); nothing is launched then.
+ */
+#define MG_ADAM_MAX_GROUPS 8
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m, *v;
+    int64_t n;
+    float lr;
+    float clamp_lo, clamp_hi;
+} mg_adam_group;
+mg_status mg_adam_step(const mg_adam_group *groups, int n_groups, float beta1, float beta2, float eps,
+                       int32_t *step, const uint32_t *status, uint32_t status_mask, mg_stream_t stream);
+
 const char *mg_status_string(mg_status s);
 const char *mg_last_error(void);
 /* Library version string. */

@@ -41,6 +41,14 @@ class MgNrf(ctypes.Structure):
                 ("n_min", c_i32), ("n_max", c_i32), ("out_scale", c_f32)]
 
 
+class MgAdamGroup(ctypes.Structure):
+    _fields_ = [("param", c_p), ("grad", c_p), ("m", c_p), ("v", c_p), ("n", c_i64), ("lr", c_f32),
+                ("clamp_lo", c_f32), ("clamp_hi", c_f32)]
+
+
+MG_WS_FAIL_BITS = 0x0F
+MG_ADAM_MAX_GROUPS = 8
+
 MG_NRF_FOURIER, MG_NRF_GRID = 0, 1
 MG_NRF_BF16, MG_NRF_FP32 = 0, 1
 
@@ -72,6 +80,8 @@ SIGNATURES = {
     "mg_nrf_param_count": (c_i64, [c_i32]),
     "mg_nrf_fwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p]),
     "mg_nrf_bwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p, c_p, c_p]),
+    "mg_adam_step": (ctypes.c_int, [ctypes.POINTER(MgAdamGroup), ctypes.c_int, c_f32, c_f32, c_f32, c_p, c_p,
+                                    ctypes.c_uint32, c_p]),
     "mg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mg_profile_stage_count": (ctypes.c_int, []),
     "mg_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),

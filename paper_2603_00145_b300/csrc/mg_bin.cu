@@ -643,6 +643,7 @@ __global__ void __launch_bounds__(1024) k_chunk_setup(const unsigned *rec_off, i
         chunk_base[S] = (unsigned)carry;
         hdr->n_chunks = carry;
         if (carry > (unsigned long long)cap_chunks) atomicOr(&hdr->flags, MG_FLAG_CAP_CHUNKS);
+        if (total > (unsigned long long)cap_rec) atomicOr(&hdr->flags, MG_FLAG_CAP_RECORDS);
     }
 }
 
@@ -716,10 +717,13 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
                                                                 const unsigned *slice_rs, const unsigned *chunk_base,
                                                                 const ushort4 *rect, const unsigned *hist, int Tmax,
                                                                 long long cap_chunks, const unsigned *tile_off,
-                                                                unsigned *entries, long long cap_entries)
+                                                                unsigned *entries, long long cap_entries,
+                                                                WsHeader *hdr)
 {
     extern __shared__ unsigned smem_u[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && hdr->n_entries > (unsigned long long)cap_entries)
+        atomicOr(&hdr->flags, MG_FLAG_CAP_ENTRIES);
     unsigned *cur = smem_u + w * Tmax;
     unsigned n_chunks = chunk_base[S];
     if ((long long)n_chunks > cap_chunks) n_chunks = (unsigned)cap_chunks;
@@ -848,6 +852,6 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     {
         MG_PROF(MG_ST_BIN_SCATTER, st);
         k_bin_scatter<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
-                                                        L.cap_chunks, tile_off, entries, L.cap_entries);
+                                                        L.cap_chunks, tile_off, entries, L.cap_entries, hdr);
     }
 }

@@ -14,7 +14,8 @@
 // walks the layers back: weight gradients dW += delta^T H (one GEMM), input
 // deltas delta W (one GEMM), accumulated per block in shared memory and
 // flushed with one atomic per parameter per block. Grid-table gradients are
-// scattered with atomics.
+// scattered with one float2 atomic per (point, level, corner): both features
+// of a level come out of one register pair of the D W_0 product.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -225,7 +226,8 @@ __device__ __forceinline__ void gemm_dTh_bf16(const bf16 *D, int ldd, const bf16
 }
 
 // P[64 x K] = D W, D [64 points][64], W [64][K]; warp w: points 16w..16w+15.
-template <int K, class Epi>
+// PAIR: epi(point, even column, value, value of the next column).
+template <int K, bool PAIR = false, class Epi>
 __device__ __forceinline__ void gemm_dw_bf16(const bf16 *D, int ldd, const bf16 *W, int ldw, int w, int lane, Epi epi)
 {
     float c[K / 8][4];
@@ -246,10 +248,15 @@ __device__ __forceinline__ void gemm_dw_bf16(const bf16 *D, int ldd, const bf16 
     const int g = lane >> 2, q = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < K / 8; ++nt) {
-        epi(16 * w + g, nt * 8 + 2 * q, c[nt][0]);
-        epi(16 * w + g, nt * 8 + 2 * q + 1, c[nt][1]);
-        epi(16 * w + g + 8, nt * 8 + 2 * q, c[nt][2]);
-        epi(16 * w + g + 8, nt * 8 + 2 * q + 1, c[nt][3]);
+        if constexpr (PAIR) {
+            epi(16 * w + g, nt * 8 + 2 * q, c[nt][0], c[nt][1]);
+            epi(16 * w + g + 8, nt * 8 + 2 * q, c[nt][2], c[nt][3]);
+        } else {
+            epi(16 * w + g, nt * 8 + 2 * q, c[nt][0]);
+            epi(16 * w + g, nt * 8 + 2 * q + 1, c[nt][1]);
+            epi(16 * w + g + 8, nt * 8 + 2 * q, c[nt][2]);
+            epi(16 * w + g + 8, nt * 8 + 2 * q + 1, c[nt][3]);
+        }
     }
 }
 
@@ -295,7 +302,8 @@ __device__ __forceinline__ void gemm_dTh_f32(const float *D, int ldd, const floa
 }
 
 // P[16 x K] = D W: warp w points 4w.., lane: point 4w + lane/8, K/8 columns
-template <int K, class Epi>
+// (PAIR as in gemm_dw_bf16).
+template <int K, bool PAIR = false, class Epi>
 __device__ __forceinline__ void gemm_dw_f32(const float *D, int ldd, const float *W, int ldw, int w, int lane, Epi epi)
 {
     const int row = 4 * w + (lane >> 3), c0 = (lane & 7) * (K / 8);
@@ -309,8 +317,14 @@ __device__ __forceinline__ void gemm_dw_f32(const float *D, int ldd, const float
         for (int i = 0; i < K / 8; ++i) c[i] = fmaf(d, W[o * ldw + c0 + i], c[i]);
     }
     __syncwarp();
+    if constexpr (PAIR) {
+        static_assert(K % 16 == 0, "column pairs");
 #pragma unroll
-    for (int i = 0; i < K / 8; ++i) epi(row, c0 + i, c[i]);
+        for (int i = 0; i < K / 8; i += 2) epi(row, c0 + i, c[i], c[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < K / 8; ++i) epi(row, c0 + i, c[i]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -407,9 +421,9 @@ struct Layout {
 };
 
 template <int ENC, bool BF16, bool TRAIN>
-__global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restrict__ xyz, long long n,
-                                                const float *__restrict__ grad_out, float *__restrict__ out,
-                                                float *__restrict__ g_params, float *__restrict__ g_table)
+__device__ __forceinline__ void nrf_body(const NrfArgs A, const float *__restrict__ xyz, long long n,
+                                         const float *__restrict__ grad_out, float *__restrict__ out,
+                                         float *__restrict__ g_params, float *__restrict__ g_table)
 {
     typedef Layout<ENC, BF16, TRAIN> LY;
     typedef typename LY::E E;
@@ -419,20 +433,22 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
     float *sBias = (float *)(smem + LY::o_bias);
     float *sWout = (float *)(smem + LY::o_wout);
     E *sH0 = (E *)(smem + LY::o_h0);
-    E *sH = (E *)(smem + LY::o_hs);
-    E *sZ = (E *)(smem + LY::o_z);
+    E *sH = (E *)(smem + LY::o_hs);  // current activations
+    E *sZ = (E *)(smem + LY::o_z);   // pre-activations Z_l of every layer (training)
     E *sD = (E *)(smem + LY::o_d);
     float *sDW = (float *)(smem + LY::o_dw);
     float *sPt = (float *)(smem + LY::o_pt);  // [P][4]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    // grid geometry in shared memory: levels are indexed at run time
+    __shared__ GridGeom sGrid;
+    if (tid == 0) sGrid = A.grid;
 
     // weights -> shared (converted to E, zero padded), biases, output layer
     for (int l = 0; l < L; ++l) {
-        const int kr = kin_real<ENC>(l), kp = kin_pad<ENC>(l), ld = LY::ldw(l);
+        const int kr = kin_real<ENC>(l), ld = LY::ldw(l);
         for (int i = tid; i < WIDTH * ld; i += NRF_NT) {
             const int o = i / ld, k = i - o * ld;
             float v = (k < kr) ? A.params[off_w<ENC>(l) + o * kr + k] : 0.f;
-            (void)kp;
             sW[LY::w_off(l) + i] = to_e<E>(v);
         }
         for (int i = tid; i < WIDTH; i += NRF_NT) sBias[l * WIDTH + i] = A.params[off_b<ENC>(l) + i];
@@ -467,12 +483,12 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
                 const int p = i / GRID_LEVELS, lv = i - p * GRID_LEVELS;
                 const float x[3] = {sPt[p * 4], sPt[p * 4 + 1], sPt[p * 4 + 2]};
                 Corner8 cr;
-                grid_corners(x, lv, A.grid, cr);
-                const float2 *tb = (const float2 *)A.table + ((size_t)lv << A.grid.log2T);
+                grid_corners(x, lv, sGrid, cr);
+                const float2 *tb = (const float2 *)A.table + ((size_t)lv << sGrid.log2T);
                 float f0 = 0.f, f1 = 0.f;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float2 v = tb[cr.idx[c]];
+                    const float2 v = __ldg(tb + cr.idx[c]);
                     f0 = fmaf(cr.wt[c], v.x, f0);
                     f1 = fmaf(cr.wt[c], v.y, f1);
                 }
@@ -507,12 +523,13 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
             }
             __syncthreads();
         }
+        const E *HL = sH;
         // ---- output layer: o = H w_out + b_out, r = s tanh(o); two threads per point
         for (int i = tid; i < 2 * P; i += NRF_NT) {
             const int p = i >> 1, half = i & 1;
             float acc = 0.f;
 #pragma unroll 8
-            for (int k = half * 32; k < half * 32 + 32; ++k) acc = fmaf(to_f(sH[p * LY::LDH + k]), sWout[k], acc);
+            for (int k = half * 32; k < half * 32 + 32; ++k) acc = fmaf(to_f(HL[p * LY::LDH + k]), sWout[k], acc);
             acc += __shfl_xor_sync(0xffffffffu, acc, 1);
             const float o = acc + sWout[WIDTH];
             const float th = tanhf(o);
@@ -529,12 +546,16 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
             continue;
         }
         __syncthreads();
-        // ---- backward of the output layer
+        // ---- backward of the output layer: two threads per output, 32 points each
         float *dWout = sDW + off_wout<ENC>();
-        for (int k = tid; k < WIDTH; k += NRF_NT) {
+        for (int i = tid; i < 2 * WIDTH; i += NRF_NT) {
+            const int k = i >> 1, half = i & 1;
             float acc = 0.f;
-            for (int p = 0; p < P; ++p) acc = fmaf(sPt[p * 4 + 3], to_f(sH[p * LY::LDH + k]), acc);
-            dWout[k] += acc;
+#pragma unroll 8
+            for (int p = half * (P / 2); p < (half + 1) * (P / 2); ++p)
+                acc = fmaf(sPt[p * 4 + 3], to_f(HL[p * LY::LDH + k]), acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            if (half == 0) dWout[k] += acc;
         }
         if (tid == 0) {
             float acc = 0.f;
@@ -545,8 +566,8 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
             const E *Zl = sZ + (size_t)(L - 1) * P * LY::LDH;
             for (int i = tid; i < P * WIDTH; i += NRF_NT) {
                 const int p = i / WIDTH, k = i - p * WIDTH;
-                const float d = sPt[p * 4 + 3] * sWout[k] * act_grad<ENC, BF16>(to_f(Zl[p * LY::LDH + k]));
-                sD[p * LY::LDH + k] = to_e<E>(d);
+                const float ag = act_grad<ENC, BF16>(to_f(Zl[p * LY::LDH + k]));
+                sD[p * LY::LDH + k] = to_e<E>(sPt[p * 4 + 3] * sWout[k] * ag);
             }
         }
         __syncthreads();
@@ -586,11 +607,15 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
                 else
                     gemm_dTh_f32<WIDTH>((const float *)sD, LY::LDH, (const float *)Hin, ldin, w, lane, epi_g);
             }
+            // bias gradients: two threads per output, half of the points each
             float *dbl = sDW + off_b<ENC>(l);
-            for (int o = tid; o < WIDTH; o += NRF_NT) {
+            for (int i = tid; i < 2 * WIDTH; i += NRF_NT) {
+                const int o = i >> 1, half = i & 1;
                 float acc = 0.f;
-                for (int p = 0; p < P; ++p) acc += to_f(sD[p * LY::LDH + o]);
-                dbl[o] += acc;
+#pragma unroll 8
+                for (int p = half * (P / 2); p < (half + 1) * (P / 2); ++p) acc += to_f(sD[p * LY::LDH + o]);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                if (half == 0) dbl[o] += acc;
             }
             __syncthreads();
             if (l > 0) {
@@ -610,21 +635,21 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
             } else if (ENC == MG_NRF_GRID && g_table) {
                 // encoding gradient: dL/dfeatures = D W_0, scattered to the grid corners
                 const E *W0 = sW + LY::w_off(0);
-                auto epi_t = [&](int p, int k, float v) {
-                    // k = 2 * level + feature
+                auto epi_t = [&](int p, int k, float v0, float v1) {
+                    // k = 2 * level: both features of one level, one float2 atomic per corner
                     if (p0 + p >= n) return;
-                    const int lv = k >> 1, f = k & 1;
+                    const int lv = k >> 1;
                     const float x[3] = {sPt[p * 4], sPt[p * 4 + 1], sPt[p * 4 + 2]};
                     Corner8 cr;
-                    grid_corners(x, lv, A.grid, cr);
-                    float *tg = g_table + (((size_t)lv << A.grid.log2T) << 1);
+                    grid_corners(x, lv, sGrid, cr);
+                    float2 *tg = (float2 *)g_table + ((size_t)lv << sGrid.log2T);
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) atomicAdd(&tg[(size_t)cr.idx[c] * 2 + f], cr.wt[c] * v);
+                    for (int c = 0; c < 8; ++c) atomicAdd(&tg[cr.idx[c]], make_float2(cr.wt[c] * v0, cr.wt[c] * v1));
                 };
                 if (BF16)
-                    gemm_dw_bf16<K0P>((const bf16 *)sD, LY::LDH, (const bf16 *)W0, LY::ldw(0), w, lane, epi_t);
+                    gemm_dw_bf16<K0P, true>((const bf16 *)sD, LY::LDH, (const bf16 *)W0, LY::ldw(0), w, lane, epi_t);
                 else
-                    gemm_dw_f32<K0P>((const float *)sD, LY::LDH, (const float *)W0, LY::ldw(0), w, lane, epi_t);
+                    gemm_dw_f32<K0P, true>((const float *)sD, LY::LDH, (const float *)W0, LY::ldw(0), w, lane, epi_t);
                 __syncthreads();
             }
         }
@@ -633,6 +658,27 @@ __global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restri
         __syncthreads();
         for (int i = tid; i < LY::DW_FLOATS; i += NRF_NT) atomicAdd(&g_params[i], sDW[i]);
     }
+}
+
+// Two entry points with the same body: the forward (inference) kernels are
+// compiled for 4 resident blocks of 4 warps per SM, which lets the compiler
+// keep more grid gathers in flight (measured: 0.39 vs 0.81 ms per 2^20
+// points for the grid BF16 forward); the training kernels keep the default
+// register allocation (their shared memory limits residency anyway).
+template <int ENC, bool BF16, bool TRAIN>
+__global__ void __launch_bounds__(NRF_NT) k_nrf(NrfArgs A, const float *__restrict__ xyz, long long n,
+                                                const float *__restrict__ grad_out, float *__restrict__ out,
+                                                float *__restrict__ g_params, float *__restrict__ g_table)
+{
+    nrf_body<ENC, BF16, TRAIN>(A, xyz, n, grad_out, out, g_params, g_table);
+}
+
+template <int ENC, bool BF16, bool TRAIN>
+__global__ void __launch_bounds__(NRF_NT, 4) k_nrf4(NrfArgs A, const float *__restrict__ xyz, long long n,
+                                                    const float *__restrict__ grad_out, float *__restrict__ out,
+                                                    float *__restrict__ g_params, float *__restrict__ g_table)
+{
+    nrf_body<ENC, BF16, TRAIN>(A, xyz, n, grad_out, out, g_params, g_table);
 }
 
 // ---------------------------------------------------------------------------
@@ -666,7 +712,7 @@ cudaError_t launch_nrf(const mg_nrf *net, const float *xyz, long long n, const f
     A.table = net->table;
     A.out_scale = net->out_scale;
     A.grid = make_grid(net);
-    auto kern = k_nrf<ENC, BF16, TRAIN>;
+    auto kern = TRAIN ? k_nrf<ENC, BF16, TRAIN> : k_nrf4<ENC, BF16, TRAIN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -178,6 +178,28 @@ def mg_render_pair_count(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L
     return int(c[0]), int(c[1])
 
 
+def mg_adam_step(groups: Sequence[dict], beta1: float, beta2: float, eps: float, step, status=None,
+                 status_mask: int = L.MG_WS_FAIL_BITS, stream=None):
+    """groups: dicts with param, grad, m, v (device FP32 tensors of one size),
+    lr and optional clamp (lo, hi). ``step``: device int32 [1]; ``status``:
+    a device tensor whose first 32-bit word predicates the update, or None."""
+    arr = (L.MgAdamGroup * len(groups))()
+    for i, g in enumerate(groups):
+        n = g["param"].numel()
+        lo, hi = g.get("clamp") or (1.0, 0.0)
+        arr[i] = L.MgAdamGroup(_dev(g["param"], "param"), _dev(g["grad"], "grad", numel=n),
+                               _dev(g["m"], "m", numel=n), _dev(g["v"], "v", numel=n), n, float(g["lr"]),
+                               float(lo), float(hi))
+    sp = _dev(step, "step", dtype=torch.int32, numel=1)
+    stp = None
+    if status is not None:
+        if not status.is_cuda or status.numel() * status.element_size() < 4:
+            raise ValueError("status must be a CUDA tensor of at least 4 bytes")
+        stp = status.data_ptr()
+    L.check(L.lib().mg_adam_step(arr, len(groups), float(beta1), float(beta2), float(eps), sp, stp,
+                                 int(status_mask), _stream_handle(stream)), "mg_adam_step")
+
+
 def mg_profile_enable(on: bool = True):
     L.check(L.lib().mg_profile_enable(1 if on else 0), "mg_profile_enable")
 
@@ -264,6 +286,11 @@ class SliceRenderer:
     def stats(self, stream=None) -> dict:
         return mg_render_stats_get(self.ws, stream)
 
+    @property
+    def status_word(self) -> torch.Tensor:
+        """The device status word of the workspace (its first 32 bits)."""
+        return self.ws[:4]
+
     def pair_count(self, mean, quat, scale, alpha, stream=None):
         """(pairs inside the K-sigma ellipsoid, evaluated pairs) of the last forward."""
         return mg_render_pair_count(mean, quat, scale, alpha, self.dev, self.opts(), self.ws, stream)
@@ -281,6 +308,43 @@ class SliceRenderer:
                                stream, raise_on_error=False)
         L.check(st, "mg_render_bwd")
         return g
+
+
+class DeviceAdam:
+    """Adam over parameter groups with the whole update in mg_adam_step (one
+    launch, moments and step counter on the device, optional clamp and a
+    device status predicate). Parameters keep their torch ``.grad``."""
+
+    def __init__(self, groups: Sequence[dict], betas=(0.9, 0.999), eps: float = 1e-8):
+        if not 1 <= len(groups) <= L.MG_ADAM_MAX_GROUPS:
+            raise ValueError("1..8 parameter groups")
+        self.groups = []
+        for g in groups:
+            p = g["param"]
+            if not (p.is_cuda and p.dtype == _F32 and p.is_contiguous()):
+                raise ValueError("parameters must be contiguous CUDA FP32 tensors")
+            self.groups.append({"param": p, "lr": float(g["lr"]), "clamp": g.get("clamp"),
+                                "m": torch.zeros_like(p), "v": torch.zeros_like(p)})
+        self.betas, self.eps = (float(betas[0]), float(betas[1])), float(eps)
+        self.step_t = torch.zeros(1, dtype=torch.int32, device=groups[0]["param"].device)
+
+    def zero_grad(self):
+        for g in self.groups:
+            g["param"].grad = None
+
+    def step(self, status=None, stream=None):
+        gs = []
+        for g in self.groups:
+            p = g["param"]
+            if p.grad is None:
+                raise RuntimeError("a parameter has no gradient")
+            gs.append({"param": p.data, "grad": p.grad.contiguous(), "m": g["m"], "v": g["v"], "lr": g["lr"],
+                       "clamp": g["clamp"]})
+        mg_adam_step(gs, self.betas[0], self.betas[1], self.eps, self.step_t, status, stream=stream)
+
+    @property
+    def steps(self) -> int:
+        return int(self.step_t.item())
 
 
 class RenderSlices(torch.autograd.Function):

@@ -40,6 +40,9 @@ class FitConfig:
     nrf_seed: int = 0
     log_every: int = 0
     seed: int = 0
+    graph: bool = True          # replay each phase's iteration as a CUDA graph
+    check_every: int = 100      # graph replays between host checks of the step counter
+    headroom: float = 1.5       # bin capacity over the warm-up iteration's need (graph mode)
 
 
 class LossL1L2(torch.autograd.Function):
@@ -104,66 +107,187 @@ def make_nrf(preset: str, precision: str, seed: int, device="cuda"):
     return ops.NRF(preset, precision, W, b, t, device=device)
 
 
+class _Trainer:
+    """One training iteration of the fit as a sequence of stream-ordered
+    launches with no host synchronisation (so it can be captured in a CUDA
+    graph): render (mg_render_fwd), optional NRF residual on a random voxel
+    batch, FP64 loss, backward (mg_render_bwd, mg_nrf_bwd) and the Adam step
+    (mg_adam_step), predicated on the forward's device status word."""
+
+    def __init__(self, stacks, target, G_init, centre, half_extent, cfg: FitConfig, device):
+        self.cfg, self.device, self.target = cfg, device, target
+        self.stacks, self.centre, self.half = stacks, centre, half_extent
+        self.model = Model(G_init, centre, half_extent, device)
+        self.R = ops.SliceRenderer(stacks, device=device, cutoff_k=cfg.cutoff_k, check=True)
+        m = self.model
+        self.adam = ops.DeviceAdam([
+            {"param": m.mean_c, "lr": cfg.lr_position},
+            {"param": m.alpha, "lr": cfg.lr_intensity, "clamp": (0.0, 1.0)},  # alpha in [0, 1] (Sec. 3.2)
+            {"param": m.log_scale, "lr": cfg.lr_scale},
+            {"param": m.quat, "lr": cfg.lr_rotation}])
+        self.ws = torch.empty(ops.mg_reduce_workspace_size(target.numel()), dtype=torch.uint8, device=device)
+        self.nrf = self.nrf_adam = self.coords = None
+        self.nrf_params = self.nrf_table = None
+
+    def enable_nrf(self):
+        cfg = self.cfg
+        self.nrf = make_nrf(cfg.nrf, cfg.nrf_precision, cfg.nrf_seed, self.device)
+        self.nrf_params = torch.nn.Parameter(self.nrf.params.clone())
+        groups = [{"param": self.nrf_params, "lr": cfg.lr_nrf}]
+        if self.nrf.table is not None:
+            self.nrf_table = torch.nn.Parameter(self.nrf.table.clone())
+            groups.append({"param": self.nrf_table, "lr": cfg.lr_table})
+        self.nrf_adam = ops.DeviceAdam(groups)
+        self.coords = voxel_coords(self.stacks, self.centre, self.half, self.device)
+        torch.cuda.manual_seed(cfg.seed + 17)  # voxel batches come from the default CUDA generator
+
+    def zero_grad(self):
+        self.adam.zero_grad()
+        if self.nrf_adam is not None:
+            self.nrf_adam.zero_grad()
+
+    def iteration(self):
+        cfg, m = self.cfg, self.model
+        mean, q, s, a = m.gaussians()
+        pred = ops.RenderSlices.apply(self.R, mean, q, s, a)
+        if self.nrf is not None:
+            n_vox = self.target.numel()
+            idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
+            r = ops.NRFFunction.apply(self.nrf, self.coords[idx], self.nrf_params, self.nrf_table)
+            pred = pred.index_add(0, idx, r)
+        # FP64 loss and its gradient in one kernel; the gradient seeds the backward directly
+        grad = torch.empty_like(pred)
+        out = torch.empty(2, dtype=torch.float64, device=pred.device)
+        ops.mg_loss_l1l2(pred.detach(), self.target, grad, out, self.ws)
+        reg = cfg.lambda_aniso * m.aniso(cfg.lambda_r)
+        torch.autograd.backward([pred, reg], [grad, None])
+        loss = out[0]
+        status = self.R.status_word
+        self.adam.step(status=status)
+        if self.nrf_adam is not None:
+            self.nrf_adam.step(status=status)
+        return loss.detach()  # holds no autograd graph between iterations
+
+    def done(self) -> int:
+        return self.adam.steps
+
+    def size_bins(self, factor: float, keep_larger: bool = True):
+        """Capacity = factor x the last forward's record and entry counts
+        (never below the current capacity when ``keep_larger``)."""
+        st = self.R.stats()
+        if st["status"] == ops.L.MG_ERR_NOT_FINITE:
+            raise ops.L.MgError(ops.L.MG_ERR_NOT_FINITE, "fit: non-finite Gaussian parameters")
+        n = self.model.mean_c.shape[0]
+        r, e = int(st["records"] * factor) + 1, int(st["entries"] * factor) + 1
+        if keep_larger:
+            r, e = max(r, self.R.caps[0]), max(e, self.R.caps[1])
+        self.R.set_capacity(r, e, n)
+
+    def finish(self):
+        if self.nrf is not None:
+            self.nrf.params = self.nrf_params.detach().contiguous()
+            if self.nrf_table is not None:
+                self.nrf.table = self.nrf_table.detach().contiguous()
+
+
+def _phase_end(cfg: FitConfig, done: int) -> int:
+    if cfg.nrf and done < cfg.nrf_start:
+        return min(cfg.nrf_start, cfg.iterations)
+    return cfg.iterations
+
+
 def fit(stacks, target, G_init, centre, half_extent, cfg: FitConfig, device="cuda", log=None):
     """Returns (model, nrf or None, stats). ``target``: flat device tensor of
-    all slice voxels."""
+    all slice voxels.
+
+    With ``cfg.graph`` each phase (before / after the NRF starts) runs two
+    eager iterations on a side stream (they size the bins, with 1.5x
+    headroom), then captures one iteration in a CUDA graph and replays it,
+    checking the device step counter every ``cfg.check_every`` iterations. An
+    iteration whose bins overflow changes nothing (the Adam step is
+    predicated on the render status), so on a lag the workspace grows, the
+    graph is captured again and the missing iterations are run."""
     torch.manual_seed(cfg.seed)
-    model = Model(G_init, centre, half_extent, device)
-    R = ops.SliceRenderer(stacks, device=device, cutoff_k=cfg.cutoff_k, check=True)
-    opt = torch.optim.Adam([
-        {"params": [model.mean_c], "lr": cfg.lr_position},
-        {"params": [model.alpha], "lr": cfg.lr_intensity},
-        {"params": [model.log_scale], "lr": cfg.lr_scale},
-        {"params": [model.quat], "lr": cfg.lr_rotation}])
-    ws = torch.empty(ops.mg_reduce_workspace_size(target.numel()), dtype=torch.uint8, device=device)
-    nrf = None
-    nrf_opt = None
-    coords = None
-    nrf_params = nrf_table = None
-    gen = torch.Generator(device=device).manual_seed(cfg.seed + 17)
-    n_vox = target.numel()
-    hist = []
     t0 = time.perf_counter()
-    for it in range(cfg.iterations):
-        if cfg.nrf and it == cfg.nrf_start:
-            nrf = make_nrf(cfg.nrf, cfg.nrf_precision, cfg.nrf_seed, device)
-            nrf_params = torch.nn.Parameter(nrf.params.clone())
-            groups = [{"params": [nrf_params], "lr": cfg.lr_nrf}]
-            if nrf.table is not None:
-                nrf_table = torch.nn.Parameter(nrf.table.clone())
-                groups.append({"params": [nrf_table], "lr": cfg.lr_table})
-            nrf_opt = torch.optim.Adam(groups)
-            coords = voxel_coords(stacks, centre, half_extent, device)
-        mean, q, s, a = model.gaussians()
-        pred = ops.RenderSlices.apply(R, mean, q, s, a)  # checks capacity every iteration (grows on overflow)
-        if nrf is not None:
-            idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=device, generator=gen)
-            r = ops.NRFFunction.apply(nrf, coords[idx], nrf_params, nrf_table)
-            pred = pred.index_add(0, idx, r)
-        loss = LossL1L2.apply(pred, target, ws)
-        total = loss.float() + cfg.lambda_aniso * model.aniso(cfg.lambda_r)
-        opt.zero_grad(set_to_none=True)
-        if nrf_opt:
-            nrf_opt.zero_grad(set_to_none=True)
-        total.backward()
-        opt.step()
-        if nrf_opt:
-            nrf_opt.step()
-        with torch.no_grad():
-            model.alpha.clamp_(0.0, 1.0)  # alpha in [0, 1] (Sec. 3.2)
-        if cfg.log_every and (it % cfg.log_every == 0 or it == cfg.iterations - 1):
-            hist.append((it, float(loss.detach())))
-            if log:
-                log(f"it {it} loss {hist[-1][1]:.6e}")
+    T = _Trainer(stacks, target, G_init, centre, half_extent, cfg, device)
+    hist = []
+    captures = 0
+    t_eager = t_capture = t_replay = 0.0
+    loss = None
+    if not cfg.graph:
+        for it in range(cfg.iterations):
+            if cfg.nrf and it == cfg.nrf_start:
+                T.enable_nrf()
+            T.zero_grad()
+            loss = T.iteration()  # the renderer checks capacity every iteration (grows on overflow)
+            if cfg.log_every and (it % cfg.log_every == 0 or it == cfg.iterations - 1):
+                hist.append((it, float(loss.detach())))
+                if log:
+                    log(f"it {it} loss {hist[-1][1]:.6e}")
+    else:
+        done = 0
+        while done < cfg.iterations:
+            if cfg.nrf and done >= cfg.nrf_start and T.nrf is None:
+                T.enable_nrf()
+            end = _phase_end(cfg, done)
+            # eager warm-up on a side stream: sizes the bins and initialises lazily created state
+            T.R.check = True
+            ta = time.perf_counter()
+            side = torch.cuda.Stream(device=device)
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(min(2, end - done)):
+                    T.zero_grad()
+                    loss = T.iteration()
+                    if cfg.log_every and done % cfg.log_every == 0:
+                        hist.append((done, float(loss)))
+                    done += 1
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            t_eager += time.perf_counter() - ta
+            if done >= end:
+                continue
+            T.size_bins(cfg.headroom, keep_larger=False)
+            graph = None
+            lags = 0
+            while done < end:
+                if graph is None:
+                    ta = time.perf_counter()
+                    T.R.check = False
+                    T.zero_grad()
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph):
+                        loss = T.iteration()
+                    captures += 1
+                    t_capture += time.perf_counter() - ta
+                ta = time.perf_counter()
+                k = min(cfg.check_every, end - done)
+                for _ in range(k):
+                    graph.replay()
+                now = T.done()  # synchronises
+                t_replay += time.perf_counter() - ta
+                if now < done + k:  # an iteration's bins overflowed: it was a no-op
+                    lags += 1
+                    if lags > 8:
+                        raise RuntimeError("fit: the bins keep overflowing after growing the workspace")
+                    graph = None
+                    T.size_bins(1.5)
+                if cfg.log_every:
+                    hist.append((now - 1, float(loss.detach())))
+                    if log:
+                        log(f"it {now - 1} loss {hist[-1][1]:.6e}")
+                done = now
+            del graph
+        T.R.check = True
     torch.cuda.synchronize()
-    st = R.stats()
+    st = T.R.stats()
     if st["status"] != 0:
         raise RuntimeError(f"render status {st['status']} during the fit")
-    if nrf is not None:
-        nrf.params = nrf_params.detach().contiguous()
-        if nrf_table is not None:
-            nrf.table = nrf_table.detach().contiguous()
-    return model, nrf, {"seconds": time.perf_counter() - t0, "history": hist, "final_loss": float(loss.detach())}
+    T.finish()
+    seconds = time.perf_counter() - t0
+    return T.model, T.nrf, {"seconds": seconds, "history": hist, "final_loss": float(loss.detach()),
+                            "graph_captures": captures, "iterations": T.done(),
+                            "seconds_eager": t_eager, "seconds_capture": t_capture, "seconds_replay": t_replay}
 
 
 def sample(model: Model, nrf, G_dim: int, spacing: float, centre=(0.0, 0.0, 0.0), cutoff_k: float = 3.0,
