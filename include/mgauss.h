@@ -229,6 +229,30 @@ mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float 
 mg_status mg_loss_l1l2_noalloc(const float *pred, const float *target, int64_t n, float *grad, double *loss_out,
                                mg_stream_t stream);
 
+/*
+ * The paper's reconstruction loss (Sec. 3.5.2) on rendered slices:
+ *   L_recon = L_L1 + lambda_ssim * (1 - mean SSIM),
+ * L_L1 = mean over all pixels of smooth_L1(pred - target) (Eq. E11: 0.5 r^2
+ * for |r| < 1, else |r| - 0.5), SSIM the structural similarity of Wang et
+ * al. (2004) of each pixel of each 2-D slice: 11 x 11 Gaussian window of
+ * standard deviation 1.5 pixels (unit sum), zero padding outside the slice,
+ * C1 = 0.01^2, C2 = 0.03^2 (intensity range 1); the mean runs over every
+ * pixel of every slice. The paper does not write L_SSIM out; 1 - mean SSIM
+ * over whole slices is the reading (the paper's lambda_SSIM is 0.5).
+ * pred, target: device FP32 slices laid out as mg_render_fwd writes them
+ * (stacks concatenated, [n_slices, H, W] each); only n_slices, H and W of the
+ * stacks are read (1 <= H, W <= 16384). grad (device FP32, same size, may be
+ * NULL) is overwritten with dL_recon/dpred. loss_out: device double[3] =
+ * {L_recon, mean smooth-L1, mean SSIM}; the sums are FP64 and fixed-order
+ * (the result is the same bit pattern on every run). Evaluation is FP32.
+ * ws: device scratch of mg_loss_recon_workspace_size bytes (0 on invalid
+ * stacks). Errors: MG_ERR_INVALID_ARG (nothing launched).
+ */
+size_t mg_loss_recon_workspace_size(const mg_stack *stacks, int n_stacks);
+mg_status mg_loss_recon(const float *pred, const float *target, const mg_stack *stacks, int n_stacks,
+                        float lambda_ssim, float *grad, double *loss_out, void *ws, size_t ws_bytes,
+                        mg_stream_t stream);
+
 /* FP64 sum of squared differences (for MSE / PSNR, Sec. 4.1.3): out: device
  * double [1] = sum (a-b)^2, fixed-order FP64 accumulation. */
 mg_status mg_sq_diff_sum(const float *a, const float *b, int64_t n, double *out, void *ws, size_t ws_bytes,

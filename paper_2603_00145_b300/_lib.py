@@ -75,6 +75,9 @@ SIGNATURES = {
     "mg_loss_l1l2": (ctypes.c_int, [c_p, c_p, c_i64, c_p, c_p, c_p, c_sz, c_p]),
     "mg_loss_l1l2_noalloc": (ctypes.c_int, [c_p, c_p, c_i64, c_p, c_p, c_p]),
     "mg_sq_diff_sum": (ctypes.c_int, [c_p, c_p, c_i64, c_p, c_p, c_sz, c_p]),
+    "mg_loss_recon_workspace_size": (c_sz, [ctypes.POINTER(MgStack), ctypes.c_int]),
+    "mg_loss_recon": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(MgStack), ctypes.c_int, c_f32, c_p, c_p, c_p, c_sz,
+                                     c_p]),
     "mg_render_pair_count": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                             ctypes.POINTER(MgOpts), c_p, c_sz, ctypes.POINTER(c_i64), c_p]),
     "mg_nrf_param_count": (c_i64, [c_i32]),

@@ -170,6 +170,24 @@ def mg_sq_diff_sum(a, b, out, ws, stream=None):
     L.check(st, "mg_sq_diff_sum")
 
 
+def mg_loss_recon_workspace_size(stacks: DeviceStacks) -> int:
+    return int(L.lib().mg_loss_recon_workspace_size(stacks.arr, stacks.n))
+
+
+def mg_loss_recon(pred, target, stacks: DeviceStacks, lambda_ssim: float, grad, loss_out, ws, stream=None):
+    """Smooth-L1 + lambda_ssim (1 - mean SSIM) over the slices of ``stacks``;
+    loss_out: device double[3] = {loss, mean smooth-L1, mean SSIM}."""
+    n = stacks.n_vox
+    _dev(pred, "pred", numel=n)
+    _dev(target, "target", numel=n)
+    gp = _dev(grad, "grad", numel=n) if grad is not None else None
+    _dev(loss_out, "loss_out", dtype=torch.float64, numel=3)
+    _dev(ws, "ws", dtype=torch.uint8)
+    L.check(L.lib().mg_loss_recon(pred.data_ptr(), target.data_ptr(), stacks.arr, stacks.n, float(lambda_ssim), gp,
+                                  loss_out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+            "mg_loss_recon")
+
+
 def mg_render_pair_count(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, ws, stream=None):
     g = _gauss(mean, quat, scale, alpha)
     c = (ctypes.c_int64 * 2)()

@@ -29,7 +29,8 @@ class FitConfig:
     lr_rotation: float = 1e-3
     lambda_aniso: float = 0.1   # Eq. E12
     lambda_r: float = 1.5       # Eq. E13
-    loss: str = "l1l2"          # the plain-fit slice loss
+    loss: str = "l1l2"          # "l1l2" (mean |r| + mean r^2) or "paper" (smooth L1 + lambda_ssim SSIM, Sec. 3.5.2)
+    lambda_ssim: float = 0.5    # Sec. 4.1.4
     cutoff_k: float = 3.0
     nrf: Optional[str] = None   # None, "paper" or "grid"
     nrf_precision: str = "bf16"
@@ -125,7 +126,12 @@ class _Trainer:
             {"param": m.alpha, "lr": cfg.lr_intensity, "clamp": (0.0, 1.0)},  # alpha in [0, 1] (Sec. 3.2)
             {"param": m.log_scale, "lr": cfg.lr_scale},
             {"param": m.quat, "lr": cfg.lr_rotation}])
-        self.ws = torch.empty(ops.mg_reduce_workspace_size(target.numel()), dtype=torch.uint8, device=device)
+        if cfg.loss not in ("l1l2", "paper"):
+            raise ValueError(f"unknown loss {cfg.loss!r}")
+        if cfg.loss == "paper":
+            self.ws = torch.empty(ops.mg_loss_recon_workspace_size(self.R.dev), dtype=torch.uint8, device=device)
+        else:
+            self.ws = torch.empty(ops.mg_reduce_workspace_size(target.numel()), dtype=torch.uint8, device=device)
         self.nrf = self.nrf_adam = self.coords = None
         self.nrf_params = self.nrf_table = None
 
@@ -155,10 +161,14 @@ class _Trainer:
             idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
             r = ops.NRFFunction.apply(self.nrf, self.coords[idx], self.nrf_params, self.nrf_table)
             pred = pred.index_add(0, idx, r)
-        # FP64 loss and its gradient in one kernel; the gradient seeds the backward directly
+        # the loss (FP64 sums) and its gradient in one kernel; the gradient seeds the backward directly
         grad = torch.empty_like(pred)
-        out = torch.empty(2, dtype=torch.float64, device=pred.device)
-        ops.mg_loss_l1l2(pred.detach(), self.target, grad, out, self.ws)
+        if cfg.loss == "paper":
+            out = torch.empty(3, dtype=torch.float64, device=pred.device)
+            ops.mg_loss_recon(pred.detach(), self.target, self.R.dev, cfg.lambda_ssim, grad, out, self.ws)
+        else:
+            out = torch.empty(2, dtype=torch.float64, device=pred.device)
+            ops.mg_loss_l1l2(pred.detach(), self.target, grad, out, self.ws)
         reg = cfg.lambda_aniso * m.aniso(cfg.lambda_r)
         torch.autograd.backward([pred, reg], [grad, None])
         loss = out[0]

@@ -68,5 +68,9 @@ def test_host_entry_points(lib):
     assert lib.mg_sample_workspace_size(1000, 64, ctypes.byref(o)) > 0
     assert lib.mg_sample_workspace_size(1000, 0, ctypes.byref(o)) == 0
     assert lib.mg_reduce_workspace_size(12345) >= 16
+    assert lib.mg_loss_recon_workspace_size(st, 2) >= 16 * (10 * 2 * 2 + 5 * 1 * 2)
+    assert lib.mg_loss_recon_workspace_size(bad, 1) == 0
+    grp = L.MgAdamGroup(None, None, None, None, 10, 0.1, 1.0, 0.0)
+    assert lib.mg_adam_step(ctypes.byref(grp), 1, 0.9, 0.999, 1e-8, None, None, 0, None) == L.MG_ERR_INVALID_ARG
     assert lib.mg_status_string(L.MG_ERR_CAPACITY) == b"workspace capacity exceeded"
     assert lib.mg_version().startswith(b"mgauss")

@@ -76,3 +76,13 @@ def test_graph_fit_recovers_from_bin_overflow(tiny):
     losses = [l for _, l in st["history"]]
     assert losses[-1] < losses[0]
     assert p > 18.0
+
+
+def test_fit_with_the_papers_ssim_loss(tiny):
+    """The fit with the paper's reconstruction loss (smooth L1 + 0.5 SSIM,
+    Sec. 3.5.2) runs through the fused loss kernel, lowers it and
+    reconstructs the phantom."""
+    p, st = _run(tiny, iterations_override=600, loss="paper")
+    losses = [l for _, l in st["history"]]
+    assert losses[-1] < 0.7 * losses[0], losses
+    assert p > 20.0, p
