@@ -161,6 +161,26 @@ mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
                         size_t ws_bytes, mg_stream_t stream);
 
 /*
+ * Gradient with respect to the slice poses T_k (the per-slice rigid
+ * transforms of Sec. 3.3.2, 6 degrees of freedom each), for joint motion
+ * estimation. Uses the per-record moments of dL/dI that the immediately
+ * preceding mg_render_bwd on this workspace accumulated (same arguments as
+ * that call's forward), so it returns the pose gradient of the same loss.
+ * g_pose: device FP32 [S_total, 6], S_total = the slices of all stacks in
+ * order; per slice k, with the slice transform world = R_k (u,v,w)^T + t_k:
+ *   g_pose[6k+0..2] = dL/dt_k (world frame),
+ *   g_pose[6k+3..5] = dL/domega_k for the rotation perturbed as
+ *                     R_k (I + [omega_k]x), omega_k in the slice's own frame
+ *                     (axes e_u, e_v, e_n), at omega_k = 0.
+ * The bins are those of the forward (piecewise constant in the poses, like
+ * the Gaussian gradients). Sums over a slice's records are FP64, fixed order.
+ * Errors: MG_ERR_STALE_WORKSPACE when no mg_render_bwd followed the matching
+ * forward on this workspace; MG_ERR_INVALID_ARG for NULL pointers.
+ */
+mg_status mg_render_pose_grad(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                              float *g_pose, void *ws, size_t ws_bytes, mg_stream_t stream);
+
+/*
  * Read-only introspection of a render workspace (for tests and tools): byte
  * offsets, inside the workspace, of the per-record arrays and of the tile
  * bins written by mg_render_fwd / mg_sample_volume. Records are ordered by

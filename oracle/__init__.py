@@ -203,6 +203,56 @@ def grad(G, stacks, rec: Records, gout: np.ndarray):
     return {"mean": gm, "quat": gq, "scale": gs, "alpha": gaa}
 
 
+def pose_grad(G, stacks, rec: Records, gout: np.ndarray) -> np.ndarray:
+    """Gradient of sum(gout * S^bin) with respect to each slice pose, records
+    frozen: [S, 6] = (dL/dt world, dL/domega) per slice, the rotation perturbed
+    as R (I + [omega]x) with omega in the slice frame (columns of R).
+
+    Moving a slice rigidly is the same, for that slice's values, as moving
+    every Gaussian by the inverse motion about the slice centre: a shift by
+    dt is mu -> mu - dt, a rotation R exp([omega]x) is mu -> t + W (mu - t)
+    and q -> w (x) q with W = R exp(-[omega]x) R^T, whose unit quaternion is
+    w = (1, -R omega / 2) to first order. So the pose gradient of slice k is
+    the chain of the Gaussian gradients of that slice alone (``grad`` on the
+    one-slice stack) through those motions. Expects unit quaternions.
+    Parity: pinned by central finite differences of ``render`` in the slice
+    transform (tests/test_oracle_pose.py)."""
+    import types
+
+    mu = np.asarray(G.mean, np.float64).reshape(-1, 3)
+    q = np.asarray(G.quat, np.float64).reshape(-1, 4)
+    go = np.asarray(gout, np.float64).reshape(-1)
+    S = sum(int(s.n_slices) for s in stacks)
+    out = np.zeros((S, 6))
+    k = 0
+    off = 0
+    for s in stacks:
+        xf_all = np.asarray(s.xform, np.float64).reshape(-1, 12)
+        for j in range(int(s.n_slices)):
+            xf = xf_all[j]
+            npx = int(s.H) * int(s.W)
+            sub = types.SimpleNamespace(n_slices=1, H=s.H, W=s.W, dx=s.dx, dy=s.dy, thickness=s.thickness,
+                                        xform=xf[None, :].copy(), n_vox=npx)
+            sel = rec.slice == k
+            rk = Records(np.zeros(int(sel.sum()), np.int32), rec.gid[sel].copy(), rec.rect[sel].copy())
+            gr = grad(G, [sub], rk, go[off:off + npx])
+            R = xf[:9].reshape(3, 3)
+            t = xf[9:]
+            gmu, gq = gr["mean"], gr["quat"]
+            out[k, :3] = -gmu.sum(axis=0)
+            d = (mu - t) @ R                      # d_i = R^T (mu_i - t), row-wise
+            out[k, 3:] = np.cross(gmu @ R, d).sum(axis=0)
+            qw, qv = q[:, 0], q[:, 1:]
+            for a in range(3):
+                v = -0.5 * R[:, a]                # vector part of the first-order quaternion of W
+                dq_w = -(qv @ v)
+                dq_v = qw[:, None] * v[None, :] + np.cross(np.broadcast_to(v, qv.shape), qv)
+                out[k, 3 + a] += float((gq[:, 0] * dq_w).sum() + (gq[:, 1:] * dq_v).sum())
+            k += 1
+            off += npx
+    return out
+
+
 def pair_counts(G, stacks, rec: Records, K: float = 3.0):
     """(pairs inside the K-sigma ellipsoid of Sigma' in FP64, evaluated pairs)."""
     L = lib()

@@ -64,6 +64,8 @@ SIGNATURES = {
                                      ctypes.POINTER(MgOpts), c_p, c_p, c_sz, c_p]),
     "mg_render_bwd": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                      ctypes.POINTER(MgOpts), c_p, c_p, c_p, c_p, c_p, c_p, c_sz, c_p]),
+    "mg_render_pose_grad": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
+                                           ctypes.POINTER(MgOpts), c_p, c_p, c_sz, c_p]),
     "mg_render_ws_layout": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                            ctypes.POINTER(MgOpts), ctypes.POINTER(MgWsLayout)]),
     "mg_sample_ws_layout": (ctypes.c_int, [c_i64, c_i32, ctypes.POINTER(MgOpts), ctypes.POINTER(MgWsLayout)]),

@@ -271,6 +271,7 @@ struct FwdTag {
     std::vector<const void *> xforms;
     float K, f64;
     long long capr, cape;
+    bool bwd_done = false;  // an mg_render_bwd has filled the moments since this forward
 };
 
 std::mutex g_tag_mu;
@@ -417,6 +418,7 @@ mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
         auto it = g_tags.find(ws);
         if (it == g_tags.end() || !same_tag(it->second, make_tag(g, st, o)))
             return fail(MG_ERR_STALE_WORKSPACE, "mg_render_bwd: no matching mg_render_fwd on this workspace");
+        it->second.bwd_done = true;
     }
     if (g->n == 0) return MG_OK;
     char *w = (char *)ws;
@@ -424,6 +426,37 @@ mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
     mg_launch_render_bwd(L, w, (const SliceDev *)(w + L.slices), tab, grad_out, g->mean, g->quat, g->scale, g->alpha,
                          g->n, o.f64_ratio, g_mean, g_quat, g_scale, g_alpha, (cudaStream_t)stream);
     return check_cuda("mg_render_bwd");
+}
+
+mg_status mg_render_pose_grad(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                              float *g_pose, void *ws, size_t ws_bytes, mg_stream_t stream)
+{
+    std::string why;
+    if (!valid_gauss(g, why)) return fail(MG_ERR_INVALID_ARG, why);
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (!valid_stacks(st, true, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (!g_pose || !ws) return fail(MG_ERR_INVALID_ARG, "g_pose or workspace is NULL");
+    long long S = 0;
+    for (const StackDesc &d : st) S += d.n_slices;
+    mg_opts o = resolve_opts(opts, g->n, S);
+    WsLayout L = make_layout(g->n, st, o);
+    if (ws_bytes < L.total) return fail(MG_ERR_INVALID_ARG, "workspace too small");
+    {
+        std::lock_guard<std::mutex> lk(g_tag_mu);
+        auto it = g_tags.find(ws);
+        if (it == g_tags.end() || !same_tag(it->second, make_tag(g, st, o)) || !it->second.bwd_done)
+            return fail(MG_ERR_STALE_WORKSPACE,
+                        "mg_render_pose_grad: no mg_render_bwd after the matching mg_render_fwd on this workspace");
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (g->n == 0) {
+        cudaMemsetAsync(g_pose, 0, sizeof(float) * 6 * (size_t)S, cs);
+        return check_cuda("mg_render_pose_grad");
+    }
+    char *w = (char *)ws;
+    mg_launch_pose_grad(L, w, (const SliceDev *)(w + L.slices), g->mean, g->quat, g->scale, g->alpha, o.f64_ratio,
+                        g_pose, cs);
+    return check_cuda("mg_render_pose_grad");
 }
 
 static mg_status fill_layout(const WsLayout &L, mg_ws_layout *out)

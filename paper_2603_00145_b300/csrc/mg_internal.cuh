@@ -155,6 +155,8 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
                           const float *grad_out, const float *mean, const float *quat, const float *scale,
                           const float *alpha, long long n, float f64_ratio, float *g_mean, float *g_quat,
                           float *g_scale, float *g_alpha, cudaStream_t st);
+void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, const float *mean, const float *quat,
+                         const float *scale, const float *alpha, float f64_ratio, float *g_pose, cudaStream_t st);
 // record geometry pass (one thread per record)
 void mg_launch_rec_geom(const WsLayout &L, char *ws, const SliceDev *slices, const float *mean, const float *quat,
                         const float *scale, const float *alpha, float K, float f64_ratio, cudaStream_t st);

@@ -365,9 +365,16 @@ __device__ __forceinline__ double c_rsqrt<double>(double x) { return 1.0 / sqrt(
 
 // Adjoint of the record geometry: (centre, conic, amp) of the record of a
 // Gaussian on a slice, given dL/d(pcx, pcy, A, B2, C, amp).
-template <typename T>
+// POSE: also the record's share of the slice-pose gradient, gpose[0..2] =
+// dL/dt (world) and gpose[3..5] = dL/domega for the slice rotation perturbed
+// as R (I + [omega]x) (omega in the slice frame). With d = R^T (mu - t) and
+// P = R^T R_gauss the record geometry's only slice-dependent inputs,
+// delta d = -omega x d and delta P = -[omega]x P, so dL/domega =
+// g_d x d + axial part of (P gP^T) (dL/dP = gP).
+template <typename T, bool POSE = false>
 __device__ void geometry_adjoint(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
-                                 T gA, T gB2, T gC, T gpx, T gpy, T gamp, T gmu[3], T gq[4], T gs[3], T &galpha)
+                                 T gA, T gB2, T gC, T gpx, T gpy, T gamp, T gmu[3], T gq[4], T gs[3], T &galpha,
+                                 T *gpose = nullptr)
 {
     // forward recomputation (same formulas as the record pass)
     T w = q[0], x = q[1], y = q[2], z = q[3];
@@ -436,6 +443,7 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     gD += f * iD * (gKuu * Huw * Huw + gKuv * Huw * Hvw + gKvv * Hvw * Hvw);
     T gHww = sig2 * gD;
     T gR[3][3];
+    T M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // P gP^T (POSE)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         T gg0 = 2 * gHuu * g[0][c] + gHuv * g[1][c] + gHuw * g[2][c];
@@ -451,9 +459,26 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
                 (gL0 * P[0][c] + gL1 * P[1][c] + gL2 * P[2][c]);
 #pragma unroll
         for (int r = 0; r < 3; ++r) gR[r][c] = Q[3 * r] * gP0 + Q[3 * r + 1] * gP1 + Q[3 * r + 2] * gP2;
+        if (POSE) {
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) {
+                M[a2][0] += P[a2][c] * gP0;
+                M[a2][1] += P[a2][c] * gP1;
+                M[a2][2] += P[a2][c] * gP2;
+            }
+        }
     }
 #pragma unroll
     for (int r = 0; r < 3; ++r) gmu[r] = Q[3 * r] * gdu + Q[3 * r + 1] * gdv + Q[3 * r + 2] * gw0;
+    if (POSE) {
+        const T u0 = Q[0] * p0 + Q[3] * p1 + Q[6] * p2, v0 = Q[1] * p0 + Q[4] * p1 + Q[7] * p2;
+        gpose[0] = -gmu[0];
+        gpose[1] = -gmu[1];
+        gpose[2] = -gmu[2];
+        gpose[3] = (gdv * w0 - gw0 * v0) + (M[2][1] - M[1][2]);
+        gpose[4] = (gw0 * u0 - gdu * w0) + (M[0][2] - M[2][0]);
+        gpose[5] = (gdu * v0 - gdv * u0) + (M[1][0] - M[0][1]);
+    }
     gq[0] = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
     gq[1] = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] +
                  w * gR[2][1] - 2 * x * gR[2][2]);
@@ -476,7 +501,7 @@ __global__ void k_zero_mom(float4 *mom, const WsHeader *hdr, long long cap_recor
 // of the record geometry -> the record's share of dL/d(mean, quat, scale,
 // alpha), written to its own 12-float slot (FP32 geometry; DBL: only the
 // records of near-degenerate Gaussians, in FP64)
-template <bool DBL>
+template <bool DBL, bool POSE = false>
 __global__ void k_chain_rec(const WsHeader *hdr, long long cap_records, const float4 *__restrict__ geo,
                             const float2 *__restrict__ geo2, const int *__restrict__ gid,
                             const int *__restrict__ rslice, const float *__restrict__ mom,
@@ -507,6 +532,20 @@ __global__ void k_chain_rec(const WsHeader *hdr, long long cap_records, const fl
         const float gpx = -la * (2.f * A * Sx + B2 * Sy);
         const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
         const SliceDev &Sd = slices[rslice[r]];
+        if (POSE) {
+            float o6[6];
+            if (DBL) {
+                double dm[3], dq[4], ds[3], da, dp[6];
+                geometry_adjoint<double, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, dm, dq, ds, da, dp);
+                for (int i = 0; i < 6; ++i) o6[i] = (float)dp[i];
+            } else {
+                float gm[3], gq[4], gs[3], ga;
+                geometry_adjoint<float, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga, o6);
+            }
+            rg[2 * r] = make_float4(o6[0], o6[1], o6[2], 0.f);
+            rg[2 * r + 1] = make_float4(o6[3], o6[4], o6[5], 0.f);
+            continue;
+        }
         float o[12];
         if (DBL) {
             double dm[3], dq[4], ds[3], da;
@@ -564,6 +603,37 @@ __global__ void k_chain_sum(long long n, const unsigned *__restrict__ goff, cons
     }
 }
 
+// K6c: one block per slice sums its records' pose shares (records of a slice
+// are contiguous) in a fixed order, in FP64
+__global__ void __launch_bounds__(256) k_pose_sum(int S, const unsigned *__restrict__ slice_rs,
+                                                  const float4 *__restrict__ rg, float *__restrict__ g_pose)
+{
+    __shared__ double red[6][8];
+    const int k = blockIdx.x;
+    if (k >= S) return;
+    const unsigned r0 = slice_rs[k], r1 = slice_rs[k + 1];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (unsigned r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const float4 a = rg[2 * (size_t)r], b = rg[2 * (size_t)r + 1];
+        acc[0] += a.x, acc[1] += a.y, acc[2] += a.z;
+        acc[3] += b.x, acc[4] += b.y, acc[5] += b.z;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0.0;
+        for (int j = 0; j < 8; ++j) v += red[threadIdx.x][j];
+        g_pose[6 * (size_t)k + threadIdx.x] = (float)v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -601,6 +671,28 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, fl
                                              (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
                                              (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), out,
                                              &hdr->tile_ctr[0]);
+}
+
+// Slice-pose gradient from the moments the last backward left in the workspace.
+void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, const float *mean, const float *quat,
+                         const float *scale, const float *alpha, float f64_ratio, float *g_pose, cudaStream_t st)
+{
+    const WsHeader *hdr = (const WsHeader *)(ws + L.hdr);
+    MG_PROF(MG_ST_CHAIN, st);
+    float4 *rg = (float4 *)(ws + L.rec_grad);
+    long long wr = (L.cap_records + 255) / 256;
+    int gr = (int)(wr < 148 * 16 ? (wr > 0 ? wr : 1) : 148 * 16);
+    k_chain_rec<false, true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
+                                                 (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
+                                                 (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
+                                                 slices, mean, quat, scale, alpha, f64_ratio, rg);
+    if (f64_ratio > 0.f)
+        k_chain_rec<true, true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
+                                                    (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
+                                                    (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
+                                                    slices, mean, quat, scale, alpha, f64_ratio, rg);
+    const unsigned *slice_rs = (const unsigned *)(ws + L.chunk_base) + (L.S + 1);
+    k_pose_sum<<<(unsigned)L.S, 256, 0, st>>>((int)L.S, slice_rs, rg, g_pose);
 }
 
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,

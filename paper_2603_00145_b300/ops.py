@@ -65,6 +65,17 @@ class DeviceStacks:
         self.n_slices = sum(int(s.n_slices) for s in self.stacks)
         self.n_tiles = sum(int(s.n_slices) * ((int(s.W) + 15) // 16) * ((int(s.H) + 15) // 16) for s in self.stacks)
 
+    def set_poses(self, xform_all: torch.Tensor):
+        """Overwrite the slice transforms in place (device [slices, 12], all
+        stacks in order); the device pointers the renderer holds stay valid."""
+        o = 0
+        for x in self.xforms:
+            x.copy_(xform_all[o:o + x.shape[0]])
+            o += x.shape[0]
+
+    def poses(self) -> torch.Tensor:
+        return torch.cat(self.xforms)
+
 
 # ---------------------------------------------------------------------------
 # the C ABI, one Python function per entry point
@@ -96,6 +107,14 @@ def mg_render_bwd(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts
     if raise_on_error:
         L.check(st, "mg_render_bwd")
     return st
+
+
+def mg_render_pose_grad(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, g_pose, ws, stream=None):
+    """g_pose: device FP32 [slices, 6] = (dL/dt world, dL/domega slice frame) per slice."""
+    g = _gauss(mean, quat, scale, alpha)
+    _dev(g_pose, "g_pose", numel=6 * stacks.n_slices)
+    L.check(L.lib().mg_render_pose_grad(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts), g_pose.data_ptr(),
+                                        ws.data_ptr(), ws.numel(), _stream_handle(stream)), "mg_render_pose_grad")
 
 
 def mg_render_ws_layout(n: int, stacks: DeviceStacks, opts: L.MgOpts) -> dict:
@@ -327,6 +346,11 @@ class SliceRenderer:
         L.check(st, "mg_render_bwd")
         return g
 
+    def pose_grad(self, mean, quat, scale, alpha):
+        """dL/d(slice pose) [slices, 6] of the loss whose dL/dI the last
+        backward received: (dL/dt world, dL/domega slice frame)."""
+        return _slice_pose_grad(self, mean, quat, scale, alpha)
+
 
 class DeviceAdam:
     """Adam over parameter groups with the whole update in mg_adam_step (one
@@ -363,6 +387,12 @@ class DeviceAdam:
     @property
     def steps(self) -> int:
         return int(self.step_t.item())
+
+
+def _slice_pose_grad(renderer, mean, quat, scale, alpha):
+    g = torch.empty(renderer.dev.n_slices, 6, dtype=_F32, device=mean.device)
+    mg_render_pose_grad(mean, quat, scale, alpha, renderer.dev, renderer.opts(), g, renderer.ws)
+    return g
 
 
 class RenderSlices(torch.autograd.Function):

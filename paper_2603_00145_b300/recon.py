@@ -300,6 +300,62 @@ def fit(stacks, target, G_init, centre, half_extent, cfg: FitConfig, device="cud
                             "seconds_eager": t_eager, "seconds_capture": t_capture, "seconds_replay": t_replay}
 
 
+def _rotvec_to_matrix(w: torch.Tensor) -> torch.Tensor:
+    """Rodrigues' formula, [S,3] -> [S,3,3] (FP64)."""
+    th = torch.linalg.norm(w, dim=1, keepdim=True)
+    k = w / th.clamp_min(1e-30)
+    K = torch.zeros(w.shape[0], 3, 3, dtype=w.dtype, device=w.device)
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 0] = -k[:, 2], k[:, 1], k[:, 2]
+    K[:, 1, 2], K[:, 2, 0], K[:, 2, 1] = -k[:, 0], -k[:, 1], k[:, 0]
+    s, c = torch.sin(th)[:, :, None], torch.cos(th)[:, :, None]
+    eye = torch.eye(3, dtype=w.dtype, device=w.device).expand_as(K)
+    return eye + s * K + (1 - c) * (K @ K)
+
+
+def register_slices(renderer: ops.SliceRenderer, mean, quat, scale, alpha, target, iterations: int = 100,
+                    lr_t: float = 0.05, lr_r: float = 0.01, lr_final: float = 0.02):
+    """Slice-to-volume registration against fixed Gaussians: the slice poses
+    T_k (Sec. 3.3.2) are corrected by Adam (mg_adam_step) on the pose
+    gradient of the L1+L2 slice loss (mg_render_pose_grad), the learning
+    rates decaying exponentially to ``lr_final`` of their start. Each pose is
+    composed from the starting transform as t = t0 + dt, R = R0 Exp(omega);
+    the pose gradient is taken at the current pose (omega in the slice
+    frame). The renderer's transforms are updated in place. Returns the loss
+    history."""
+    dev = mean.device
+    D = renderer.dev
+    x0 = D.poses().double()
+    S = x0.shape[0]
+    R0, t0 = x0[:, :9].reshape(S, 3, 3), x0[:, 9:]
+    dt = torch.zeros(S, 3, dtype=torch.float32, device=dev)
+    om = torch.zeros(S, 3, dtype=torch.float32, device=dev)
+    adam = ops.DeviceAdam([{"param": dt, "lr": lr_t}, {"param": om, "lr": lr_r}])
+    n = target.numel()
+    grad = torch.empty(n, dtype=torch.float32, device=dev)
+    out = torch.empty(2, dtype=torch.float64, device=dev)
+    ws = torch.empty(ops.mg_reduce_workspace_size(n), dtype=torch.uint8, device=dev)
+
+    def apply():
+        R = R0 @ _rotvec_to_matrix(om.double())
+        D.set_poses(torch.cat([R.reshape(S, 9), t0 + dt.double()], dim=1).float())
+
+    hist = []
+    for it in range(iterations):
+        decay = lr_final ** (it / max(iterations - 1, 1))
+        adam.groups[0]["lr"], adam.groups[1]["lr"] = lr_t * decay, lr_r * decay
+        apply()
+        pred = renderer.forward(mean, quat, scale, alpha)
+        ops.mg_loss_l1l2(pred, target, grad, out, ws)
+        renderer.backward(mean, quat, scale, alpha, grad)
+        g = renderer.pose_grad(mean, quat, scale, alpha)
+        dt.grad = g[:, :3].contiguous()
+        om.grad = g[:, 3:].contiguous()
+        adam.step()
+        hist.append(float(out[0]))
+    apply()
+    return hist
+
+
 def sample(model: Model, nrf, G_dim: int, spacing: float, centre=(0.0, 0.0, 0.0), cutoff_k: float = 3.0,
            batch: int = 1 << 22):
     """The isotropic G^3 volume (z, y, x): Gaussian mixture (Eq. E7) plus the
