@@ -15,6 +15,10 @@
  *     Sigma'_i = Sigma_i + sig_s^2 n_k n_k^T,   sig_s^2 = FWHM^2 / (8 ln 2),
  *
  * which is Eq. E7 exactly when the thickness is 0 (volume sampling, Sec. 3.1).
+ * A stack may also carry an in-plane Gaussian PSF (FWHM psf_u, psf_v along
+ * the slice axes e_u, e_v; the paper models none): the full 3-D PSF
+ * P = diag(psf_u^2, psf_v^2, thickness^2)/(8 ln 2) in the slice frame adds to
+ * the covariance the same way, Sigma'_i = Sigma_i + R_k P R_k^T.
  * Like the paper's local Gaussian set G_local (Sec. 3.3.1), the sum is
  * restricted per 16x16 voxel tile: Gaussian i contributes to every voxel of a
  * tile of slice k iff its (i,k) record lists that tile (the record predicate
@@ -42,8 +46,9 @@
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v);  Sww = Lww + sig2;  K2 = K*K;
  *   sig2 = (float)(thickness^2 * 0.18033688011112042) (computed in double);
  *   the record exists iff  w0*w0 <= K2*Sww  (the K-sigma slab test); its pixel box:
- *   r2 = max(K2 - (w0*w0)/Sww, 0);  Cuu = max(Luu - (Luw*Luw)/Sww, 0);
- *   Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0);  cu = u0 - (Luw*w0)/Sww;  cv = v0 - (Lvw*w0)/Sww;
+ *   r2 = max(K2 - (w0*w0)/Sww, 0);  Cuu = max(Luu - (Luw*Luw)/Sww, 0) + pu2;
+ *   Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0) + pv2;  cu = u0 - (Luw*w0)/Sww;  cv = v0 - (Lvw*w0)/Sww;
+ *   pu2 = (float)(psf_u^2 * 0.18033688011112042), pv2 likewise (computed in double);
  *   ru = sqrt(r2*Cuu), rv = sqrt(r2*Cvv);  hx = 0.5*(W-1), hy = 0.5*(H-1);
  *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx),
  *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy);
@@ -102,6 +107,7 @@ typedef struct {
     float dx, dy;           /* pixel spacing (mm), > 0 */
     float thickness;        /* slice-profile FWHM (mm), >= 0; 0 = point sampling (Eq. E7) */
     const float *xform;     /* device [n_slices,12] */
+    float psf_u, psf_v;     /* in-plane Gaussian PSF FWHM (mm) along e_u, e_v, >= 0; 0 = none */
 } mg_stack;
 
 typedef struct {

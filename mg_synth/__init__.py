@@ -66,6 +66,8 @@ class Stack:
     dy: float
     thickness: float          # slice-profile FWHM in mm; 0 = point sampling
     xform: np.ndarray         # [n_slices,12] float32
+    psf_u: float = 0.0        # in-plane PSF FWHM (mm) along e_u; 0 = none
+    psf_v: float = 0.0        # in-plane PSF FWHM (mm) along e_v
 
     def __post_init__(self):
         self.xform = np.ascontiguousarray(self.xform, dtype=np.float32).reshape(self.n_slices, 12)
@@ -128,7 +130,7 @@ SAGITTAL = np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], dtype=np.float64)   # u=y
 def make_stack(frame: np.ndarray, n_slices: int, H: int, W: int, dx: float, dy: float,
                thickness: float, spacing: float, centre=(0.0, 0.0, 0.0),
                rng: np.random.Generator | None = None, max_rot_deg: float = 0.0,
-               max_trans_mm: float = 0.0) -> Stack:
+               max_trans_mm: float = 0.0, psf_u: float = 0.0, psf_v: float = 0.0) -> Stack:
     """A stack of parallel slices along ``frame``'s third column, ``spacing`` mm apart,
     centred on ``centre``; optional per-slice rigid motion (random axis, angle up
     to ``max_rot_deg``; translation uniform in a ball of ``max_trans_mm``)."""
@@ -147,7 +149,8 @@ def make_stack(frame: np.ndarray, n_slices: int, H: int, W: int, dx: float, dy: 
             tk = tk + d
         xf[k, :9] = Rk.reshape(-1)
         xf[k, 9:] = tk
-    return Stack(n_slices, H, W, float(dx), float(dy), float(thickness), xf.astype(np.float32))
+    return Stack(n_slices, H, W, float(dx), float(dy), float(thickness), xf.astype(np.float32), float(psf_u),
+                 float(psf_v))
 
 
 def volume_stack(G: int, spacing: float, centre=(0.0, 0.0, 0.0)) -> Stack:
@@ -383,7 +386,7 @@ def pick_slices(stacks: Sequence[Stack], picks):
     out, ranges = [], []
     for si, k in picks:
         s = stacks[si]
-        out.append(Stack(1, s.H, s.W, s.dx, s.dy, s.thickness, s.xform[k:k + 1]))
+        out.append(Stack(1, s.H, s.W, s.dx, s.dy, s.thickness, s.xform[k:k + 1], s.psf_u, s.psf_v))
         o = bases[si] + k * s.H * s.W
         ranges.append((o, o + s.H * s.W))
     return out, ranges

@@ -53,13 +53,14 @@ def lib():
         p = ctypes.c_void_p
         i64 = ctypes.c_int64
         L.or_make_records.restype = i64
-        L.or_make_records.argtypes = [i64, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, ctypes.c_float, i64, p, p, p]
+        L.or_make_records.argtypes = [i64, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, ctypes.c_float, i64, p, p,
+                                      p]
         L.or_render.restype = None
-        L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, i64, p, p, p, ctypes.c_int, p]
+        L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, ctypes.c_int, p]
         L.or_grad.restype = None
-        L.or_grad.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p]
+        L.or_grad.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p]
         L.or_pair_counts.restype = None
-        L.or_pair_counts.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, i64, p, p, p,
+        L.or_pair_counts.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p,
                                      ctypes.c_double, p]
         _lib = L
     return _lib
@@ -82,12 +83,14 @@ class _StackArgs:
         self.dx = np.array([s.dx for s in stacks], dtype=dtype)
         self.dy = np.array([s.dy for s in stacks], dtype=dtype)
         self.thk = np.array([s.thickness for s in stacks], dtype=dtype)
+        self.psf = np.array([[getattr(s, "psf_u", 0.0), getattr(s, "psf_v", 0.0)] for s in stacks],
+                            dtype=dtype).reshape(-1)
         self.xf = np.ascontiguousarray(np.concatenate([np.asarray(s.xform).reshape(-1, 12) for s in stacks])
                                        .astype(dtype))
 
     def args(self):
         return [self.n, _ptr(self.nsl), _ptr(self.H), _ptr(self.W), _ptr(self.dx), _ptr(self.dy), _ptr(self.thk),
-                _ptr(self.xf)]
+                _ptr(self.psf), _ptr(self.xf)]
 
 
 def _gargs(G, dtype=np.float32):
@@ -232,6 +235,7 @@ def pose_grad(G, stacks, rec: Records, gout: np.ndarray) -> np.ndarray:
             xf = xf_all[j]
             npx = int(s.H) * int(s.W)
             sub = types.SimpleNamespace(n_slices=1, H=s.H, W=s.W, dx=s.dx, dy=s.dy, thickness=s.thickness,
+                                        psf_u=getattr(s, "psf_u", 0.0), psf_v=getattr(s, "psf_v", 0.0),
                                         xform=xf[None, :].copy(), n_vox=npx)
             sel = rec.slice == k
             rk = Records(np.zeros(int(sel.sum()), np.int32), rec.gid[sel].copy(), rec.rect[sel].copy())

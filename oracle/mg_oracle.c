@@ -21,6 +21,10 @@
  *                      alpha sqrt(|Sigma| / |Sigma'|) exp(-1/2 y^T Sigma'^-1 y),
  *                      Sigma' = Sigma + sig2 n n^T, y = x - mu. With sig2 = 0
  *                      this is E7 exactly.
+ *   In-plane PSF:      a stack may add a Gaussian PSF of FWHM pu, pv along the
+ *                      slice axes e_u, e_v (the paper models none): then
+ *                      Sigma' = Sigma + R_k diag(pu^2, pv^2, th^2) R_k^T / (8 ln 2)
+ *                      with the same form of the term.
  *   Truncation:        the paper already restricts the sum to a local set
  *                      G_local (Sec. 3.3.1). Here the local set of a slice
  *                      voxel is the set of Gaussians whose record for that
@@ -39,7 +43,7 @@
  *   Sww = Lww + sig2;  K2 = K*K
  *   the record exists iff  w0*w0 <= K2*Sww  (the K-sigma slab test)
  *   r2 = max(K2 - (w0*w0)/Sww, 0)
- *   Cuu = max(Luu - (Luw*Luw)/Sww, 0),  Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0)
+ *   Cuu = max(Luu - (Luw*Luw)/Sww, 0) + pu2,  Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0) + pv2
  *   cu = u0 - (Luw*w0)/Sww,  cv = v0 - (Lvw*w0)/Sww
  *   ru = sqrt(r2*Cuu),  rv = sqrt(r2*Cvv)
  *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx), hx = 0.5*(W-1)
@@ -48,7 +52,8 @@
  *   jh>=0 (false for NaN); a non-empty box has il,jl clamped up to 0 and ih,jh
  *   down to W-1,H-1 and lists the tiles [il/16, ih/16] x [jl/16, jh/16]
  *   (integer division); an empty box lists none (rectangle (1,1,0,0))
- *   sig2 = (float)(thickness^2 * 0.18033688011112042) computed in double.
+ *   sig2 = (float)(thickness^2 * 0.18033688011112042) computed in double,
+ *   pu2, pv2 likewise from the in-plane PSF FWHM (0 without a PSF).
  * (u,v) bounds of the ellipse {y : y^T Sigma'^-1 y <= K^2} cut by the plane
  * w = 0 are cu +- ru, cv +- rv: the in-plane conditional covariance of Sigma'
  * is C = Sigma'_uv - Sigma'_uv,w Sigma'_w,uv / Sww and the cut ellipse has
@@ -67,16 +72,17 @@
 /* ------------------------------------------------------------------ */
 typedef struct {
     int H, W, TX, TY;
-    float dx, dy, thk;
+    float dx, dy, thk, pu, pv; /* pu, pv: in-plane PSF FWHM along e_u, e_v (0 = none) */
     const float *xf;   /* 12 floats: Q row-major, then t (record predicate) */
-    double dxd, dyd, thkd;
+    double dxd, dyd, thkd, pud, pvd;
     const double *xfd; /* the same in FP64 (evaluation) */
     int64_t out_base;  /* offset of this slice's [H,W] image in the output */
 } or_slice;
 
 static or_slice *or_build_slices(int n_stacks, const int32_t *nsl, const int32_t *H, const int32_t *W,
-                                 const float *dx, const float *dy, const float *thk, const float *xform,
-                                 const double *dxd, const double *dyd, const double *thkd, const double *xformd,
+                                 const float *dx, const float *dy, const float *thk, const float *psf,
+                                 const float *xform, const double *dxd, const double *dyd, const double *thkd,
+                                 const double *psfd, const double *xformd,
                                  int *S_out)
 {
     int S = 0;
@@ -94,12 +100,16 @@ static or_slice *or_build_slices(int n_stacks, const int32_t *nsl, const int32_t
                 sl[k].dx = dx[s];
                 sl[k].dy = dy[s];
                 sl[k].thk = thk[s];
+                sl[k].pu = psf[2 * s];
+                sl[k].pv = psf[2 * s + 1];
                 sl[k].xf = xform + (size_t)k * 12;
             }
             if (xformd) {
                 sl[k].dxd = dxd[s];
                 sl[k].dyd = dyd[s];
                 sl[k].thkd = thkd[s];
+                sl[k].pud = psfd[2 * s];
+                sl[k].pvd = psfd[2 * s + 1];
                 sl[k].xfd = xformd + (size_t)k * 12;
             }
             sl[k].out_base = base;
@@ -171,10 +181,14 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     if (!(ww <= K2 * Sww)) return 0;
     float r2 = K2 - ww / Sww;
     if (r2 < 0.0f) r2 = 0.0f;
+    float pu2 = (float)((double)sl->pu * (double)sl->pu * OR_FWHM2VAR);
+    float pv2 = (float)((double)sl->pv * (double)sl->pv * OR_FWHM2VAR);
     float Cuu = Luu - (Luw * Luw) / Sww;
     if (Cuu < 0.0f) Cuu = 0.0f;
+    Cuu = Cuu + pu2;
     float Cvv = Lvv - (Lvw * Lvw) / Sww;
     if (Cvv < 0.0f) Cvv = 0.0f;
+    Cvv = Cvv + pv2;
     float cu = u0 - (Luw * w0) / Sww;
     float cv = v0 - (Lvw * w0) / Sww;
     float ru = sqrtf(r2 * Cuu), rv = sqrtf(r2 * Cvv);
@@ -203,11 +217,12 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
  * within a slice. Returns the total; fills at most cap. */
 int64_t or_make_records(int64_t n, const float *mean, const float *quat, const float *scale, int n_stacks,
                         const int32_t *nsl, const int32_t *H, const int32_t *W, const float *dx, const float *dy,
-                        const float *thk, const float *xform, float K, int64_t cap, int32_t *rec_slice,
+                        const float *thk, const float *psf, const float *xform, float K, int64_t cap,
+                        int32_t *rec_slice,
                         int32_t *rec_gid, int32_t *rec_rect)
 {
     int S;
-    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, dx, dy, thk, xform, NULL, NULL, NULL, NULL, &S);
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, dx, dy, thk, psf, xform, NULL, NULL, NULL, NULL, NULL, &S);
     int64_t *cnt = (int64_t *)calloc((size_t)S + 1, sizeof(int64_t));
 #pragma omp parallel for schedule(dynamic)
     for (int k = 0; k < S; ++k) {
@@ -327,11 +342,17 @@ static void term_setup(const double *mu, const double *q, const double *s, doubl
     cov_d(q, s, T->Sg, T->R);
     double dS;
     inv3(T->Sg, T->Sgi, &dS);
+    /* Sigma' = Sigma + R_k diag(pu^2, pv^2, sig^2) R_k^T: the slice's 3-D PSF
+     * (in-plane PSF and slice profile) in world coordinates */
     const double *Q = sl->xfd;
-    double n[3] = {Q[2], Q[5], Q[8]};
-    double sig2 = sl->thkd * sl->thkd * OR_FWHM2VAR;
+    double var[3] = {sl->pud * sl->pud * OR_FWHM2VAR, sl->pvd * sl->pvd * OR_FWHM2VAR,
+                     sl->thkd * sl->thkd * OR_FWHM2VAR};
     for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) T->Sp[r][c] = T->Sg[r][c] + sig2 * n[r] * n[c];
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int a = 0; a < 3; ++a) acc += Q[3 * r + a] * var[a] * Q[3 * c + a];
+            T->Sp[r][c] = T->Sg[r][c] + acc;
+        }
     double dSp;
     inv3(T->Sp, T->P, &dSp);
     T->c = sqrt(dS / dSp);
@@ -366,11 +387,12 @@ static double quad_form(const or_term *T, const double x[3], double y[3], double
 /* exact = 0: S^bin from the records; exact = 1: every Gaussian at every pixel. */
 void or_render(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
                const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy,
-               const double *thk, const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
+               const double *thk, const double *psf, const double *xform, int64_t nrec, const int32_t *rec_slice,
+               const int32_t *rec_gid,
                const int32_t *rec_rect, int exact, double *out)
 {
     int S;
-    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, dx, dy, thk, xform, &S);
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
     int64_t total = 0;
     for (int k = 0; k < S; ++k) total += (int64_t)sl[k].H * sl[k].W;
     memset(out, 0, sizeof(double) * (size_t)total);
@@ -438,12 +460,12 @@ void or_render(int64_t n, const double *mean, const double *quat, const double *
  */
 void or_grad(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
              const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy, const double *thk,
-             const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
+             const double *psf, const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
              const int32_t *rec_rect, const double *gout, double *gmean, double *gquat, double *gscale,
              double *galpha)
 {
     int S;
-    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, dx, dy, thk, xform, &S);
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
     double *rg = (double *)calloc((size_t)(nrec > 0 ? nrec : 1) * 11, sizeof(double));
 #pragma omp parallel for schedule(dynamic)
     for (int64_t r = 0; r < nrec; ++r) {
@@ -525,12 +547,13 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
  * (FP64), counts[1] = all evaluated pairs (record, pixel in a listed tile). */
 void or_pair_counts(int64_t n_unused, const double *mean, const double *quat, const double *scale, const double *alpha,
                     int n_stacks, const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx,
-                    const double *dy, const double *thk, const double *xform, int64_t nrec, const int32_t *rec_slice,
+                    const double *dy, const double *thk, const double *psf, const double *xform, int64_t nrec,
+                    const int32_t *rec_slice,
                     const int32_t *rec_gid, const int32_t *rec_rect, double K, int64_t *counts)
 {
     (void)n_unused;
     int S;
-    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, dx, dy, thk, xform, &S);
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
     int64_t inside = 0, evald = 0;
 #pragma omp parallel for schedule(dynamic) reduction(+ : inside, evald)
     for (int64_t r = 0; r < nrec; ++r) {

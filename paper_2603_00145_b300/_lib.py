@@ -19,7 +19,7 @@ class MgGaussians(ctypes.Structure):
 
 class MgStack(ctypes.Structure):
     _fields_ = [("n_slices", c_i32), ("H", c_i32), ("W", c_i32), ("dx", c_f32), ("dy", c_f32),
-                ("thickness", c_f32), ("xform", c_p)]
+                ("thickness", c_f32), ("xform", c_p), ("psf_u", c_f32), ("psf_v", c_f32)]
 
 
 class MgOpts(ctypes.Structure):

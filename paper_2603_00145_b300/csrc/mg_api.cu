@@ -95,6 +95,7 @@ struct StackDesc {
     int n_slices, H, W;
     float dx, dy, thickness;
     const float *xform;
+    float psf_u, psf_v;
 };
 
 mg_opts resolve_opts(const mg_opts *o, long long n, long long S)
@@ -127,6 +128,10 @@ bool valid_stacks(const std::vector<StackDesc> &st, bool need_xform, std::string
         if (!(d.dx > 0.f) || !(d.dy > 0.f) || !(d.thickness >= 0.f) || !isfinite(d.dx) || !isfinite(d.dy) ||
             !isfinite(d.thickness)) {
             why = "stack " + std::to_string(s) + ": need dx, dy > 0 and thickness >= 0, finite";
+            return false;
+        }
+        if (!(d.psf_u >= 0.f) || !(d.psf_v >= 0.f) || !isfinite(d.psf_u) || !isfinite(d.psf_v)) {
+            why = "stack " + std::to_string(s) + ": need psf_u, psf_v >= 0, finite";
             return false;
         }
         if (need_xform && !d.xform) {
@@ -231,6 +236,8 @@ StackIn make_stack_in(const std::vector<StackDesc> &st)
         in.dx[s] = st[s].dx;
         in.dy[s] = st[s].dy;
         in.sig2[s] = (float)((double)st[s].thickness * (double)st[s].thickness * FWHM2VAR);
+        in.pu2[s] = (float)((double)st[s].psf_u * (double)st[s].psf_u * FWHM2VAR);
+        in.pv2[s] = (float)((double)st[s].psf_v * (double)st[s].psf_v * FWHM2VAR);
         in.xform[s] = st[s].xform;
     }
     return in;
@@ -242,7 +249,7 @@ std::vector<StackDesc> to_desc(const mg_stack *stacks, int n_stacks)
     if (!stacks || n_stacks < 1 || n_stacks > MG_MAX_STACKS) return v;
     for (int s = 0; s < n_stacks; ++s)
         v.push_back({stacks[s].n_slices, stacks[s].H, stacks[s].W, stacks[s].dx, stacks[s].dy, stacks[s].thickness,
-                     stacks[s].xform});
+                     stacks[s].xform, stacks[s].psf_u, stacks[s].psf_v});
     return v;
 }
 
@@ -286,7 +293,8 @@ FwdTag make_tag(const mg_gaussians *g, const std::vector<StackDesc> &st, const m
     t.p[2] = g->scale;
     t.p[3] = g->alpha;
     for (const StackDesc &d : st) {
-        t.stack_key.insert(t.stack_key.end(), {(float)d.n_slices, (float)d.H, (float)d.W, d.dx, d.dy, d.thickness});
+        t.stack_key.insert(t.stack_key.end(),
+                           {(float)d.n_slices, (float)d.H, (float)d.W, d.dx, d.dy, d.thickness, d.psf_u, d.psf_v});
         t.xforms.push_back(d.xform);
     }
     t.K = o.cutoff_k;
@@ -485,7 +493,7 @@ mg_status mg_render_ws_layout(const mg_gaussians *g, const mg_stack *stacks, int
 mg_status mg_sample_ws_layout(int64_t n, int32_t G, const mg_opts *opts, mg_ws_layout *out)
 {
     if (!out || n < 0 || G < 1 || G > 1024) return fail(MG_ERR_INVALID_ARG, "bad arguments");
-    std::vector<StackDesc> st = {{G, G, G, 1.f, 1.f, 0.f, nullptr}};
+    std::vector<StackDesc> st = {{G, G, G, 1.f, 1.f, 0.f, nullptr, 0.f, 0.f}};
     return fill_layout(make_layout(n, st, resolve_opts(opts, n, G)), out);
 }
 
@@ -506,9 +514,9 @@ mg_status mg_render_stats_get(const void *ws, size_t ws_bytes, mg_render_stats *
     stats->records = (int64_t)h.n_records;
     stats->entries = (int64_t)h.n_entries;
     long long tiles = 0;
-    for (size_t s = 0; s < tag.stack_key.size() / 6; ++s) {
-        long long ns = (long long)tag.stack_key[6 * s], H = (long long)tag.stack_key[6 * s + 1],
-                  W = (long long)tag.stack_key[6 * s + 2];
+    for (size_t s = 0; s < tag.stack_key.size() / 8; ++s) {
+        long long ns = (long long)tag.stack_key[8 * s], H = (long long)tag.stack_key[8 * s + 1],
+                  W = (long long)tag.stack_key[8 * s + 2];
         tiles += ns * ((W + 15) / 16) * ((H + 15) / 16);
     }
     stats->tiles = tiles;
@@ -525,7 +533,7 @@ mg_status mg_render_stats_get(const void *ws, size_t ws_bytes, mg_render_stats *
 size_t mg_sample_workspace_size(int64_t n, int32_t G, const mg_opts *opts)
 {
     if (n < 0 || G < 1 || G > 1024) return 0;
-    std::vector<StackDesc> st = {{G, G, G, 1.f, 1.f, 0.f, nullptr}};
+    std::vector<StackDesc> st = {{G, G, G, 1.f, 1.f, 0.f, nullptr, 0.f, 0.f}};
     mg_opts o = resolve_opts(opts, n, G);
     return make_layout(n, st, o).total;
 }

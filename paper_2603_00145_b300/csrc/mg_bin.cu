@@ -44,6 +44,8 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
     d.dx = in.dx[s];
     d.dy = in.dy[s];
     d.sig2 = in.sig2[s];
+    d.pu2 = in.planes ? 0.f : in.pu2[s];
+    d.pv2 = in.planes ? 0.f : in.pv2[s];
     d.hx = 0.5f * (float)(d.W - 1);
     d.hy = 0.5f * (float)(d.H - 1);
     d.same_frame = 0;
@@ -301,8 +303,10 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     if (r2 < 0.0f) r2 = 0.0f;
     float Cuu = __fsub_rn(f.Luu, __fdiv_rn(__fmul_rn(f.Luw, f.Luw), Sww));
     if (Cuu < 0.0f) Cuu = 0.0f;
+    Cuu = __fadd_rn(Cuu, S.pu2);
     float Cvv = __fsub_rn(f.Lvv, __fdiv_rn(__fmul_rn(f.Lvw, f.Lvw), Sww));
     if (Cvv < 0.0f) Cvv = 0.0f;
+    Cvv = __fadd_rn(Cvv, S.pv2);
     float cu = __fsub_rn(u0, __fdiv_rn(__fmul_rn(f.Luw, w0), Sww));
     float cv = __fsub_rn(v0, __fdiv_rn(__fmul_rn(f.Lvw, w0), Sww));
     float ru = __fsqrt_rn(__fmul_rn(r2, Cuu));
@@ -423,7 +427,25 @@ __device__ void record_geometry(const float *mu, const float *q, const float *s,
     o.A = kap * Kuu * dx * dx;
     o.B2 = 2 * kap * Kuv * dx * dy;
     o.C = kap * Kvv * dy * dy;
-    o.amp = (T)alpha * rD * t_exp<T>((T)(-0.5) * w0 * wS);
+    T amp = (T)alpha * rD * t_exp<T>((T)(-0.5) * w0 * wS);
+    if (S.pu2 > 0.f || S.pv2 > 0.f) {
+        // in-plane PSF: the conditional covariance C = K^-1 gains diag(pu2, pv2):
+        // (K^-1 + P)^-1 = [[Kuu + pv2 |K|, Kuv], [Kuv, Kvv + pu2 |K|]] / m,
+        // m = det(I + P K) = 1 + pu2 Kuu + pv2 Kvv + pu2 pv2 |K|; |Sigma'| grows by m
+        const T pu2 = (T)S.pu2, pv2 = (T)S.pv2;
+        const T dK = Kuu * Kvv - Kuv * Kuv;
+        const T m = 1 + pu2 * Kuu + pv2 * Kvv + pu2 * pv2 * dK;
+        const T im = t_rcp<T>(m);
+        const T nu = (Kuu + pv2 * dK) * im, nv = (Kvv + pu2 * dK) * im;
+        Kuv = Kuv * im;
+        Kuu = nu;
+        Kvv = nv;
+        amp = amp * t_rsqrt<T>(m);
+        o.A = kap * Kuu * dx * dx;
+        o.B2 = 2 * kap * Kuv * dx * dy;
+        o.C = kap * Kvv * dy * dy;
+    }
+    o.amp = amp;
     T r2 = (T)K2 - w0 * wS;  // the cut ellipse is q <= r2 (natural units)
     o.thr = kap * (r2 > 0 ? r2 : (T)0);
 }

@@ -24,6 +24,7 @@ struct SliceDev {
     float Q[9];  // rotation, row-major (columns e_u, e_v, e_n)
     float t[3];
     float sig2;  // FP32 profile variance (record predicate)
+    float pu2, pv2;  // FP32 in-plane PSF variances along e_u, e_v (0: none)
     float dx, dy, hx, hy;  // spacing, 0.5*(W-1), 0.5*(H-1)
     int W, H, TX, TY;
     int tile_base;  // global index of tile (0,0)
@@ -50,6 +51,7 @@ struct StackIn {
     int n_slices[MG_MAX_STACKS];
     int H[MG_MAX_STACKS], W[MG_MAX_STACKS];
     float dx[MG_MAX_STACKS], dy[MG_MAX_STACKS], sig2[MG_MAX_STACKS];
+    float pu2[MG_MAX_STACKS], pv2[MG_MAX_STACKS];
     const float *xform[MG_MAX_STACKS];
     // volume-plane mode (inference sampling): one stack of G z-planes built
     // from centre / spacing instead of xform

@@ -426,6 +426,26 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     T gKuv = gB2 * 2 * kap * dx * dy;
     T gKvv = gC * kap * dy * dy;
     T gcu = gpx * c_rcp<T>(dx), gcv = gpy * c_rcp<T>(dy);
+    if (S.pu2 > 0.f || S.pv2 > 0.f) {
+        // adjoint of the in-plane PSF step K -> (K^-1 + P)^-1, amp -> amp m^-1/2
+        // (record pass): gradients with respect to the PSF-free K and amp
+        T Huu = g[0][0] * g[0][0] + g[0][1] * g[0][1] + g[0][2] * g[0][2];
+        T Huv = g[0][0] * g[1][0] + g[0][1] * g[1][1] + g[0][2] * g[1][2];
+        T Hvv = g[1][0] * g[1][0] + g[1][1] * g[1][1] + g[1][2] * g[1][2];
+        T K0uu = Huu - f * Huw * Huw, K0uv = Huv - f * Huw * Hvw, K0vv = Hvv - f * Hvw * Hvw;
+        const T pu2 = (T)S.pu2, pv2 = (T)S.pv2;
+        T dK = K0uu * K0vv - K0uv * K0uv;
+        T m = 1 + pu2 * K0uu + pv2 * K0vv + pu2 * pv2 * dK;
+        T im = c_rcp<T>(m), rm = c_rsqrt<T>(m);
+        T Kpuu = (K0uu + pv2 * dK) * im, Kpuv = K0uv * im, Kpvv = (K0vv + pu2 * dK) * im;
+        T gm = -(gKuu * Kpuu + gKuv * Kpuv + gKvv * Kpvv) * im - (T)0.5 * gamp * amp * rm * im;
+        T gNuu = gKuu * im, gNuv = gKuv * im, gNvv = gKvv * im;
+        T gdK = pv2 * gNuu + pu2 * gNvv + gm * pu2 * pv2;
+        gKuu = gNuu + gm * pu2 + gdK * K0vv;
+        gKvv = gNvv + gm * pv2 + gdK * K0uu;
+        gKuv = gNuv - 2 * gdK * K0uv;
+        gamp = gamp * rm;
+    }
     galpha = gamp * rD * E;
     T ga = gamp * amp;
     T gD = (T)(-0.5) * ga * iD;

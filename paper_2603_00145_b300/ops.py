@@ -58,7 +58,7 @@ class DeviceStacks:
         arr = (L.MgStack * len(self.stacks))()
         for i, (s, x) in enumerate(zip(self.stacks, self.xforms)):
             arr[i] = L.MgStack(int(s.n_slices), int(s.H), int(s.W), float(s.dx), float(s.dy), float(s.thickness),
-                               x.data_ptr())
+                               x.data_ptr(), float(getattr(s, "psf_u", 0.0)), float(getattr(s, "psf_v", 0.0)))
         self.arr = arr
         self.n = len(self.stacks)
         self.n_vox = sum(int(s.n_slices) * int(s.H) * int(s.W) for s in self.stacks)

@@ -42,6 +42,14 @@ def test_pose_gradient_mixed_stacks(seed):
     _check(G, stacks, seed)
 
 
+def test_pose_gradient_with_in_plane_psf():
+    rng = np.random.default_rng(6)
+    G = _unit32(ms.random_gaussians(200, 320, box=(-18, 18), sigma=(0.6, 3.0), aniso=3.0))
+    stacks = [ms.make_stack(ms.random_rotations(1, rng)[0], 5, 40, 36, 0.9, 0.9, 2.0, 2.5, psf_u=1.4, psf_v=0.7),
+              ms.make_stack(ms.AXIAL, 4, 30, 30, 1.0, 1.0, 3.0, 3.0, psf_u=0.0, psf_v=1.2)]
+    _check(G, stacks, 8)
+
+
 def test_pose_gradient_degenerate_gaussians():
     """Needles and pancakes take the FP64 record geometry in the chain too."""
     rng = np.random.default_rng(4)

@@ -22,13 +22,13 @@ FWHM2VAR = 1.0 / (8.0 * np.log(2.0))
 TILE = 16
 
 
-def _plane_quadratic(mu, q, s, xf, sig2):
-    """q(u,v) = y^T Sigma'^-1 y for y = R_k (u,v,0) + t_k - mu as (A [2x2], b [2], c)."""
+def _plane_quadratic(mu, q, s, xf, psf_var):
+    """q(u,v) = y^T Sigma'^-1 y for y = R_k (u,v,0) + t_k - mu as (A [2x2], b [2], c);
+    Sigma' = Sigma + R_k diag(psf_var) R_k^T (in-plane PSF and slice profile)."""
     R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
     Sg = R @ np.diag(np.asarray(s, np.float64) ** 2) @ R.T
     Rk = xf[:9].reshape(3, 3)
-    n = Rk[:, 2]
-    P = np.linalg.inv(Sg + sig2 * np.outer(n, n))
+    P = np.linalg.inv(Sg + Rk @ np.diag(psf_var) @ Rk.T)
     B = Rk[:, :2]               # world = B (u,v) + t
     d0 = xf[9:] - mu            # y = B uv + d0
     A = B.T @ P @ B
@@ -78,7 +78,7 @@ def test_records_vs_brute_force(seed, K):
     G = ms.random_gaussians(80, 50 + seed, box=(-26, 26), sigma=(0.6, 4.0), aniso=4.0)
     stacks = [ms.make_stack(ms.AXIAL, 5, 40, 37, 1.0, 1.2, 3.0, 2.5),
               ms.make_stack(ms.random_rotations(1, rng)[0], 4, 33, 50, 0.8, 0.9, 2.0, 3.0,
-                            rng=rng, max_rot_deg=5.0, max_trans_mm=1.0),
+                            rng=rng, max_rot_deg=5.0, max_trans_mm=1.0, psf_u=1.6, psf_v=0.9),
               ms.make_stack(ms.SAGITTAL, 3, 20, 20, 1.5, 1.5, 0.0, 4.0)]
     rec = orc.records(G, stacks, K)
     have = {(int(k), int(g)): tuple(int(v) for v in r) for k, g, r in zip(rec.slice, rec.gid, rec.rect)}
@@ -87,7 +87,7 @@ def test_records_vs_brute_force(seed, K):
     assert np.all(np.diff(key) > 0)
     k0 = 0
     for st in stacks:
-        sig2 = st.thickness ** 2 * FWHM2VAR
+        psf_var = np.array([st.psf_u ** 2, st.psf_v ** 2, st.thickness ** 2]) * FWHM2VAR
         ii, jj = np.meshgrid(np.arange(st.W), np.arange(st.H), indexing="xy")
         uv = np.stack([(ii - 0.5 * (st.W - 1)) * st.dx, (jj - 0.5 * (st.H - 1)) * st.dy], axis=-1)
         for k in range(st.n_slices):
@@ -95,7 +95,7 @@ def test_records_vs_brute_force(seed, K):
             for g in range(G.n):
                 q = G.quat[g].astype(np.float64)
                 q /= np.linalg.norm(q)
-                A, b, c = _plane_quadratic(G.mean[g].astype(np.float64), q, G.scale[g], xf, sig2)
+                A, b, c = _plane_quadratic(G.mean[g].astype(np.float64), q, G.scale[g], xf, psf_var)
                 qv = np.einsum("hwi,ij,hwj->hw", uv, A, uv) + 2 * uv @ b + c
                 got = have.get((k0 + k, g))
                 inside = qv <= K * K * (1 - 1e-5)
