@@ -44,6 +44,10 @@ KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 6, "k1_emit": 1
 # MUFU ex2 ops): forward q (2 FMA) + accumulate (1 FMA) + 1 ex2; backward q
 # (2 FMA) + w = g 2^q (1 MUL) + three moment accumulations (3) + 1 ex2.
 PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (6, 1)}
+# DRAM bytes (read + write) per launch of the evaluation kernels on this
+# workload, from one ncu capture of the current kernels
+# (profiles/k_render_fwd_bwd_feta256_full.md); None once a kernel changes.
+PROFILED_TRAFFIC = {"render_fwd": (113.9 + 38.3) * 1e6, "render_bwd": (252.8 + 70.1) * 1e6}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).
@@ -248,7 +252,8 @@ def run_mgauss(args, rank, world, local_rank):
     achieved = pairs_eval / (dom_ms / 1e3)
     peak = alu_peak_pairs(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(dom) if args.workload == "feta" else None,
+            "traffic_unit": "bytes per launch (ncu capture)",
             "peak_basis": (f"{N_SM} SMs x min({FP32_LANES}/{PAIR_OPS[dom][0]} FP32, {MUFU_LANES}/{PAIR_OPS[dom][1]} "
                            f"MUFU) pairs/clk x {SM_MHZ:.0f} MHz (nominal unit counts)"),
             "units_per_launch": pairs_eval}
@@ -320,6 +325,13 @@ def run_recon(args, dev):
     wl, G, target, vol = build_workload(args.workload, args.seed, dev, keep_volume=True)
     gd = vol.shape[0]
     half = wl.phantom.fov_mm / 2
+    # untimed warm-up of every form (lazy module loading, first graph captures, allocator growth)
+    for kw in RECON_FORMS.values():
+        cfg = recon.FitConfig(iterations=40, nrf_start=20, nrf_batch=1 << 20, **kw)
+        model, nrf, _ = recon.fit(wl.stacks, target, G, (0.0, 0.0, 0.0), half, cfg, device=dev)
+        recon.sample(model, nrf, gd, wl.phantom.spacing)
+        del model, nrf
+    torch.cuda.synchronize()
     forms = {}
     for name, kw in RECON_FORMS.items():
         runs = []
