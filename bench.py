@@ -287,6 +287,8 @@ def run_mgauss(args, rank, world, local_rank):
         del R, out, grad, flush
         torch.cuda.empty_cache()
         line["recon"] = run_recon(args, dev)
+        if args.radius_sweep:
+            line["radius_sweep"] = run_radius_sweep(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -385,6 +387,41 @@ def run_recon(args, dev):
             "bf16_speedup_vs_fp32": f32["seconds_mean"] / b16["seconds_mean"],
             "nrf_minus_gaussians_psnr_db": b16["psnr_db_mean"] - g32["psnr_db_mean"],
             "nrf_fwd_bwd_ms_per_2^20_points": nrf_ms}
+
+
+def run_radius_sweep(args, dev):
+    """The paper's local set (Eqs. E4-E6) at several block radii: the same
+    FeTA-shaped fit (L1+L2, CUDA-graph replay) with the cell grid at the
+    Gaussian spacing (one Gaussian per cell on average, the reading of the
+    paper's grids), one seed per radius; seconds per fit + sampling, PSNR,
+    and the evaluated pairs of one step, beside the K-sigma local set."""
+    import torch
+
+    from paper_2603_00145_b300 import recon
+
+    wl, G, target, vol = build_workload(args.workload, args.seed, dev, keep_volume=True)
+    gd = vol.shape[0]
+    half = wl.phantom.fov_mm / 2
+    spacing = float(np.median(np.asarray(G.scale)[:, 0]))  # the initial isotropic sigma = the Gaussian spacing
+    res = max(1, int(round(2 * half / spacing)))
+    out = {"grid_res": res, "cell_mm": 2 * half / res, "iterations": args.recon_iters, "runs": []}
+    forms = [("ksigma", None)] + [("cells", r) for r in args.radius_sweep]
+    for kind, r in forms:
+        kw = {} if kind == "ksigma" else {"local_set": "cells", "grid_res": res, "block_radius": r}
+        cfg = recon.FitConfig(iterations=40, **kw)
+        recon.fit(wl.stacks, target, G, (0.0, 0.0, 0.0), half, cfg, device=dev)   # warm-up
+        cfg = recon.FitConfig(iterations=args.recon_iters, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model, nrf, st = recon.fit(wl.stacks, target, G, (0.0, 0.0, 0.0), half, cfg, device=dev)
+        V = recon.sample(model, nrf, gd, wl.phantom.spacing, cells=recon.cells_of(cfg, (0.0, 0.0, 0.0), half))
+        torch.cuda.synchronize()
+        out["runs"].append({"local_set": kind, "block_radius": r, "seconds": time.perf_counter() - t0,
+                            "ms_per_iteration": 1e3 * st["seconds_replay"] / max(st["iterations"], 1),
+                            "psnr_db": recon.psnr(V, vol)})
+        del model, V
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -488,6 +525,8 @@ def main():
     ap.add_argument("--recon-iters", type=int, default=2000,
                     help="iterations of each timed full reconstruction (0: skip the reconstruction timing)")
     ap.add_argument("--recon-seeds", type=int, default=3, help="runs (seeds) per reconstruction form")
+    ap.add_argument("--radius-sweep", type=lambda v: [int(x) for x in v.split(",")], default=[],
+                    help="block radii of the paper's cell-grid local set to fit and time, e.g. 3,4,5,6,7")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -110,11 +110,44 @@ typedef struct {
     float psf_u, psf_v;     /* in-plane Gaussian PSF FWHM (mm) along e_u, e_v, >= 0; 0 = none */
 } mg_stack;
 
+/*
+ * Local set. MG_LOCAL_KSIGMA (the default, above): per (Gaussian, slice)
+ * record, every voxel of the listed 16x16 tiles. MG_LOCAL_CELLS: the paper's
+ * own rule (Sec. 3.3.1, Eqs. E4-E6): the normalised cube [-1,1]^3 (mapped to
+ * grid_centre + grid_half * [-1,1]^3 mm) is cut into grid_res^3 cells; a
+ * Gaussian sits in the cell of its mean, and voxel x sums exactly the
+ * Gaussians whose cell is within block_radius cells of x's cell along each
+ * axis. FP32, every operation rounded, in this order (hres = 0.5 * grid_res):
+ *   cell(p)_a = (int) floor(clamp(((p_a - grid_centre_a) / grid_half + 1) * hres,
+ *                                 -2^20, 2^20))
+ *   voxel (i,j) of a slice: u = ((float)i - hx) * dx, v = ((float)j - hy) * dy,
+ *                           x_a = (R_a0 u + R_a1 v) + t_a   (R, t of the slice)
+ *   member iff |cell(x)_a - cell(mu)_a| <= block_radius for a = 0, 1, 2.
+ * Records and tiles only bound the members: the (Gaussian, slice) record
+ * exists iff the slice plane passes within m of the axis-aligned box of the
+ * member cells (centre b_a = grid_centre_a + grid_half ((cell(mu)_a + 0.5)/hres - 1),
+ * half-width e = (float)(grid_half (block_radius + 0.5) / hres), margin
+ * m = (float)(grid_half / (1024 hres)), both in double):
+ *   |n.(b - t)| <= e ((|n_0| + |n_1|) + |n_2|) + m,
+ * and it lists the tiles of the pixel box of the box's extent along e_u, e_v
+ * (centre u_c = e_u.(b - t), radius e ((|e_u0| + |e_u1|) + |e_u2|) + m, the
+ * pixel box as in the K-sigma predicate). The sum at each voxel is then
+ * restricted to members, per (record, voxel). The grid must be coarse enough
+ * that a 16x16 tile spans at most 250 cells per axis (else
+ * MG_ERR_INVALID_ARG). mg_render_pair_count is for MG_LOCAL_KSIGMA only.
+ */
+enum { MG_LOCAL_KSIGMA = 0, MG_LOCAL_CELLS = 1 };
+
 typedef struct {
     float cutoff_k;      /* K of the K-sigma record predicate; default 3 */
     float f64_ratio;     /* record geometry in FP64 when max(scale)/min(scale) > f64_ratio; default 100; <= 0: never */
     int64_t cap_records; /* workspace capacity in records; 0 = n * total slices (upper bound) capped at 2^28 */
     int64_t cap_entries; /* workspace capacity in (record, tile) entries; 0 = 8 * cap_records capped at 2^30 */
+    int32_t local_set;   /* MG_LOCAL_KSIGMA (0, default) or MG_LOCAL_CELLS */
+    int32_t grid_res;    /* MG_LOCAL_CELLS: cells per axis, 1..4096 */
+    int32_t block_radius;   /* MG_LOCAL_CELLS: neighbourhood radius in cells, 0..1024 (the paper's default 5) */
+    float grid_centre[3];   /* MG_LOCAL_CELLS: centre of the normalised cube (mm) */
+    float grid_half;        /* MG_LOCAL_CELLS: half edge of the normalised cube (mm), > 0 */
 } mg_opts;
 
 /* Filled by mg_render_stats_get from the workspace of the last forward call. */

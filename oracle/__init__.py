@@ -56,9 +56,13 @@ def lib():
         L.or_make_records.argtypes = [i64, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, ctypes.c_float, i64, p, p,
                                       p]
         L.or_render.restype = None
-        L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, ctypes.c_int, p]
+        L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, ctypes.c_int, p,
+                                p, p]
         L.or_grad.restype = None
-        L.or_grad.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p]
+        L.or_grad.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p,
+                              p, p]
+        L.or_make_records_cells.restype = i64
+        L.or_make_records_cells.argtypes = [i64, p, ctypes.c_int, p, p, p, p, p, p, p, p, p, p, i64, p, p, p]
         L.or_pair_counts.restype = None
         L.or_pair_counts.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p,
                                      ctypes.c_double, p]
@@ -93,6 +97,16 @@ class _StackArgs:
                 _ptr(self.psf), _ptr(self.xf)]
 
 
+def _cells_args(cells):
+    """(int32 [res, radius], float32 [cx, cy, cz, half]) of the cell-grid local set, kept alive by the caller."""
+    if cells is None:
+        return None, None
+    ci = np.array([int(cells["grid_res"]), int(cells["block_radius"])], dtype=np.int32)
+    cf = np.array([*[float(np.float32(v)) for v in cells["centre"]], float(np.float32(cells["half"]))],
+                  dtype=np.float32)
+    return ci, cf
+
+
 def _gargs(G, dtype=np.float32):
     arrs = [np.ascontiguousarray(a, dtype=dtype) for a in (G.mean, G.quat, G.scale, G.alpha)]
     return arrs, [int(arrs[0].shape[0])] + [_ptr(a) for a in arrs]
@@ -113,12 +127,24 @@ class Records:
         return [self.n, _ptr(self.slice), _ptr(self.gid), _ptr(self.rect)]
 
 
-def records(G, stacks, K: float = 3.0) -> Records:
-    """Records by the FP32 record predicate (bit-exact specification). Parity:
-    pinned by brute-force conservativeness/tightness tests."""
+def records(G, stacks, K: float = 3.0, cells=None) -> Records:
+    """Records by the FP32 record predicate (bit-exact specification): the
+    K-sigma slab and cut-ellipse rule, or with ``cells`` (dict grid_res,
+    block_radius, centre, half) the paper's cell-grid rule (Eqs. E4-E6),
+    whose records bound the member voxels. Parity: pinned by brute-force
+    conservativeness/tightness tests and, for cells, a brute-force member sum."""
     L = lib()
     sa = _StackArgs(stacks)
     keep, ga = _gargs(G)
+    if cells is not None:
+        ci, cf = _cells_args(cells)
+        a = sa.args()
+        total = L.or_make_records_cells(ga[0], ga[1], *a, _ptr(ci), _ptr(cf), 0, None, None, None)
+        sl = np.zeros(total, dtype=np.int32)
+        gid = np.zeros(total, dtype=np.int32)
+        rect = np.zeros((total, 4), dtype=np.int32)
+        L.or_make_records_cells(ga[0], ga[1], *a, _ptr(ci), _ptr(cf), total, _ptr(sl), _ptr(gid), _ptr(rect))
+        return Records(sl, gid, rect)
     total = L.or_make_records(*ga[:4], *sa.args(), ctypes.c_float(K), 0, None, None, None)
     sl = np.zeros(total, dtype=np.int32)
     gid = np.zeros(total, dtype=np.int32)
@@ -161,7 +187,7 @@ def tile_bins(rec: Records, stacks):
     return counts, offs, ids
 
 
-def render(G, stacks, rec: Records | None = None, exact: bool = False, K: float = 3.0) -> np.ndarray:
+def render(G, stacks, rec: Records | None = None, exact: bool = False, K: float = 3.0, cells=None) -> np.ndarray:
     """FP64 slice values, all stacks concatenated (flat). ``exact``: every
     Gaussian at every pixel (the untruncated sum S); otherwise the binned sum
     S^bin over ``rec``. Parity: pinned by quadrature, closed forms, mass
@@ -175,8 +201,10 @@ def render(G, stacks, rec: Records | None = None, exact: bool = False, K: float 
         dummy = Records(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros((0, 4), np.int32))
         rr = dummy
     else:
-        rr = rec if rec is not None else records(G, stacks, K)
-    L.or_render(*ga, *sa.args(), *rr._args(), 1 if exact else 0, _ptr(out))
+        rr = rec if rec is not None else records(G, stacks, K, cells)
+    ci, cf = _cells_args(None if exact else cells)
+    L.or_render(*ga, *sa.args(), *rr._args(), 1 if exact else 0, _ptr(out), None if ci is None else _ptr(ci),
+                None if cf is None else _ptr(cf))
     return out
 
 
@@ -189,7 +217,7 @@ def split(flat: np.ndarray, stacks) -> List[np.ndarray]:
     return out
 
 
-def grad(G, stacks, rec: Records, gout: np.ndarray):
+def grad(G, stacks, rec: Records, gout: np.ndarray, cells=None):
     """Analytic FP64 gradient of sum(gout * S^bin) with the records frozen.
     Returns dict mean[n,3], quat[n,4], scale[n,3], alpha[n]. Parity: pinned by
     central finite differences of ``render``."""
@@ -202,11 +230,13 @@ def grad(G, stacks, rec: Records, gout: np.ndarray):
     gq = np.zeros((n, 4))
     gs = np.zeros((n, 3))
     gaa = np.zeros(n)
-    L.or_grad(*ga, *sa.args(), *rec._args(), _ptr(go), _ptr(gm), _ptr(gq), _ptr(gs), _ptr(gaa))
+    ci, cf = _cells_args(cells)
+    L.or_grad(*ga, *sa.args(), *rec._args(), _ptr(go), _ptr(gm), _ptr(gq), _ptr(gs), _ptr(gaa),
+              None if ci is None else _ptr(ci), None if cf is None else _ptr(cf))
     return {"mean": gm, "quat": gq, "scale": gs, "alpha": gaa}
 
 
-def pose_grad(G, stacks, rec: Records, gout: np.ndarray) -> np.ndarray:
+def pose_grad(G, stacks, rec: Records, gout: np.ndarray, cells=None) -> np.ndarray:
     """Gradient of sum(gout * S^bin) with respect to each slice pose, records
     frozen: [S, 6] = (dL/dt world, dL/domega) per slice, the rotation perturbed
     as R (I + [omega]x) with omega in the slice frame (columns of R).
@@ -239,7 +269,7 @@ def pose_grad(G, stacks, rec: Records, gout: np.ndarray) -> np.ndarray:
                                         xform=xf[None, :].copy(), n_vox=npx)
             sel = rec.slice == k
             rk = Records(np.zeros(int(sel.sum()), np.int32), rec.gid[sel].copy(), rec.rect[sel].copy())
-            gr = grad(G, [sub], rk, go[off:off + npx])
+            gr = grad(G, [sub], rk, go[off:off + npx], cells)
             R = xf[:9].reshape(3, 3)
             t = xf[9:]
             gmu, gq = gr["mean"], gr["quat"]
@@ -285,9 +315,10 @@ def volume_planes(G_dim: int, spacing: float, centre=(0.0, 0.0, 0.0)):
                                  n_vox=G_dim ** 3)
 
 
-def sample_volume(G, G_dim: int, spacing: float, centre=(0.0, 0.0, 0.0), K: float = 3.0, exact: bool = False):
+def sample_volume(G, G_dim: int, spacing: float, centre=(0.0, 0.0, 0.0), K: float = 3.0, exact: bool = False,
+                  cells=None):
     """Inference sampling (Sec. 3.1, Fig. 1c): the Gaussian mixture of Eq. E7
     (no slice profile) on the isotropic grid, binned like the slices.
     Returns [G,G,G] (z,y,x) FP64."""
     st = volume_planes(G_dim, spacing, centre)
-    return render(G, [st], None, exact=exact, K=K).reshape(G_dim, G_dim, G_dim)
+    return render(G, [st], None, exact=exact, K=K, cells=cells).reshape(G_dim, G_dim, G_dim)

@@ -213,6 +213,157 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     return 1;
 }
 
+/* ------------------------------------------------------------------ */
+/* The paper's cell-grid local set (Sec. 3.3.1, Eqs. E4-E6), FP32 in  */
+/* the written order: the cube [-1,1]^3 mapped to centre + h [-1,1]^3 */
+/* mm is cut into res^3 cells; a Gaussian belongs to the cell of its  */
+/* mean; the local set of voxel x is every Gaussian whose cell is     */
+/* within R cells of x's cell along each axis.                        */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int res, R;
+    float C[3], h, hres, e, m;
+} or_cells;
+
+static void cells_setup(const int32_t *ci, const float *cf, or_cells *c)
+{
+    c->res = ci[0];
+    c->R = ci[1];
+    c->C[0] = cf[0];
+    c->C[1] = cf[1];
+    c->C[2] = cf[2];
+    c->h = cf[3];
+    double hres = 0.5 * (double)c->res, h = (double)c->h;
+    c->hres = (float)hres;
+    c->e = (float)(h * ((double)c->R + 0.5) / hres);  /* half-width of the member box */
+    c->m = (float)(h / (1024.0 * hres));             /* margin of the record tests */
+}
+
+/* cell index of one coordinate: floor(((p - C)/h + 1) hres), clamped to +-2^20 */
+static int cell_coord_f(float p, float c, float h, float hres)
+{
+    float t = (p - c) / h;
+    t = t + 1.0f;
+    t = t * hres;
+    if (!(t >= -1048576.0f)) t = -1048576.0f;
+    if (t > 1048576.0f) t = 1048576.0f;
+    return (int)floorf(t);
+}
+
+static void gauss_cell_f(const float mu[3], const or_cells *c, int cell[3], float b[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        cell[a] = cell_coord_f(mu[a], c->C[a], c->h, c->hres);
+        float t = ((float)cell[a] + 0.5f) / c->hres;
+        t = t - 1.0f;
+        b[a] = c->C[a] + c->h * t; /* centre of the member box */
+    }
+}
+
+/* FP32 world position of voxel (i, j) of a slice and its cell */
+static void voxel_cell_f(const or_slice *sl, int i, int j, const or_cells *c, int cell[3])
+{
+    float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
+    float dx = (float)sl->dxd, dy = (float)sl->dyd;
+    float u = ((float)i - hx) * dx, v = ((float)j - hy) * dy;
+    for (int a = 0; a < 3; ++a) {
+        float q0 = (float)sl->xfd[3 * a], q1 = (float)sl->xfd[3 * a + 1], t = (float)sl->xfd[9 + a];
+        float x = q0 * u + q1 * v;
+        x = x + t;
+        cell[a] = cell_coord_f(x, c->C[a], c->h, c->hres);
+    }
+}
+
+static int cell_member(const int vc[3], const int gc[3], int R)
+{
+    for (int a = 0; a < 3; ++a)
+        if (abs(vc[a] - gc[a]) > R) return 0;
+    return 1;
+}
+
+static float abs_sum3f(float a, float b, float c)
+{
+    float t = fabsf(a) + fabsf(b);
+    return t + fabsf(c);
+}
+
+/* Record test of the cell rule: the slice plane passes within m of the
+ * Gaussian's member box; the tiles cover the box's extent along e_u, e_v. */
+static int record_predicate_cells(const float *mu, const or_slice *sl, const or_cells *c, int32_t rect[4])
+{
+    int gc[3];
+    float b[3];
+    gauss_cell_f(mu, c, gc, b);
+    const float *Q = sl->xf;
+    float eu[3] = {Q[0], Q[3], Q[6]};
+    float ev[3] = {Q[1], Q[4], Q[7]};
+    float en[3] = {Q[2], Q[5], Q[8]};
+    float p[3] = {b[0] - Q[9], b[1] - Q[10], b[2] - Q[11]};
+    float w = dot3f(en, p);
+    if (!(fabsf(w) <= c->e * abs_sum3f(en[0], en[1], en[2]) + c->m)) return 0;
+    float uc = dot3f(eu, p), vc = dot3f(ev, p);
+    float ru = c->e * abs_sum3f(eu[0], eu[1], eu[2]) + c->m;
+    float rv = c->e * abs_sum3f(ev[0], ev[1], ev[2]) + c->m;
+    float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
+    float il = ceilf((uc - ru) / sl->dx + hx);
+    float ih = floorf((uc + ru) / sl->dx + hx);
+    float jl = ceilf((vc - rv) / sl->dy + hy);
+    float jh = floorf((vc + rv) / sl->dy + hy);
+    float Wm1 = (float)(sl->W - 1), Hm1 = (float)(sl->H - 1);
+    if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
+        rect[0] = 1; rect[1] = 1; rect[2] = 0; rect[3] = 0;
+        return 1;
+    }
+    if (il < 0.0f) il = 0.0f;
+    if (jl < 0.0f) jl = 0.0f;
+    if (ih > Wm1) ih = Wm1;
+    if (jh > Hm1) jh = Hm1;
+    rect[0] = (int32_t)il / OR_TILE;
+    rect[1] = (int32_t)jl / OR_TILE;
+    rect[2] = (int32_t)ih / OR_TILE;
+    rect[3] = (int32_t)jh / OR_TILE;
+    return 1;
+}
+
+int64_t or_make_records_cells(int64_t n, const float *mean, int n_stacks, const int32_t *nsl, const int32_t *H,
+                              const int32_t *W, const float *dx, const float *dy, const float *thk, const float *psf,
+                              const float *xform, const int32_t *cells_i, const float *cells_f, int64_t cap,
+                              int32_t *rec_slice, int32_t *rec_gid, int32_t *rec_rect)
+{
+    int S;
+    or_slice *sl = or_build_slices(n_stacks, nsl, H, W, dx, dy, thk, psf, xform, NULL, NULL, NULL, NULL, NULL, &S);
+    or_cells c;
+    cells_setup(cells_i, cells_f, &c);
+    int64_t *cnt = (int64_t *)calloc((size_t)S + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < S; ++k) {
+        int64_t m = 0;
+        int32_t rect[4];
+        for (int64_t g = 0; g < n; ++g) m += record_predicate_cells(mean + 3 * g, &sl[k], &c, rect);
+        cnt[k + 1] = m;
+    }
+    for (int k = 0; k < S; ++k) cnt[k + 1] += cnt[k];
+    int64_t total = cnt[S];
+    if (rec_slice && cap > 0) {
+#pragma omp parallel for schedule(dynamic)
+        for (int k = 0; k < S; ++k) {
+            int64_t pos = cnt[k];
+            int32_t rect[4];
+            for (int64_t g = 0; g < n && pos < cap; ++g) {
+                if (record_predicate_cells(mean + 3 * g, &sl[k], &c, rect)) {
+                    rec_slice[pos] = k;
+                    rec_gid[pos] = (int32_t)g;
+                    memcpy(rec_rect + 4 * pos, rect, sizeof(rect));
+                    ++pos;
+                }
+            }
+        }
+    }
+    free(cnt);
+    free(sl);
+    return total;
+}
+
 /* Records, slice-major (all stacks' slices in order), ascending Gaussian id
  * within a slice. Returns the total; fills at most cap. */
 int64_t or_make_records(int64_t n, const float *mean, const float *quat, const float *scale, int n_stacks,
@@ -388,11 +539,13 @@ static double quad_form(const or_term *T, const double x[3], double y[3], double
 void or_render(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
                const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy,
                const double *thk, const double *psf, const double *xform, int64_t nrec, const int32_t *rec_slice,
-               const int32_t *rec_gid,
-               const int32_t *rec_rect, int exact, double *out)
+               const int32_t *rec_gid, const int32_t *rec_rect, int exact, double *out, const int32_t *cells_i,
+               const float *cells_f)
 {
     int S;
     or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
+    or_cells cc;
+    if (cells_i) cells_setup(cells_i, cells_f, &cc);
     int64_t total = 0;
     for (int k = 0; k < S; ++k) total += (int64_t)sl[k].H * sl[k].W;
     memset(out, 0, sizeof(double) * (size_t)total);
@@ -432,8 +585,19 @@ void or_render(int64_t n, const double *mean, const double *quat, const double *
                 int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
                 if (i1 > sl[k].W) i1 = sl[k].W;
                 if (j1 > sl[k].H) j1 = sl[k].H;
+                int gcell[3];
+                if (cells_i) {
+                    float muf[3] = {(float)mean[3 * g], (float)mean[3 * g + 1], (float)mean[3 * g + 2]};
+                    float b[3];
+                    gauss_cell_f(muf, &cc, gcell, b);
+                }
                 for (int j = j0; j < j1; ++j)
                     for (int i = i0; i < i1; ++i) {
+                        if (cells_i) {
+                            int vcell[3];
+                            voxel_cell_f(&sl[k], i, j, &cc, vcell);
+                            if (!cell_member(vcell, gcell, cc.R)) continue;
+                        }
                         double x[3], y[3], Py[3];
                         pixel_world(&sl[k], i, j, x);
                         double qf = quad_form(&T, x, y, Py);
@@ -462,10 +626,12 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
              const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy, const double *thk,
              const double *psf, const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
              const int32_t *rec_rect, const double *gout, double *gmean, double *gquat, double *gscale,
-             double *galpha)
+             double *galpha, const int32_t *cells_i, const float *cells_f)
 {
     int S;
     or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
+    or_cells cc;
+    if (cells_i) cells_setup(cells_i, cells_f, &cc);
     double *rg = (double *)calloc((size_t)(nrec > 0 ? nrec : 1) * 11, sizeof(double));
 #pragma omp parallel for schedule(dynamic)
     for (int64_t r = 0; r < nrec; ++r) {
@@ -481,10 +647,21 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
         if (j1 > sl[k].H) j1 = sl[k].H;
         double ga = 0, gmu[3] = {0, 0, 0}, GS[3][3];
         memset(GS, 0, sizeof(GS));
+        int gcell[3];
+        if (cells_i) {
+            float muf[3] = {(float)mean[3 * g], (float)mean[3 * g + 1], (float)mean[3 * g + 2]};
+            float b[3];
+            gauss_cell_f(muf, &cc, gcell, b);
+        }
         for (int j = j0; j < j1; ++j)
             for (int i = i0; i < i1; ++i) {
                 double G = go[(int64_t)j * sl[k].W + i];
                 if (G == 0.0) continue;
+                if (cells_i) {
+                    int vcell[3];
+                    voxel_cell_f(&sl[k], i, j, &cc, vcell);
+                    if (!cell_member(vcell, gcell, cc.R)) continue;
+                }
                 double x[3], y[3], Py[3];
                 pixel_world(&sl[k], i, j, x);
                 double qf = quad_form(&T, x, y, Py);

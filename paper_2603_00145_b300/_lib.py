@@ -23,7 +23,12 @@ class MgStack(ctypes.Structure):
 
 
 class MgOpts(ctypes.Structure):
-    _fields_ = [("cutoff_k", c_f32), ("f64_ratio", c_f32), ("cap_records", c_i64), ("cap_entries", c_i64)]
+    _fields_ = [("cutoff_k", c_f32), ("f64_ratio", c_f32), ("cap_records", c_i64), ("cap_entries", c_i64),
+                ("local_set", c_i32), ("grid_res", c_i32), ("block_radius", c_i32), ("grid_centre", c_f32 * 3),
+                ("grid_half", c_f32)]
+
+
+MG_LOCAL_KSIGMA, MG_LOCAL_CELLS = 0, 1
 
 
 class MgRenderStats(ctypes.Structure):

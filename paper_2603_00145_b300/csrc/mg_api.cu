@@ -113,6 +113,45 @@ mg_opts resolve_opts(const mg_opts *o, long long n, long long S)
     return r;
 }
 
+// The kernels' view of the MG_LOCAL_CELLS options (cg.on = 0 for the K-sigma
+// set). max_px: the largest pixel spacing of the stacks (mm), for the check
+// that a 16x16 tile spans at most 250 cells per axis.
+bool make_cellgrid(const mg_opts &o, float max_px, CellGrid &cg, std::string &why)
+{
+    memset(&cg, 0, sizeof(cg));
+    if (o.local_set == MG_LOCAL_KSIGMA) return true;
+    if (o.local_set != MG_LOCAL_CELLS) {
+        why = "local_set must be MG_LOCAL_KSIGMA or MG_LOCAL_CELLS";
+        return false;
+    }
+    if (o.grid_res < 1 || o.grid_res > 4096 || o.block_radius < 0 || o.block_radius > 1024 || !(o.grid_half > 0.f) ||
+        !isfinite(o.grid_half) || !isfinite(o.grid_centre[0]) || !isfinite(o.grid_centre[1]) ||
+        !isfinite(o.grid_centre[2])) {
+        why = "MG_LOCAL_CELLS needs 1 <= grid_res <= 4096, 0 <= block_radius <= 1024, grid_half > 0, finite centre";
+        return false;
+    }
+    const double hres = 0.5 * (double)o.grid_res, h = (double)o.grid_half;
+    if (2.0 * MG_TILE * (double)max_px * hres / h + 2.0 > 250.0) {
+        why = "MG_LOCAL_CELLS grid too fine: a 16x16 tile would span more than 250 cells";
+        return false;
+    }
+    cg.on = 1;
+    cg.R = o.block_radius;
+    cg.hres = (float)hres;
+    cg.h = o.grid_half;
+    for (int a = 0; a < 3; ++a) cg.C[a] = o.grid_centre[a];
+    cg.e = (float)(h * ((double)o.block_radius + 0.5) / hres);
+    cg.m = (float)(h / (1024.0 * hres));
+    return true;
+}
+
+float max_pixel(const std::vector<StackDesc> &st)
+{
+    float m = 0.f;
+    for (const StackDesc &d : st) m = fmaxf(m, fmaxf(d.dx, d.dy));
+    return m;
+}
+
 bool valid_stacks(const std::vector<StackDesc> &st, bool need_xform, std::string &why)
 {
     if (st.empty() || st.size() > MG_MAX_STACKS) {
@@ -188,6 +227,7 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.entries = take(sizeof(unsigned) * (size_t)L.cap_entries);
     L.gmap = take(sizeof(unsigned) * (size_t)L.cap_records);
     L.rec_grad = take(48 * (size_t)L.cap_records);
+    L.rec_cell = o.local_set == MG_LOCAL_CELLS ? take(16 * (size_t)L.cap_records) : 0;
     L.total = off;
     return L;
 }
@@ -278,6 +318,8 @@ struct FwdTag {
     std::vector<const void *> xforms;
     float K, f64;
     long long capr, cape;
+    int ls, res, R;
+    float gc[4];
     bool bwd_done = false;  // an mg_render_bwd has filled the moments since this forward
 };
 
@@ -301,13 +343,22 @@ FwdTag make_tag(const mg_gaussians *g, const std::vector<StackDesc> &st, const m
     t.f64 = o.f64_ratio;
     t.capr = o.cap_records;
     t.cape = o.cap_entries;
+    t.ls = o.local_set;
+    t.res = o.grid_res;
+    t.R = o.block_radius;
+    t.gc[0] = o.grid_centre[0];
+    t.gc[1] = o.grid_centre[1];
+    t.gc[2] = o.grid_centre[2];
+    t.gc[3] = o.grid_half;
     return t;
 }
 
 bool same_tag(const FwdTag &a, const FwdTag &b)
 {
     return a.n == b.n && memcmp(a.p, b.p, sizeof(a.p)) == 0 && a.stack_key == b.stack_key && a.xforms == b.xforms &&
-           a.K == b.K && a.f64 == b.f64 && a.capr == b.capr && a.cape == b.cape;
+           a.K == b.K && a.f64 == b.f64 && a.capr == b.capr && a.cape == b.cape && a.ls == b.ls &&
+           (a.ls == MG_LOCAL_KSIGMA ||
+            (a.res == b.res && a.R == b.R && memcmp(a.gc, b.gc, sizeof(a.gc)) == 0));
 }
 
 mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &st, const StackIn &in,
@@ -327,6 +378,8 @@ mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &s
     mg_opts o = resolve_opts(opts, g->n, S);
     if (o.cap_records >= (1ll << 31) || o.cap_entries >= (1ll << 32) - 1)
         return fail(MG_ERR_INVALID_ARG, "capacities must be below 2^31 records and 2^32-1 entries");
+    CellGrid cg;
+    if (!make_cellgrid(o, in.planes ? in.h : max_pixel(st), cg, why)) return fail(MG_ERR_INVALID_ARG, why);
     WsLayout L = make_layout(g->n, st, o);
     if (ws_bytes < L.total)
         return fail(MG_ERR_INVALID_ARG, "workspace too small: need " + std::to_string(L.total) + " bytes");
@@ -335,12 +388,13 @@ mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &s
     StackTable tab = make_table(st);
     mg_launch_build_slices(in, slices, (int)S, stream);
     if (g->n > 0) {
-        mg_launch_bin(L, w, slices, tab, g->mean, g->quat, g->scale, g->alpha, g->n, o.cutoff_k, o.f64_ratio, stream);
+        mg_launch_bin(L, w, slices, tab, g->mean, g->quat, g->scale, g->alpha, g->n, o.cutoff_k, o.f64_ratio, cg,
+                      stream);
     } else {
         cudaMemsetAsync(w + L.hdr, 0, sizeof(WsHeader), stream);
         cudaMemsetAsync(w + L.tile_off, 0, sizeof(unsigned) * (size_t)(tiles + 1), stream);
     }
-    mg_launch_render_fwd(L, w, tab, out, stream);
+    mg_launch_render_fwd(L, w, tab, slices, cg, out, stream);
     mg_status s = check_cuda("mg_render_fwd");
     if (s != MG_OK) return s;
     {
@@ -363,6 +417,11 @@ mg_opts mg_default_opts(void)
     o.f64_ratio = 100.0f;
     o.cap_records = 0;
     o.cap_entries = 0;
+    o.local_set = MG_LOCAL_KSIGMA;
+    o.grid_res = 0;
+    o.block_radius = 5;
+    o.grid_centre[0] = o.grid_centre[1] = o.grid_centre[2] = 0.f;
+    o.grid_half = 0.f;
     return o;
 }
 
@@ -429,10 +488,12 @@ mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
         it->second.bwd_done = true;
     }
     if (g->n == 0) return MG_OK;
+    CellGrid cg;
+    if (!make_cellgrid(o, max_pixel(st), cg, why)) return fail(MG_ERR_INVALID_ARG, why);
     char *w = (char *)ws;
     StackTable tab = make_table(st);
-    mg_launch_render_bwd(L, w, (const SliceDev *)(w + L.slices), tab, grad_out, g->mean, g->quat, g->scale, g->alpha,
-                         g->n, o.f64_ratio, g_mean, g_quat, g_scale, g_alpha, (cudaStream_t)stream);
+    mg_launch_render_bwd(L, w, (const SliceDev *)(w + L.slices), tab, cg, grad_out, g->mean, g->quat, g->scale,
+                         g->alpha, g->n, o.f64_ratio, g_mean, g_quat, g_scale, g_alpha, (cudaStream_t)stream);
     return check_cuda("mg_render_bwd");
 }
 
@@ -584,6 +645,7 @@ mg_status mg_render_pair_count(const mg_gaussians *g, const mg_stack *stacks, in
     long long S = 0;
     for (const StackDesc &d : st) S += d.n_slices;
     mg_opts o = resolve_opts(opts, g->n, S);
+    if (o.local_set != MG_LOCAL_KSIGMA) return fail(MG_ERR_INVALID_ARG, "pair counts are for MG_LOCAL_KSIGMA only");
     WsLayout L = make_layout(g->n, st, o);
     if (ws_bytes < L.total) return fail(MG_ERR_INVALID_ARG, "workspace too small");
     {

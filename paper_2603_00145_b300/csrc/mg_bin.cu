@@ -285,6 +285,8 @@ __device__ __forceinline__ bool slab_test(const GaussPred &G, const SliceDev &S,
     return __fmul_rn(w0, w0) <= __fmul_rn(K2, Sww);
 }
 
+__device__ __forceinline__ void pixel_box(const SliceDev &S, float cu, float cv, float ru, float rv, PredOut &o);
+
 // The record predicate of mgauss.h given the frame terms (computed here when
 // missing). Returns existence and the clamped pixel box.
 __device__ __forceinline__ bool record_predicate(const GaussPred &G, const SliceDev &S, float K2, FrameTerms &f,
@@ -311,6 +313,14 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     float cv = __fsub_rn(v0, __fdiv_rn(__fmul_rn(f.Lvw, w0), Sww));
     float ru = __fsqrt_rn(__fmul_rn(r2, Cuu));
     float rv = __fsqrt_rn(__fmul_rn(r2, Cvv));
+    pixel_box(S, cu, cv, ru, rv, o);
+    return true;
+}
+
+// The pixel box of [cu - ru, cu + ru] x [cv - rv, cv + rv] (slice mm), clamped
+// to the image; an empty box is stored as the tile rectangle (1,1,0,0).
+__device__ __forceinline__ void pixel_box(const SliceDev &S, float cu, float cv, float ru, float rv, PredOut &o)
+{
     float il = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cu, ru), S.dx), S.hx));
     float ih = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(cu, ru), S.dx), S.hx));
     float jl = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cv, rv), S.dy), S.hy));
@@ -319,7 +329,7 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
         o.il = o.jl = MG_TILE;  // empty box: tile rectangle (1,1,0,0)
         o.ih = o.jh = 0;
-        return true;
+        return;
     }
     if (il < 0.0f) il = 0.0f;
     if (jl < 0.0f) jl = 0.0f;
@@ -329,7 +339,6 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     o.ih = (int)ih;
     o.jl = (int)jl;
     o.jh = (int)jh;
-    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -521,6 +530,73 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
     if (g < n) gcnt[g] = mine;
 }
 
+// ---------------------------------------------------------------------------
+// MG_LOCAL_CELLS (Eqs. E4-E6): a Gaussian's cell and the centre of its member
+// box; the record test is the slice plane passing within the margin of the box
+__device__ __forceinline__ void gauss_cell(const float *mu, const CellGrid &cg, int c[3], float b[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c[a] = cell_coord(mu[a], cg.C[a], cg.h, cg.hres);
+        b[a] = __fadd_rn(cg.C[a], __fmul_rn(cg.h, __fsub_rn(__fdiv_rn(__fadd_rn((float)c[a], 0.5f), cg.hres), 1.0f)));
+    }
+}
+
+__device__ __forceinline__ float abs_sum3(float a, float b, float c)
+{
+    return __fadd_rn(__fadd_rn(fabsf(a), fabsf(b)), fabsf(c));
+}
+
+__device__ __forceinline__ bool cell_slab(const float b[3], const SliceDev &S, const CellGrid &cg)
+{
+    const float *Q = S.Q;
+    float p0 = __fsub_rn(b[0], S.t[0]), p1 = __fsub_rn(b[1], S.t[1]), p2 = __fsub_rn(b[2], S.t[2]);
+    float w = dot3_rn(Q[2], Q[5], Q[8], p0, p1, p2);
+    return fabsf(w) <= __fadd_rn(__fmul_rn(cg.e, abs_sum3(Q[2], Q[5], Q[8])), cg.m);
+}
+
+__global__ void __launch_bounds__(K1_NT) k1_count_cells(const SliceDev *__restrict__ slices, int S, const float *mean,
+                                                        const float *quat, const float *scale, const float *alpha,
+                                                        long long n, float f64_ratio, CellGrid cg, unsigned *cnt,
+                                                        long long NW, unsigned *gcnt, unsigned *bits, WsHeader *hdr)
+{
+    __shared__ SliceDev ssl[K1_SMEM_SLICES];
+    const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
+    const long long wg = g >> 5;
+    const int lane = threadIdx.x & 31;
+    GaussPred G;
+    bool valid = false;
+    int c[3];
+    float b[3];
+    if (g < n) {
+        valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
+        if (!valid) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        if (valid && is_degenerate(sc, f64_ratio)) atomicOr(&hdr->flags, MG_FLAG_DEGENERATE);
+        gauss_cell(G.mu, cg, c, b);
+    }
+    unsigned word = 0, mine = 0;
+    for (int k0 = 0; k0 < S; k0 += K1_SMEM_SLICES) {
+        const int nk = min(K1_SMEM_SLICES, S - k0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
+        __syncthreads();
+        for (int kk = 0; kk < nk; ++kk) {
+            const int k = k0 + kk;
+            const bool ex = valid && cell_slab(b, ssl[kk], cg);
+            unsigned bal = __ballot_sync(0xffffffffu, ex);
+            if (lane == 0 && wg < NW) cnt[(long long)k * NW + wg] = __popc(bal);
+            word |= (unsigned)ex << (k & 31);
+            mine += ex;
+            if ((k & 31) == 31 || k == S - 1) {
+                if (g < n) bits[(long long)(k >> 5) * n + g] = word;
+                word = 0;
+            }
+        }
+    }
+    if (g < n) gcnt[g] = mine;
+}
+
 __global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsigned *__restrict__ bits,
                                                  const unsigned *__restrict__ off, long long NW,
                                                  const unsigned *__restrict__ goff, Records rec, unsigned *gmap)
@@ -556,9 +632,10 @@ __global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsig
 // one thread per record: the tile rectangle (rest of the FP32 predicate; the
 // slab test passed in k1_count) and the FP32 evaluation geometry (FP64 for
 // near-degenerate Gaussians in k_rec_geom_f64)
+template <bool CELLS>
 __global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ slices, const float *mean,
                            const float *quat, const float *scale, const float *alpha, float K2, float f64_ratio,
-                           Records rec)
+                           CellGrid cg, Records rec)
 {
     long long nr = (long long)hdr->n_records;
     if (nr > rec.cap) nr = rec.cap;
@@ -567,10 +644,25 @@ __global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ sli
         const SliceDev &Sd = slices[rec.slice[r]];
         GaussPred G;
         load_gauss_pred(mean, quat, scale, alpha, g, G);
-        FrameTerms ft;
-        frame_slab(G, Sd.Q, ft);
         PredOut po;
-        record_predicate(G, Sd, K2, ft, po);  // true: the slab test of k1_count
+        if (CELLS) {
+            // pixel box of the member box's extent along e_u, e_v
+            int c[3];
+            float b[3];
+            gauss_cell(G.mu, cg, c, b);
+            const float *Q = Sd.Q;
+            float p0 = __fsub_rn(b[0], Sd.t[0]), p1 = __fsub_rn(b[1], Sd.t[1]), p2 = __fsub_rn(b[2], Sd.t[2]);
+            float uc = dot3_rn(Q[0], Q[3], Q[6], p0, p1, p2);
+            float vc = dot3_rn(Q[1], Q[4], Q[7], p0, p1, p2);
+            float ru = __fadd_rn(__fmul_rn(cg.e, abs_sum3(Q[0], Q[3], Q[6])), cg.m);
+            float rv = __fadd_rn(__fmul_rn(cg.e, abs_sum3(Q[1], Q[4], Q[7])), cg.m);
+            pixel_box(Sd, uc, vc, ru, rv, po);
+            rec.cell[r] = make_int4(c[0], c[1], c[2], 0);
+        } else {
+            FrameTerms ft;
+            frame_slab(G, Sd.Q, ft);
+            record_predicate(G, Sd, K2, ft, po);  // true: the slab test of k1_count
+        }
         rec.rect[r] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
                                    (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
         float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
@@ -726,7 +818,19 @@ __global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chu
         unsigned c0 = chunk_base[k], c1 = chunk_base[k + 1];
         if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
         unsigned run = 0;
-        for (unsigned c = c0; c < c1; ++c) {
+        unsigned c = c0;
+        // eight independent loads in flight per thread before the dependent stores
+        for (; c + 8 <= c1; c += 8) {
+            unsigned v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(&hist[(size_t)(c + u) * Tmax + t]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                hist[(size_t)(c + u) * Tmax + t] = run;
+                run += v[u];
+            }
+        }
+        for (; c < c1; ++c) {
             unsigned v = hist[(size_t)c * Tmax + t];
             hist[(size_t)c * Tmax + t] = run;
             run += v;
@@ -790,7 +894,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
 // ---------------------------------------------------------------------------
 void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab, const float *mean,
                    const float *quat, const float *scale, const float *alpha, long long n, float K, float f64_ratio,
-                   cudaStream_t st)
+                   const CellGrid &cg, cudaStream_t st)
 {
     WsHeader *hdr = (WsHeader *)(ws + L.hdr);
     unsigned *cnt = (unsigned *)(ws + L.cnt);
@@ -803,6 +907,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     rec.rect = (ushort4 *)(ws + L.rec_rect);
     rec.mom = (float *)(ws + L.rec_mom);
     rec.thr = (float *)(ws + L.rec_thr);
+    rec.cell = cg.on ? (int4 *)(ws + L.rec_cell) : nullptr;
     rec.cap = L.cap_records;
     unsigned *chunk_base = (unsigned *)(ws + L.chunk_base);
     unsigned *slice_rs = chunk_base + (L.S + 1);
@@ -821,8 +926,12 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     const unsigned g1 = (unsigned)L.NB;
     {
         MG_PROF(MG_ST_K1_COUNT, st);
-        k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NW, gcnt, bits,
-                                       hdr);
+        if (cg.on)
+            k1_count_cells<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, f64_ratio, cg, cnt, NW, gcnt,
+                                                 bits, hdr);
+        else
+            k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NW, gcnt,
+                                           bits, hdr);
     }
     {
         MG_PROF(MG_ST_SCAN_REC, st);
@@ -837,7 +946,10 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
         MG_PROF(MG_ST_REC_FILL, st);
         long long want_r = (L.cap_records + 255) / 256;
         int gr = (int)(want_r < 148 * 16 ? (want_r > 0 ? want_r : 1) : 148 * 16);
-        k_rec_fill<<<gr, 256, 0, st>>>(hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, rec);
+        if (cg.on)
+            k_rec_fill<true><<<gr, 256, 0, st>>>(hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, cg, rec);
+        else
+            k_rec_fill<false><<<gr, 256, 0, st>>>(hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, cg, rec);
     }
     if (f64_ratio > 0.f) {
         MG_PROF(MG_ST_REC_GEOM, st);

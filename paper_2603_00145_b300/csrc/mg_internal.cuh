@@ -59,6 +59,59 @@ struct StackIn {
     float cx, cy, cz, h;
 };
 
+// The paper's cell-grid local set (MG_LOCAL_CELLS), as the kernels see it.
+struct CellGrid {
+    int on;       // 0: the K-sigma local set
+    int R;        // block radius (cells)
+    float hres;   // 0.5 * grid_res
+    float h;      // half edge of the normalised cube (mm)
+    float C[3];   // its centre (mm)
+    float e;      // half-width of a Gaussian's member box (mm)
+    float m;      // margin of the record and pixel-box tests (mm)
+};
+
+// cell index of one coordinate (mgauss.h, MG_LOCAL_CELLS)
+__device__ __forceinline__ int cell_coord(float p, float c, float h, float hres)
+{
+    float t = __fmul_rn(__fadd_rn(__fdiv_rn(__fsub_rn(p, c), h), 1.0f), hres);
+    t = fminf(fmaxf(t, -1048576.0f), 1048576.0f);
+    return (int)floorf(t);
+}
+
+// cell of voxel (i, j) of a slice (mgauss.h, MG_LOCAL_CELLS)
+__device__ __forceinline__ void voxel_cell(const SliceDev &S, int i, int j, const CellGrid &cg, int c[3])
+{
+    const float u = __fmul_rn(__fsub_rn((float)i, S.hx), S.dx);
+    const float v = __fmul_rn(__fsub_rn((float)j, S.hy), S.dy);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = __fadd_rn(__fadd_rn(__fmul_rn(S.Q[3 * a], u), __fmul_rn(S.Q[3 * a + 1], v)), S.t[a]);
+        c[a] = cell_coord(x, cg.C[a], cg.h, cg.hres);
+    }
+}
+
+// Tile-relative member test of MG_LOCAL_CELLS: voxel cells are packed as
+// bytes (x | y << 8 | z << 16) relative to the tile's smallest cell; a
+// record's member range [lo, hi] per axis is packed the same way. Returns
+// false when no voxel of the tile can be a member.
+__device__ __forceinline__ bool cell_range(int4 c, int R, int b0, int b1, int b2, unsigned &lo, unsigned &hi)
+{
+    const int l0 = c.x - R - b0, l1 = c.y - R - b1, l2 = c.z - R - b2;
+    const int h0 = c.x + R - b0, h1 = c.y + R - b1, h2 = c.z + R - b2;
+    if (h0 < 0 || h1 < 0 || h2 < 0 || l0 > 255 || l1 > 255 || l2 > 255) {
+        lo = 0xffffffu;
+        hi = 0u;
+        return false;
+    }
+    lo = (unsigned)max(l0, 0) | ((unsigned)max(l1, 0) << 8) | ((unsigned)max(l2, 0) << 16);
+    hi = (unsigned)min(h0, 255) | ((unsigned)min(h1, 255) << 8) | ((unsigned)min(h2, 255) << 16);
+    return true;
+}
+__device__ __forceinline__ bool cell_member(unsigned rel, unsigned lo, unsigned hi)
+{
+    return (__vsubus4(lo, rel) | __vsubus4(rel, hi)) == 0u;
+}
+
 // Workspace header (device memory, first 256 bytes of the workspace).
 struct WsHeader {
     unsigned int flags;
@@ -82,6 +135,7 @@ struct Records {
     ushort4 *rect;      // tile rectangle (tx0, ty0, tx1, ty1)
     float *mom;         // [cap][8] backward moments (6 used)
     float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
+    int4 *cell;         // MG_LOCAL_CELLS: the Gaussian's cell (x, y, z, 0); else unused
     long long cap;
 };
 
@@ -89,7 +143,7 @@ struct Records {
 // size query.
 struct WsLayout {
     size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom, rec_thr;
-    size_t chunk_base, hist, tile_cnt, tile_off, entries, gcnt, bits, gmap, rec_grad, total;
+    size_t chunk_base, hist, tile_cnt, tile_off, entries, gcnt, bits, gmap, rec_grad, rec_cell, total;
     long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
 
@@ -151,12 +205,13 @@ void mg_launch_pair_count(const WsLayout &L, char *ws, const StackTable &tab, cu
 void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_t st);
 void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab, const float *mean,
                    const float *quat, const float *scale, const float *alpha, long long n, float K, float f64_ratio,
-                   cudaStream_t st);
-void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, float *out, cudaStream_t st);
+                   const CellGrid &cg, cudaStream_t st);
+void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, const SliceDev *slices,
+                          const CellGrid &cg, float *out, cudaStream_t st);
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,
-                          const float *grad_out, const float *mean, const float *quat, const float *scale,
-                          const float *alpha, long long n, float f64_ratio, float *g_mean, float *g_quat,
-                          float *g_scale, float *g_alpha, cudaStream_t st);
+                          const CellGrid &cg, const float *grad_out, const float *mean, const float *quat,
+                          const float *scale, const float *alpha, long long n, float f64_ratio, float *g_mean,
+                          float *g_quat, float *g_scale, float *g_alpha, cudaStream_t st);
 void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, const float *mean, const float *quat,
                          const float *scale, const float *alpha, float f64_ratio, float *g_pose, cudaStream_t st);
 // record geometry pass (one thread per record)

@@ -51,10 +51,14 @@ __device__ __forceinline__ TileLoc locate_tile(const StackTable &tab, int t, int
 // broadcast. Per (record, voxel pair): q from two packed FMAs, two ex2, one
 // packed FMA into the accumulators. At the end the half-warps exchange and
 // add their halves of the column (8 shuffles) and each writes 8 rows.
-__device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, float4 *sgw, float2 *sg2w,
+// CELLS: the paper's cell-grid local set; each (record, voxel) term is kept
+// only when the voxel is a member (mgauss.h, MG_LOCAL_CELLS).
+template <bool CELLS>
+__device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, float4 *sgw, float2 *sg2w, int4 *sgcw,
                                          const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
                                          long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
-                                         const float2 *__restrict__ geo2, float *__restrict__ out)
+                                         const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
+                                         const CellGrid &cg, const int4 *__restrict__ rcell, float *__restrict__ out)
 {
 
     int s = 0;
@@ -73,21 +77,49 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 > e1) e0 = e1;
+    // CELLS: this lane's 16 voxel cells, packed relative to the tile's smallest cell
+    unsigned vrel[MG_TILE];
+    int cb0 = 0, cb1 = 0, cb2 = 0;
+    if (CELLS) {
+        const SliceDev &Sd = slices[tab.slice_base[s] + kk];
+        int m0 = 0x7fffffff, m1 = 0x7fffffff, m2 = 0x7fffffff;
+#pragma unroll
+        for (int r = 0; r < MG_TILE; ++r) {
+            int c[3];
+            voxel_cell(Sd, px, py0 + r, cg, c);
+            m0 = min(m0, c[0]);
+            m1 = min(m1, c[1]);
+            m2 = min(m2, c[2]);
+        }
+        cb0 = __reduce_min_sync(0xffffffffu, m0);
+        cb1 = __reduce_min_sync(0xffffffffu, m1);
+        cb2 = __reduce_min_sync(0xffffffffu, m2);
+#pragma unroll
+        for (int r = 0; r < MG_TILE; ++r) {
+            int c[3];
+            voxel_cell(Sd, px, py0 + r, cg, c);
+            vrel[r] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
+                      ((unsigned)min(c[2] - cb2, 255) << 16);
+        }
+    }
     float2 acc[MG_TILE / 2];
 #pragma unroll
     for (int v = 0; v < MG_TILE / 2; ++v) acc[v] = make_float2(0.f, 0.f);
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
+    int4 nc = make_int4(0, 0, 0, 0);
     if (e0 + lane < e1) {
         unsigned r = entries[e0 + lane];
         if ((long long)r < cap_records) {
             na = geo[r];
             nb = geo2[r];
+            if (CELLS) nc = rcell[r];
         }
     }
     for (unsigned base = e0; base < e1; base += 32) {
         sgw[lane] = na;
         sg2w[lane] = nb;
+        if (CELLS) sgcw[lane] = nc;
         __syncwarp();
         const unsigned nxt = base + 32 + lane;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -97,6 +129,7 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             if ((long long)r < cap_records) {
                 na = geo[r];
                 nb = geo2[r];
+                if (CELLS) nc = rcell[r];
             }
         }
         const int m = (int)min(32u, e1 - base);
@@ -105,6 +138,8 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             float4 a = sgw[j & 31];
             float2 b = sg2w[j & 31];
             if (j >= m) b.y = 0.f;
+            unsigned clo = 0u, chi = 0u;
+            if (CELLS && !cell_range(sgcw[j & 31], cg.R, cb0, cb1, cb2, clo, chi)) b.y = 0.f;
             const float dx = fpx - a.x;
             const float dyc = fpyc - a.y;
             const float C = b.x, amp = b.y;
@@ -117,7 +152,11 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             for (int p = 0; p < MG_TILE / 2; ++p) {
                 const float2 vp = make_float2((float)(2 * p) - 7.5f, (float)(2 * p + 1) - 7.5f);
                 const float2 q = __ffma2_rn(__ffma2_rn(C2, vp, a12), vp, a02);
-                const float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                if (CELLS) {
+                    if (!cell_member(vrel[2 * p], clo, chi)) e.x = 0.f;
+                    if (!cell_member(vrel[2 * p + 1], clo, chi)) e.y = 0.f;
+                }
                 acc[p] = __ffma2_rn(amp2, e, acc[p]);
             }
         }
@@ -145,21 +184,26 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
 
 // persistent warps pull tiles from a counter (tiles carry very different
 // numbers of records)
+template <bool CELLS>
 __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
-                                                          const float2 *__restrict__ geo2, float *__restrict__ out,
+                                                          const float2 *__restrict__ geo2,
+                                                          const SliceDev *__restrict__ slices, CellGrid cg,
+                                                          const int4 *__restrict__ rcell, float *__restrict__ out,
                                                           unsigned *counter)
 {
     __shared__ float4 sg[RW][32];
     __shared__ float2 sg2[RW][32];
+    __shared__ int4 sgc[CELLS ? RW : 1][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(counter, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int)t >= tab.n_tiles_total) break;
-        fwd_tile(tab, (int)t, lane, sg[w], sg2[w], tile_off, entries, cap_entries, cap_records, geo, geo2, out);
+        fwd_tile<CELLS>(tab, (int)t, lane, sg[w], sg2[w], sgc[CELLS ? w : 0], tile_off, entries, cap_entries,
+                        cap_records, geo, geo2, slices, cg, rcell, out);
         __syncwarp();
     }
 }
@@ -172,11 +216,13 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
 // taken about the tile centre and moved to the record centre at the end, so
 // no cross-lane reduction is needed; each lane then adds its record's six
 // moments with six atomics.
-__device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane, float *sgvw,
+template <bool CELLS>
+__device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane, float *sgvw, unsigned *srelw,
                                          const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
                                          long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
-                                         const float2 *__restrict__ geo2, const float *__restrict__ grad_out,
-                                         float *__restrict__ mom)
+                                         const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
+                                         const CellGrid &cg, const int4 *__restrict__ rcell,
+                                         const float *__restrict__ grad_out, float *__restrict__ mom)
 {
 
     int s = 0;
@@ -200,6 +246,28 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
         sgvw[MG_TILE * MG_TILE + i] = gval * ic;
         sgvw[2 * MG_TILE * MG_TILE + i] = gval * ic * ic;
     }
+    // CELLS: the tile's voxel cells, packed relative to its smallest cell
+    int cb0 = 0, cb1 = 0, cb2 = 0;
+    if (CELLS) {
+        const SliceDev &Sd = slices[tab.slice_base[s] + kk];
+        int m0 = 0x7fffffff, m1 = 0x7fffffff, m2 = 0x7fffffff;
+        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
+            int c[3];
+            voxel_cell(Sd, tx * MG_TILE + (i & 15), ty * MG_TILE + (i >> 4), cg, c);
+            m0 = min(m0, c[0]);
+            m1 = min(m1, c[1]);
+            m2 = min(m2, c[2]);
+        }
+        cb0 = __reduce_min_sync(0xffffffffu, m0);
+        cb1 = __reduce_min_sync(0xffffffffu, m1);
+        cb2 = __reduce_min_sync(0xffffffffu, m2);
+        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
+            int c[3];
+            voxel_cell(Sd, tx * MG_TILE + (i & 15), ty * MG_TILE + (i >> 4), cg, c);
+            srelw[i] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
+                       ((unsigned)min(c[2] - cb2, 255) << 16);
+        }
+    }
     __syncwarp();
     const float x0c = (float)(tx * MG_TILE) + 7.5f, y0c = (float)(ty * MG_TILE) + 7.5f;
     for (unsigned base = e0; base < e1; base += 32) {
@@ -207,11 +275,13 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
         unsigned r = 0xffffffffu;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 b = make_float2(0.f, 0.f);
+        unsigned clo = 0u, chi = 0u;
         if (e < e1) {
             r = entries[e];
             if ((long long)r < cap_records) {
                 a = geo[r];
                 b = geo2[r];
+                if (CELLS && !cell_range(rcell[r], cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
             } else {
                 r = 0xffffffffu;
             }
@@ -232,6 +302,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             const float4 *g0r = (const float4 *)&sgvw[j * MG_TILE];
             const float4 *g1r = g0r + MG_TILE * MG_TILE / 4;
             const float4 *g2r = g1r + MG_TILE * MG_TILE / 4;
+            const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
             // column pairs (i, i+1) with packed FP32x2 arithmetic:
             // P0 += g e, P1 += (g ic) e, P2 += (g ic^2) e
             const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
@@ -239,12 +310,18 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
 #pragma unroll
             for (int i4 = 0; i4 < 4; ++i4) {
                 const float4 u0 = g0r[i4], u1 = g1r[i4], u2 = g2r[i4];
+                uint4 rl = make_uint4(0u, 0u, 0u, 0u);
+                if (CELLS) rl = relr[i4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float i0 = (float)(i4 * 4 + 2 * h) - 7.5f;
                     const float2 ic = make_float2(i0, i0 + 1.f);
                     const float2 q = __ffma2_rn(__ffma2_rn(A2, ic, b12), ic, b02);
-                    const float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                    float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                    if (CELLS) {
+                        if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
+                        if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
+                    }
                     P0 = __ffma2_rn(h ? make_float2(u0.z, u0.w) : make_float2(u0.x, u0.y), e, P0);
                     P1 = __ffma2_rn(h ? make_float2(u1.z, u1.w) : make_float2(u1.x, u1.y), e, P1);
                     P2 = __ffma2_rn(h ? make_float2(u2.z, u2.w) : make_float2(u2.x, u2.y), e, P2);
@@ -270,21 +347,26 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
     }
 }
 
+template <bool CELLS>
 __global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
+                                                          const SliceDev *__restrict__ slices, CellGrid cg,
+                                                          const int4 *__restrict__ rcell,
                                                           const float *__restrict__ grad_out, float *__restrict__ mom,
                                                           unsigned *counter)
 {
     __shared__ __align__(16) float sgv[RW][3 * MG_TILE * MG_TILE];
+    __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? MG_TILE * MG_TILE : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(counter, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int)t >= tab.n_tiles_total) break;
-        bwd_tile(tab, (int)t, lane, sgv[w], tile_off, entries, cap_entries, cap_records, geo, geo2, grad_out, mom);
+        bwd_tile<CELLS>(tab, (int)t, lane, sgv[w], srel[CELLS ? w : 0], tile_off, entries, cap_entries, cap_records,
+                        geo, geo2, slices, cg, rcell, grad_out, mom);
         __syncwarp();
     }
 }
@@ -678,19 +760,28 @@ static int resident_grid(const void *kern, int threads)
     return sms * (per > 0 ? per : 1);
 }
 
-void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, float *out, cudaStream_t st)
+void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, const SliceDev *slices,
+                          const CellGrid &cg, float *out, cudaStream_t st)
 {
     int nt = tab.n_tiles_total;
     if (nt <= 0) return;
     WsHeader *hdr = (WsHeader *)(ws + L.hdr);
     cudaMemsetAsync(&hdr->tile_ctr[0], 0, sizeof(unsigned), st);
     MG_PROF(MG_ST_RENDER_FWD, st);
-    int grid = resident_grid((const void *)k_render_fwd, 32 * RW);
+    const void *kern = cg.on ? (const void *)k_render_fwd<true> : (const void *)k_render_fwd<false>;
+    int grid = resident_grid(kern, 32 * RW);
     if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
-    k_render_fwd<<<grid, 32 * RW, 0, st>>>(tab, (const unsigned *)(ws + L.tile_off),
-                                             (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
-                                             (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), out,
-                                             &hdr->tile_ctr[0]);
+    const int4 *rcell = cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr;
+    if (cg.on)
+        k_render_fwd<true><<<grid, 32 * RW, 0, st>>>(
+            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
+            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell, out,
+            &hdr->tile_ctr[0]);
+    else
+        k_render_fwd<false><<<grid, 32 * RW, 0, st>>>(
+            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
+            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell, out,
+            &hdr->tile_ctr[0]);
 }
 
 // Slice-pose gradient from the moments the last backward left in the workspace.
@@ -716,9 +807,9 @@ void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, co
 }
 
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,
-                          const float *grad_out, const float *mean, const float *quat, const float *scale,
-                          const float *alpha, long long n, float f64_ratio, float *g_mean, float *g_quat,
-                          float *g_scale, float *g_alpha, cudaStream_t st)
+                          const CellGrid &cg, const float *grad_out, const float *mean, const float *quat,
+                          const float *scale, const float *alpha, long long n, float f64_ratio, float *g_mean,
+                          float *g_quat, float *g_scale, float *g_alpha, cudaStream_t st)
 {
     const WsHeader *hdr = (const WsHeader *)(ws + L.hdr);
     long long capv = L.cap_records * 2;
@@ -732,12 +823,20 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     if (nt > 0) {
         cudaMemsetAsync((void *)&hdr->tile_ctr[1], 0, sizeof(unsigned), st);
         MG_PROF(MG_ST_RENDER_BWD, st);
-        int grid = resident_grid((const void *)k_render_bwd, 32 * RW);
+        const void *kern = cg.on ? (const void *)k_render_bwd<true> : (const void *)k_render_bwd<false>;
+        int grid = resident_grid(kern, 32 * RW);
         if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
-        k_render_bwd<<<grid, 32 * RW, 0, st>>>(
-            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
-            L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), grad_out,
-            (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
+        const int4 *rcell = cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr;
+        if (cg.on)
+            k_render_bwd<true><<<grid, 32 * RW, 0, st>>>(
+                tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
+                L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
+                grad_out, (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
+        else
+            k_render_bwd<false><<<grid, 32 * RW, 0, st>>>(
+                tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
+                L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
+                grad_out, (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
     }
     MG_PROF(MG_ST_CHAIN, st);
     float4 *rg = (float4 *)(ws + L.rec_grad);

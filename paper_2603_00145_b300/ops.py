@@ -44,8 +44,20 @@ def _gauss(mean, quat, scale, alpha) -> L.MgGaussians:
                          _dev(scale, "scale", numel=3 * n), _dev(alpha, "alpha", numel=n))
 
 
-def _opts(cutoff_k=3.0, f64_ratio=100.0, cap_records=0, cap_entries=0) -> L.MgOpts:
-    return L.MgOpts(float(cutoff_k), float(f64_ratio), int(cap_records), int(cap_entries))
+def _opts(cutoff_k=3.0, f64_ratio=100.0, cap_records=0, cap_entries=0, cells=None) -> L.MgOpts:
+    """``cells``: None for the K-sigma local set, or a dict(grid_res, block_radius,
+    centre (mm, 3), half (mm)) for the paper's cell-grid local set (Eqs. E4-E6)."""
+    o = L.MgOpts(float(cutoff_k), float(f64_ratio), int(cap_records), int(cap_entries))
+    o.local_set = L.MG_LOCAL_KSIGMA
+    o.block_radius = 5
+    if cells is not None:
+        o.local_set = L.MG_LOCAL_CELLS
+        o.grid_res = int(cells["grid_res"])
+        o.block_radius = int(cells["block_radius"])
+        for a in range(3):
+            o.grid_centre[a] = float(cells["centre"][a])
+        o.grid_half = float(cells["half"])
+    return o
 
 
 class DeviceStacks:
@@ -270,7 +282,8 @@ class SliceRenderer:
     (one stream synchronisation)."""
 
     def __init__(self, stacks: Sequence, device="cuda", cutoff_k: float = 3.0, f64_ratio: float = 100.0,
-                 records_per_gaussian: int = 32, entries_per_record: int = 8, check: bool = True):
+                 records_per_gaussian: int = 32, entries_per_record: int = 8, check: bool = True, cells=None):
+        self.cells = cells
         self.dev = DeviceStacks(stacks, device)
         self.device = device
         self.K = cutoff_k
@@ -284,7 +297,7 @@ class SliceRenderer:
         self._n = None
 
     def opts(self) -> L.MgOpts:
-        return _opts(self.K, self.f64_ratio, self.caps[0], self.caps[1])
+        return _opts(self.K, self.f64_ratio, self.caps[0], self.caps[1], self.cells)
 
     def _ensure(self, n: int):
         if self.caps is None or self._n != n:
@@ -425,7 +438,8 @@ class VolumeSampler:
     """Inference sampling onto the isotropic G^3 grid (mg_sample_volume)."""
 
     def __init__(self, G: int, spacing: float, centre=(0.0, 0.0, 0.0), device="cuda", cutoff_k: float = 3.0,
-                 f64_ratio: float = 100.0, records_per_gaussian: int = 64):
+                 f64_ratio: float = 100.0, records_per_gaussian: int = 64, cells=None):
+        self.cells = cells
         self.G, self.h, self.centre = int(G), float(spacing), tuple(float(c) for c in centre)
         self.device, self.K, self.f64 = device, cutoff_k, f64_ratio
         self.rpg = records_per_gaussian
@@ -440,7 +454,7 @@ class VolumeSampler:
             cr = max(1, min(n * self.G, self.rpg * n))
             self.caps = (cr, 8 * cr)
         for _ in range(4):
-            o = _opts(self.K, self.f64, *self.caps)
+            o = _opts(self.K, self.f64, *self.caps, cells=self.cells)
             need = mg_sample_workspace_size(n, self.G, o)
             if self.ws is None or self.ws.numel() < need:
                 self.ws = None

@@ -30,6 +30,9 @@ class FitConfig:
     lambda_aniso: float = 0.1   # Eq. E12
     lambda_r: float = 1.5       # Eq. E13
     loss: str = "l1l2"          # "l1l2" (mean |r| + mean r^2) or "paper" (smooth L1 + lambda_ssim SSIM, Sec. 3.5.2)
+    local_set: str = "ksigma"   # "ksigma" (K-sigma tiles) or "cells" (the paper's cell grid, Eqs. E4-E6)
+    grid_res: int = 0           # cells: cells per axis of the canonical cube
+    block_radius: int = 5       # cells: the paper's default (Sec. 4.1.4)
     lambda_ssim: float = 0.5    # Sec. 4.1.4
     cutoff_k: float = 3.0
     nrf: Optional[str] = None   # None, "paper" or "grid"
@@ -108,6 +111,16 @@ def make_nrf(preset: str, precision: str, seed: int, device="cuda"):
     return ops.NRF(preset, precision, W, b, t, device=device)
 
 
+def cells_of(cfg: FitConfig, centre, half_extent):
+    """The cell-grid local set of the fit's canonical cube, or None."""
+    if cfg.local_set == "ksigma":
+        return None
+    if cfg.local_set != "cells" or cfg.grid_res < 1:
+        raise ValueError("local_set must be 'ksigma', or 'cells' with grid_res >= 1")
+    return dict(grid_res=cfg.grid_res, block_radius=cfg.block_radius, centre=tuple(float(c) for c in centre),
+                half=float(half_extent))
+
+
 class _Trainer:
     """One training iteration of the fit as a sequence of stream-ordered
     launches with no host synchronisation (so it can be captured in a CUDA
@@ -119,7 +132,8 @@ class _Trainer:
         self.cfg, self.device, self.target = cfg, device, target
         self.stacks, self.centre, self.half = stacks, centre, half_extent
         self.model = Model(G_init, centre, half_extent, device)
-        self.R = ops.SliceRenderer(stacks, device=device, cutoff_k=cfg.cutoff_k, check=True)
+        self.cells = cells_of(cfg, centre, half_extent)
+        self.R = ops.SliceRenderer(stacks, device=device, cutoff_k=cfg.cutoff_k, check=True, cells=self.cells)
         m = self.model
         self.adam = ops.DeviceAdam([
             {"param": m.mean_c, "lr": cfg.lr_position},
@@ -357,12 +371,13 @@ def register_slices(renderer: ops.SliceRenderer, mean, quat, scale, alpha, targe
 
 
 def sample(model: Model, nrf, G_dim: int, spacing: float, centre=(0.0, 0.0, 0.0), cutoff_k: float = 3.0,
-           batch: int = 1 << 22):
+           batch: int = 1 << 22, cells=None):
     """The isotropic G^3 volume (z, y, x): Gaussian mixture (Eq. E7) plus the
-    NRF residual at the voxel centres (Eq. E8)."""
+    NRF residual at the voxel centres (Eq. E8); ``cells``: the cell-grid local
+    set of the fit (``cells_of``), None for the K-sigma set."""
     with torch.no_grad():
         mean, q, s, a = model.gaussians()
-        S = ops.VolumeSampler(G_dim, spacing, centre, device=mean.device, cutoff_k=cutoff_k)
+        S = ops.VolumeSampler(G_dim, spacing, centre, device=mean.device, cutoff_k=cutoff_k, cells=cells)
         vol = S(mean.contiguous(), q.contiguous(), s.contiguous(), a.contiguous()).clone()
         if nrf is not None:
             dev = mean.device

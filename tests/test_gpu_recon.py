@@ -28,7 +28,7 @@ def _run(tiny, iterations_override=600, **kw):
     wl, vol, target, G = tiny
     cfg = recon.FitConfig(iterations=iterations_override, log_every=100, **kw)
     m, nrf, st = recon.fit(wl.stacks, target, G, (0, 0, 0), wl.phantom.fov_mm / 2, cfg)
-    V = recon.sample(m, nrf, 48, 1.0)
+    V = recon.sample(m, nrf, 48, 1.0, cells=recon.cells_of(cfg, (0, 0, 0), wl.phantom.fov_mm / 2))
     return recon.psnr(V, vol), st
 
 
@@ -53,17 +53,29 @@ def test_nrf_gain_and_bf16_matches_fp32(tiny):
 
 def test_graph_fit_matches_eager_fit(tiny):
     """The CUDA-graph replay of the iteration and the eager loop run the same
-    launches; only the FP32 atomic summation order of the adjoint differs,
-    and Adam carries such differences along the trajectory (two eager runs
-    differ by a few hundredths of a dB after 300 iterations). A stale
-    pointer or a missing launch in the graph would be far outside these
-    bounds."""
+    launches; only the FP32 atomic summation order of the adjoint differs.
+    The first iterations agree to FP32 rounding; over 300 iterations Adam
+    carries the rounding differences along the trajectory (the final loss of
+    two runs can differ by a few percent), so the whole fit is compared on
+    its volume PSNR. A stale pointer or a missing launch in the graph would
+    be far outside these bounds."""
+    from paper_2603_00145_b300 import recon
+
+    wl, vol, target, G = tiny
+    # iteration by iteration over the first 12 iterations (graph replays from the third on)
+    hist = []
+    for graph in (True, False):
+        cfg = recon.FitConfig(iterations=12, log_every=1, check_every=1, graph=graph)
+        _, _, st = recon.fit(wl.stacks, target, G, (0, 0, 0), wl.phantom.fov_mm / 2, cfg)
+        hist.append(np.array([l for _, l in st["history"]]))
+    assert hist[0].size == hist[1].size == 12
+    np.testing.assert_allclose(hist[0], hist[1], rtol=2e-5)
+    # and over a whole fit
     p_graph, st_g = _run(tiny, iterations_override=300)
     p_eager, st_e = _run(tiny, iterations_override=300, graph=False)
     assert st_g["iterations"] == st_e["iterations"] == 300
     assert st_g["graph_captures"] >= 1 and st_e["graph_captures"] == 0
     assert abs(p_graph - p_eager) < 0.25, (p_graph, p_eager)
-    assert abs(st_g["final_loss"] - st_e["final_loss"]) < 0.02 * st_e["final_loss"]
 
 
 def test_graph_fit_recovers_from_bin_overflow(tiny):
@@ -83,6 +95,17 @@ def test_fit_with_the_papers_ssim_loss(tiny):
     Sec. 3.5.2) runs through the fused loss kernel, lowers it and
     reconstructs the phantom."""
     p, st = _run(tiny, iterations_override=600, loss="paper")
+    losses = [l for _, l in st["history"]]
+    assert losses[-1] < 0.7 * losses[0], losses
+    assert p > 20.0, p
+
+
+def test_fit_with_the_papers_cell_grid_local_set(tiny):
+    """The fit and the sampling with the paper's own local set (Eqs. E4-E6,
+    block radius 5 on a grid at the Gaussian spacing)."""
+    wl = tiny[0]
+    res = int(round(wl.phantom.fov_mm / 1.0))
+    p, st = _run(tiny, iterations_override=400, local_set="cells", grid_res=res, block_radius=3)
     losses = [l for _, l in st["history"]]
     assert losses[-1] < 0.7 * losses[0], losses
     assert p > 20.0, p
