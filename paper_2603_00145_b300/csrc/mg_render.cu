@@ -44,23 +44,25 @@ __device__ __forceinline__ TileLoc locate_tile(const StackTable &tab, int t, int
     return L;
 }
 
-// K4: one warp per 16x16 tile. The two half-warps take alternate records of
-// the tile's list; lane c of a half-warp owns pixel column c of the tile (16
-// rows), so the per-record set-up is shared by 16 voxels. Records are staged
-// 32 at a time in shared memory (software-pipelined global loads) and read by
-// broadcast. Per (record, voxel pair): q from two packed FMAs, two ex2, one
-// packed FMA into the accumulators. At the end the half-warps exchange and
-// add their halves of the column (8 shuffles) and each writes 8 rows.
+// K4: one warp per 16x16 tile. The four quarter-warps take every fourth
+// record of the tile's list; lane c of a quarter owns pixel columns 2c and
+// 2c+1 of the tile over all 16 rows, so the per-record set-up is shared by 32
+// voxels. Records are staged 32 at a time in shared memory (software-
+// pipelined global loads) and read by broadcast. Per row: the quadratic of
+// both columns with two packed FMAs (the row offset is an exact packed
+// counter), two ex2, one packed FMA into the row's (column, column + 1)
+// accumulator. At the end the quarters reduce-scatter their partial sums
+// (24 shuffles, fixed order) and each lane writes 4 rows of its two columns.
 // CELLS: the paper's cell-grid local set; each (record, voxel) term is kept
 // only when the voxel is a member (mgauss.h, MG_LOCAL_CELLS).
 template <bool CELLS>
 __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, float4 *sgw, float2 *sg2w, int4 *sgcw,
-                                         const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
-                                         long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
+                                         unsigned *srelw, const unsigned *__restrict__ tile_off,
+                                         const unsigned *__restrict__ entries, long long cap_entries,
+                                         long long cap_records, const float4 *__restrict__ geo,
                                          const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
                                          const CellGrid &cg, const int4 *__restrict__ rcell, float *__restrict__ out)
 {
-
     int s = 0;
     while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
     const int TX = tab.TX[s], T = TX * tab.TY[s];
@@ -69,24 +71,22 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
     const int ty = within / TX, tx = within - ty * TX;
     const int W = tab.W[s], H = tab.H[s];
     const long long pixbase = tab.pix_base[s] + (long long)kk * H * W;
-    const int half = lane >> 4, col = lane & 15;
-    const int px = tx * MG_TILE + col, py0 = ty * MG_TILE;
+    const int qw = lane >> 3, c8 = lane & 7;
+    const int px0 = tx * MG_TILE + 2 * c8, py0 = ty * MG_TILE;
     // rows are addressed relative to the tile's middle row (offsets +-7.5) to
     // keep the terms of the expanded quadratic small
-    const float fpx = (float)px, fpyc = (float)py0 + 7.5f;
+    const float fpx = (float)px0, fpyc = (float)py0 + 7.5f;
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 > e1) e0 = e1;
-    // CELLS: this lane's 16 voxel cells, packed relative to the tile's smallest cell
-    unsigned vrel[MG_TILE];
+    // CELLS: the tile's voxel cells, packed relative to its smallest cell
     int cb0 = 0, cb1 = 0, cb2 = 0;
     if (CELLS) {
         const SliceDev &Sd = slices[tab.slice_base[s] + kk];
         int m0 = 0x7fffffff, m1 = 0x7fffffff, m2 = 0x7fffffff;
-#pragma unroll
-        for (int r = 0; r < MG_TILE; ++r) {
+        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
             int c[3];
-            voxel_cell(Sd, px, py0 + r, cg, c);
+            voxel_cell(Sd, tx * MG_TILE + (i & 15), py0 + (i >> 4), cg, c);
             m0 = min(m0, c[0]);
             m1 = min(m1, c[1]);
             m2 = min(m2, c[2]);
@@ -94,17 +94,18 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
         cb0 = __reduce_min_sync(0xffffffffu, m0);
         cb1 = __reduce_min_sync(0xffffffffu, m1);
         cb2 = __reduce_min_sync(0xffffffffu, m2);
-#pragma unroll
-        for (int r = 0; r < MG_TILE; ++r) {
+        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
             int c[3];
-            voxel_cell(Sd, px, py0 + r, cg, c);
-            vrel[r] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
-                      ((unsigned)min(c[2] - cb2, 255) << 16);
+            voxel_cell(Sd, tx * MG_TILE + (i & 15), py0 + (i >> 4), cg, c);
+            srelw[i] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
+                       ((unsigned)min(c[2] - cb2, 255) << 16);
         }
+        __syncwarp();
     }
-    float2 acc[MG_TILE / 2];
+    float2 acc[MG_TILE];  // per row: (column px0, column px0 + 1)
 #pragma unroll
-    for (int v = 0; v < MG_TILE / 2; ++v) acc[v] = make_float2(0.f, 0.f);
+    for (int r = 0; r < MG_TILE; ++r) acc[r] = make_float2(0.f, 0.f);
+    const float2 one2 = make_float2(1.f, 1.f);
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 nc = make_int4(0, 0, 0, 0);
@@ -133,51 +134,66 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             }
         }
         const int m = (int)min(32u, e1 - base);
-        for (int j2 = 0; j2 < m; j2 += 2) {
-            const int j = j2 + half;  // this half-warp's record (zero record past the end)
-            float4 a = sgw[j & 31];
+        for (int j4 = 0; j4 < m; j4 += 4) {
+            const int j = j4 + qw;  // this quarter-warp's record (zero record past the end)
+            const float4 a = sgw[j & 31];
             float2 b = sg2w[j & 31];
             if (j >= m) b.y = 0.f;
             unsigned clo = 0u, chi = 0u;
             if (CELLS && !cell_range(sgcw[j & 31], cg.R, cb0, cb1, cb2, clo, chi)) b.y = 0.f;
-            const float dx = fpx - a.x;
-            const float dyc = fpyc - a.y;
-            const float C = b.x, amp = b.y;
-            const float cdy = C * dyc;
-            const float a1 = fmaf(a.w, dx, cdy + cdy);
-            const float a0 = fmaf(fmaf(a.z, dx, a.w * dyc), dx, cdy * dyc);
-            const float2 C2 = make_float2(C, C), a12 = make_float2(a1, a1), a02 = make_float2(a0, a0);
-            const float2 amp2 = make_float2(amp, amp);
+            // q(column, v) = C v^2 + (B dx + 2 C dyc) v + (A dx^2 + B dx dyc + C dyc^2),
+            // dx the column's offset from the record centre, v = row - 7.5
+            const float A = a.z, B = a.w, C = b.x;
+            const float dx = fpx - a.x, dx1 = dx + 1.f, dyc = fpyc - a.y;
+            const float Bdy = B * dyc, Cdy = C * dyc, Cdy2 = Cdy + Cdy, Cdd = Cdy * dyc;
+            const float2 a12 = make_float2(fmaf(B, dx, Cdy2), fmaf(B, dx1, Cdy2));
+            const float2 a02 = make_float2(fmaf(fmaf(A, dx, Bdy), dx, Cdd), fmaf(fmaf(A, dx1, Bdy), dx1, Cdd));
+            const float2 C2 = make_float2(C, C), amp2 = make_float2(b.y, b.y);
+            float2 vv = make_float2(-7.5f, -7.5f);
 #pragma unroll
-            for (int p = 0; p < MG_TILE / 2; ++p) {
-                const float2 vp = make_float2((float)(2 * p) - 7.5f, (float)(2 * p + 1) - 7.5f);
-                const float2 q = __ffma2_rn(__ffma2_rn(C2, vp, a12), vp, a02);
+            for (int r = 0; r < MG_TILE; ++r) {
+                const float2 q = __ffma2_rn(__ffma2_rn(C2, vv, a12), vv, a02);
                 float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
                 if (CELLS) {
-                    if (!cell_member(vrel[2 * p], clo, chi)) e.x = 0.f;
-                    if (!cell_member(vrel[2 * p + 1], clo, chi)) e.y = 0.f;
+                    const uint2 rl = *(const uint2 *)&srelw[r * MG_TILE + 2 * c8];
+                    if (!cell_member(rl.x, clo, chi)) e.x = 0.f;
+                    if (!cell_member(rl.y, clo, chi)) e.y = 0.f;
                 }
-                acc[p] = __ffma2_rn(amp2, e, acc[p]);
+                acc[r] = __ffma2_rn(amp2, e, acc[r]);
+                vv = __ffma2_rn(one2, one2, vv);  // exact: v + 1
             }
         }
         __syncwarp();
     }
-    // half 0 keeps rows 0..7 and half 1 rows 8..15 of the column
+    // reduce-scatter over the four quarters (lanes c8, c8 + 8, c8 + 16, c8 + 24):
+    // across xor 16 the upper pair keeps rows 8..15, across xor 8 the odd one
+    // keeps the upper four of those rows
+    const bool up16 = (qw >> 1) != 0, up8 = (qw & 1) != 0;
 #pragma unroll
-    for (int p = 0; p < MG_TILE / 4; ++p) {
-        const float2 send = half ? acc[p] : acc[p + MG_TILE / 4];
+    for (int r = 0; r < MG_TILE / 2; ++r) {
+        const float2 send = up16 ? acc[r] : acc[r + MG_TILE / 2];
         float2 recv;
         recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
         recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
-        const float2 keep = half ? acc[p + MG_TILE / 4] : acc[p];
-        acc[p] = make_float2(keep.x + recv.x, keep.y + recv.y);
+        const float2 keep = up16 ? acc[r + MG_TILE / 2] : acc[r];
+        acc[r] = make_float2(keep.x + recv.x, keep.y + recv.y);
     }
-    if (px < W) {
-        const int r0 = py0 + half * (MG_TILE / 2);
 #pragma unroll
-        for (int p = 0; p < MG_TILE / 4; ++p) {
-            if (r0 + 2 * p < H) out[pixbase + (long long)(r0 + 2 * p) * W + px] = acc[p].x;
-            if (r0 + 2 * p + 1 < H) out[pixbase + (long long)(r0 + 2 * p + 1) * W + px] = acc[p].y;
+    for (int r = 0; r < MG_TILE / 4; ++r) {
+        const float2 send = up8 ? acc[r] : acc[r + MG_TILE / 4];
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
+        const float2 keep = up8 ? acc[r + MG_TILE / 4] : acc[r];
+        acc[r] = make_float2(keep.x + recv.x, keep.y + recv.y);
+    }
+    const int r0 = py0 + (up16 ? MG_TILE / 2 : 0) + (up8 ? MG_TILE / 4 : 0);
+#pragma unroll
+    for (int r = 0; r < MG_TILE / 4; ++r) {
+        if (r0 + r < H) {
+            float *row = out + pixbase + (long long)(r0 + r) * W;
+            if (px0 < W) row[px0] = acc[r].x;
+            if (px0 + 1 < W) row[px0 + 1] = acc[r].y;
         }
     }
 }
@@ -185,7 +201,7 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
 // persistent warps pull tiles from a counter (tiles carry very different
 // numbers of records)
 template <bool CELLS>
-__global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
+__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 5) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
@@ -196,14 +212,15 @@ __global__ void __launch_bounds__(32 * RW) k_render_fwd(StackTable tab, const un
     __shared__ float4 sg[RW][32];
     __shared__ float2 sg2[RW][32];
     __shared__ int4 sgc[CELLS ? RW : 1][32];
+    __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? MG_TILE * MG_TILE : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(counter, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int)t >= tab.n_tiles_total) break;
-        fwd_tile<CELLS>(tab, (int)t, lane, sg[w], sg2[w], sgc[CELLS ? w : 0], tile_off, entries, cap_entries,
-                        cap_records, geo, geo2, slices, cg, rcell, out);
+        fwd_tile<CELLS>(tab, (int)t, lane, sg[w], sg2[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off, entries,
+                        cap_entries, cap_records, geo, geo2, slices, cg, rcell, out);
         __syncwarp();
     }
 }
@@ -270,6 +287,12 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
     }
     __syncwarp();
     const float x0c = (float)(tx * MG_TILE) + 7.5f, y0c = (float)(ty * MG_TILE) + 7.5f;
+    // column offsets as register pairs, formed once per tile (see fwd_tile)
+    const float rz = __uint_as_float(e1 & 0x80000000u);
+    float2 icr[MG_TILE / 2];
+#pragma unroll
+    for (int c = 0; c < MG_TILE / 2; ++c)
+        icr[c] = make_float2((float)(2 * c) - 7.5f + rz, (float)(2 * c + 1) - 7.5f + rz);
     for (unsigned base = e0; base < e1; base += 32) {
         const unsigned e = base + lane;
         unsigned r = 0xffffffffu;
@@ -314,8 +337,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
                 if (CELLS) rl = relr[i4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float i0 = (float)(i4 * 4 + 2 * h) - 7.5f;
-                    const float2 ic = make_float2(i0, i0 + 1.f);
+                    const float2 ic = icr[i4 * 2 + h];
                     const float2 q = __ffma2_rn(__ffma2_rn(A2, ic, b12), ic, b02);
                     float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
                     if (CELLS) {
@@ -348,7 +370,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
 }
 
 template <bool CELLS>
-__global__ void __launch_bounds__(32 * RW) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
+__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 1) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
