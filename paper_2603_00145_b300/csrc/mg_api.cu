@@ -480,11 +480,13 @@ mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
     mg_opts o = resolve_opts(opts, g->n, S);
     WsLayout L = make_layout(g->n, st, o);
     if (ws_bytes < L.total) return fail(MG_ERR_INVALID_ARG, "workspace too small");
+    bool again = false;  // a backward already ran on this forward: its moments must be cleared
     {
         std::lock_guard<std::mutex> lk(g_tag_mu);
         auto it = g_tags.find(ws);
         if (it == g_tags.end() || !same_tag(it->second, make_tag(g, st, o)))
             return fail(MG_ERR_STALE_WORKSPACE, "mg_render_bwd: no matching mg_render_fwd on this workspace");
+        again = it->second.bwd_done;
         it->second.bwd_done = true;
     }
     if (g->n == 0) return MG_OK;
@@ -493,7 +495,8 @@ mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
     char *w = (char *)ws;
     StackTable tab = make_table(st);
     mg_launch_render_bwd(L, w, (const SliceDev *)(w + L.slices), tab, cg, grad_out, g->mean, g->quat, g->scale,
-                         g->alpha, g->n, o.f64_ratio, g_mean, g_quat, g_scale, g_alpha, (cudaStream_t)stream);
+                         g->alpha, g->n, o.f64_ratio, g_mean, g_quat, g_scale, g_alpha, again,
+                         (cudaStream_t)stream);
     return check_cuda("mg_render_bwd");
 }
 

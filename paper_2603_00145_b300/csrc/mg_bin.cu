@@ -482,52 +482,54 @@ __device__ __forceinline__ bool is_degenerate(const float *s, float ratio)
 constexpr int K1_NT = 256;
 constexpr int K1_SMEM_SLICES = 256;  // slices staged in shared memory at a time
 
+// One thread per (Gaussian, window of 32 slices): blockIdx.y is the window,
+// so the slab tests of one Gaussian run in parallel over the windows; the
+// frame terms are formed at the window's first slice and reused while the
+// rotation and profile stay the same. gcnt must be zero on entry (summed
+// over the windows with one atomic per thread).
 __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ slices, int S,
                                                   const float *mean, const float *quat, const float *scale,
                                                   const float *alpha, long long n, float K2, float f64_ratio,
                                                   unsigned *cnt, long long NW, unsigned *gcnt, unsigned *bits,
                                                   WsHeader *hdr)
 {
-    __shared__ SliceDev ssl[K1_SMEM_SLICES];
+    __shared__ SliceDev ssl[32];
     const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
     const long long wg = g >> 5;
     const int lane = threadIdx.x & 31;
+    const int wd = blockIdx.y, k0 = wd * 32, nk = min(32, S - k0);
+    for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
     GaussPred G;
     bool valid = false;
     if (g < n) {
         valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
-        if (!valid) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
-        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
-        if (valid && is_degenerate(sc, f64_ratio)) atomicOr(&hdr->flags, MG_FLAG_DEGENERATE);
+        if (wd == 0) {
+            if (!valid) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
+            float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+            if (valid && is_degenerate(sc, f64_ratio)) atomicOr(&hdr->flags, MG_FLAG_DEGENERATE);
+        }
     }
+    __syncthreads();
     FrameTerms f;
     f.full = false;
     f.Lww = 0.f;
-    unsigned word = 0, mine = 0;
-    for (int k0 = 0; k0 < S; k0 += K1_SMEM_SLICES) {
-        const int nk = min(K1_SMEM_SLICES, S - k0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nk; i += K1_NT) ssl[i] = slices[k0 + i];
-        __syncthreads();
-        for (int kk = 0; kk < nk; ++kk) {
-            const int k = k0 + kk;
-            const SliceDev &Sd = ssl[kk];
-            bool ex = false;
-            if (valid) {
-                if (!Sd.same_frame || k == 0) frame_slab(G, Sd.Q, f);
-                ex = slab_test(G, Sd, K2, f.Lww);
-            }
-            unsigned bal = __ballot_sync(0xffffffffu, ex);
-            if (lane == 0 && wg < NW) cnt[(long long)k * NW + wg] = __popc(bal);
-            word |= (unsigned)ex << (k & 31);
-            mine += ex;
-            if ((k & 31) == 31 || k == S - 1) {
-                if (g < n) bits[(long long)(k >> 5) * n + g] = word;
-                word = 0;
-            }
+    unsigned word = 0;
+    for (int kk = 0; kk < nk; ++kk) {
+        const int k = k0 + kk;
+        const SliceDev &Sd = ssl[kk];
+        bool ex = false;
+        if (valid) {
+            if (!Sd.same_frame || kk == 0) frame_slab(G, Sd.Q, f);
+            ex = slab_test(G, Sd, K2, f.Lww);
         }
+        unsigned bal = __ballot_sync(0xffffffffu, ex);
+        if (lane == 0 && wg < NW) cnt[(long long)k * NW + wg] = __popc(bal);
+        word |= (unsigned)ex << kk;
     }
-    if (g < n) gcnt[g] = mine;
+    if (g < n) {
+        bits[(long long)wd * n + g] = word;
+        if (word) atomicAdd(&gcnt[g], (unsigned)__popc(word));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -665,6 +667,9 @@ __global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ sli
         }
         rec.rect[r] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
                                    (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+        // the backward's moment slots start at zero (it accumulates into them)
+        ((float4 *)rec.mom)[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ((float4 *)rec.mom)[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
         if (is_degenerate(sc, f64_ratio)) continue;
         float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
@@ -926,12 +931,14 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     const unsigned g1 = (unsigned)L.NB;
     {
         MG_PROF(MG_ST_K1_COUNT, st);
-        if (cg.on)
+        if (cg.on) {
             k1_count_cells<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, f64_ratio, cg, cnt, NW, gcnt,
                                                  bits, hdr);
-        else
-            k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NW, gcnt,
-                                           bits, hdr);
+        } else {
+            cudaMemsetAsync(gcnt, 0, sizeof(unsigned) * (size_t)n, st);
+            k1_count<<<dim3(g1, (unsigned)L.SW), K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio,
+                                                                 cnt, NW, gcnt, bits, hdr);
+        }
     }
     {
         MG_PROF(MG_ST_SCAN_REC, st);

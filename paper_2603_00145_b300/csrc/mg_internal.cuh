@@ -211,7 +211,7 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, co
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,
                           const CellGrid &cg, const float *grad_out, const float *mean, const float *quat,
                           const float *scale, const float *alpha, long long n, float f64_ratio, float *g_mean,
-                          float *g_quat, float *g_scale, float *g_alpha, cudaStream_t st);
+                          float *g_quat, float *g_scale, float *g_alpha, bool zero_moments, cudaStream_t st);
 void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, const float *mean, const float *quat,
                          const float *scale, const float *alpha, float f64_ratio, float *g_pose, cudaStream_t st);
 // record geometry pass (one thread per record)

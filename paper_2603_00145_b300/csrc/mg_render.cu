@@ -727,6 +727,90 @@ __global__ void k_chain_sum(long long n, const unsigned *__restrict__ goff, cons
     }
 }
 
+// FP64 record-geometry adjoint out of line: near-degenerate Gaussians are
+// rare, and inlining it would size every thread's registers for it
+__device__ __noinline__ void geometry_adjoint_f64(const float *mu, const float *q, const float *s, float alpha,
+                                                  const SliceDev &S, float gA, float gB2, float gC, float gpx,
+                                                  float gpy, float gamp, float o[11])
+{
+    double dm[3], dq[4], ds[3], da;
+    geometry_adjoint<double>(mu, q, s, alpha, S, gA, gB2, gC, gpx, gpy, gamp, dm, dq, ds, da);
+    for (int i = 0; i < 3; ++i) o[i] = (float)dm[i], o[7 + i] = (float)ds[i];
+    for (int i = 0; i < 4; ++i) o[3 + i] = (float)dq[i];
+    o[10] = (float)da;
+}
+
+// K6 fused: one thread per Gaussian visits its records in slice order (the
+// Gaussian-major list), turns each record's moments into dL/d(centre, conic,
+// amplitude), chains them through the record geometry (FP64 for
+// near-degenerate Gaussians) and sums in that fixed order; the Gaussian's
+// parameters are read once and nothing per record is written.
+__global__ void __launch_bounds__(128, 3) k_chain_fused(long long n, const unsigned *__restrict__ goff,
+                                                     const unsigned *__restrict__ gmap, long long cap_records,
+                                                     const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
+                                                     const int *__restrict__ rslice, const float *__restrict__ mom,
+                                                     const SliceDev *__restrict__ slices,
+                                                     const float *__restrict__ mean, const float *__restrict__ quat,
+                                                     const float *__restrict__ scale, const float *__restrict__ alpha,
+                                                     float f64_ratio, float *g_mean, float *g_quat, float *g_scale,
+                                                     float *g_alpha)
+{
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        unsigned long long j0 = goff[g], j1 = goff[g + 1];
+        if ((long long)j1 > cap_records) j1 = cap_records;
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
+        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
+        const float al = alpha[g];
+        const float mx = fmaxf(fmaxf(sc[0], sc[1]), sc[2]), mn = fminf(fminf(sc[0], sc[1]), sc[2]);
+        const bool dbl = f64_ratio > 0.f && mx > f64_ratio * mn;
+        float acc[11];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) acc[i] = 0.f;
+        for (unsigned long long j = j0; j < j1; ++j) {
+            const unsigned r = gmap[j];
+            if ((long long)r >= cap_records) continue;
+            const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
+            const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
+            const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
+            const float4 a = geo[r];
+            const float2 b = geo2[r];
+            const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
+            const float la = amp * 0.69314718055994531f;
+            const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
+            const float gpx = -la * (2.f * A * Sx + B2 * Sy);
+            const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
+            const SliceDev &Sd = slices[rslice[r]];
+            float o[11];
+            if (dbl) {
+                geometry_adjoint_f64(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, o);
+            } else {
+                float gm[3], gq[4], gs[3], ga;
+                geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga);
+                for (int i = 0; i < 3; ++i) o[i] = gm[i], o[7 + i] = gs[i];
+                for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
+                o[10] = ga;
+            }
+#pragma unroll
+            for (int i = 0; i < 11; ++i) acc[i] += o[i];
+        }
+        // gradient on the unit sphere: drop the component along q (the
+        // normalisation q = q_raw/|q_raw| removes it, and the rotation formula
+        // is only a rotation for unit q)
+        const float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+        const float rad =
+            qq > 0.f ? (acc[3] * qv[0] + acc[4] * qv[1] + acc[5] * qv[2] + acc[6] * qv[3]) / qq : 0.f;
+        g_mean[3 * g] = acc[0];
+        g_mean[3 * g + 1] = acc[1];
+        g_mean[3 * g + 2] = acc[2];
+        for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = acc[3 + i] - rad * qv[i];
+        g_scale[3 * g] = acc[7];
+        g_scale[3 * g + 1] = acc[8];
+        g_scale[3 * g + 2] = acc[9];
+        g_alpha[g] = acc[10];
+    }
+}
+
 // K6c: one block per slice sums its records' pose shares (records of a slice
 // are contiguous) in a fixed order, in FP64
 __global__ void __launch_bounds__(256) k_pose_sum(int S, const unsigned *__restrict__ slice_rs,
@@ -831,13 +915,14 @@ void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, co
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,
                           const CellGrid &cg, const float *grad_out, const float *mean, const float *quat,
                           const float *scale, const float *alpha, long long n, float f64_ratio, float *g_mean,
-                          float *g_quat, float *g_scale, float *g_alpha, cudaStream_t st)
+                          float *g_quat, float *g_scale, float *g_alpha, bool zero_moments, cudaStream_t st)
 {
     const WsHeader *hdr = (const WsHeader *)(ws + L.hdr);
-    long long capv = L.cap_records * 2;
-    int gz = (int)((capv + 255) / 256 < 148 * 16 ? (capv + 255) / 256 : 148 * 16);
-    if (gz < 1) gz = 1;
-    {
+    if (zero_moments) {
+        // the record pass zeroes the moments; a second backward on the same forward clears them again
+        long long capv = L.cap_records * 2;
+        int gz = (int)((capv + 255) / 256 < 148 * 16 ? (capv + 255) / 256 : 148 * 16);
+        if (gz < 1) gz = 1;
         MG_PROF(MG_ST_ZERO, st);
         k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), hdr, L.cap_records);
     }
@@ -861,20 +946,11 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
                 grad_out, (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
     }
     MG_PROF(MG_ST_CHAIN, st);
-    float4 *rg = (float4 *)(ws + L.rec_grad);
-    long long wr = (L.cap_records + 255) / 256;
-    int gr = (int)(wr < 148 * 16 ? (wr > 0 ? wr : 1) : 148 * 16);
-    k_chain_rec<false><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
-                                           (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
-                                           (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom), slices,
-                                           mean, quat, scale, alpha, f64_ratio, rg);
-    if (f64_ratio > 0.f)
-        k_chain_rec<true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
-                                              (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
-                                              (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
-                                              slices, mean, quat, scale, alpha, f64_ratio, rg);
-    int gc = (int)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
-    if (gc < 1) gc = 1;
-    k_chain_sum<<<gc, 256, 0, st>>>(n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
-                                    L.cap_records, rg, quat, g_mean, g_quat, g_scale, g_alpha);
+    long long wg = (n + 127) / 128;
+    int gc = (int)(wg < 148 * 32 ? (wg > 0 ? wg : 1) : 148 * 32);
+    k_chain_fused<<<gc, 128, 0, st>>>(n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
+                                      L.cap_records, (const float4 *)(ws + L.rec_geo),
+                                      (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_slice),
+                                      (const float *)(ws + L.rec_mom), slices, mean, quat, scale, alpha, f64_ratio,
+                                      g_mean, g_quat, g_scale, g_alpha);
 }
