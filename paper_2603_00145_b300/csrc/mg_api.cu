@@ -226,7 +226,7 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.tile_off = take(sizeof(unsigned) * (size_t)(tiles + 1));
     L.entries = take(sizeof(unsigned) * (size_t)L.cap_entries);
     L.gmap = take(sizeof(unsigned) * (size_t)L.cap_records);
-    L.rec_grad = take(48 * (size_t)L.cap_records);
+    L.rec_grad = take(32 * (size_t)L.cap_records);  // slice-pose shares: 2 float4 per record
     L.rec_cell = o.local_set == MG_LOCAL_CELLS ? take(16 * (size_t)L.cap_records) : 0;
     L.total = off;
     return L;

@@ -1,16 +1,17 @@
 // mg_render.cu -- per-tile evaluation of the additive Gaussian mixture
 // (Sec. 3.3.2, Eq. E7 with the slice profile) and its adjoint.
 //
-// K4 k_render_fwd : one warp per 16x16 tile; lane = one pixel column, 8 rows.
-//     The tile's records are staged 32 at a time through shared memory and
-//     read back by broadcast; per (record, voxel): q = A dx^2 + B2 dx dy +
-//     C dy^2 (conic pre-scaled to log2 units), I += amp * 2^q.
-// K5 k_render_bwd : the same sweep with dL/dI; per record each lane forms
-//     six moments of w = g 2^q (sum w, w dx, w dy, w dx^2, w dx dy, w dy^2),
-//     the warp reduce-scatters them with 8 shuffles, and six lanes issue one
-//     atomic each into the record's moment slots. Nothing per pair is stored.
-// K6 k_chain : per record, moments -> dL/d(centre, conic, amp) -> adjoint of
-//     the record geometry -> dL/d(mean, quat, scale, alpha) (atomics).
+// K4 k_render_fwd : one warp per 16x16 tile (persistent warps pull tiles);
+//     records staged 32 at a time through shared memory and read back by
+//     broadcast; per (record, voxel): q = A dx^2 + B2 dx dy + C dy^2 (conic
+//     pre-scaled to log2 units), I += amp * 2^q.
+// K5 k_render_bwd : lane = record; each lane sweeps the tile's 256 voxels
+//     and forms six moments of w = g 2^q (sum w, w dx, w dy, w dx^2, w dx dy,
+//     w dy^2); six atomics per (record, tile). Nothing per pair is stored.
+// K6 k_chain_fused : per Gaussian, its records' moments -> dL/d(centre,
+//     conic, amp) -> adjoint of the record geometry -> dL/d(mean, quat,
+//     scale, alpha), summed in a fixed order (no atomics).
+// k_pose_rec / k_pose_sum : the slice-pose gradient from the same moments.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -621,17 +622,17 @@ __global__ void k_zero_mom(float4 *mom, const WsHeader *hdr, long long cap_recor
         mom[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// K6a: one thread per record: moments -> dL/d(centre, conic, amp) -> adjoint
-// of the record geometry -> the record's share of dL/d(mean, quat, scale,
-// alpha), written to its own 12-float slot (FP32 geometry; DBL: only the
+// Slice-pose shares: one thread per record, moments -> dL/d(centre, conic,
+// amp) -> adjoint of the record geometry -> the record's share of dL/dT_k
+// (dL/dt, dL/domega), written to its slot (FP32 geometry; DBL: only the
 // records of near-degenerate Gaussians, in FP64)
-template <bool DBL, bool POSE = false>
-__global__ void k_chain_rec(const WsHeader *hdr, long long cap_records, const float4 *__restrict__ geo,
-                            const float2 *__restrict__ geo2, const int *__restrict__ gid,
-                            const int *__restrict__ rslice, const float *__restrict__ mom,
-                            const SliceDev *__restrict__ slices, const float *__restrict__ mean,
-                            const float *__restrict__ quat, const float *__restrict__ scale,
-                            const float *__restrict__ alpha, float f64_ratio, float4 *__restrict__ rg)
+template <bool DBL>
+__global__ void k_pose_rec(const WsHeader *hdr, long long cap_records, const float4 *__restrict__ geo,
+                           const float2 *__restrict__ geo2, const int *__restrict__ gid, const int *__restrict__ rslice,
+                           const float *__restrict__ mom, const SliceDev *__restrict__ slices,
+                           const float *__restrict__ mean, const float *__restrict__ quat,
+                           const float *__restrict__ scale, const float *__restrict__ alpha, float f64_ratio,
+                           float4 *__restrict__ rg)
 {
     if (DBL && !(hdr->flags & MG_FLAG_DEGENERATE)) return;
     long long nr = (long long)hdr->n_records;
@@ -656,74 +657,17 @@ __global__ void k_chain_rec(const WsHeader *hdr, long long cap_records, const fl
         const float gpx = -la * (2.f * A * Sx + B2 * Sy);
         const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
         const SliceDev &Sd = slices[rslice[r]];
-        if (POSE) {
-            float o6[6];
-            if (DBL) {
-                double dm[3], dq[4], ds[3], da, dp[6];
-                geometry_adjoint<double, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, dm, dq, ds, da, dp);
-                for (int i = 0; i < 6; ++i) o6[i] = (float)dp[i];
-            } else {
-                float gm[3], gq[4], gs[3], ga;
-                geometry_adjoint<float, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga, o6);
-            }
-            rg[2 * r] = make_float4(o6[0], o6[1], o6[2], 0.f);
-            rg[2 * r + 1] = make_float4(o6[3], o6[4], o6[5], 0.f);
-            continue;
-        }
-        float o[12];
+        float o6[6];
         if (DBL) {
-            double dm[3], dq[4], ds[3], da;
-            geometry_adjoint<double>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, dm, dq, ds, da);
-            for (int i = 0; i < 3; ++i) o[i] = (float)dm[i], o[7 + i] = (float)ds[i];
-            for (int i = 0; i < 4; ++i) o[3 + i] = (float)dq[i];
-            o[10] = (float)da;
+            double dm[3], dq[4], ds[3], da, dp[6];
+            geometry_adjoint<double, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, dm, dq, ds, da, dp);
+            for (int i = 0; i < 6; ++i) o6[i] = (float)dp[i];
         } else {
             float gm[3], gq[4], gs[3], ga;
-            geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga);
-            for (int i = 0; i < 3; ++i) o[i] = gm[i], o[7 + i] = gs[i];
-            for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
-            o[10] = ga;
+            geometry_adjoint<float, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga, o6);
         }
-        o[11] = 0.f;
-        rg[3 * r] = make_float4(o[0], o[1], o[2], o[3]);
-        rg[3 * r + 1] = make_float4(o[4], o[5], o[6], o[7]);
-        rg[3 * r + 2] = make_float4(o[8], o[9], o[10], o[11]);
-    }
-}
-
-// K6b: one thread per Gaussian sums its records' shares in slice order (fixed
-// order, no atomics) and writes every gradient once
-__global__ void k_chain_sum(long long n, const unsigned *__restrict__ goff, const unsigned *__restrict__ gmap,
-                            long long cap_records, const float4 *__restrict__ rg, const float *__restrict__ quat,
-                            float *g_mean, float *g_quat, float *g_scale, float *g_alpha)
-{
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
-        unsigned long long j0 = goff[g], j1 = goff[g + 1];
-        if ((long long)j1 > cap_records) j1 = cap_records;
-        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
-        for (unsigned long long j = j0; j < j1; ++j) {
-            const unsigned r = gmap[j];
-            if ((long long)r >= cap_records) continue;
-            const float4 a = rg[3 * (size_t)r], b = rg[3 * (size_t)r + 1], c = rg[3 * (size_t)r + 2];
-            s0.x += a.x, s0.y += a.y, s0.z += a.z, s0.w += a.w;
-            s1.x += b.x, s1.y += b.y, s1.z += b.z, s1.w += b.w;
-            s2.x += c.x, s2.y += c.y, s2.z += c.z;
-        }
-        // gradient on the unit sphere: drop the component along q (the
-        // normalisation q = q_raw/|q_raw| removes it, and the rotation formula
-        // is only a rotation for unit q)
-        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
-        float aq[4] = {s0.w, s1.x, s1.y, s1.z};
-        float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-        float rad = qq > 0.f ? (aq[0] * qv[0] + aq[1] * qv[1] + aq[2] * qv[2] + aq[3] * qv[3]) / qq : 0.f;
-        g_mean[3 * g] = s0.x;
-        g_mean[3 * g + 1] = s0.y;
-        g_mean[3 * g + 2] = s0.z;
-        for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = aq[i] - rad * qv[i];
-        g_scale[3 * g] = s1.w;
-        g_scale[3 * g + 1] = s2.x;
-        g_scale[3 * g + 2] = s2.y;
-        g_alpha[g] = s2.z;
+        rg[2 * r] = make_float4(o6[0], o6[1], o6[2], 0.f);
+        rg[2 * r + 1] = make_float4(o6[3], o6[4], o6[5], 0.f);
     }
 }
 
@@ -899,12 +843,12 @@ void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, co
     float4 *rg = (float4 *)(ws + L.rec_grad);
     long long wr = (L.cap_records + 255) / 256;
     int gr = (int)(wr < 148 * 16 ? (wr > 0 ? wr : 1) : 148 * 16);
-    k_chain_rec<false, true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
+    k_pose_rec<false><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
                                                  (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
                                                  (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
                                                  slices, mean, quat, scale, alpha, f64_ratio, rg);
     if (f64_ratio > 0.f)
-        k_chain_rec<true, true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
+        k_pose_rec<true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
                                                     (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
                                                     (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
                                                     slices, mean, quat, scale, alpha, f64_ratio, rg);
