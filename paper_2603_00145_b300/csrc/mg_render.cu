@@ -294,22 +294,42 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
 #pragma unroll
     for (int c = 0; c < MG_TILE / 2; ++c)
         icr[c] = make_float2((float)(2 * c) - 7.5f + rz, (float)(2 * c + 1) - 7.5f + rz);
+    // the next batch of 32 records is fetched while the current one is swept
+    unsigned nr = 0xffffffffu;
+    float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 nb = make_float2(0.f, 0.f);
+    int4 ncl = make_int4(0, 0, 0, 0);
+    if (e0 + lane < e1) {
+        nr = entries[e0 + lane];
+        if ((long long)nr < cap_records) {
+            na = geo[nr];
+            nb = geo2[nr];
+            if (CELLS) ncl = rcell[nr];
+        } else {
+            nr = 0xffffffffu;
+        }
+    }
     for (unsigned base = e0; base < e1; base += 32) {
-        const unsigned e = base + lane;
-        unsigned r = 0xffffffffu;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 b = make_float2(0.f, 0.f);
-        unsigned clo = 0u, chi = 0u;
-        if (e < e1) {
-            r = entries[e];
-            if ((long long)r < cap_records) {
-                a = geo[r];
-                b = geo2[r];
-                if (CELLS && !cell_range(rcell[r], cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
+        unsigned r = nr;
+        const float4 a = na;
+        const float2 b = nb;
+        const int4 cl = ncl;
+        const unsigned en = base + 32 + lane;
+        nr = 0xffffffffu;
+        na = make_float4(0.f, 0.f, 0.f, 0.f);
+        nb = make_float2(0.f, 0.f);
+        if (en < e1) {
+            nr = entries[en];
+            if ((long long)nr < cap_records) {
+                na = geo[nr];
+                nb = geo2[nr];
+                if (CELLS) ncl = rcell[nr];
             } else {
-                r = 0xffffffffu;
+                nr = 0xffffffffu;
             }
         }
+        unsigned clo = 0u, chi = 0u;
+        if (CELLS && r != 0xffffffffu && !cell_range(cl, cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
         const float A = a.z, B2 = a.w, C = b.x;
         const float dxc = x0c - a.x;   // column offset of the tile centre from the record centre
         const float dyc = y0c - a.y;   // row offset of the tile centre
