@@ -382,6 +382,30 @@ mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float
                      float *g_table, mg_stream_t stream);
 
 /*
+ * Parameterisation of the fit (Sec. 3.2) and the anisotropy regulariser
+ * (Eqs. E12, E13), so that a training step needs no framework autograd for
+ * them. Per Gaussian i (device FP32 arrays):
+ *   mean_i  = centre + half * mean_c_i        (canonical coordinates; centre: HOST float[3], mm)
+ *   quat_i  = q_raw_i / |q_raw_i|             ([n,4], 16-byte aligned)
+ *   scale_i = exp(ls_i)
+ *   L_aniso = (1/n) sum_i max(0, max_a scale_ia / min_a scale_ia - lambda_r)
+ * (E13 writes the ratio on the log-scales; the ratio of the scales is the
+ * reading). mg_params_fwd writes mean, quat, scale and, when aniso_out
+ * (device double[1]) is given, L_aniso in FP64 with a fixed summation order
+ * (ws: device scratch of mg_params_workspace_size(n) bytes). mg_params_bwd
+ * writes dL/d(mean_c, q_raw, ls) for L = (the loss whose gradients g_mean,
+ * g_quat, g_scale are given) + lambda_aniso * L_aniso; a tie for the largest or
+ * smallest scale takes the first index. Errors: MG_ERR_INVALID_ARG.
+ */
+size_t mg_params_workspace_size(int64_t n);
+mg_status mg_params_fwd(int64_t n, const float *mean_c, const float *quat_raw, const float *log_scale,
+                        const float centre[3], float half, float lambda_r, float *mean, float *quat, float *scale,
+                        double *aniso_out, void *ws, size_t ws_bytes, mg_stream_t stream);
+mg_status mg_params_bwd(int64_t n, const float *quat_raw, const float *log_scale, float half, float lambda_r,
+                        float lambda_aniso, const float *g_mean, const float *g_quat, const float *g_scale,
+                        float *g_mean_c, float *g_quat_raw, float *g_log_scale, mg_stream_t stream);
+
+/*
  * Device status word of a render workspace. The first 32-bit word of a
  * workspace filled by mg_render_fwd / mg_sample_volume holds the forward's
  * status bits; a bit of MG_WS_FAIL_BITS set means the forward failed (bins

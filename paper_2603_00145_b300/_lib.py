@@ -92,6 +92,10 @@ SIGNATURES = {
     "mg_nrf_bwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p, c_p, c_p]),
     "mg_adam_step": (ctypes.c_int, [ctypes.POINTER(MgAdamGroup), ctypes.c_int, c_f32, c_f32, c_f32, c_p, c_p,
                                     ctypes.c_uint32, c_p]),
+    "mg_params_workspace_size": (c_sz, [c_i64]),
+    "mg_params_fwd": (ctypes.c_int, [c_i64, c_p, c_p, c_p, ctypes.POINTER(c_f32), c_f32, c_f32, c_p, c_p, c_p, c_p,
+                                     c_p, c_sz, c_p]),
+    "mg_params_bwd": (ctypes.c_int, [c_i64, c_p, c_p, c_f32, c_f32, c_f32, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "mg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mg_profile_stage_count": (ctypes.c_int, []),
     "mg_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),

@@ -249,6 +249,35 @@ def mg_adam_step(groups: Sequence[dict], beta1: float, beta2: float, eps: float,
                                  int(status_mask), _stream_handle(stream)), "mg_adam_step")
 
 
+def mg_params_workspace_size(n: int) -> int:
+    return int(L.lib().mg_params_workspace_size(int(n)))
+
+
+def mg_params_fwd(mean_c, quat_raw, log_scale, centre, half: float, lambda_r: float, mean, quat, scale,
+                  aniso_out=None, ws=None, stream=None):
+    n = mean_c.numel() // 3
+    args = [_dev(mean_c, "mean_c", numel=3 * n), _dev(quat_raw, "quat_raw", numel=4 * n),
+            _dev(log_scale, "log_scale", numel=3 * n)]
+    c = (ctypes.c_float * 3)(*[float(v) for v in centre])
+    outs = [_dev(mean, "mean", numel=3 * n), _dev(quat, "quat", numel=4 * n), _dev(scale, "scale", numel=3 * n)]
+    ap = _dev(aniso_out, "aniso_out", dtype=torch.float64, numel=1) if aniso_out is not None else None
+    wp = _dev(ws, "ws", dtype=torch.uint8) if ws is not None else None
+    L.check(L.lib().mg_params_fwd(n, *args, c, float(half), float(lambda_r), *outs, ap, wp,
+                                  ws.numel() if ws is not None else 0, _stream_handle(stream)), "mg_params_fwd")
+
+
+def mg_params_bwd(quat_raw, log_scale, half: float, lambda_r: float, lambda_aniso: float, g_mean, g_quat, g_scale,
+                  g_mean_c, g_quat_raw, g_log_scale, stream=None):
+    n = quat_raw.numel() // 4
+    L.check(L.lib().mg_params_bwd(n, _dev(quat_raw, "quat_raw", numel=4 * n), _dev(log_scale, "log_scale", numel=3 * n),
+                                  float(half), float(lambda_r), float(lambda_aniso),
+                                  _dev(g_mean, "g_mean", numel=3 * n), _dev(g_quat, "g_quat", numel=4 * n),
+                                  _dev(g_scale, "g_scale", numel=3 * n), _dev(g_mean_c, "g_mean_c", numel=3 * n),
+                                  _dev(g_quat_raw, "g_quat_raw", numel=4 * n),
+                                  _dev(g_log_scale, "g_log_scale", numel=3 * n), _stream_handle(stream)),
+            "mg_params_bwd")
+
+
 def mg_profile_enable(on: bool = True):
     L.check(L.lib().mg_profile_enable(1 if on else 0), "mg_profile_enable")
 

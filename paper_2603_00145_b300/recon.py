@@ -148,6 +148,14 @@ class _Trainer:
             self.ws = torch.empty(ops.mg_reduce_workspace_size(target.numel()), dtype=torch.uint8, device=device)
         self.nrf = self.nrf_adam = self.coords = None
         self.nrf_params = self.nrf_table = None
+        # device buffers of the parameterisation (mg_params_fwd / _bwd)
+        n = m.mean_c.shape[0]
+        f32 = dict(dtype=torch.float32, device=device)
+        self.mean, self.q, self.s = torch.empty(n, 3, **f32), torch.empty(n, 4, **f32), torch.empty(n, 3, **f32)
+        self.g_mc, self.g_qr, self.g_ls = torch.empty(n, 3, **f32), torch.empty(n, 4, **f32), torch.empty(n, 3, **f32)
+        self.aniso = torch.zeros(1, dtype=torch.float64, device=device)
+        self.ws_p = torch.empty(ops.mg_params_workspace_size(n), dtype=torch.uint8, device=device)
+        self.pred = torch.empty(self.R.dev.n_vox, **f32)
 
     def enable_nrf(self):
         cfg = self.cfg
@@ -167,30 +175,45 @@ class _Trainer:
             self.nrf_adam.zero_grad()
 
     def iteration(self):
+        """One step, all in this library's kernels except the NRF batch
+        bookkeeping (random voxel indices, gather, index_add)."""
         cfg, m = self.cfg, self.model
-        mean, q, s, a = m.gaussians()
-        pred = ops.RenderSlices.apply(self.R, mean, q, s, a)
-        if self.nrf is not None:
-            n_vox = self.target.numel()
-            idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
-            r = ops.NRFFunction.apply(self.nrf, self.coords[idx], self.nrf_params, self.nrf_table)
-            pred = pred.index_add(0, idx, r)
-        # the loss (FP64 sums) and its gradient in one kernel; the gradient seeds the backward directly
-        grad = torch.empty_like(pred)
-        if cfg.loss == "paper":
-            out = torch.empty(3, dtype=torch.float64, device=pred.device)
-            ops.mg_loss_recon(pred.detach(), self.target, self.R.dev, cfg.lambda_ssim, grad, out, self.ws)
-        else:
-            out = torch.empty(2, dtype=torch.float64, device=pred.device)
-            ops.mg_loss_l1l2(pred.detach(), self.target, grad, out, self.ws)
-        reg = cfg.lambda_aniso * m.aniso(cfg.lambda_r)
-        torch.autograd.backward([pred, reg], [grad, None])
-        loss = out[0]
-        status = self.R.status_word
-        self.adam.step(status=status)
-        if self.nrf_adam is not None:
-            self.nrf_adam.step(status=status)
-        return loss.detach()  # holds no autograd graph between iterations
+        with torch.no_grad():
+            ops.mg_params_fwd(m.mean_c, m.quat, m.log_scale, self.centre, self.half, cfg.lambda_r, self.mean, self.q,
+                              self.s, self.aniso, self.ws_p)
+            pred = self.R.forward(self.mean, self.q, self.s, m.alpha, out=self.pred)
+            if self.nrf is not None:
+                n_vox = self.target.numel()
+                idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
+                xyz = self.coords[idx]
+                r = torch.empty(idx.numel(), dtype=torch.float32, device=self.device)
+                ops.mg_nrf_fwd(self.nrf, xyz, r, self.nrf_params, self.nrf_table)
+                pred.index_add_(0, idx, r)
+            # the loss (FP64 sums) and its gradient dL/dpred in one kernel
+            grad = torch.empty_like(pred)
+            if cfg.loss == "paper":
+                out = torch.empty(3, dtype=torch.float64, device=pred.device)
+                ops.mg_loss_recon(pred, self.target, self.R.dev, cfg.lambda_ssim, grad, out, self.ws)
+            else:
+                out = torch.empty(2, dtype=torch.float64, device=pred.device)
+                ops.mg_loss_l1l2(pred, self.target, grad, out, self.ws)
+            if self.nrf is not None:
+                g_r = grad[idx]
+                gp = torch.empty_like(self.nrf_params)
+                gt = torch.empty_like(self.nrf_table) if self.nrf_table is not None else None
+                ops.mg_nrf_bwd(self.nrf, xyz, g_r, gp, gt, self.nrf_params, self.nrf_table)
+                self.nrf_params.grad = gp
+                if gt is not None:
+                    self.nrf_table.grad = gt
+            gm, gq, gs, ga = self.R.backward(self.mean, self.q, self.s, m.alpha, grad)
+            ops.mg_params_bwd(m.quat, m.log_scale, self.half, cfg.lambda_r, cfg.lambda_aniso, gm, gq, gs, self.g_mc,
+                              self.g_qr, self.g_ls)
+            m.mean_c.grad, m.quat.grad, m.log_scale.grad, m.alpha.grad = self.g_mc, self.g_qr, self.g_ls, ga
+            status = self.R.status_word
+            self.adam.step(status=status)
+            if self.nrf_adam is not None:
+                self.nrf_adam.step(status=status)
+        return out[0]
 
     def done(self) -> int:
         return self.adam.steps
