@@ -118,6 +118,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# whole-job throughput over ranks (independent replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+def job_throughput(units_local: float, ms_local: float, steps: int, dist=None, device="cpu"):
+    """(units/s of the whole job, ms per step of the slowest rank, units per
+    step of the whole job): every rank ran ``steps`` steps of its own replica
+    in ``ms_local`` ms, processing ``units_local`` units per step; the job's
+    time is the slowest rank's and its units are the sum over ranks."""
+    import torch
+
+    ms, units = float(ms_local), float(units_local)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), float(u.item())
+    ms_step = ms / steps
+    return units / (ms_step / 1e3), ms_step, units
+
+
+# ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
 def build_workload(name: str, seed: int, device, keep_volume: bool = False):
@@ -202,13 +223,7 @@ def run_mgauss(args, rank, world, local_rank):
     prof = mg_profile_read(reset=True)
     clk = clocks.stop()
     ms_total = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value_rank = pairs_inside / (ms_step / 1e3)
-    value = value_rank * world
+    value, ms_step, pairs_job = job_throughput(pairs_inside, ms_total, args.steps, dist, dev)
     st = R.stats()
     assert st["status"] == 0, f"device status {st['status']} during the timed steps"
 
@@ -239,11 +254,8 @@ def run_mgauss(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_ms += e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = pairs_inside * world / (e2e_ms / args.steps / 1e3)
+    e2e_value, e2e_ms_step, _ = job_throughput(pairs_inside, e2e_ms, args.steps, dist, dev)
+    e2e_ms = e2e_ms_step * args.steps
 
     # roofline of the dominant evaluation kernel, timed live with CUDA events
     stages = {k: v for k, v in prof.items() if v[1] > 0}
