@@ -9,7 +9,8 @@
 // One block per 32 x 32 output tile of a slice. The tile's inputs with a
 // 10-pixel halo (52 x 52) are staged in shared memory; the five windowed
 // moments (mu_x, mu_y, E_xx, E_yy, E_xy) are formed on the 42 x 42 region
-// (tile + 5-pixel halo) by a horizontal then a vertical 11-tap pass; each
+// (tile + 5-pixel halo) by a horizontal then a vertical 11-tap pass (each
+// thread 4 consecutive outputs from 14 loaded values); each
 // pixel of that region inside the slice gives SSIM_p and the three
 // sensitivities dSSIM_p/d(mu_x, E_xx, E_xy) scaled by dL/dSSIM_p; a second
 // pair of passes sums them over the window of each output pixel (the
@@ -34,7 +35,7 @@ constexpr int RAD = 5;           // window radius (11 taps)
 constexpr int NTAP = 2 * RAD + 1;
 constexpr int MR = TS + 2 * RAD; // moment / sensitivity region edge (42)
 constexpr int IR = TS + 4 * RAD; // input region edge (52)
-constexpr int SS_NT = 256;
+constexpr int SS_NT = 512;
 constexpr float C1 = 1e-4f;      // (0.01 * 1)^2
 constexpr float C2 = 9e-4f;      // (0.03 * 1)^2
 
@@ -48,15 +49,31 @@ struct SsimStacks {
     float lam;                          // lambda_SSIM
 };
 
+constexpr int IRP = IR + 4;   // input row pitch: a 4-wide group reads 14 values from any group start
+
 struct SsimSmem {
-    float x[IR][IR], y[IR][IR];
+    float x[IR][IRP], y[IR][IRP];
     union {
-        float h[5][IR][MR];  // horizontal moment sums
-        float t[3][MR][TS];  // horizontal sums of the sensitivities
+        float h[5][IR + 4][MR];  // horizontal moment sums (4 spare rows for the last 4-row group)
+        float t[3][MR][TS];      // horizontal sums of the sensitivities
     } a;
-    float s[3][MR][MR];      // sensitivities on the moment region
+    float s[3][MR][MR];          // sensitivities on the moment region
     double red[2][SS_NT / 32];
 };
+
+// Each thread computes 4 consecutive outputs of a window pass from 14 loaded
+// values (4 + 10 halo) instead of 4 x 11: the passes are bound by shared-memory
+// loads. Every output sums its 11 taps in the same order as a single pass.
+__device__ __forceinline__ void taps4(const float (&v)[14], const float *g, float (&o)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < NTAP; ++j) m = fmaf(g[j], v[i + j], m);
+        o[i] = m;
+    }
+}
 
 __global__ void __launch_bounds__(SS_NT) k_loss_recon(const float *__restrict__ pred, const float *__restrict__ target,
                                                       SsimStacks T, float *__restrict__ grad,
@@ -76,12 +93,12 @@ __global__ void __launch_bounds__(SS_NT) k_loss_recon(const float *__restrict__ 
     const long long base = T.pix_base[st] + (long long)k * H * W;
     const int oy = ty * TS, ox = tx * TS;
 
-    // 1. inputs with a 2 * RAD halo, zero outside the slice
-    for (int i = tid; i < IR * IR; i += SS_NT) {
-        const int r = i / IR, c = i - r * IR;
+    // 1. inputs with a 2 * RAD halo, zero outside the slice (and in the pitch padding)
+    for (int i = tid; i < IR * IRP; i += SS_NT) {
+        const int r = i / IRP, c = i - r * IRP;
         const int py = oy - 2 * RAD + r, px = ox - 2 * RAD + c;
         float xv = 0.f, yv = 0.f;
-        if (py >= 0 && py < H && px >= 0 && px < W) {
+        if (c < IR && py >= 0 && py < H && px >= 0 && px < W) {
             xv = pred[base + (long long)py * W + px];
             yv = target[base + (long long)py * W + px];
         }
@@ -89,95 +106,117 @@ __global__ void __launch_bounds__(SS_NT) k_loss_recon(const float *__restrict__ 
         sm.y[r][c] = yv;
     }
     __syncthreads();
-    // 2. horizontal window sums of x, y, x^2, y^2, x y
-    for (int i = tid; i < IR * MR; i += SS_NT) {
-        const int r = i / MR, c = i - r * MR;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+    // 2. horizontal window sums of x, y, x^2, y^2, x y: row r, columns c0..c0+3
+    constexpr int G2 = (MR + 3) / 4;  // 11 column groups
+    for (int i = tid; i < IR * G2; i += SS_NT) {
+        const int r = i / G2, c0 = 4 * (i - r * G2);
+        float xv[14], yv[14], v[14], o[4];
 #pragma unroll
-        for (int j = 0; j < NTAP; ++j) {
-            const float xv = sm.x[r][c + j], yv = sm.y[r][c + j], gj = T.g[j];
-            m0 = fmaf(gj, xv, m0);
-            m1 = fmaf(gj, yv, m1);
-            m2 = fmaf(gj, xv * xv, m2);
-            m3 = fmaf(gj, yv * yv, m3);
-            m4 = fmaf(gj, xv * yv, m4);
+        for (int q = 0; q < 3; ++q) {
+            const float4 a4 = *(const float4 *)&sm.x[r][c0 + 4 * q];
+            const float4 b4 = *(const float4 *)&sm.y[r][c0 + 4 * q];
+            xv[4 * q] = a4.x, xv[4 * q + 1] = a4.y, xv[4 * q + 2] = a4.z, xv[4 * q + 3] = a4.w;
+            yv[4 * q] = b4.x, yv[4 * q + 1] = b4.y, yv[4 * q + 2] = b4.z, yv[4 * q + 3] = b4.w;
         }
-        sm.a.h[0][r][c] = m0;
-        sm.a.h[1][r][c] = m1;
-        sm.a.h[2][r][c] = m2;
-        sm.a.h[3][r][c] = m3;
-        sm.a.h[4][r][c] = m4;
+        {
+            const float2 a2 = *(const float2 *)&sm.x[r][c0 + 12];
+            const float2 b2 = *(const float2 *)&sm.y[r][c0 + 12];
+            xv[12] = a2.x, xv[13] = a2.y, yv[12] = b2.x, yv[13] = b2.y;
+        }
+        const int nv = min(4, MR - c0);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+#pragma unroll
+            for (int j = 0; j < 14; ++j)
+                v[j] = m == 0 ? xv[j] : m == 1 ? yv[j] : m == 2 ? xv[j] * xv[j] : m == 3 ? yv[j] * yv[j] : xv[j] * yv[j];
+            taps4(v, T.g, o);
+            for (int q = 0; q < nv; ++q) sm.a.h[m][r][c0 + q] = o[q];
+        }
     }
     __syncthreads();
-    // 3. vertical sums -> SSIM_p and its sensitivities (zero outside the slice)
+    // 3. vertical sums -> SSIM_p and its sensitivities (zero outside the slice):
+    //    column c, rows r0..r0+3
     const float dlds = -T.lam * T.inv_n;
     float ssum = 0.f;
-    for (int i = tid; i < MR * MR; i += SS_NT) {
-        const int r = i / MR, c = i - r * MR;
-        const int py = oy - RAD + r, px = ox - RAD + c;
-        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-        if (py >= 0 && py < H && px >= 0 && px < W) {
-            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    for (int i = tid; i < MR * G2; i += SS_NT) {
+        const int g3 = i / MR, c = i - g3 * MR, r0 = 4 * g3;
+        float mo[5][4];
 #pragma unroll
-            for (int j = 0; j < NTAP; ++j) {
-                const float gj = T.g[j];
-                mx = fmaf(gj, sm.a.h[0][r + j][c], mx);
-                my = fmaf(gj, sm.a.h[1][r + j][c], my);
-                exx = fmaf(gj, sm.a.h[2][r + j][c], exx);
-                eyy = fmaf(gj, sm.a.h[3][r + j][c], eyy);
-                exy = fmaf(gj, sm.a.h[4][r + j][c], exy);
+        for (int m = 0; m < 5; ++m) {
+            float v[14], o[4];
+#pragma unroll
+            for (int j = 0; j < 14; ++j) v[j] = sm.a.h[m][r0 + j][c];
+            taps4(v, T.g, o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mo[m][q] = o[q];
+        }
+        const int px = ox - RAD + c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q;
+            if (r >= MR) break;
+            const int py = oy - RAD + r;
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+            if (py >= 0 && py < H && px >= 0 && px < W) {
+                const float mx = mo[0][q], my = mo[1][q], exx = mo[2][q], eyy = mo[3][q], exy = mo[4][q];
+                const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+                const float a1 = 2.f * mx * my + C1, a2 = 2.f * sxy + C2;
+                const float b1 = mx * mx + my * my + C1, b2 = sxx + syy + C2;
+                const float sv = (a1 * a2) / (b1 * b2);
+                if (r >= RAD && r < RAD + TS && c >= RAD && c < RAD + TS) ssum += sv;
+                const float ia1 = 1.f / a1, ia2 = 1.f / a2, ib1 = 1.f / b1, ib2 = 1.f / b2;
+                d0 = dlds * sv * 2.f * (my * (ia1 - ia2) + mx * (ib2 - ib1));  // dS/dmu_x
+                d1 = -dlds * sv * ib2;                                         // dS/dE_xx
+                d2 = dlds * sv * 2.f * ia2;                                    // dS/dE_xy
             }
-            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-            const float a1 = 2.f * mx * my + C1, a2 = 2.f * sxy + C2;
-            const float b1 = mx * mx + my * my + C1, b2 = sxx + syy + C2;
-            const float s = (a1 * a2) / (b1 * b2);
-            if (r >= RAD && r < RAD + TS && c >= RAD && c < RAD + TS) ssum += s;
-            const float ia1 = 1.f / a1, ia2 = 1.f / a2, ib1 = 1.f / b1, ib2 = 1.f / b2;
-            d0 = dlds * s * 2.f * (my * (ia1 - ia2) + mx * (ib2 - ib1));  // dS/dmu_x
-            d1 = -dlds * s * ib2;                                          // dS/dE_xx
-            d2 = dlds * s * 2.f * ia2;                                     // dS/dE_xy
+            sm.s[0][r][c] = d0;
+            sm.s[1][r][c] = d1;
+            sm.s[2][r][c] = d2;
         }
-        sm.s[0][r][c] = d0;
-        sm.s[1][r][c] = d1;
-        sm.s[2][r][c] = d2;
     }
     __syncthreads();
-    // 4. horizontal window sums of the sensitivities (the moment sums are dead)
-    for (int i = tid; i < MR * TS; i += SS_NT) {
-        const int r = i / TS, c = i - r * TS;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    // 4. horizontal window sums of the sensitivities (the moment sums are dead):
+    //    row r, columns c0..c0+3
+    constexpr int G4 = TS / 4;  // 8 column groups
+    for (int i = tid; i < MR * G4; i += SS_NT) {
+        const int g4 = i / MR, r = i - g4 * MR, c0 = 4 * g4;
 #pragma unroll
-        for (int j = 0; j < NTAP; ++j) {
-            const float gj = T.g[j];
-            u0 = fmaf(gj, sm.s[0][r][c + j], u0);
-            u1 = fmaf(gj, sm.s[1][r][c + j], u1);
-            u2 = fmaf(gj, sm.s[2][r][c + j], u2);
+        for (int m = 0; m < 3; ++m) {
+            float v[14], o[4];
+#pragma unroll
+            for (int j = 0; j < 14; ++j) v[j] = sm.s[m][r][c0 + j];
+            taps4(v, T.g, o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sm.a.t[m][r][c0 + q] = o[q];
         }
-        sm.a.t[0][r][c] = u0;
-        sm.a.t[1][r][c] = u1;
-        sm.a.t[2][r][c] = u2;
     }
     __syncthreads();
-    // 5. vertical sums, gradient of the tile, smooth-L1 term
+    // 5. vertical sums, gradient of the tile, smooth-L1 term: column c, rows r0..r0+3
     float lsum = 0.f;
-    for (int i = tid; i < TS * TS; i += SS_NT) {
-        const int r = i / TS, c = i - r * TS;
-        const int py = oy + r, px = ox + c;
-        if (py >= H || px >= W) continue;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    for (int i = tid; i < TS * G4; i += SS_NT) {
+        const int g5 = i / TS, c = i - g5 * TS, r0 = 4 * g5;
+        float u[3][4];
 #pragma unroll
-        for (int j = 0; j < NTAP; ++j) {
-            const float gj = T.g[j];
-            u0 = fmaf(gj, sm.a.t[0][r + j][c], u0);
-            u1 = fmaf(gj, sm.a.t[1][r + j][c], u1);
-            u2 = fmaf(gj, sm.a.t[2][r + j][c], u2);
+        for (int m = 0; m < 3; ++m) {
+            float v[14], o[4];
+#pragma unroll
+            for (int j = 0; j < 14; ++j) v[j] = sm.a.t[m][r0 + j][c];
+            taps4(v, T.g, o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u[m][q] = o[q];
         }
-        const float xv = sm.x[r + 2 * RAD][c + 2 * RAD], yv = sm.y[r + 2 * RAD][c + 2 * RAD];
-        const float res = xv - yv, ar = fabsf(res);
-        lsum += ar < 1.f ? 0.5f * res * res : ar - 0.5f;
-        if (grad) {
-            const float gl1 = (ar < 1.f ? res : copysignf(1.f, res)) * T.inv_n;
-            grad[base + (long long)py * W + px] = gl1 + u0 + 2.f * xv * u1 + yv * u2;
+        const int px = ox + c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int py = oy + r0 + q;
+            if (py >= H || px >= W) continue;
+            const float xv = sm.x[r0 + q + 2 * RAD][c + 2 * RAD], yv = sm.y[r0 + q + 2 * RAD][c + 2 * RAD];
+            const float res = xv - yv, ar = fabsf(res);
+            lsum += ar < 1.f ? 0.5f * res * res : ar - 0.5f;
+            if (grad) {
+                const float gl1 = (ar < 1.f ? res : copysignf(1.f, res)) * T.inv_n;
+                grad[base + (long long)py * W + px] = gl1 + u[0][q] + 2.f * xv * u[1][q] + yv * u[2][q];
+            }
         }
     }
     // block partials in FP64
