@@ -40,3 +40,18 @@ def test_backward_vs_central_fd():
             args_m = [m if a is arr else a for a in (mc, qr, ls)]
             fd = (L(*args_p) - L(*args_m)) / (2 * h)
             assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, g[idx])
+
+
+def test_forward_known_values():
+    """Values fixed by hand: a scaled identity quaternion normalises to the
+    identity, an isotropic Gaussian has scale ratio 1 (no penalty above
+    lambda_r = 1.5), scales (1, 2, 8) have ratio 8 (penalty 6.5); the mean of
+    the two is 3.25."""
+    mc = np.array([[0.0, 0.0, 0.0], [1.0, -1.0, 0.5]])
+    qr = np.array([[2.0, 0.0, 0.0, 0.0], [0.0, 3.0, 0.0, 4.0]])
+    ls = np.log(np.array([[0.5, 0.5, 0.5], [2.0, 8.0, 1.0]]))
+    mean, q, s, an = params.forward(mc, qr, ls, (10.0, 20.0, 30.0), 4.0, 1.5)
+    np.testing.assert_allclose(mean, [[10.0, 20.0, 30.0], [14.0, 16.0, 32.0]], rtol=1e-15)
+    np.testing.assert_allclose(q, [[1.0, 0.0, 0.0, 0.0], [0.0, 0.6, 0.0, 0.8]], atol=1e-15)
+    np.testing.assert_allclose(s, [[0.5, 0.5, 0.5], [2.0, 8.0, 1.0]], rtol=1e-14)
+    assert abs(an - 3.25) < 1e-12
