@@ -72,19 +72,29 @@ def ssim_map(x, y) -> np.ndarray:
     return (a1 * a2) / (b1 * b2)
 
 
+def sensitivities(mx, my, exx, eyy, exy):
+    """SSIM_p and its partial derivatives with respect to mu_x, E_xx and
+    E_xy (the moments of the predicted image), from the window moments.
+    SSIM_p = N / D with N = a1 a2, D = b1 b2; by the quotient rule
+    (N' D - N D') / D^2. a1 and a2 vanish for anti-correlated windows, while
+    b1 >= C1 and b2 >= C2, so only D is divided by."""
+    sxx, syy, sxy = exx - mx * mx, eyy - my * my, exy - mx * my
+    a1, a2 = 2.0 * mx * my + C1, 2.0 * sxy + C2
+    b1, b2 = mx * mx + my * my + C1, sxx + syy + C2
+    d = b1 * b2
+    s = (a1 * a2) / d
+    # N' = (2 my a2 - 2 my a1, 0, 2 a1), D' = (2 mx b2 - 2 mx b1, b1, 0)
+    d_mx = 2.0 * (my * (a2 - a1) - s * mx * (b2 - b1)) / d
+    d_exx = -s / b2
+    d_exy = 2.0 * a1 / d
+    return s, d_mx, d_exx, d_exy
+
+
 def ssim_grad(x, y, dl_ds) -> np.ndarray:
     """dL/dx for a per-pixel upstream gradient dL/dSSIM_p (2-D arrays)."""
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
-    mx, my, exx, eyy, exy = _moments(x, y)
-    sxx, syy, sxy = exx - mx * mx, eyy - my * my, exy - mx * my
-    a1, a2 = 2.0 * mx * my + C1, 2.0 * sxy + C2
-    b1, b2 = mx * mx + my * my + C1, sxx + syy + C2
-    s = (a1 * a2) / (b1 * b2)
-    # partial derivatives of SSIM_p with respect to mu_x, E_xx and E_xy
-    d_mx = s * (2.0 * my / a1 - 2.0 * my / a2 - 2.0 * mx / b1 + 2.0 * mx / b2)
-    d_exx = -s / b2
-    d_exy = 2.0 * s / a2
+    _, d_mx, d_exx, d_exy = sensitivities(*_moments(x, y))
     u = np.asarray(dl_ds, np.float64)
     return _blur(u * d_mx) + 2.0 * x * _blur(u * d_exx) + y * _blur(u * d_exy)
 

@@ -162,12 +162,16 @@ __global__ void __launch_bounds__(SS_NT) k_loss_recon(const float *__restrict__ 
                 const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
                 const float a1 = 2.f * mx * my + C1, a2 = 2.f * sxy + C2;
                 const float b1 = mx * mx + my * my + C1, b2 = sxx + syy + C2;
-                const float sv = (a1 * a2) / (b1 * b2);
+                // S = N / D, N = a1 a2, D = b1 b2; b1 >= C1 and b2 >= C2, while
+                // a1 and a2 vanish for anti-correlated windows: the quotient
+                // rule divides by D only
+                const float iD = 1.f / (b1 * b2);
+                const float sv = (a1 * a2) * iD;
                 if (r >= RAD && r < RAD + TS && c >= RAD && c < RAD + TS) ssum += sv;
-                const float ia1 = 1.f / a1, ia2 = 1.f / a2, ib1 = 1.f / b1, ib2 = 1.f / b2;
-                d0 = dlds * sv * 2.f * (my * (ia1 - ia2) + mx * (ib2 - ib1));  // dS/dmu_x
-                d1 = -dlds * sv * ib2;                                         // dS/dE_xx
-                d2 = dlds * sv * 2.f * ia2;                                    // dS/dE_xy
+                const float k2 = 2.f * dlds * iD;
+                d0 = k2 * (my * (a2 - a1) - sv * mx * (b2 - b1));  // dS/dmu_x
+                d1 = -dlds * sv / b2;                               // dS/dE_xx
+                d2 = k2 * a1;                                       // dS/dE_xy
             }
             sm.s[0][r][c] = d0;
             sm.s[1][r][c] = d1;

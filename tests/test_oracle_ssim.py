@@ -70,3 +70,31 @@ def test_gradient_matches_central_differences():
         xm[k][i, j] -= h
         fd = (ssim.recon_loss(xp, ys)[0] - ssim.recon_loss(xm, ys)[0]) / (2 * h)
         assert abs(fd - g[k][i, j]) <= 1e-7 * max(1.0, abs(fd)) + 1e-10, (k, i, j, fd, g[k][i, j])
+
+
+def test_sensitivities_where_the_numerator_factors_vanish():
+    """mu_x = mu_y = 0 and E_xy = -C2/2 make a2 = 2 s_xy + C2 exactly zero (and
+    a1 = C1): SSIM_p = 0 there, its derivatives are finite and equal central
+    finite differences of SSIM_p in (mu_x, E_xx, E_xy)."""
+    from oracle.ssim import C2, sensitivities
+
+    pt = dict(mx=0.0, my=0.0, exx=0.01, eyy=0.02, exy=-C2 / 2)
+    s, d_mx, d_exx, d_exy = sensitivities(**pt)
+    assert s == 0.0 and np.isfinite([d_mx, d_exx, d_exy]).all()
+    for key, got in (("mx", d_mx), ("exx", d_exx), ("exy", d_exy)):
+        h = 1e-7
+        up, dn = dict(pt), dict(pt)
+        up[key] += h
+        dn[key] -= h
+        fd = (sensitivities(**up)[0] - sensitivities(**dn)[0]) / (2 * h)
+        assert abs(fd - got) <= 1e-6 * max(1.0, abs(got)), (key, fd, got)
+    # and at a generic point
+    pt = dict(mx=0.3, my=0.5, exx=0.2, eyy=0.4, exy=0.1)
+    s, *ds = sensitivities(**pt)
+    for key, got in zip(("mx", "exx", "exy"), ds):
+        h = 1e-6
+        up, dn = dict(pt), dict(pt)
+        up[key] += h
+        dn[key] -= h
+        fd = (sensitivities(**up)[0] - sensitivities(**dn)[0]) / (2 * h)
+        assert abs(fd - got) <= 1e-7 * max(1.0, abs(got)), (key, fd, got)
