@@ -20,8 +20,8 @@
  * P = diag(psf_u^2, psf_v^2, thickness^2)/(8 ln 2) in the slice frame adds to
  * the covariance the same way, Sigma'_i = Sigma_i + R_k P R_k^T.
  * Like the paper's local Gaussian set G_local (Sec. 3.3.1), the sum is
- * restricted per 16x16 voxel tile: Gaussian i contributes to every voxel of a
- * tile of slice k iff its (i,k) record lists that tile (the record predicate
+ * restricted per 8x8 voxel tile (MG_TILE_EDGE): Gaussian i contributes to every voxel
+ * of a tile of slice k iff its (i,k) record lists that tile (the record predicate
  * below: a K-sigma slab test plus the tile rectangle of the cut ellipse).
  *
  * CONVENTIONS
@@ -54,9 +54,9 @@
  *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy);
  *   the box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0 (NaN: empty);
  *   a non-empty box is clamped (il,jl up to 0, ih,jh down to W-1,H-1) and lists the
- *   tiles [il/16, ih/16] x [jl/16, jh/16]; an empty box lists no tile (stored as the
+ *   tiles [il/8, ih/8] x [jl/8, jh/8]; an empty box lists no tile (stored as the
  *   tile rectangle (1,1,0,0)).
- *   Tile (tx,ty) of a slice covers pixels 16tx..16tx+15 x 16ty..16ty+15.
+ *   Tile (tx,ty) of a slice covers pixels 8tx..8tx+7 x 8ty..8ty+7.
  *   The count of records and of (record, tile) entries is therefore exact
  *   and reproducible bit for bit by any IEEE FP32 implementation.
  *
@@ -83,6 +83,8 @@ extern "C" {
 #endif
 
 typedef struct CUstream_st *mg_stream_t; /* a cudaStream_t */
+
+#define MG_TILE_EDGE 8 /* edge of the evaluation tiles in pixels (record rectangles are in tiles) */
 
 typedef enum {
     MG_OK = 0,
@@ -112,7 +114,7 @@ typedef struct {
 
 /*
  * Local set. MG_LOCAL_KSIGMA (the default, above): per (Gaussian, slice)
- * record, every voxel of the listed 16x16 tiles. MG_LOCAL_CELLS: the paper's
+ * record, every voxel of the listed 8x8 tiles. MG_LOCAL_CELLS: the paper's
  * own rule (Sec. 3.3.1, Eqs. E4-E6): the normalised cube [-1,1]^3 (mapped to
  * grid_centre + grid_half * [-1,1]^3 mm) is cut into grid_res^3 cells; a
  * Gaussian sits in the cell of its mean, and voxel x sums exactly the
@@ -133,7 +135,7 @@ typedef struct {
  * (centre u_c = e_u.(b - t), radius e ((|e_u0| + |e_u1|) + |e_u2|) + m, the
  * pixel box as in the K-sigma predicate). The sum at each voxel is then
  * restricted to members, per (record, voxel). The grid must be coarse enough
- * that a 16x16 tile spans at most 250 cells per axis (else
+ * that an 8x8 tile spans at most 250 cells per axis (else
  * MG_ERR_INVALID_ARG). mg_render_pair_count is for MG_LOCAL_KSIGMA only.
  */
 enum { MG_LOCAL_KSIGMA = 0, MG_LOCAL_CELLS = 1 };
@@ -153,7 +155,7 @@ typedef struct {
 /* Filled by mg_render_stats_get from the workspace of the last forward call. */
 typedef struct {
     int64_t records;         /* (Gaussian, slice) records that exist */
-    int64_t entries;         /* (record, tile) entries = evaluated (record, 16x16 tile) pairs */
+    int64_t entries;         /* (record, tile) entries = evaluated (record, 8x8 tile) pairs */
     int64_t tiles;           /* tiles over all slices */
     int64_t cap_records, cap_entries;
     int32_t status;          /* MG_OK, MG_ERR_CAPACITY or MG_ERR_NOT_FINITE */

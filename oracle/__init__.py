@@ -28,7 +28,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mg_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libmgoracle.so")
-TILE = 16
+TILE = 8
 FWHM2VAR = 0.18033688011112042  # 1 / (8 ln 2)
 
 

@@ -28,7 +28,7 @@
  *   Truncation:        the paper already restricts the sum to a local set
  *                      G_local (Sec. 3.3.1). Here the local set of a slice
  *                      voxel is the set of Gaussians whose record for that
- *                      slice lists the voxel's 16x16 tile (record predicate
+ *                      slice lists the voxel's 8x8 tile (record predicate
  *                      below, K-sigma ellipsoid of Sigma').
  *
  * Record predicate (evaluated in FP32, IEEE round-to-nearest, every operation
@@ -50,7 +50,7 @@
  *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy), hy = 0.5*(H-1)
  *   the pixel box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1,
  *   jh>=0 (false for NaN); a non-empty box has il,jl clamped up to 0 and ih,jh
- *   down to W-1,H-1 and lists the tiles [il/16, ih/16] x [jl/16, jh/16]
+ *   down to W-1,H-1 and lists the tiles [il/8, ih/8] x [jl/8, jh/8]
  *   (integer division); an empty box lists none (rectangle (1,1,0,0))
  *   sig2 = (float)(thickness^2 * 0.18033688011112042) computed in double,
  *   pu2, pv2 likewise from the in-plane PSF FWHM (0 without a PSF).
@@ -64,7 +64,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_TILE 16
+#define OR_TILE 8
 #define OR_FWHM2VAR 0.18033688011112042 /* 1 / (8 ln 2) */
 
 /* ------------------------------------------------------------------ */

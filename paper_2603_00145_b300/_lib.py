@@ -52,6 +52,7 @@ class MgAdamGroup(ctypes.Structure):
 
 
 MG_WS_FAIL_BITS = 0x0F
+MG_TILE_EDGE = 8  # edge of the evaluation tiles in pixels
 MG_ADAM_MAX_GROUPS = 8
 
 MG_NRF_FOURIER, MG_NRF_GRID = 0, 1

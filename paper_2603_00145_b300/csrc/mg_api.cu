@@ -132,7 +132,7 @@ bool make_cellgrid(const mg_opts &o, float max_px, CellGrid &cg, std::string &wh
     }
     const double hres = 0.5 * (double)o.grid_res, h = (double)o.grid_half;
     if (2.0 * MG_TILE * (double)max_px * hres / h + 2.0 > 250.0) {
-        why = "MG_LOCAL_CELLS grid too fine: a 16x16 tile would span more than 250 cells";
+        why = "MG_LOCAL_CELLS grid too fine: an 8x8 tile would span more than 250 cells";
         return false;
     }
     cg.on = 1;
@@ -224,10 +224,13 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.hist = take(sizeof(unsigned) * (size_t)L.cap_chunks * (size_t)tmax);
     L.tile_cnt = take(sizeof(unsigned) * (size_t)tiles);
     L.tile_off = take(sizeof(unsigned) * (size_t)(tiles + 1));
+    L.tile_list = take(sizeof(unsigned) * (size_t)tiles);
     L.entries = take(sizeof(unsigned) * (size_t)L.cap_entries);
     L.gmap = take(sizeof(unsigned) * (size_t)L.cap_records);
     L.rec_grad = take(32 * (size_t)L.cap_records);  // slice-pose shares: 2 float4 per record
     L.rec_cell = o.local_set == MG_LOCAL_CELLS ? take(16 * (size_t)L.cap_records) : 0;
+    L.rec_f64 = take((size_t)L.cap_records);
+    L.rec_mom64 = take(48 * (size_t)L.cap_records);
     L.total = off;
     return L;
 }
@@ -390,11 +393,13 @@ mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &s
     if (g->n > 0) {
         mg_launch_bin(L, w, slices, tab, g->mean, g->quat, g->scale, g->alpha, g->n, o.cutoff_k, o.f64_ratio, cg,
                       stream);
+        mg_launch_render_fwd(L, w, tab, slices, cg, out, stream);
     } else {
+        // no Gaussians: empty bins and a zero output
         cudaMemsetAsync(w + L.hdr, 0, sizeof(WsHeader), stream);
         cudaMemsetAsync(w + L.tile_off, 0, sizeof(unsigned) * (size_t)(tiles + 1), stream);
+        cudaMemsetAsync(out, 0, sizeof(float) * (size_t)tab.pix_base[tab.n_stacks], stream);
     }
-    mg_launch_render_fwd(L, w, tab, slices, cg, out, stream);
     mg_status s = check_cuda("mg_render_fwd");
     if (s != MG_OK) return s;
     {

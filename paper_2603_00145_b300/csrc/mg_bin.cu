@@ -667,11 +667,18 @@ __global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ sli
         }
         rec.rect[r] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
                                    (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
-        // the backward's moment slots start at zero (it accumulates into them)
+        // the backward's moment slots start at zero (it accumulates into them);
+        // near-degenerate Gaussians accumulate in FP64
         ((float4 *)rec.mom)[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
         ((float4 *)rec.mom)[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
-        if (is_degenerate(sc, f64_ratio)) continue;
+        const bool dg = is_degenerate(sc, f64_ratio);
+        rec.f64[r] = dg ? 1 : 0;
+        if (dg) {
+            double2 *m2 = (double2 *)(rec.mom64 + 6 * r);
+            m2[0] = m2[1] = m2[2] = make_double2(0.0, 0.0);
+            continue;
+        }
         float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
         RecGeomT<float> o;
         record_geometry<float>(G.mu, qv, sc, alpha[g], Sd, K2, o);
@@ -780,7 +787,11 @@ __device__ __forceinline__ int find_slice(const unsigned *chunk_base, int S, uns
     return lo;
 }
 
+// warps (chunks) per block of the histogram and scatter passes: each warp
+// holds a counter per tile of a slice in shared memory, so large slices get
+// fewer warps per block
 constexpr int BIN_WARPS = 4;
+constexpr size_t BIN_SMEM_MAX = 200 * 1024;
 
 __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *slices, int S, const unsigned *slice_rs,
                                                              const unsigned *chunk_base, const ushort4 *rect,
@@ -791,7 +802,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
     unsigned *hs = smem_u + w * Tmax;
     unsigned n_chunks = chunk_base[S];
     if ((long long)n_chunks > cap_chunks) n_chunks = (unsigned)cap_chunks;
-    for (unsigned c = blockIdx.x * BIN_WARPS + w; c < n_chunks; c += gridDim.x * BIN_WARPS) {
+    const unsigned nw = blockDim.x >> 5;
+    for (unsigned c = blockIdx.x * nw + w; c < n_chunks; c += gridDim.x * nw) {
         int k = find_slice(chunk_base, S, c);
         const int TX = slices[k].TX, Tk = TX * slices[k].TY;
         unsigned r0 = slice_rs[k] + (c - chunk_base[k]) * MG_CHUNK;
@@ -810,37 +822,57 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
     }
 }
 
-// per (slice, tile): exclusive prefix over the slice's chunks; tile totals
+// per (slice, tile): exclusive prefix over the slice's chunks; tile totals;
+// and the tile list of the render kernels: tiles with records appended at
+// the front, tiles without at the back (warp-aggregated atomics; the order
+// within each part is arbitrary and does not change any result)
 __global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chunk_base, unsigned *hist, int Tmax,
-                              long long cap_chunks, unsigned *tile_cnt)
+                              long long cap_chunks, unsigned *tile_cnt, unsigned *tile_list, long long n_tiles,
+                              WsHeader *hdr)
 {
     long long total = (long long)S * Tmax;
+    const unsigned lt = lanemask_lt();
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         int k = (int)(idx / Tmax), t = (int)(idx % Tmax);
-        int Tk = slices[k].TX * slices[k].TY;
-        if (t >= Tk) continue;
-        unsigned c0 = chunk_base[k], c1 = chunk_base[k + 1];
-        if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
+        const int Tk = slices[k].TX * slices[k].TY;
+        const bool real = t < Tk;
         unsigned run = 0;
-        unsigned c = c0;
-        // eight independent loads in flight per thread before the dependent stores
-        for (; c + 8 <= c1; c += 8) {
-            unsigned v[8];
+        if (real) {
+            unsigned c0 = chunk_base[k], c1 = chunk_base[k + 1];
+            if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
+            unsigned c = c0;
+            // eight independent loads in flight per thread before the dependent stores
+            for (; c + 8 <= c1; c += 8) {
+                unsigned v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(&hist[(size_t)(c + u) * Tmax + t]);
+                for (int u = 0; u < 8; ++u) v[u] = __ldcg(&hist[(size_t)(c + u) * Tmax + t]);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                hist[(size_t)(c + u) * Tmax + t] = run;
-                run += v[u];
+                for (int u = 0; u < 8; ++u) {
+                    hist[(size_t)(c + u) * Tmax + t] = run;
+                    run += v[u];
+                }
             }
+            for (; c < c1; ++c) {
+                unsigned v = hist[(size_t)c * Tmax + t];
+                hist[(size_t)c * Tmax + t] = run;
+                run += v;
+            }
+            tile_cnt[slices[k].tile_base + t] = run;
         }
-        for (; c < c1; ++c) {
-            unsigned v = hist[(size_t)c * Tmax + t];
-            hist[(size_t)c * Tmax + t] = run;
-            run += v;
+        const unsigned am = __activemask();
+        const bool busy = real && run > 0, idle = real && run == 0;
+        const unsigned bb = __ballot_sync(am, busy), ib = __ballot_sync(am, idle);
+        const int leader = __ffs(am) - 1;
+        unsigned pb = 0, pi = 0;
+        if ((int)(threadIdx.x & 31) == leader) {
+            if (bb) pb = atomicAdd(&hdr->n_busy, (unsigned)__popc(bb));
+            if (ib) pi = atomicAdd(&hdr->n_idle, (unsigned)__popc(ib));
         }
-        tile_cnt[slices[k].tile_base + t] = run;
+        pb = __shfl_sync(am, pb, leader);
+        pi = __shfl_sync(am, pi, leader);
+        if (busy) tile_list[pb + __popc(bb & lt)] = (unsigned)(slices[k].tile_base + t);
+        if (idle) tile_list[n_tiles - 1 - (long long)(pi + __popc(ib & lt))] = (unsigned)(slices[k].tile_base + t);
     }
 }
 
@@ -859,7 +891,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
     unsigned n_chunks = chunk_base[S];
     if ((long long)n_chunks > cap_chunks) n_chunks = (unsigned)cap_chunks;
     const unsigned lt = lanemask_lt();
-    for (unsigned c = blockIdx.x * BIN_WARPS + w; c < n_chunks; c += gridDim.x * BIN_WARPS) {
+    const unsigned nw = blockDim.x >> 5;
+    for (unsigned c = blockIdx.x * nw + w; c < n_chunks; c += gridDim.x * nw) {
         int k = find_slice(chunk_base, S, c);
         const int TX = slices[k].TX, Tk = TX * slices[k].TY, tb = slices[k].tile_base;
         unsigned r0 = slice_rs[k] + (c - chunk_base[k]) * MG_CHUNK;
@@ -911,6 +944,8 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     rec.slice = (int *)(ws + L.rec_slice);
     rec.rect = (ushort4 *)(ws + L.rec_rect);
     rec.mom = (float *)(ws + L.rec_mom);
+    rec.f64 = (unsigned char *)(ws + L.rec_f64);
+    rec.mom64 = (double *)(ws + L.rec_mom64);
     rec.thr = (float *)(ws + L.rec_thr);
     rec.cell = cg.on ? (int4 *)(ws + L.rec_cell) : nullptr;
     rec.cap = L.cap_records;
@@ -968,23 +1003,26 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
         k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, (int)NW, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
     }
     const int Tmax = (int)L.max_tiles;
-    size_t smem = (size_t)BIN_WARPS * Tmax * sizeof(unsigned);
+    int bw = BIN_WARPS;
+    while (bw > 1 && (size_t)bw * Tmax * sizeof(unsigned) > BIN_SMEM_MAX) --bw;
+    size_t smem = (size_t)bw * Tmax * sizeof(unsigned);
     if (smem > 48 * 1024) {
         cudaFuncSetAttribute(k_bin_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    long long want = (L.cap_chunks + BIN_WARPS - 1) / BIN_WARPS;
+    long long want = (L.cap_chunks + bw - 1) / bw;
     int gb = (int)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
     {
         MG_PROF(MG_ST_BIN_HIST, st);
-        k_bin_hist<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+        k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
                                                      L.cap_chunks);
     }
     long long tot = (long long)S * Tmax;
     int gc = (int)((tot + 255) / 256 < 148 * 32 ? (tot + 255) / 256 : 148 * 32);
     {
         MG_PROF(MG_ST_BIN_COLSCAN, st);
-        k_bin_colscan<<<gc, 256, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt);
+        k_bin_colscan<<<gc, 256, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt,
+                                          (unsigned *)(ws + L.tile_list), L.n_tiles, hdr);
     }
     {
         MG_PROF(MG_ST_SCAN_TILES, st);
@@ -992,7 +1030,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_BIN_SCATTER, st);
-        k_bin_scatter<<<gb, 32 * BIN_WARPS, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+        k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
                                                         L.cap_chunks, tile_off, entries, L.cap_entries, hdr);
     }
 }

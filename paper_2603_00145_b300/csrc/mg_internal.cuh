@@ -6,9 +6,9 @@
 
 #include "mgauss.h"
 
-#define MG_TILE 16             // tile edge in pixels (record rectangles are in tiles)
+#define MG_TILE MG_TILE_EDGE    // tile edge in pixels (record rectangles are in tiles)
 #define MG_MAX_STACKS 32
-#define MG_MAX_TILES_SLICE 4096  // 1024 x 1024 pixels
+#define MG_MAX_TILES_SLICE 16384 // 1024 x 1024 pixels
 #define MG_CHUNK 512           // records per binning chunk (one warp each)
 #define MG_SCAN_BLOCKS 256     // blocks of the three-phase scan
 
@@ -123,7 +123,9 @@ struct WsHeader {
     unsigned long long pairs_inside;     // mg_render_pair_count
     unsigned long long pairs_evaluated;
     unsigned int tile_ctr[2];  // work counters of the persistent render kernels
-    unsigned long long reserved[24];
+    unsigned int n_busy;       // tiles with records (front of the tile list)
+    unsigned int n_idle;       // tiles without records (back of the tile list)
+    unsigned long long reserved[23];
 };
 
 // Records are stored as structure-of-arrays.
@@ -136,6 +138,8 @@ struct Records {
     float *mom;         // [cap][8] backward moments (6 used)
     float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
     int4 *cell;         // MG_LOCAL_CELLS: the Gaussian's cell (x, y, z, 0); else unused
+    unsigned char *f64; // 1: near-degenerate Gaussian (FP64 geometry and FP64 moments)
+    double *mom64;      // [cap][6] backward moments of the FP64 records (FP64 accumulation)
     long long cap;
 };
 
@@ -143,7 +147,8 @@ struct Records {
 // size query.
 struct WsLayout {
     size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom, rec_thr;
-    size_t chunk_base, hist, tile_cnt, tile_off, entries, gcnt, bits, gmap, rec_grad, rec_cell, total;
+    size_t chunk_base, hist, tile_cnt, tile_off, tile_list, entries, gcnt, bits, gmap, rec_grad, rec_cell, rec_f64,
+        rec_mom64, total;
     long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
 

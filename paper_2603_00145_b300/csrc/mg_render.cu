@@ -1,13 +1,15 @@
 // mg_render.cu -- per-tile evaluation of the additive Gaussian mixture
 // (Sec. 3.3.2, Eq. E7 with the slice profile) and its adjoint.
 //
-// K4 k_render_fwd : one warp per 16x16 tile (persistent warps pull tiles);
-//     records staged 32 at a time through shared memory and read back by
-//     broadcast; per (record, voxel): q = A dx^2 + B2 dx dy + C dy^2 (conic
-//     pre-scaled to log2 units), I += amp * 2^q.
-// K5 k_render_bwd : lane = record; each lane sweeps the tile's 256 voxels
+// K4 k_render_fwd : one warp per 8x8 tile (persistent warps pull tiles);
+//     records staged 32 at a time through shared memory, each already in
+//     the tile's frame: q(x, y) = A x^2 + B x y + C y^2 + D x + E y + F with
+//     (x, y) the voxel's offset from the tile centre (log2 units), and
+//     I += amp * 2^q.
+// K5 k_render_bwd : lane = record; each lane sweeps the tile's 64 voxels
 //     and forms six moments of w = g 2^q (sum w, w dx, w dy, w dx^2, w dx dy,
-//     w dy^2); six atomics per (record, tile). Nothing per pair is stored.
+//     w dy^2); two vector atomics per (record, tile). Nothing per pair is
+//     stored.
 // K6 k_chain_fused : per Gaussian, its records' moments -> dL/d(centre,
 //     conic, amp) -> adjoint of the record geometry -> dL/d(mean, quat,
 //     scale, alpha), summed in a fixed order (no atomics).
@@ -18,8 +20,12 @@
 
 #include "mg_internal.cuh"
 
-constexpr int RW = 4;     // warps (tiles) per block
-constexpr int VPT = 8;    // voxels per thread (a column strip)
+static_assert(MG_TILE == 8, "the evaluation kernels are laid out for 8x8 tiles");
+
+constexpr int RW = 4;                           // warps (tiles) per block
+constexpr int NV = MG_TILE * MG_TILE;           // voxels per tile (64)
+constexpr int VPT = NV / 32;                    // voxels per lane in the pair count (2)
+constexpr float TC = 0.5f * (MG_TILE - 1);      // tile-centre offset of the first row / column (3.5)
 
 struct TileLoc {
     int W, H, px, py0;
@@ -40,73 +46,126 @@ __device__ __forceinline__ TileLoc locate_tile(const StackTable &tab, int t, int
     L.W = tab.W[s];
     L.H = tab.H[s];
     L.pixbase = tab.pix_base[s] + (long long)kk * L.H * L.W;
-    L.px = tx * MG_TILE + (lane & 15);
-    L.py0 = ty * MG_TILE + (lane >> 4) * VPT;
+    L.px = tx * MG_TILE + (lane % MG_TILE);
+    L.py0 = ty * MG_TILE + (lane / MG_TILE) * VPT;
     return L;
 }
 
-// K4: one warp per 16x16 tile. The four quarter-warps take every fourth
-// record of the tile's list; lane c of a quarter owns pixel columns 2c and
-// 2c+1 of the tile over all 16 rows, so the per-record set-up is shared by 32
-// voxels. Records are staged 32 at a time in shared memory (software-
-// pipelined global loads) and read by broadcast. Per row: the quadratic of
-// both columns with two packed FMAs (the row offset is an exact packed
-// counter), two ex2, one packed FMA into the row's (column, column + 1)
-// accumulator. At the end the quarters reduce-scatter their partial sums
-// (24 shuffles, fixed order) and each lane writes 4 rows of its two columns.
+struct TileId {
+    int s, kk, tx, ty, W, H;
+    long long pixbase;
+};
+
+__device__ __forceinline__ TileId tile_id(const StackTable &tab, int t)
+{
+    TileId d;
+    int s = 0;
+    while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
+    const int TX = tab.TX[s], T = TX * tab.TY[s];
+    const int local = t - tab.tile_base[s];
+    d.s = s;
+    d.kk = local / T;
+    const int within = local - d.kk * T;
+    d.ty = within / TX;
+    d.tx = within - d.ty * TX;
+    d.W = tab.W[s];
+    d.H = tab.H[s];
+    d.pixbase = tab.pix_base[s] + (long long)d.kk * d.H * d.W;
+    return d;
+}
+
+// The exponent of a record about the centre (x0c, y0c) of a tile: with
+// dx0 = x0c - cx, dy0 = y0c - cy (the tile centre's offset from the record
+// centre) and (x, y) a voxel's offset from the tile centre,
+// A (dx0+x)^2 + B (dx0+x)(dy0+y) + C (dy0+y)^2 = A x^2 + B x y + C y^2 + D x + E y + F.
+struct TileQuad {
+    float D, E, F;
+};
+__device__ __forceinline__ TileQuad tile_quad(float A, float B, float C, float dx0, float dy0)
+{
+    TileQuad t;
+    const float Bdy = B * dy0;
+    t.D = fmaf(2.f * A, dx0, Bdy);
+    t.E = fmaf(B, dx0, 2.f * C * dy0);
+    t.F = fmaf(fmaf(A, dx0, Bdy), dx0, (C * dy0) * dy0);
+    return t;
+}
+
+// CELLS: the tile's voxel cells packed relative to its smallest cell (one
+// word per voxel, row-major), and that smallest cell
+__device__ __forceinline__ void tile_cells(const SliceDev &Sd, const CellGrid &cg, int tx, int ty, int lane,
+                                           unsigned *srelw, int &cb0, int &cb1, int &cb2)
+{
+    int m0 = 0x7fffffff, m1 = 0x7fffffff, m2 = 0x7fffffff;
+    for (int i = lane; i < NV; i += 32) {
+        int c[3];
+        voxel_cell(Sd, tx * MG_TILE + (i % MG_TILE), ty * MG_TILE + (i / MG_TILE), cg, c);
+        m0 = min(m0, c[0]);
+        m1 = min(m1, c[1]);
+        m2 = min(m2, c[2]);
+    }
+    cb0 = __reduce_min_sync(0xffffffffu, m0);
+    cb1 = __reduce_min_sync(0xffffffffu, m1);
+    cb2 = __reduce_min_sync(0xffffffffu, m2);
+    for (int i = lane; i < NV; i += 32) {
+        int c[3];
+        voxel_cell(Sd, tx * MG_TILE + (i % MG_TILE), ty * MG_TILE + (i / MG_TILE), cg, c);
+        srelw[i] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
+                   ((unsigned)min(c[2] - cb2, 255) << 16);
+    }
+    __syncwarp();
+}
+
+// Staged records of a forward warp, one float4 array per term so that the
+// four quarter-warps' broadcast reads of consecutive records are
+// conflict-free: (A, A, B, B), (C, C, D, D), (E, E, F, F), (amp, amp, -, -).
+struct FwdStage {
+    float4 ab[32], cd[32], ef[32], am[32];
+};
+
+// K4: one warp per 8x8 tile. Eight lane groups of four take every eighth
+// record of the tile's list; lane c of a group owns pixel columns 2c and
+// 2c+1 of the tile over its 8 rows, so a record's set-up is shared by 16
+// voxels. Per record and lane: the two columns' coefficients
+// a1 = B x + E, a0 = (A x + D) x + F as one packed pair each (three FP32x2
+// FMAs), then per row q = (C y + a1) y + a0 (two packed FMAs), two ex2 and
+// one packed FMA into the row's accumulator. The lane that stages a record
+// rewrites it in the tile frame once. At the end the groups reduce-scatter
+// their partial sums (14 shuffles, fixed order) and each lane writes one row
+// of its two columns.
 // CELLS: the paper's cell-grid local set; each (record, voxel) term is kept
 // only when the voxel is a member (mgauss.h, MG_LOCAL_CELLS).
 template <bool CELLS>
-__device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, float4 *sgw, float2 *sg2w, int4 *sgcw,
+__device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, FwdStage &sw, int4 *sgcw,
                                          unsigned *srelw, const unsigned *__restrict__ tile_off,
                                          const unsigned *__restrict__ entries, long long cap_entries,
                                          long long cap_records, const float4 *__restrict__ geo,
                                          const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
                                          const CellGrid &cg, const int4 *__restrict__ rcell, float *__restrict__ out)
 {
-    int s = 0;
-    while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
-    const int TX = tab.TX[s], T = TX * tab.TY[s];
-    const int local = t - tab.tile_base[s];
-    const int kk = local / T, within = local - kk * T;
-    const int ty = within / TX, tx = within - ty * TX;
-    const int W = tab.W[s], H = tab.H[s];
-    const long long pixbase = tab.pix_base[s] + (long long)kk * H * W;
-    const int qw = lane >> 3, c8 = lane & 7;
-    const int px0 = tx * MG_TILE + 2 * c8, py0 = ty * MG_TILE;
-    // rows are addressed relative to the tile's middle row (offsets +-7.5) to
-    // keep the terms of the expanded quadratic small
-    const float fpx = (float)px0, fpyc = (float)py0 + 7.5f;
+    const TileId d = tile_id(tab, t);
+    const int grp = lane >> 2, c4 = lane & 3;
+    const float x0c = (float)(d.tx * MG_TILE) + TC, y0c = (float)(d.ty * MG_TILE) + TC;
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 > e1) e0 = e1;
-    // CELLS: the tile's voxel cells, packed relative to its smallest cell
     int cb0 = 0, cb1 = 0, cb2 = 0;
+    uint2 rel[MG_TILE];  // CELLS: this lane's two columns of voxel cells, per row
     if (CELLS) {
-        const SliceDev &Sd = slices[tab.slice_base[s] + kk];
-        int m0 = 0x7fffffff, m1 = 0x7fffffff, m2 = 0x7fffffff;
-        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
-            int c[3];
-            voxel_cell(Sd, tx * MG_TILE + (i & 15), py0 + (i >> 4), cg, c);
-            m0 = min(m0, c[0]);
-            m1 = min(m1, c[1]);
-            m2 = min(m2, c[2]);
-        }
-        cb0 = __reduce_min_sync(0xffffffffu, m0);
-        cb1 = __reduce_min_sync(0xffffffffu, m1);
-        cb2 = __reduce_min_sync(0xffffffffu, m2);
-        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
-            int c[3];
-            voxel_cell(Sd, tx * MG_TILE + (i & 15), py0 + (i >> 4), cg, c);
-            srelw[i] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
-                       ((unsigned)min(c[2] - cb2, 255) << 16);
-        }
-        __syncwarp();
+        tile_cells(slices[tab.slice_base[d.s] + d.kk], cg, d.tx, d.ty, lane, srelw, cb0, cb1, cb2);
+#pragma unroll
+        for (int r = 0; r < MG_TILE; ++r) rel[r] = *(const uint2 *)&srelw[r * MG_TILE + 2 * c4];
     }
-    float2 acc[MG_TILE];  // per row: (column px0, column px0 + 1)
+    // lane constants: the two column offsets and each row's offset as a pair
+    // (an opaque zero added so that they stay in registers)
+    const float rz = __uint_as_float(e1 & 0x80000000u);
+    const float2 xo2 = make_float2((float)(2 * c4) - TC + rz, (float)(2 * c4 + 1) - TC + rz);
+    float2 yy[MG_TILE];
+#pragma unroll
+    for (int r = 0; r < MG_TILE; ++r) yy[r] = make_float2((float)r - TC + rz, (float)r - TC + rz);
+    float2 acc[MG_TILE];  // per row: (column 2 c4, column 2 c4 + 1)
 #pragma unroll
     for (int r = 0; r < MG_TILE; ++r) acc[r] = make_float2(0.f, 0.f);
-    const float2 one2 = make_float2(1.f, 1.f);
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 nc = make_int4(0, 0, 0, 0);
@@ -119,9 +178,16 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
         }
     }
     for (unsigned base = e0; base < e1; base += 32) {
-        sgw[lane] = na;
-        sg2w[lane] = nb;
-        if (CELLS) sgcw[lane] = nc;
+        {
+            // stage this lane's record in the tile frame (a zero record past the end)
+            const float A = na.z, B = na.w, C = nb.x;
+            const TileQuad tq = tile_quad(A, B, C, x0c - na.x, y0c - na.y);
+            sw.ab[lane] = make_float4(A, A, B, B);
+            sw.cd[lane] = make_float4(C, C, tq.D, tq.D);
+            sw.ef[lane] = make_float4(tq.E, tq.E, tq.F, tq.F);
+            sw.am[lane] = make_float4(nb.y, nb.y, 0.f, 0.f);
+            if (CELLS) sgcw[lane] = nc;
+        }
         __syncwarp();
         const unsigned nxt = base + 32 + lane;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -135,175 +201,154 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             }
         }
         const int m = (int)min(32u, e1 - base);
-        for (int j4 = 0; j4 < m; j4 += 4) {
-            const int j = j4 + qw;  // this quarter-warp's record (zero record past the end)
-            const float4 a = sgw[j & 31];
-            float2 b = sg2w[j & 31];
-            if (j >= m) b.y = 0.f;
+        for (int j8 = 0; j8 < m; j8 += 8) {
+            const int j = j8 + grp;  // this group's record (a zero record past the end)
+            const float4 ab = sw.ab[j], cd = sw.cd[j], ef = sw.ef[j], am = sw.am[j];
+            const float2 A2 = make_float2(ab.x, ab.y), B2 = make_float2(ab.z, ab.w);
+            const float2 C2 = make_float2(cd.x, cd.y), D2 = make_float2(cd.z, cd.w);
+            const float2 E2 = make_float2(ef.x, ef.y), F2 = make_float2(ef.z, ef.w);
+            float2 amp2 = make_float2(am.x, am.y);
             unsigned clo = 0u, chi = 0u;
-            if (CELLS && !cell_range(sgcw[j & 31], cg.R, cb0, cb1, cb2, clo, chi)) b.y = 0.f;
-            // q(column, v) = C v^2 + (B dx + 2 C dyc) v + (A dx^2 + B dx dyc + C dyc^2),
-            // dx the column's offset from the record centre, v = row - 7.5
-            const float A = a.z, B = a.w, C = b.x;
-            const float dx = fpx - a.x, dx1 = dx + 1.f, dyc = fpyc - a.y;
-            const float Bdy = B * dyc, Cdy = C * dyc, Cdy2 = Cdy + Cdy, Cdd = Cdy * dyc;
-            const float2 a12 = make_float2(fmaf(B, dx, Cdy2), fmaf(B, dx1, Cdy2));
-            const float2 a02 = make_float2(fmaf(fmaf(A, dx, Bdy), dx, Cdd), fmaf(fmaf(A, dx1, Bdy), dx1, Cdd));
-            const float2 C2 = make_float2(C, C), amp2 = make_float2(b.y, b.y);
-            float2 vv = make_float2(-7.5f, -7.5f);
+            if (CELLS && !cell_range(sgcw[j], cg.R, cb0, cb1, cb2, clo, chi)) amp2 = make_float2(0.f, 0.f);
+            const float2 a1 = __ffma2_rn(B2, xo2, E2);
+            const float2 a0 = __ffma2_rn(__ffma2_rn(A2, xo2, D2), xo2, F2);
 #pragma unroll
             for (int r = 0; r < MG_TILE; ++r) {
-                const float2 q = __ffma2_rn(__ffma2_rn(C2, vv, a12), vv, a02);
+                const float2 q = __ffma2_rn(__ffma2_rn(C2, yy[r], a1), yy[r], a0);
                 float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
                 if (CELLS) {
-                    const uint2 rl = *(const uint2 *)&srelw[r * MG_TILE + 2 * c8];
-                    if (!cell_member(rl.x, clo, chi)) e.x = 0.f;
-                    if (!cell_member(rl.y, clo, chi)) e.y = 0.f;
+                    if (!cell_member(rel[r].x, clo, chi)) e.x = 0.f;
+                    if (!cell_member(rel[r].y, clo, chi)) e.y = 0.f;
                 }
                 acc[r] = __ffma2_rn(amp2, e, acc[r]);
-                vv = __ffma2_rn(one2, one2, vv);  // exact: v + 1
             }
         }
         __syncwarp();
     }
-    // reduce-scatter over the four quarters (lanes c8, c8 + 8, c8 + 16, c8 + 24):
-    // across xor 16 the upper pair keeps rows 8..15, across xor 8 the odd one
-    // keeps the upper four of those rows
-    const bool up16 = (qw >> 1) != 0, up8 = (qw & 1) != 0;
+    // reduce-scatter over the eight groups (lanes c4 + 4 g): across xor 16
+    // the upper groups keep rows 4..7, across xor 8 the upper two of the
+    // four, across xor 4 the upper one of the two; group g ends with row g
 #pragma unroll
-    for (int r = 0; r < MG_TILE / 2; ++r) {
-        const float2 send = up16 ? acc[r] : acc[r + MG_TILE / 2];
-        float2 recv;
-        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
-        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
-        const float2 keep = up16 ? acc[r + MG_TILE / 2] : acc[r];
-        acc[r] = make_float2(keep.x + recv.x, keep.y + recv.y);
-    }
+    for (int k = 0; k < 3; ++k) {
+        const int half = 4 >> k;  // rows kept after this step: 4, 2, 1
+        const bool up = (lane >> (4 - k)) & 1;
 #pragma unroll
-    for (int r = 0; r < MG_TILE / 4; ++r) {
-        const float2 send = up8 ? acc[r] : acc[r + MG_TILE / 4];
-        float2 recv;
-        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
-        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
-        const float2 keep = up8 ? acc[r + MG_TILE / 4] : acc[r];
-        acc[r] = make_float2(keep.x + recv.x, keep.y + recv.y);
-    }
-    const int r0 = py0 + (up16 ? MG_TILE / 2 : 0) + (up8 ? MG_TILE / 4 : 0);
-#pragma unroll
-    for (int r = 0; r < MG_TILE / 4; ++r) {
-        if (r0 + r < H) {
-            float *row = out + pixbase + (long long)(r0 + r) * W;
-            if (px0 < W) row[px0] = acc[r].x;
-            if (px0 + 1 < W) row[px0 + 1] = acc[r].y;
+        for (int r = 0; r < half; ++r) {
+            const float2 send = up ? acc[r] : acc[r + half];
+            float2 recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16 >> k);
+            recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16 >> k);
+            const float2 keep = up ? acc[r + half] : acc[r];
+            acc[r] = make_float2(keep.x + recv.x, keep.y + recv.y);
         }
+    }
+    const int px = d.tx * MG_TILE + 2 * c4, py = d.ty * MG_TILE + grp;
+    if (py < d.H) {
+        float *row = out + d.pixbase + (long long)py * d.W;
+        if (px < d.W) row[px] = acc[0].x;
+        if (px + 1 < d.W) row[px + 1] = acc[0].y;
     }
 }
 
-// persistent warps pull tiles from a counter (tiles carry very different
-// numbers of records)
+// Tiles without records are written with zeros first (32 list entries per
+// warp and step, no dependent loads); then persistent warps pull the tiles
+// with records from a counter (tiles carry very different numbers of
+// records).
 template <bool CELLS>
-__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 5) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
+__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
                                                           const SliceDev *__restrict__ slices, CellGrid cg,
-                                                          const int4 *__restrict__ rcell, float *__restrict__ out,
+                                                          const int4 *__restrict__ rcell,
+                                                          const unsigned *__restrict__ tile_list,
+                                                          const WsHeader *__restrict__ hdr, float *__restrict__ out,
                                                           unsigned *counter)
 {
-    __shared__ float4 sg[RW][32];
-    __shared__ float2 sg2[RW][32];
+    __shared__ FwdStage sg[RW];
     __shared__ int4 sgc[CELLS ? RW : 1][32];
-    __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? MG_TILE * MG_TILE : 4];
+    __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n_tiles = tab.n_tiles_total;
+    const long long n_idle = hdr->n_idle, n_busy = hdr->n_busy;
+    const long long gw = (long long)blockIdx.x * RW + w, nw = (long long)gridDim.x * RW;
+    for (long long i0 = gw * 32; i0 < n_idle; i0 += nw * 32) {
+        const unsigned tl = (i0 + lane < n_idle) ? tile_list[n_tiles - 1 - (i0 + lane)] : 0xffffffffu;
+        const int nu = (int)min(32LL, n_idle - i0);
+        for (int u = 0; u < nu; ++u) {
+            const unsigned t = __shfl_sync(0xffffffffu, tl, u);
+            const TileId d = tile_id(tab, (int)t);
+            const int px = d.tx * MG_TILE + (lane % MG_TILE), py = d.ty * MG_TILE + (lane / MG_TILE) * VPT;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v)
+                if (px < d.W && py + v < d.H) out[d.pixbase + (long long)(py + v) * d.W + px] = 0.f;
+        }
+    }
     for (;;) {
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if ((int)t >= tab.n_tiles_total) break;
-        fwd_tile<CELLS>(tab, (int)t, lane, sg[w], sg2[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off, entries,
-                        cap_entries, cap_records, geo, geo2, slices, cg, rcell, out);
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(counter, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if ((long long)i >= n_busy) break;
+        fwd_tile<CELLS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off,
+                        entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, out);
         __syncwarp();
     }
 }
 
 // K5, "one lane per record": lane l takes record l of the tile's next 32
-// entries and sweeps all 256 voxels of the tile, reading dL/dI from shared
-// memory by broadcast. Per voxel: q from two FMAs (quadratic in the column
-// offset), w = g 2^q, and three row sums (w, i w, i^2 w); per row the row
-// sums fold into six moment accumulators with the row offset. Moments are
+// entries and sweeps all 64 voxels of the tile, reading dL/dI from shared
+// memory by broadcast. Per row y: b1 = B y + D, b0 = (C y + E) y + F; per
+// column pair q = (A x + b1) x + b0 with packed FP32x2 FMAs, w = g 2^q, and
+// three row sums (w, x w, x^2 w) from the tile's products g, g x, g x^2; per
+// row the row sums fold into six moment accumulators with y. Moments are
 // taken about the tile centre and moved to the record centre at the end, so
 // no cross-lane reduction is needed; each lane then adds its record's six
-// moments with six atomics.
+// moments with a float4 and a float2 atomic.
 template <bool CELLS>
 __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane, float *sgvw, unsigned *srelw,
                                          const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
                                          long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
                                          const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
                                          const CellGrid &cg, const int4 *__restrict__ rcell,
-                                         const float *__restrict__ grad_out, float *__restrict__ mom)
+                                         const unsigned char *__restrict__ f64, const float *__restrict__ grad_out,
+                                         float *__restrict__ mom, double *__restrict__ mom64)
 {
-
-    int s = 0;
-    while (s + 1 < tab.n_stacks && t >= tab.tile_base[s + 1]) ++s;
-    const int TX = tab.TX[s], T = TX * tab.TY[s];
-    const int local = t - tab.tile_base[s];
-    const int kk = local / T, within = local - kk * T;
-    const int ty = within / TX, tx = within - ty * TX;
-    const int W = tab.W[s], H = tab.H[s];
-    const long long pixbase = tab.pix_base[s] + (long long)kk * H * W;
+    const TileId d = tile_id(tab, t);
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 >= e1) return;
-    // dL/dI of the tile and its products with the column offset ic and ic^2
+    // dL/dI of the tile and its products with the column offset x and x^2
     // (shared by all records of the tile)
-    for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
-        const int px = tx * MG_TILE + (i & 15), py = ty * MG_TILE + (i >> 4);
-        const float gval = (px < W && py < H) ? grad_out[pixbase + (long long)py * W + px] : 0.f;
-        const float ic = (float)(i & 15) - 7.5f;
+    for (int i = lane; i < NV; i += 32) {
+        const int px = d.tx * MG_TILE + (i % MG_TILE), py = d.ty * MG_TILE + (i / MG_TILE);
+        const float gval = (px < d.W && py < d.H) ? grad_out[d.pixbase + (long long)py * d.W + px] : 0.f;
+        const float x = (float)(i % MG_TILE) - TC;
         sgvw[i] = gval;
-        sgvw[MG_TILE * MG_TILE + i] = gval * ic;
-        sgvw[2 * MG_TILE * MG_TILE + i] = gval * ic * ic;
+        sgvw[NV + i] = gval * x;
+        sgvw[2 * NV + i] = gval * x * x;
     }
-    // CELLS: the tile's voxel cells, packed relative to its smallest cell
     int cb0 = 0, cb1 = 0, cb2 = 0;
-    if (CELLS) {
-        const SliceDev &Sd = slices[tab.slice_base[s] + kk];
-        int m0 = 0x7fffffff, m1 = 0x7fffffff, m2 = 0x7fffffff;
-        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
-            int c[3];
-            voxel_cell(Sd, tx * MG_TILE + (i & 15), ty * MG_TILE + (i >> 4), cg, c);
-            m0 = min(m0, c[0]);
-            m1 = min(m1, c[1]);
-            m2 = min(m2, c[2]);
-        }
-        cb0 = __reduce_min_sync(0xffffffffu, m0);
-        cb1 = __reduce_min_sync(0xffffffffu, m1);
-        cb2 = __reduce_min_sync(0xffffffffu, m2);
-        for (int i = lane; i < MG_TILE * MG_TILE; i += 32) {
-            int c[3];
-            voxel_cell(Sd, tx * MG_TILE + (i & 15), ty * MG_TILE + (i >> 4), cg, c);
-            srelw[i] = (unsigned)min(c[0] - cb0, 255) | ((unsigned)min(c[1] - cb1, 255) << 8) |
-                       ((unsigned)min(c[2] - cb2, 255) << 16);
-        }
-    }
+    if (CELLS) tile_cells(slices[tab.slice_base[d.s] + d.kk], cg, d.tx, d.ty, lane, srelw, cb0, cb1, cb2);
     __syncwarp();
-    const float x0c = (float)(tx * MG_TILE) + 7.5f, y0c = (float)(ty * MG_TILE) + 7.5f;
-    // column offsets as register pairs, formed once per tile (see fwd_tile)
+    const float x0c = (float)(d.tx * MG_TILE) + TC, y0c = (float)(d.ty * MG_TILE) + TC;
+    // column offsets as register pairs, formed once per tile (an opaque zero
+    // added so that they stay in registers)
     const float rz = __uint_as_float(e1 & 0x80000000u);
-    float2 icr[MG_TILE / 2];
+    float2 xp[MG_TILE / 2];
 #pragma unroll
-    for (int c = 0; c < MG_TILE / 2; ++c)
-        icr[c] = make_float2((float)(2 * c) - 7.5f + rz, (float)(2 * c + 1) - 7.5f + rz);
+    for (int c = 0; c < MG_TILE / 2; ++c) xp[c] = make_float2((float)(2 * c) - TC + rz, (float)(2 * c + 1) - TC + rz);
     // the next batch of 32 records is fetched while the current one is swept
     unsigned nr = 0xffffffffu;
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 ncl = make_int4(0, 0, 0, 0);
+    unsigned char nf = 0;
     if (e0 + lane < e1) {
         nr = entries[e0 + lane];
         if ((long long)nr < cap_records) {
             na = geo[nr];
             nb = geo2[nr];
+            nf = f64[nr];
             if (CELLS) ncl = rcell[nr];
         } else {
             nr = 0xffffffffu;
@@ -314,15 +359,18 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
         const float4 a = na;
         const float2 b = nb;
         const int4 cl = ncl;
+        const bool dbl = nf != 0;
         const unsigned en = base + 32 + lane;
         nr = 0xffffffffu;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
         nb = make_float2(0.f, 0.f);
+        nf = 0;
         if (en < e1) {
             nr = entries[en];
             if ((long long)nr < cap_records) {
                 na = geo[nr];
                 nb = geo2[nr];
+                nf = f64[nr];
                 if (CELLS) ncl = rcell[nr];
             } else {
                 nr = 0xffffffffu;
@@ -330,36 +378,34 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
         }
         unsigned clo = 0u, chi = 0u;
         if (CELLS && r != 0xffffffffu && !cell_range(cl, cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
-        const float A = a.z, B2 = a.w, C = b.x;
-        const float dxc = x0c - a.x;   // column offset of the tile centre from the record centre
-        const float dyc = y0c - a.y;   // row offset of the tile centre
-        const float A2x = 2.f * A * dxc, Ax = A * dxc;
+        const float A = a.z, B = a.w, C = b.x;
+        const float dx0 = x0c - a.x;  // the tile centre's offset from the record centre
+        const float dy0 = y0c - a.y;
+        const TileQuad tq = tile_quad(A, B, C, dx0, dy0);
         const float2 A2 = make_float2(A, A);
         float T0 = 0.f, T1 = 0.f, T2 = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
-        float jc = -7.5f;
+        float y = -TC;
 #pragma unroll 1
-        for (int j = 0; j < MG_TILE; ++j, jc += 1.f) {
-            const float dy = dyc + jc;
-            const float u = B2 * dy;
-            const float b1 = A2x + u;
-            const float b0 = fmaf(Ax + u, dxc, (C * dy) * dy);
+        for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
+            const float b1 = fmaf(B, y, tq.D);
+            const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
             const float4 *g0r = (const float4 *)&sgvw[j * MG_TILE];
-            const float4 *g1r = g0r + MG_TILE * MG_TILE / 4;
-            const float4 *g2r = g1r + MG_TILE * MG_TILE / 4;
+            const float4 *g1r = g0r + NV / 4;
+            const float4 *g2r = g1r + NV / 4;
             const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
             // column pairs (i, i+1) with packed FP32x2 arithmetic:
-            // P0 += g e, P1 += (g ic) e, P2 += (g ic^2) e
+            // P0 += g e, P1 += (g x) e, P2 += (g x^2) e
             const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
             float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4) {
+            for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
                 const float4 u0 = g0r[i4], u1 = g1r[i4], u2 = g2r[i4];
                 uint4 rl = make_uint4(0u, 0u, 0u, 0u);
                 if (CELLS) rl = relr[i4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float2 ic = icr[i4 * 2 + h];
-                    const float2 q = __ffma2_rn(__ffma2_rn(A2, ic, b12), ic, b02);
+                    const float2 x = xp[i4 * 2 + h];
+                    const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
                     float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
                     if (CELLS) {
                         if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
@@ -374,42 +420,59 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             T0 += R0;
             T1 += R1;
             T2 += R2;
-            Y0 = fmaf(jc, R0, Y0);
-            Y1 = fmaf(jc, R1, Y1);
-            Y2 = fmaf(jc * jc, R0, Y2);
+            Y0 = fmaf(y, R0, Y0);
+            Y1 = fmaf(y, R1, Y1);
+            Y2 = fmaf(y * y, R0, Y2);
         }
         if (r != 0xffffffffu) {
-            float *mr = mom + (size_t)r * 8;
-            atomicAdd(mr + 0, T0);
-            atomicAdd(mr + 1, fmaf(dxc, T0, T1));
-            atomicAdd(mr + 2, fmaf(dyc, T0, Y0));
-            atomicAdd(mr + 3, fmaf(dxc, fmaf(dxc, T0, T1 + T1), T2));
-            atomicAdd(mr + 4, fmaf(dxc, fmaf(dyc, T0, Y0), fmaf(dyc, T1, Y1)));
-            atomicAdd(mr + 5, fmaf(dyc, fmaf(dyc, T0, Y0 + Y0), Y2));
+            if (dbl) {
+                // near-degenerate Gaussian: the moments about its centre are
+                // small differences of large terms, so the shift from the tile
+                // centre (exact offsets) and the sum over tiles are in FP64
+                const double X = (double)x0c - (double)a.x, Y = (double)y0c - (double)a.y;
+                const double t0 = T0, t1 = T1, t2 = T2, y0 = Y0, y1 = Y1, y2 = Y2;
+                double *mr = mom64 + (size_t)r * 6;
+                atomicAdd(mr + 0, t0);
+                atomicAdd(mr + 1, fma(X, t0, t1));
+                atomicAdd(mr + 2, fma(Y, t0, y0));
+                atomicAdd(mr + 3, fma(X, fma(X, t0, t1 + t1), t2));
+                atomicAdd(mr + 4, fma(X, fma(Y, t0, y0), fma(Y, t1, y1)));
+                atomicAdd(mr + 5, fma(Y, fma(Y, t0, y0 + y0), y2));
+            } else {
+                float *mr = mom + (size_t)r * 8;
+                atomicAdd((float4 *)mr, make_float4(T0, fmaf(dx0, T0, T1), fmaf(dy0, T0, Y0),
+                                                    fmaf(dx0, fmaf(dx0, T0, T1 + T1), T2)));
+                atomicAdd((float2 *)(mr + 4), make_float2(fmaf(dx0, fmaf(dy0, T0, Y0), fmaf(dy0, T1, Y1)),
+                                                          fmaf(dy0, fmaf(dy0, T0, Y0 + Y0), Y2)));
+            }
         }
     }
 }
 
 template <bool CELLS>
-__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 1) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
+__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 6) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
                                                           const SliceDev *__restrict__ slices, CellGrid cg,
                                                           const int4 *__restrict__ rcell,
+                                                          const unsigned *__restrict__ tile_list,
+                                                          const WsHeader *__restrict__ hdr,
+                                                          const unsigned char *__restrict__ f64,
                                                           const float *__restrict__ grad_out, float *__restrict__ mom,
-                                                          unsigned *counter)
+                                                          double *__restrict__ mom64, unsigned *counter)
 {
-    __shared__ __align__(16) float sgv[RW][3 * MG_TILE * MG_TILE];
-    __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? MG_TILE * MG_TILE : 4];
+    __shared__ __align__(16) float sgv[RW][3 * NV];
+    __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n_busy = hdr->n_busy;  // tiles without records contribute nothing
     for (;;) {
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if ((int)t >= tab.n_tiles_total) break;
-        bwd_tile<CELLS>(tab, (int)t, lane, sgv[w], srel[CELLS ? w : 0], tile_off, entries, cap_entries, cap_records,
-                        geo, geo2, slices, cg, rcell, grad_out, mom);
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(counter, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if ((long long)i >= n_busy) break;
+        bwd_tile<CELLS>(tab, (int)tile_list[i], lane, sgv[w], srel[CELLS ? w : 0], tile_off, entries, cap_entries,
+                        cap_records, geo, geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
         __syncwarp();
     }
 }
@@ -633,13 +696,15 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
                  x * gR[2][0] + y * gR[2][1]);
 }
 
-__global__ void k_zero_mom(float4 *mom, const WsHeader *hdr, long long cap_records)
+__global__ void k_zero_mom(float4 *mom, const unsigned char *__restrict__ f64, double2 *mom64, const WsHeader *hdr,
+                           long long cap_records)
 {
     long long n = (long long)hdr->n_records;
     if (n > cap_records) n = cap_records;
-    long long nv = n * 2;  // 8 floats per record
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
-        mom[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        mom[2 * r] = mom[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);  // 8 floats per record
+        if (f64[r]) mom64[3 * r] = mom64[3 * r + 1] = mom64[3 * r + 2] = make_double2(0.0, 0.0);
+    }
 }
 
 // Slice-pose shares: one thread per record, moments -> dL/d(centre, conic,
@@ -649,7 +714,8 @@ __global__ void k_zero_mom(float4 *mom, const WsHeader *hdr, long long cap_recor
 template <bool DBL>
 __global__ void k_pose_rec(const WsHeader *hdr, long long cap_records, const float4 *__restrict__ geo,
                            const float2 *__restrict__ geo2, const int *__restrict__ gid, const int *__restrict__ rslice,
-                           const float *__restrict__ mom, const SliceDev *__restrict__ slices,
+                           const float *__restrict__ mom, const double *__restrict__ mom64,
+                           const SliceDev *__restrict__ slices,
                            const float *__restrict__ mean, const float *__restrict__ quat,
                            const float *__restrict__ scale, const float *__restrict__ alpha, float f64_ratio,
                            float4 *__restrict__ rg)
@@ -666,23 +732,30 @@ __global__ void k_pose_rec(const WsHeader *hdr, long long cap_records, const flo
         float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
         float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
         float al = alpha[g];
-        const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
-        const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
-        const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
         const float4 a = geo[r];
         const float2 b = geo2[r];
         const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
-        const float la = amp * 0.69314718055994531f;
-        const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
-        const float gpx = -la * (2.f * A * Sx + B2 * Sy);
-        const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
         const SliceDev &Sd = slices[rslice[r]];
         float o6[6];
         if (DBL) {
+            // the FP64 moments of a near-degenerate Gaussian, chained in FP64
+            const double *m = mom64 + (size_t)r * 6;
+            const double S0 = m[0], Sx = m[1], Sy = m[2], Sxx = m[3], Sxy = m[4], Syy = m[5];
+            const double la = (double)amp * 0.6931471805599453;
+            const double gpx = -la * (2.0 * A * Sx + (double)B2 * Sy);
+            const double gpy = -la * ((double)B2 * Sx + 2.0 * C * Sy);
             double dm[3], dq[4], ds[3], da, dp[6];
-            geometry_adjoint<double, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, dm, dq, ds, da, dp);
+            geometry_adjoint<double, true>(mu, qv, sc, al, Sd, la * Sxx, la * Sxy, la * Syy, gpx, gpy, S0, dm, dq,
+                                           ds, da, dp);
             for (int i = 0; i < 6; ++i) o6[i] = (float)dp[i];
         } else {
+            const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
+            const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
+            const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
+            const float la = amp * 0.69314718055994531f;
+            const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
+            const float gpx = -la * (2.f * A * Sx + B2 * Sy);
+            const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
             float gm[3], gq[4], gs[3], ga;
             geometry_adjoint<float, true>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga, o6);
         }
@@ -691,17 +764,37 @@ __global__ void k_pose_rec(const WsHeader *hdr, long long cap_records, const flo
     }
 }
 
-// FP64 record-geometry adjoint out of line: near-degenerate Gaussians are
-// rare, and inlining it would size every thread's registers for it
-__device__ __noinline__ void geometry_adjoint_f64(const float *mu, const float *q, const float *s, float alpha,
-                                                  const SliceDev &S, float gA, float gB2, float gC, float gpx,
-                                                  float gpy, float gamp, float o[11])
+// The chain of a near-degenerate Gaussian, out of line (rare, and inlining
+// it would size every thread's registers for it): its records' FP64
+// moments through the FP64 record-geometry adjoint, summed in FP64 in the
+// order of the Gaussian-major list; o = dL/d(mean[3], quat[4], scale[3], alpha).
+__device__ __noinline__ void chain_gaussian_f64(const float *mu, const float *q, const float *s, float alpha,
+                                                unsigned long long j0, unsigned long long j1,
+                                                const unsigned *__restrict__ gmap, long long cap_records,
+                                                const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
+                                                const int *__restrict__ rslice, const double *__restrict__ mom64,
+                                                const SliceDev *__restrict__ slices, float o[11])
 {
-    double dm[3], dq[4], ds[3], da;
-    geometry_adjoint<double>(mu, q, s, alpha, S, gA, gB2, gC, gpx, gpy, gamp, dm, dq, ds, da);
-    for (int i = 0; i < 3; ++i) o[i] = (float)dm[i], o[7 + i] = (float)ds[i];
-    for (int i = 0; i < 4; ++i) o[3 + i] = (float)dq[i];
-    o[10] = (float)da;
+    double acc[11];
+    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
+    for (unsigned long long j = j0; j < j1; ++j) {
+        const unsigned r = gmap[j];
+        if ((long long)r >= cap_records) continue;
+        const float4 a = geo[r];
+        const float2 b = geo2[r];
+        const double A = a.z, B2 = a.w, C = b.x;
+        const double *m = mom64 + (size_t)r * 6;
+        const double la = (double)b.y * 0.6931471805599453;
+        const double gpx = -la * (2.0 * A * m[1] + B2 * m[2]);
+        const double gpy = -la * (B2 * m[1] + 2.0 * C * m[2]);
+        double dm[3], dq[4], ds[3], da;
+        geometry_adjoint<double>(mu, q, s, alpha, slices[rslice[r]], la * m[3], la * m[4], la * m[5], gpx, gpy, m[0],
+                                 dm, dq, ds, da);
+        for (int i = 0; i < 3; ++i) acc[i] += dm[i], acc[7 + i] += ds[i];
+        for (int i = 0; i < 4; ++i) acc[3 + i] += dq[i];
+        acc[10] += da;
+    }
+    for (int i = 0; i < 11; ++i) o[i] = (float)acc[i];
 }
 
 // K6 fused: one thread per Gaussian visits its records in slice order (the
@@ -713,6 +806,7 @@ __global__ void __launch_bounds__(128, 3) k_chain_fused(long long n, const unsig
                                                      const unsigned *__restrict__ gmap, long long cap_records,
                                                      const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
                                                      const int *__restrict__ rslice, const float *__restrict__ mom,
+                                                     const double *__restrict__ mom64,
                                                      const SliceDev *__restrict__ slices,
                                                      const float *__restrict__ mean, const float *__restrict__ quat,
                                                      const float *__restrict__ scale, const float *__restrict__ alpha,
@@ -731,24 +825,26 @@ __global__ void __launch_bounds__(128, 3) k_chain_fused(long long n, const unsig
         float acc[11];
 #pragma unroll
         for (int i = 0; i < 11; ++i) acc[i] = 0.f;
+        if (dbl) {
+            chain_gaussian_f64(mu, qv, sc, al, j0, j1, gmap, cap_records, geo, geo2, rslice, mom64, slices, acc);
+            j1 = j0;  // done
+        }
         for (unsigned long long j = j0; j < j1; ++j) {
             const unsigned r = gmap[j];
             if ((long long)r >= cap_records) continue;
-            const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
-            const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
-            const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
             const float4 a = geo[r];
             const float2 b = geo2[r];
             const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
-            const float la = amp * 0.69314718055994531f;
-            const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
-            const float gpx = -la * (2.f * A * Sx + B2 * Sy);
-            const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
             const SliceDev &Sd = slices[rslice[r]];
             float o[11];
-            if (dbl) {
-                geometry_adjoint_f64(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, o);
-            } else {
+            {
+                const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
+                const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
+                const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
+                const float la = amp * 0.69314718055994531f;
+                const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
+                const float gpx = -la * (2.f * A * Sx + B2 * Sy);
+                const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
                 float gm[3], gq[4], gs[3], ga;
                 geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga);
                 for (int i = 0; i < 3; ++i) o[i] = gm[i], o[7 + i] = gs[i];
@@ -845,13 +941,13 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, co
     if (cg.on)
         k_render_fwd<true><<<grid, 32 * RW, 0, st>>>(
             tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
-            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell, out,
-            &hdr->tile_ctr[0]);
+            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
+            (const unsigned *)(ws + L.tile_list), hdr, out, &hdr->tile_ctr[0]);
     else
         k_render_fwd<false><<<grid, 32 * RW, 0, st>>>(
             tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
-            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell, out,
-            &hdr->tile_ctr[0]);
+            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
+            (const unsigned *)(ws + L.tile_list), hdr, out, &hdr->tile_ctr[0]);
 }
 
 // Slice-pose gradient from the moments the last backward left in the workspace.
@@ -866,11 +962,13 @@ void mg_launch_pose_grad(const WsLayout &L, char *ws, const SliceDev *slices, co
     k_pose_rec<false><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
                                                  (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
                                                  (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
+                                                 (const double *)(ws + L.rec_mom64),
                                                  slices, mean, quat, scale, alpha, f64_ratio, rg);
     if (f64_ratio > 0.f)
         k_pose_rec<true><<<gr, 256, 0, st>>>(hdr, L.cap_records, (const float4 *)(ws + L.rec_geo),
                                                     (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_gid),
                                                     (const int *)(ws + L.rec_slice), (const float *)(ws + L.rec_mom),
+                                                 (const double *)(ws + L.rec_mom64),
                                                     slices, mean, quat, scale, alpha, f64_ratio, rg);
     const unsigned *slice_rs = (const unsigned *)(ws + L.chunk_base) + (L.S + 1);
     k_pose_sum<<<(unsigned)L.S, 256, 0, st>>>((int)L.S, slice_rs, rg, g_pose);
@@ -888,7 +986,8 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
         int gz = (int)((capv + 255) / 256 < 148 * 16 ? (capv + 255) / 256 : 148 * 16);
         if (gz < 1) gz = 1;
         MG_PROF(MG_ST_ZERO, st);
-        k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), hdr, L.cap_records);
+        k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), (const unsigned char *)(ws + L.rec_f64),
+                                       (double2 *)(ws + L.rec_mom64), hdr, L.cap_records);
     }
     int nt = tab.n_tiles_total;
     if (nt > 0) {
@@ -902,12 +1001,14 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
             k_render_bwd<true><<<grid, 32 * RW, 0, st>>>(
                 tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
-                grad_out, (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
+                (const unsigned *)(ws + L.tile_list), hdr, (const unsigned char *)(ws + L.rec_f64), grad_out,
+                (float *)(ws + L.rec_mom), (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
         else
             k_render_bwd<false><<<grid, 32 * RW, 0, st>>>(
                 tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
-                grad_out, (float *)(ws + L.rec_mom), (unsigned *)&hdr->tile_ctr[1]);
+                (const unsigned *)(ws + L.tile_list), hdr, (const unsigned char *)(ws + L.rec_f64), grad_out,
+                (float *)(ws + L.rec_mom), (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
     }
     MG_PROF(MG_ST_CHAIN, st);
     long long wg = (n + 127) / 128;
@@ -915,6 +1016,7 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     k_chain_fused<<<gc, 128, 0, st>>>(n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
                                       L.cap_records, (const float4 *)(ws + L.rec_geo),
                                       (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_slice),
-                                      (const float *)(ws + L.rec_mom), slices, mean, quat, scale, alpha, f64_ratio,
+                                      (const float *)(ws + L.rec_mom), (const double *)(ws + L.rec_mom64), slices,
+                                      mean, quat, scale, alpha, f64_ratio,
                                       g_mean, g_quat, g_scale, g_alpha);
 }

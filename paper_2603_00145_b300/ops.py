@@ -75,7 +75,8 @@ class DeviceStacks:
         self.n = len(self.stacks)
         self.n_vox = sum(int(s.n_slices) * int(s.H) * int(s.W) for s in self.stacks)
         self.n_slices = sum(int(s.n_slices) for s in self.stacks)
-        self.n_tiles = sum(int(s.n_slices) * ((int(s.W) + 15) // 16) * ((int(s.H) + 15) // 16) for s in self.stacks)
+        T = L.MG_TILE_EDGE
+        self.n_tiles = sum(int(s.n_slices) * ((int(s.W) + T - 1) // T) * ((int(s.H) + T - 1) // T) for s in self.stacks)
 
     def set_poses(self, xform_all: torch.Tensor):
         """Overwrite the slice transforms in place (device [slices, 12], all

@@ -74,3 +74,17 @@ def test_host_entry_points(lib):
     assert lib.mg_adam_step(ctypes.byref(grp), 1, 0.9, 0.999, 1e-8, None, None, 0, None) == L.MG_ERR_INVALID_ARG
     assert lib.mg_status_string(L.MG_ERR_CAPACITY) == b"workspace capacity exceeded"
     assert lib.mg_version().startswith(b"mgauss")
+
+
+def test_tile_edge_agrees_with_the_header():
+    """The binding's and the oracle's tile edge are the header's MG_TILE_EDGE
+    (the tile size is part of the definition of the local set)."""
+    import re
+
+    import oracle
+    from paper_2603_00145_b300 import _lib
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "mgauss.h")).read()
+    edge = int(re.search(r"#define MG_TILE_EDGE (\d+)", hdr).group(1))
+    assert edge == _lib.MG_TILE_EDGE == oracle.TILE

@@ -19,7 +19,7 @@ import mg_synth as ms
 import oracle as orc
 
 FWHM2VAR = 1.0 / (8.0 * np.log(2.0))
-TILE = 16
+TILE = 8
 
 
 def _plane_quadratic(mu, q, s, xf, psf_var):
