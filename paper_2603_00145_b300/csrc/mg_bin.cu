@@ -898,7 +898,18 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
         unsigned r0 = slice_rs[k] + (c - chunk_base[k]) * MG_CHUNK;
         unsigned r1 = min(r0 + MG_CHUNK, slice_rs[k + 1]);
         const unsigned *hin = hist + (size_t)c * Tmax;
-        for (int t = lane; t < Tk; t += 32) cur[t] = tile_off[tb + t] + hin[t];
+        {
+            // eight independent load pairs in flight per lane
+            int t = lane;
+            for (; t + 7 * 32 < Tk; t += 8 * 32) {
+                unsigned o[8], h[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) o[u] = tile_off[tb + t + 32 * u], h[u] = hin[t + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cur[t + 32 * u] = o[u] + h[u];
+            }
+            for (; t < Tk; t += 32) cur[t] = tile_off[tb + t] + hin[t];
+        }
         __syncwarp();
         for (unsigned base = r0; base < r1; base += 32) {
             unsigned r = base + lane;
@@ -907,10 +918,15 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
             int wdt = rc.z - rc.x + 1;
             int area = have ? wdt * (rc.w - rc.y + 1) : 0;
             int maxa = __reduce_max_sync(0xffffffffu, area);
+            int jx = rc.x, jy = rc.y;  // the rectangle's tiles in row-major order
             for (int j = 0; j < maxa; ++j) {
                 bool act = j < area;
                 unsigned t = 0xffffffffu;
-                if (act) t = (unsigned)((rc.y + j / wdt) * TX + rc.x + j % wdt);
+                if (act) t = (unsigned)(jy * TX + jx);
+                if (++jx > (int)rc.z) {
+                    jx = rc.x;
+                    ++jy;
+                }
                 unsigned peers = __match_any_sync(0xffffffffu, t);
                 unsigned before = peers & lt;
                 unsigned pos = 0;

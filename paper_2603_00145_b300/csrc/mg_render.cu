@@ -166,17 +166,18 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
     float2 acc[MG_TILE];  // per row: (column 2 c4, column 2 c4 + 1)
 #pragma unroll
     for (int r = 0; r < MG_TILE; ++r) acc[r] = make_float2(0.f, 0.f);
+    // loads run two steps ahead: record ids two batches ahead, their
+    // geometry one batch ahead (a zero record past the end)
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 nc = make_int4(0, 0, 0, 0);
-    if (e0 + lane < e1) {
-        unsigned r = entries[e0 + lane];
-        if ((long long)r < cap_records) {
-            na = geo[r];
-            nb = geo2[r];
-            if (CELLS) nc = rcell[r];
-        }
+    unsigned er = (e0 + lane < e1) ? entries[e0 + lane] : 0xffffffffu;
+    if ((long long)er < cap_records) {
+        na = geo[er];
+        nb = geo2[er];
+        if (CELLS) nc = rcell[er];
     }
+    er = (e0 + 32 + lane < e1) ? entries[e0 + 32 + lane] : 0xffffffffu;
     for (unsigned base = e0; base < e1; base += 32) {
         {
             // stage this lane's record in the tile frame (a zero record past the end)
@@ -189,17 +190,14 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             if (CELLS) sgcw[lane] = nc;
         }
         __syncwarp();
-        const unsigned nxt = base + 32 + lane;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
         nb = make_float2(0.f, 0.f);
-        if (nxt < e1) {
-            unsigned r = entries[nxt];
-            if ((long long)r < cap_records) {
-                na = geo[r];
-                nb = geo2[r];
-                if (CELLS) nc = rcell[r];
-            }
+        if ((long long)er < cap_records) {
+            na = geo[er];
+            nb = geo2[er];
+            if (CELLS) nc = rcell[er];
         }
+        er = (base + 64 + lane < e1) ? entries[base + 64 + lane] : 0xffffffffu;
         const int m = (int)min(32u, e1 - base);
         for (int j8 = 0; j8 < m; j8 += 8) {
             const int j = j8 + grp;  // this group's record (a zero record past the end)
@@ -338,44 +336,40 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
 #pragma unroll
     for (int c = 0; c < MG_TILE / 2; ++c) xp[c] = make_float2((float)(2 * c) - TC + rz, (float)(2 * c + 1) - TC + rz);
     // the next batch of 32 records is fetched while the current one is swept
+    // loads run two steps ahead: record ids two batches ahead, their
+    // geometry one batch ahead
     unsigned nr = 0xffffffffu;
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 ncl = make_int4(0, 0, 0, 0);
     unsigned char nf = 0;
-    if (e0 + lane < e1) {
-        nr = entries[e0 + lane];
-        if ((long long)nr < cap_records) {
-            na = geo[nr];
-            nb = geo2[nr];
-            nf = f64[nr];
-            if (CELLS) ncl = rcell[nr];
-        } else {
-            nr = 0xffffffffu;
-        }
+    unsigned er = (e0 + lane < e1) ? entries[e0 + lane] : 0xffffffffu;
+    if ((long long)er < cap_records) {
+        nr = er;
+        na = geo[er];
+        nb = geo2[er];
+        nf = f64[er];
+        if (CELLS) ncl = rcell[er];
     }
+    er = (e0 + 32 + lane < e1) ? entries[e0 + 32 + lane] : 0xffffffffu;
     for (unsigned base = e0; base < e1; base += 32) {
         unsigned r = nr;
         const float4 a = na;
         const float2 b = nb;
         const int4 cl = ncl;
         const bool dbl = nf != 0;
-        const unsigned en = base + 32 + lane;
         nr = 0xffffffffu;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
         nb = make_float2(0.f, 0.f);
         nf = 0;
-        if (en < e1) {
-            nr = entries[en];
-            if ((long long)nr < cap_records) {
-                na = geo[nr];
-                nb = geo2[nr];
-                nf = f64[nr];
-                if (CELLS) ncl = rcell[nr];
-            } else {
-                nr = 0xffffffffu;
-            }
+        if ((long long)er < cap_records) {
+            nr = er;
+            na = geo[er];
+            nb = geo2[er];
+            nf = f64[er];
+            if (CELLS) ncl = rcell[er];
         }
+        er = (base + 64 + lane < e1) ? entries[base + 64 + lane] : 0xffffffffu;
         unsigned clo = 0u, chi = 0u;
         if (CELLS && r != 0xffffffffu && !cell_range(cl, cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
         const float A = a.z, B = a.w, C = b.x;
@@ -385,7 +379,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
         const float2 A2 = make_float2(A, A);
         float T0 = 0.f, T1 = 0.f, T2 = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
         float y = -TC;
-#pragma unroll 1
+#pragma unroll 2
         for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
             const float b1 = fmaf(B, y, tq.D);
             const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
@@ -450,7 +444,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
 }
 
 template <bool CELLS>
-__global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 6) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
+__global__ void __launch_bounds__(32 * RW, 4) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
