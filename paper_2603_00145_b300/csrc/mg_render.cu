@@ -270,16 +270,19 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
     const long long n_tiles = tab.n_tiles_total;
     const long long n_idle = hdr->n_idle, n_busy = hdr->n_busy;
     const long long gw = (long long)blockIdx.x * RW + w, nw = (long long)gridDim.x * RW;
-    for (long long i0 = gw * 32; i0 < n_idle; i0 += nw * 32) {
-        const unsigned tl = (i0 + lane < n_idle) ? tile_list[n_tiles - 1 - (i0 + lane)] : 0xffffffffu;
-        const int nu = (int)min(32LL, n_idle - i0);
-        for (int u = 0; u < nu; ++u) {
-            const unsigned t = __shfl_sync(0xffffffffu, tl, u);
-            const TileId d = tile_id(tab, (int)t);
-            const int px = d.tx * MG_TILE + (lane % MG_TILE), py = d.ty * MG_TILE + (lane / MG_TILE) * VPT;
-#pragma unroll
-            for (int v = 0; v < VPT; ++v)
-                if (px < d.W && py + v < d.H) out[d.pixbase + (long long)(py + v) * d.W + px] = 0.f;
+    for (long long i = gw * 32 + lane; i < n_idle; i += nw * 32) {
+        // one lane per empty tile: its rows as two float4 stores where aligned
+        const TileId d = tile_id(tab, (int)tile_list[n_tiles - 1 - i]);
+        const int px0 = d.tx * MG_TILE, py0 = d.ty * MG_TILE;
+        const int nx = min(MG_TILE, d.W - px0), ny = min(MG_TILE, d.H - py0);
+        for (int r = 0; r < ny; ++r) {
+            float *row = out + d.pixbase + (long long)(py0 + r) * d.W + px0;
+            if (nx == MG_TILE && ((uintptr_t)row & 15) == 0) {
+                ((float4 *)row)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ((float4 *)row)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for (int c = 0; c < nx; ++c) row[c] = 0.f;
+            }
         }
     }
     for (;;) {
