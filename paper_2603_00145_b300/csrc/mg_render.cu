@@ -556,25 +556,55 @@ __device__ __forceinline__ double c_rsqrt<double>(double x) { return 1.0 / sqrt(
 // P = R^T R_gauss the record geometry's only slice-dependent inputs,
 // delta d = -omega x d and delta P = -[omega]x P, so dL/domega =
 // g_d x d + axial part of (P gP^T) (dL/dP = gP).
-template <typename T, bool POSE = false>
-__device__ void geometry_adjoint(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
-                                 T gA, T gB2, T gC, T gpx, T gpy, T gamp, T gmu[3], T gq[4], T gs[3], T &galpha,
-                                 T *gpose = nullptr)
+// Per-Gaussian part of the record geometry: the rotation of q and the scales.
+template <typename T>
+struct GaussFrame {
+    T R[3][3], sc[3], isc[3];
+};
+template <typename T>
+__device__ __forceinline__ void gauss_frame(const float *q, const float *s, GaussFrame<T> &F)
 {
-    // forward recomputation (same formulas as the record pass)
-    T w = q[0], x = q[1], y = q[2], z = q[3];
-    T R[3][3];
-    R[0][0] = 1 - 2 * (y * y + z * z);
-    R[0][1] = 2 * (x * y - w * z);
-    R[0][2] = 2 * (x * z + w * y);
-    R[1][0] = 2 * (x * y + w * z);
-    R[1][1] = 1 - 2 * (x * x + z * z);
-    R[1][2] = 2 * (y * z - w * x);
-    R[2][0] = 2 * (x * z - w * y);
-    R[2][1] = 2 * (y * z + w * x);
-    R[2][2] = 1 - 2 * (x * x + y * y);
-    T sc[3] = {s[0], s[1], s[2]};
-    T isc[3] = {c_rcp<T>(sc[0]), c_rcp<T>(sc[1]), c_rcp<T>(sc[2])};
+    const T w = q[0], x = q[1], y = q[2], z = q[3];
+    F.R[0][0] = 1 - 2 * (y * y + z * z);
+    F.R[0][1] = 2 * (x * y - w * z);
+    F.R[0][2] = 2 * (x * z + w * y);
+    F.R[1][0] = 2 * (x * y + w * z);
+    F.R[1][1] = 1 - 2 * (x * x + z * z);
+    F.R[1][2] = 2 * (y * z - w * x);
+    F.R[2][0] = 2 * (x * z - w * y);
+    F.R[2][1] = 2 * (y * z + w * x);
+    F.R[2][2] = 1 - 2 * (x * x + y * y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        F.sc[c] = s[c];
+        F.isc[c] = c_rcp<T>(F.sc[c]);
+    }
+}
+
+// dL/dq from dL/dR (R the rotation of q; linear in dL/dR, so it may be
+// applied once to a sum over records).
+template <typename T>
+__device__ __forceinline__ void quat_adjoint(const float *q, const T gR[3][3], T gq[4])
+{
+    const T w = q[0], x = q[1], y = q[2], z = q[3];
+    gq[0] = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+    gq[1] = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] +
+                 w * gR[2][1] - 2 * x * gR[2][2]);
+    gq[2] = 2 * (-2 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] - w * gR[2][0] +
+                 z * gR[2][1] - 2 * y * gR[2][2]);
+    gq[3] = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2 * z * gR[1][1] + y * gR[1][2] +
+                 x * gR[2][0] + y * gR[2][1]);
+}
+
+// Adjoint of one record's geometry (the record pass's formulas recomputed):
+// dL/d(conic A, B2, C, centre px, py, amp) -> dL/d(mean, R, scale, alpha),
+// ADDED to gmu, gR, gs, galpha; POSE: also the record's share of the slice
+// pose gradient (dL/dt, dL/domega) written to gpose.
+template <typename T, bool POSE = false>
+__device__ __forceinline__ void record_adjoint(const GaussFrame<T> &F, const float *mu, float alpha, const SliceDev &S,
+                                               T gA, T gB2, T gC, T gpx, T gpy, T gamp, T gmu[3], T gR[3][3],
+                                               T gs[3], T &galpha, T *gpose = nullptr)
+{
     T Q[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Q[i] = (T)S.Q[i];
@@ -583,9 +613,9 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            P[a][c] = Q[a] * R[0][c] + Q[3 + a] * R[1][c] + Q[6 + a] * R[2][c];
-            g[a][c] = P[a][c] * isc[c];
-            Lm[a][c] = P[a][c] * sc[c];
+            P[a][c] = Q[a] * F.R[0][c] + Q[3 + a] * F.R[1][c] + Q[6 + a] * F.R[2][c];
+            g[a][c] = P[a][c] * F.isc[c];
+            Lm[a][c] = P[a][c] * F.sc[c];
         }
     T p0 = (T)mu[0] - (T)S.t[0], p1 = (T)mu[1] - (T)S.t[1], p2 = (T)mu[2] - (T)S.t[2];
     T w0 = Q[2] * p0 + Q[5] * p1 + Q[8] * p2;
@@ -631,7 +661,7 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
         gKuv = gNuv - 2 * gdK * K0uv;
         gamp = gamp * rm;
     }
-    galpha = gamp * rD * E;
+    galpha += gamp * rD * E;
     T ga = gamp * amp;
     T gD = (T)(-0.5) * ga * iD;
     T gw0 = -ga * wS;
@@ -647,7 +677,6 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
     T gHvw = -f * (2 * gKvv * Hvw + gKuv * Huw);
     gD += f * iD * (gKuu * Huw * Huw + gKuv * Huw * Hvw + gKvv * Hvw * Hvw);
     T gHww = sig2 * gD;
-    T gR[3][3];
     T M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // P gP^T (POSE)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -657,13 +686,13 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
         T gL0 = gSuw * Lm[2][c];
         T gL1 = gSvw * Lm[2][c];
         T gL2 = gSuw * Lm[0][c] + gSvw * Lm[1][c] + 2 * gSww * Lm[2][c];
-        T gP0 = gg0 * isc[c] + gL0 * sc[c];
-        T gP1 = gg1 * isc[c] + gL1 * sc[c];
-        T gP2 = gg2 * isc[c] + gL2 * sc[c];
-        gs[c] = -(gg0 * g[0][c] + gg1 * g[1][c] + gg2 * g[2][c]) * isc[c] +
-                (gL0 * P[0][c] + gL1 * P[1][c] + gL2 * P[2][c]);
+        T gP0 = gg0 * F.isc[c] + gL0 * F.sc[c];
+        T gP1 = gg1 * F.isc[c] + gL1 * F.sc[c];
+        T gP2 = gg2 * F.isc[c] + gL2 * F.sc[c];
+        gs[c] += -(gg0 * g[0][c] + gg1 * g[1][c] + gg2 * g[2][c]) * F.isc[c] +
+                 (gL0 * P[0][c] + gL1 * P[1][c] + gL2 * P[2][c]);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) gR[r][c] = Q[3 * r] * gP0 + Q[3 * r + 1] * gP1 + Q[3 * r + 2] * gP2;
+        for (int r = 0; r < 3; ++r) gR[r][c] += Q[3 * r] * gP0 + Q[3 * r + 1] * gP1 + Q[3 * r + 2] * gP2;
         if (POSE) {
 #pragma unroll
             for (int a2 = 0; a2 < 3; ++a2) {
@@ -673,24 +702,37 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
             }
         }
     }
+    T rmu[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) gmu[r] = Q[3 * r] * gdu + Q[3 * r + 1] * gdv + Q[3 * r + 2] * gw0;
+    for (int r = 0; r < 3; ++r) {
+        rmu[r] = Q[3 * r] * gdu + Q[3 * r + 1] * gdv + Q[3 * r + 2] * gw0;
+        gmu[r] += rmu[r];
+    }
     if (POSE) {
         const T u0 = Q[0] * p0 + Q[3] * p1 + Q[6] * p2, v0 = Q[1] * p0 + Q[4] * p1 + Q[7] * p2;
-        gpose[0] = -gmu[0];
-        gpose[1] = -gmu[1];
-        gpose[2] = -gmu[2];
+        gpose[0] = -rmu[0];
+        gpose[1] = -rmu[1];
+        gpose[2] = -rmu[2];
         gpose[3] = (gdv * w0 - gw0 * v0) + (M[2][1] - M[1][2]);
         gpose[4] = (gw0 * u0 - gdu * w0) + (M[0][2] - M[2][0]);
         gpose[5] = (gdu * v0 - gdv * u0) + (M[1][0] - M[0][1]);
     }
-    gq[0] = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
-    gq[1] = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] +
-                 w * gR[2][1] - 2 * x * gR[2][2]);
-    gq[2] = 2 * (-2 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] - w * gR[2][0] +
-                 z * gR[2][1] - 2 * y * gR[2][2]);
-    gq[3] = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2 * z * gR[1][1] + y * gR[1][2] +
-                 x * gR[2][0] + y * gR[2][1]);
+}
+
+// The whole adjoint of one record (the Gaussian's frame computed here).
+template <typename T, bool POSE = false>
+__device__ void geometry_adjoint(const float *mu, const float *q, const float *s, float alpha, const SliceDev &S,
+                                 T gA, T gB2, T gC, T gpx, T gpy, T gamp, T gmu[3], T gq[4], T gs[3], T &galpha,
+                                 T *gpose = nullptr)
+{
+    GaussFrame<T> F;
+    gauss_frame<T>(q, s, F);
+    T gR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    gmu[0] = gmu[1] = gmu[2] = 0;
+    gs[0] = gs[1] = gs[2] = 0;
+    galpha = 0;
+    record_adjoint<T, POSE>(F, mu, alpha, S, gA, gB2, gC, gpx, gpy, gamp, gmu, gR, gs, galpha, gpose);
+    quat_adjoint<T>(q, gR, gq);
 }
 
 __global__ void k_zero_mom(float4 *mom, const unsigned char *__restrict__ f64, double2 *mom64, const WsHeader *hdr,
@@ -772,8 +814,9 @@ __device__ __noinline__ void chain_gaussian_f64(const float *mu, const float *q,
                                                 const int *__restrict__ rslice, const double *__restrict__ mom64,
                                                 const SliceDev *__restrict__ slices, float o[11])
 {
-    double acc[11];
-    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
+    GaussFrame<double> F;
+    gauss_frame<double>(q, s, F);
+    double gmu[3] = {0, 0, 0}, gR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gs[3] = {0, 0, 0}, ga = 0;
     for (unsigned long long j = j0; j < j1; ++j) {
         const unsigned r = gmap[j];
         if ((long long)r >= cap_records) continue;
@@ -784,22 +827,25 @@ __device__ __noinline__ void chain_gaussian_f64(const float *mu, const float *q,
         const double la = (double)b.y * 0.6931471805599453;
         const double gpx = -la * (2.0 * A * m[1] + B2 * m[2]);
         const double gpy = -la * (B2 * m[1] + 2.0 * C * m[2]);
-        double dm[3], dq[4], ds[3], da;
-        geometry_adjoint<double>(mu, q, s, alpha, slices[rslice[r]], la * m[3], la * m[4], la * m[5], gpx, gpy, m[0],
-                                 dm, dq, ds, da);
-        for (int i = 0; i < 3; ++i) acc[i] += dm[i], acc[7 + i] += ds[i];
-        for (int i = 0; i < 4; ++i) acc[3 + i] += dq[i];
-        acc[10] += da;
+        record_adjoint<double>(F, mu, alpha, slices[rslice[r]], la * m[3], la * m[4], la * m[5], gpx, gpy, m[0], gmu,
+                               gR, gs, ga);
     }
-    for (int i = 0; i < 11; ++i) o[i] = (float)acc[i];
+    double gq[4];
+    quat_adjoint<double>(q, gR, gq);
+    for (int i = 0; i < 3; ++i) o[i] = (float)gmu[i], o[7 + i] = (float)gs[i];
+    for (int i = 0; i < 4; ++i) o[3 + i] = (float)gq[i];
+    o[10] = (float)ga;
 }
 
 // K6 fused: one thread per Gaussian visits its records in slice order (the
 // Gaussian-major list), turns each record's moments into dL/d(centre, conic,
-// amplitude), chains them through the record geometry (FP64 for
-// near-degenerate Gaussians) and sums in that fixed order; the Gaussian's
-// parameters are read once and nothing per record is written.
-__global__ void __launch_bounds__(128, 3) k_chain_fused(long long n, const unsigned *__restrict__ goff,
+// amplitude) and chains them through the record geometry (FP64 for
+// near-degenerate Gaussians), summing in that fixed order; the Gaussian's
+// frame (rotation, scales) is formed once, the records add to dL/d(mean,
+// R, scale, alpha), and dL/dq follows from dL/dR once. The next record's
+// data is loaded while the current one is chained. Nothing per record is
+// written.
+__global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsigned *__restrict__ goff,
                                                      const unsigned *__restrict__ gmap, long long cap_records,
                                                      const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
                                                      const int *__restrict__ rslice, const float *__restrict__ mom,
@@ -813,58 +859,74 @@ __global__ void __launch_bounds__(128, 3) k_chain_fused(long long n, const unsig
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
         unsigned long long j0 = goff[g], j1 = goff[g + 1];
         if ((long long)j1 > cap_records) j1 = cap_records;
+        if (j0 > j1) j0 = j1;
         float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
         float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
         float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
         const float al = alpha[g];
         const float mx = fmaxf(fmaxf(sc[0], sc[1]), sc[2]), mn = fminf(fminf(sc[0], sc[1]), sc[2]);
         const bool dbl = f64_ratio > 0.f && mx > f64_ratio * mn;
-        float acc[11];
-#pragma unroll
-        for (int i = 0; i < 11; ++i) acc[i] = 0.f;
+        float o[11];
         if (dbl) {
-            chain_gaussian_f64(mu, qv, sc, al, j0, j1, gmap, cap_records, geo, geo2, rslice, mom64, slices, acc);
-            j1 = j0;  // done
-        }
-        for (unsigned long long j = j0; j < j1; ++j) {
-            const unsigned r = gmap[j];
-            if ((long long)r >= cap_records) continue;
-            const float4 a = geo[r];
-            const float2 b = geo2[r];
-            const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
-            const SliceDev &Sd = slices[rslice[r]];
-            float o[11];
-            {
-                const float4 m0 = *(const float4 *)(mom + (size_t)r * 8);
-                const float2 m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
+            chain_gaussian_f64(mu, qv, sc, al, j0, j1, gmap, cap_records, geo, geo2, rslice, mom64, slices, o);
+        } else {
+            GaussFrame<float> F;
+            gauss_frame<float>(qv, sc, F);
+            float gmu[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            float gs[3] = {0.f, 0.f, 0.f}, ga = 0.f;
+            // the next record's data, loaded one record ahead
+            unsigned nr = j0 < j1 ? gmap[j0] : 0xffffffffu;
+            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nm0 = na;
+            float2 nb = make_float2(0.f, 0.f), nm1 = nb;
+            int ns = 0;
+            if ((long long)nr < cap_records) {
+                na = geo[nr];
+                nb = geo2[nr];
+                nm0 = *(const float4 *)(mom + (size_t)nr * 8);
+                nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
+                ns = rslice[nr];
+            }
+            for (unsigned long long j = j0; j < j1; ++j) {
+                const unsigned r = nr;
+                const float4 a = na, m0 = nm0;
+                const float2 b = nb, m1 = nm1;
+                const int sl = ns;
+                nr = j + 1 < j1 ? gmap[j + 1] : 0xffffffffu;
+                if ((long long)nr < cap_records) {
+                    na = geo[nr];
+                    nb = geo2[nr];
+                    nm0 = *(const float4 *)(mom + (size_t)nr * 8);
+                    nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
+                    ns = rslice[nr];
+                }
+                if ((long long)r >= cap_records) continue;
+                const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
                 const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
                 const float la = amp * 0.69314718055994531f;
-                const float gA = la * Sxx, gB2 = la * Sxy, gC = la * Syy;
                 const float gpx = -la * (2.f * A * Sx + B2 * Sy);
                 const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
-                float gm[3], gq[4], gs[3], ga;
-                geometry_adjoint<float>(mu, qv, sc, al, Sd, gA, gB2, gC, gpx, gpy, S0, gm, gq, gs, ga);
-                for (int i = 0; i < 3; ++i) o[i] = gm[i], o[7 + i] = gs[i];
-                for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
-                o[10] = ga;
+                record_adjoint<float>(F, mu, al, slices[sl], la * Sxx, la * Sxy, la * Syy, gpx, gpy, S0, gmu, gR, gs,
+                                      ga);
             }
-#pragma unroll
-            for (int i = 0; i < 11; ++i) acc[i] += o[i];
+            float gq[4];
+            quat_adjoint<float>(qv, gR, gq);
+            for (int i = 0; i < 3; ++i) o[i] = gmu[i], o[7 + i] = gs[i];
+            for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
+            o[10] = ga;
         }
         // gradient on the unit sphere: drop the component along q (the
         // normalisation q = q_raw/|q_raw| removes it, and the rotation formula
         // is only a rotation for unit q)
         const float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-        const float rad =
-            qq > 0.f ? (acc[3] * qv[0] + acc[4] * qv[1] + acc[5] * qv[2] + acc[6] * qv[3]) / qq : 0.f;
-        g_mean[3 * g] = acc[0];
-        g_mean[3 * g + 1] = acc[1];
-        g_mean[3 * g + 2] = acc[2];
-        for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = acc[3 + i] - rad * qv[i];
-        g_scale[3 * g] = acc[7];
-        g_scale[3 * g + 1] = acc[8];
-        g_scale[3 * g + 2] = acc[9];
-        g_alpha[g] = acc[10];
+        const float rad = qq > 0.f ? (o[3] * qv[0] + o[4] * qv[1] + o[5] * qv[2] + o[6] * qv[3]) / qq : 0.f;
+        g_mean[3 * g] = o[0];
+        g_mean[3 * g + 1] = o[1];
+        g_mean[3 * g + 2] = o[2];
+        for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = o[3 + i] - rad * qv[i];
+        g_scale[3 * g] = o[7];
+        g_scale[3 * g + 1] = o[8];
+        g_scale[3 * g + 2] = o[9];
+        g_alpha[g] = o[10];
     }
 }
 
