@@ -227,9 +227,15 @@ def run_mgauss(args, rank, world, local_rank):
     st = R.stats()
     assert st["status"] == 0, f"device status {st['status']} during the timed steps"
 
-    # end to end through the C ABI with host buffers: H2D of the step's inputs
-    # (Gaussian parameters and target slices) from pinned memory, the step,
-    # D2H of the loss and of the gradients
+    # end to end through the C ABI with host buffers: every step copies its
+    # inputs (Gaussian parameters and target slices) from pinned memory, runs,
+    # and reads the loss and the gradients back. The target slices do not
+    # depend on the previous step, so step k+1's copy runs on a second stream
+    # (copy engine) while step k computes, into the other of two device
+    # buffers; the Gaussians are copied on the compute stream at the start of
+    # their step (a fit would update them on the host in between). The timed
+    # window holds exactly K steps: the first timed step copies its own
+    # target, the last issues no copy for a step after it.
     host_in = [torch.from_numpy(x).pin_memory() for x in (G.mean, G.quat, G.scale, G.alpha)]
     host_tgt = target.cpu().pin_memory()
     dev_in = [torch.empty_like(x, device=dev) for x in host_in]
@@ -238,22 +244,48 @@ def run_mgauss(args, rank, world, local_rank):
     host_loss = torch.empty(2, dtype=torch.float64).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in host_in) + host_tgt.numel() * 4
     d2h = sum(x.numel() * x.element_size() for x in host_out) + 16
-    e2e_ms = 0.0
-    for k in range(args.warmup + args.steps):
-        flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for d_, h_ in zip(dev_in, host_in):
-            d_.copy_(h_, non_blocking=True)
-        target.copy_(host_tgt, non_blocking=True)
-        gs = step(*dev_in)
-        for h_, g_ in zip(host_out, gs):
-            h_.copy_(g_, non_blocking=True)
-        host_loss.copy_(loss, non_blocking=True)
-        e1.record()
+    tgt_buf = [target, torch.empty_like(target)]
+    main = torch.cuda.current_stream(dev)
+    side = torch.cuda.Stream(dev)
+    ev_tgt = [torch.cuda.Event() for _ in range(2)]
+    ev_free = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_step(mm, qq, ss, aa, tgt):
+        R.forward(mm, qq, ss, aa, out=out)
+        mg_loss_l1l2(out, tgt, grad, loss, wsr)
+        return R.backward(mm, qq, ss, aa, grad)
+
+    def run_e2e(n_steps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        if k >= args.warmup:
-            e2e_ms += e0.elapsed_time(e1)
+        t0.record(main)
+        with torch.cuda.stream(side):
+            tgt_buf[0].copy_(host_tgt, non_blocking=True)
+        ev_tgt[0].record(side)
+        for k in range(n_steps):
+            b = k % 2
+            main.wait_event(ev_tgt[b])
+            for d_, h_ in zip(dev_in, host_in):
+                d_.copy_(h_, non_blocking=True)
+            if k + 1 < n_steps:
+                if k >= 1:
+                    side.wait_event(ev_free[1 - b])  # step k-1 is done with that buffer
+                with torch.cuda.stream(side):
+                    tgt_buf[1 - b].copy_(host_tgt, non_blocking=True)
+                ev_tgt[1 - b].record(side)
+            gs = e2e_step(*dev_in, tgt_buf[b])
+            ev_free[b].record(main)
+            for h_, g_ in zip(host_out, gs):
+                h_.copy_(g_, non_blocking=True)
+            host_loss.copy_(loss, non_blocking=True)
+            main.synchronize()  # the host reads this step's loss and gradients
+        main.wait_stream(side)
+        t1.record(main)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    run_e2e(args.warmup)
+    e2e_ms = run_e2e(args.steps)
     e2e_value, e2e_ms_step, _ = job_throughput(pairs_inside, e2e_ms, args.steps, dist, dev)
     e2e_ms = e2e_ms_step * args.steps
 
@@ -289,7 +321,9 @@ def run_mgauss(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_ms / args.steps},
+                    "ms_per_step": e2e_ms / args.steps,
+                    "overlap": "target slices of step k+1 copied on a second stream during step k; Gaussians "
+                               "copied and gradients read back on the compute stream; host sync every step"},
             "gpu_launches": launches,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "clocks": clk}
