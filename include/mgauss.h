@@ -41,7 +41,7 @@
  *   R = [[1-2(yy+zz), 2(xy-wz), 2(xz+wy)], [2(xy+wz), 1-2(xx+zz), 2(yz-wx)],
  *        [2(xz-wy), 2(yz+wx), 1-2(xx+yy)]];  M_rc = R_rc s_c;
  *   Sigma_rc = (M_r0 M_c0 + M_r1 M_c1) + M_r2 M_c2;  a.b = (a0 b0 + a1 b1) + a2 b2;
- *   p = mu - t;  w0 = e_n.p, u0 = e_u.p, v0 = e_v.p;  (Sigma a)_r = Sigma_r . a;
+ *   p = mu - t;  w0 = (e_n.mu) - (e_n.t), u0 = e_u.p, v0 = e_v.p;  (Sigma a)_r = Sigma_r . a;
  *   Lww = e_n.(Sigma e_n), Luw = e_u.(Sigma e_n), Lvw = e_v.(Sigma e_n),
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v);  Sww = Lww + sig2;  K2 = K*K;
  *   sig2 = (float)(thickness^2 * 0.18033688011112042) (computed in double);

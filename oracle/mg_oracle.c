@@ -37,7 +37,7 @@
  *   R    = standard rotation of q (entries as in quat_rot_f below)
  *   M    = R diag(s);  Sigma_rc = (M_r0 M_c0 + M_r1 M_c1) + M_r2 M_c2
  *   p    = mu - t;  e_u, e_v, e_n = columns of Q;  a.b = (a0 b0 + a1 b1) + a2 b2
- *   w0 = e_n.p, u0 = e_u.p, v0 = e_v.p
+ *   w0 = (e_n.mu) - (e_n.t), u0 = e_u.p, v0 = e_v.p
  *   Lww = e_n.(Sigma e_n), Luw = e_u.(Sigma e_n), Lvw = e_v.(Sigma e_n),
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v), (Sigma a)_r = (S_r0 a0 + S_r1 a1) + S_r2 a2
  *   Sww = Lww + sig2;  K2 = K*K
@@ -165,7 +165,8 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     float ev[3] = {Q[1], Q[4], Q[7]};
     float en[3] = {Q[2], Q[5], Q[8]};
     float p[3] = {mu[0] - Q[9], mu[1] - Q[10], mu[2] - Q[11]};
-    float w0 = dot3f(en, p), u0 = dot3f(eu, p), v0 = dot3f(ev, p);
+    float wm = dot3f(en, mu), wt = dot3f(en, &Q[9]);
+    float w0 = wm - wt, u0 = dot3f(eu, p), v0 = dot3f(ev, p);
     float sn[3], su[3], sv[3];
     for (int r = 0; r < 3; ++r) {
         sn[r] = dot3f(Sg[r], en);

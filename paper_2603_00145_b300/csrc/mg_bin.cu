@@ -67,6 +67,7 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
             d.same_frame = same;
         }
     }
+    d.ent = __fadd_rn(__fadd_rn(__fmul_rn(d.Q[2], d.t[0]), __fmul_rn(d.Q[5], d.t[1])), __fmul_rn(d.Q[8], d.t[2]));
     out[k] = d;
 }
 
@@ -240,6 +241,8 @@ struct PredOut {
 // slice's rotation only (reused across the slices of a stack without motion).
 struct FrameTerms {
     float Lww;
+    float wmu;  // e_n . mu
+    float k2sww;  // K2 * (Lww + sig2) of the frame's profile (slab test)
     float Luw, Lvw, Luu, Lvv;
     bool full;  // Luw..Lvv computed
 };
@@ -251,6 +254,7 @@ __device__ __forceinline__ void frame_slab(const GaussPred &G, const float *Q, F
     float sn1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], en0, en1, en2);
     float sn2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], en0, en1, en2);
     f.Lww = dot3_rn(en0, en1, en2, sn0, sn1, sn2);
+    f.wmu = dot3_rn(en0, en1, en2, G.mu[0], G.mu[1], G.mu[2]);
     f.full = false;
 }
 
@@ -262,6 +266,8 @@ __device__ __forceinline__ void frame_full(const GaussPred &G, const float *Q, F
     float sn0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], en0, en1, en2);
     float sn1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], en0, en1, en2);
     float sn2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], en0, en1, en2);
+    f.Lww = dot3_rn(en0, en1, en2, sn0, sn1, sn2);
+    f.wmu = dot3_rn(en0, en1, en2, G.mu[0], G.mu[1], G.mu[2]);
     f.Luw = dot3_rn(eu0, eu1, eu2, sn0, sn1, sn2);
     f.Lvw = dot3_rn(ev0, ev1, ev2, sn0, sn1, sn2);
     float su0 = dot3_rn(G.Sg[0][0], G.Sg[0][1], G.Sg[0][2], eu0, eu1, eu2);
@@ -275,14 +281,12 @@ __device__ __forceinline__ void frame_full(const GaussPred &G, const float *Q, F
     f.full = true;
 }
 
-// The record-existence part of the predicate: the K-sigma slab test.
-__device__ __forceinline__ bool slab_test(const GaussPred &G, const SliceDev &S, float K2, float Lww)
+// The record-existence part of the predicate: the K-sigma slab test, with
+// the frame's e_n . mu and K2 * Sww (f.k2sww set by the caller).
+__device__ __forceinline__ bool slab_test(const FrameTerms &f, const SliceDev &S)
 {
-    const float *Q = S.Q;
-    float p0 = __fsub_rn(G.mu[0], S.t[0]), p1 = __fsub_rn(G.mu[1], S.t[1]), p2 = __fsub_rn(G.mu[2], S.t[2]);
-    float w0 = dot3_rn(Q[2], Q[5], Q[8], p0, p1, p2);
-    float Sww = __fadd_rn(Lww, S.sig2);
-    return __fmul_rn(w0, w0) <= __fmul_rn(K2, Sww);
+    const float w0 = __fsub_rn(f.wmu, S.ent);
+    return __fmul_rn(w0, w0) <= f.k2sww;
 }
 
 __device__ __forceinline__ void pixel_box(const SliceDev &S, float cu, float cv, float ru, float rv, PredOut &o);
@@ -294,7 +298,7 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
 {
     const float *Q = S.Q;
     float p0 = __fsub_rn(G.mu[0], S.t[0]), p1 = __fsub_rn(G.mu[1], S.t[1]), p2 = __fsub_rn(G.mu[2], S.t[2]);
-    float w0 = dot3_rn(Q[2], Q[5], Q[8], p0, p1, p2);
+    float w0 = __fsub_rn(f.wmu, S.ent);
     float Sww = __fadd_rn(f.Lww, S.sig2);
     float ww = __fmul_rn(w0, w0);
     if (!(ww <= __fmul_rn(K2, Sww))) return false;
@@ -519,8 +523,11 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
         const SliceDev &Sd = ssl[kk];
         bool ex = false;
         if (valid) {
-            if (!Sd.same_frame || kk == 0) frame_slab(G, Sd.Q, f);
-            ex = slab_test(G, Sd, K2, f.Lww);
+            if (!Sd.same_frame || kk == 0) {
+                frame_slab(G, Sd.Q, f);
+                f.k2sww = __fmul_rn(K2, __fadd_rn(f.Lww, Sd.sig2));
+            }
+            ex = slab_test(f, Sd);
         }
         unsigned bal = __ballot_sync(0xffffffffu, ex);
         if (lane == 0 && wg < NW) cnt[(long long)k * NW + wg] = __popc(bal);

@@ -24,6 +24,7 @@ struct SliceDev {
     float Q[9];  // rotation, row-major (columns e_u, e_v, e_n)
     float t[3];
     float sig2;  // FP32 profile variance (record predicate)
+    float ent;   // e_n . t in FP32 (record predicate: w0 = e_n . mu - e_n . t)
     float pu2, pv2;  // FP32 in-plane PSF variances along e_u, e_v (0: none)
     float dx, dy, hx, hy;  // spacing, 0.5*(W-1), 0.5*(H-1)
     int W, H, TX, TY;
