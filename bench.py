@@ -430,9 +430,17 @@ def run_recon(args, dev):
             "nrf": "hash grid 16x2, 2x64 ReLU, on at half, 2^20 voxels/iter",
             "forms": forms,
             "bf16_minus_fp32_psnr_db": b16["psnr_db_mean"] - f32["psnr_db_mean"],
+            # paired by seed (same NRF initialisation and batches); the standard
+            # error says how far the mean difference is resolved
+            "bf16_minus_fp32_psnr_db_sem": _paired_sem(b16["runs"], f32["runs"]),
             "bf16_speedup_vs_fp32": f32["seconds_mean"] / b16["seconds_mean"],
             "nrf_minus_gaussians_psnr_db": b16["psnr_db_mean"] - g32["psnr_db_mean"],
             "nrf_fwd_bwd_ms_per_2^20_points": nrf_ms}
+
+
+def _paired_sem(runs_a, runs_b):
+    d = [a["psnr_db"] - b["psnr_db"] for a, b in zip(runs_a, runs_b)]
+    return statistics.stdev(d) / len(d) ** 0.5 if len(d) > 1 else None
 
 
 def run_radius_sweep(args, dev):
@@ -570,7 +578,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--recon-iters", type=int, default=2000,
                     help="iterations of each timed full reconstruction (0: skip the reconstruction timing)")
-    ap.add_argument("--recon-seeds", type=int, default=3, help="runs (seeds) per reconstruction form")
+    ap.add_argument("--recon-seeds", type=int, default=5, help="runs (seeds) per reconstruction form")
     ap.add_argument("--radius-sweep", type=lambda v: [int(x) for x in v.split(",")], default=[],
                     help="block radii of the paper's cell-grid local set to fit and time, e.g. 3,4,5,6,7")
     args = ap.parse_args()
