@@ -375,7 +375,7 @@ mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &s
     long long S = 0, tiles = 0;
     for (const StackDesc &d : st) {
         S += d.n_slices;
-        tiles += (long long)d.n_slices * ((d.W + 15) / 16) * ((d.H + 15) / 16);
+        tiles += (long long)d.n_slices * ((d.W + MG_TILE - 1) / MG_TILE) * ((d.H + MG_TILE - 1) / MG_TILE);
     }
     if (tiles >= (1ll << 31) || S >= (1ll << 20)) return fail(MG_ERR_INVALID_ARG, "too many slices or tiles");
     mg_opts o = resolve_opts(opts, g->n, S);
@@ -586,7 +586,7 @@ mg_status mg_render_stats_get(const void *ws, size_t ws_bytes, mg_render_stats *
     for (size_t s = 0; s < tag.stack_key.size() / 8; ++s) {
         long long ns = (long long)tag.stack_key[8 * s], H = (long long)tag.stack_key[8 * s + 1],
                   W = (long long)tag.stack_key[8 * s + 2];
-        tiles += ns * ((W + 15) / 16) * ((H + 15) / 16);
+        tiles += ns * ((W + MG_TILE - 1) / MG_TILE) * ((H + MG_TILE - 1) / MG_TILE);
     }
     stats->tiles = tiles;
     stats->cap_records = tag.capr;

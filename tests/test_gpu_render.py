@@ -30,6 +30,8 @@ def _check_bins(G, stacks, R, K=3.0):
     rec = orc.records(G, stacks, K)
     st, (gid, sl, rect, toff, ent) = gpu_bins(R, G.n)
     assert st["status"] == 0
+    assert st["tiles"] == R.dev.n_tiles == sum(
+        s.n_slices * -(-s.W // orc.TILE) * -(-s.H // orc.TILE) for s in stacks)
     assert st["records"] == rec.n
     assert np.array_equal(gid.numpy(), rec.gid) and np.array_equal(sl.numpy(), rec.slice)
     assert np.array_equal(rect.numpy(), rec.rect)
