@@ -185,6 +185,22 @@ mg_status mg_render_fwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
                         void *ws, size_t ws_bytes, mg_stream_t stream);
 
 /*
+ * mg_render_fwd with the L1 + L2 slice loss of mg_loss_l1l2 fused into the
+ * writes of the evaluation kernel (Sec. 3.5.2 with the plain fit's loss; an
+ * addition of this library): out as mg_render_fwd; with r = out - target,
+ * grad[total voxels] (device FP32, may be NULL) receives
+ * dloss/dout = (sign(r) + 2 r) / n bit for bit as mg_loss_l1l2 computes it, and
+ * loss_out (device double[2]) = {mean|r| + mean r^2, sum r^2}, FP32 partials per
+ * 8x8 tile added in FP64 in tile order (deterministic; it differs from
+ * mg_loss_l1l2 only by the grouping of the FP32 partial sums, ~1e-8 relative). target: device FP32, same layout as out. The
+ * workspace is that of mg_render_fwd and serves mg_render_bwd afterwards.
+ * Errors: those of mg_render_fwd; target or loss_out NULL: MG_ERR_INVALID_ARG.
+ */
+mg_status mg_render_fwd_l1l2(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                             const float *target, float *out, float *grad, double *loss_out, void *ws, size_t ws_bytes,
+                             mg_stream_t stream);
+
+/*
  * Adjoint of mg_render_fwd (the paper trains by differentiable rendering,
  * Sec. 3.1): given grad_out = dL/d(out) (device, FP32, total voxels), writes
  * dL/dmean [n,3], dL/dquat [n,4] (derivative of the rotation formula above in

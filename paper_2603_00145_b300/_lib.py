@@ -68,6 +68,8 @@ SIGNATURES = {
                                         ctypes.POINTER(MgOpts)]),
     "mg_render_fwd": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                      ctypes.POINTER(MgOpts), c_p, c_p, c_sz, c_p]),
+    "mg_render_fwd_l1l2": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
+                                          ctypes.POINTER(MgOpts), c_p, c_p, c_p, c_p, c_p, c_sz, c_p]),
     "mg_render_bwd": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                      ctypes.POINTER(MgOpts), c_p, c_p, c_p, c_p, c_p, c_p, c_sz, c_p]),
     "mg_render_pose_grad": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,

@@ -225,6 +225,9 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.tile_cnt = take(sizeof(unsigned) * (size_t)tiles);
     L.tile_off = take(sizeof(unsigned) * (size_t)(tiles + 1));
     L.tile_list = take(sizeof(unsigned) * (size_t)tiles);
+    // loss partials: per tile and per block of 2048 tiles (fused forward), or per
+    // reduction block (no Gaussians)
+    L.tile_loss = take(16 * (size_t)(tiles + tiles / 2048 + 1 > 148 * 8 ? tiles + tiles / 2048 + 1 : 148 * 8));
     L.entries = take(sizeof(unsigned) * (size_t)L.cap_entries);
     L.gmap = take(sizeof(unsigned) * (size_t)L.cap_records);
     L.rec_grad = take(32 * (size_t)L.cap_records);  // slice-pose shares: 2 float4 per record
@@ -365,7 +368,8 @@ bool same_tag(const FwdTag &a, const FwdTag &b)
 }
 
 mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &st, const StackIn &in,
-                          const mg_opts *opts, float *out, void *ws, size_t ws_bytes, cudaStream_t stream)
+                          const mg_opts *opts, float *out, void *ws, size_t ws_bytes, cudaStream_t stream,
+                          const float *target = nullptr, float *grad = nullptr, double *loss_out = nullptr)
 {
     std::string why;
     if (!valid_gauss(g, why)) return fail(MG_ERR_INVALID_ARG, why);
@@ -393,12 +397,15 @@ mg_status render_fwd_impl(const mg_gaussians *g, const std::vector<StackDesc> &s
     if (g->n > 0) {
         mg_launch_bin(L, w, slices, tab, g->mean, g->quat, g->scale, g->alpha, g->n, o.cutoff_k, o.f64_ratio, cg,
                       stream);
-        mg_launch_render_fwd(L, w, tab, slices, cg, out, stream);
+        mg_launch_render_fwd(L, w, tab, slices, cg, out, stream, target, grad, loss_out, tab.pix_base[tab.n_stacks]);
     } else {
         // no Gaussians: empty bins and a zero output
         cudaMemsetAsync(w + L.hdr, 0, sizeof(WsHeader), stream);
         cudaMemsetAsync(w + L.tile_off, 0, sizeof(unsigned) * (size_t)(tiles + 1), stream);
         cudaMemsetAsync(out, 0, sizeof(float) * (size_t)tab.pix_base[tab.n_stacks], stream);
+        if (target)
+            mg_launch_loss_l1l2(out, target, tab.pix_base[tab.n_stacks], grad, loss_out, (double *)(w + L.tile_loss),
+                                stream);
     }
     mg_status s = check_cuda("mg_render_fwd");
     if (s != MG_OK) return s;
@@ -467,6 +474,17 @@ mg_status mg_render_fwd(const mg_gaussians *g, const mg_stack *stacks, int n_sta
     if (st.empty()) return fail(MG_ERR_INVALID_ARG, "stacks is NULL or n_stacks not in [1, 32]");
     StackIn in = make_stack_in(st);
     return render_fwd_impl(g, st, in, opts, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+mg_status mg_render_fwd_l1l2(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
+                             const float *target, float *out, float *grad, double *loss_out, void *ws, size_t ws_bytes,
+                             mg_stream_t stream)
+{
+    std::vector<StackDesc> st = to_desc(stacks, n_stacks);
+    if (st.empty()) return fail(MG_ERR_INVALID_ARG, "stacks is NULL or n_stacks not in [1, 32]");
+    if (!target || !loss_out) return fail(MG_ERR_INVALID_ARG, "mg_render_fwd_l1l2: target and loss_out are required");
+    StackIn in = make_stack_in(st);
+    return render_fwd_impl(g, st, in, opts, out, ws, ws_bytes, (cudaStream_t)stream, target, grad, loss_out);
 }
 
 mg_status mg_render_bwd(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,

@@ -148,7 +148,7 @@ struct Records {
 // size query.
 struct WsLayout {
     size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom, rec_thr;
-    size_t chunk_base, hist, tile_cnt, tile_off, tile_list, entries, gcnt, bits, gmap, rec_grad, rec_cell, rec_f64,
+    size_t chunk_base, hist, tile_cnt, tile_off, tile_list, tile_loss, entries, gcnt, bits, gmap, rec_grad, rec_cell, rec_f64,
         rec_mom64, total;
     long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
@@ -213,7 +213,8 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
                    const float *quat, const float *scale, const float *alpha, long long n, float K, float f64_ratio,
                    const CellGrid &cg, cudaStream_t st);
 void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, const SliceDev *slices,
-                          const CellGrid &cg, float *out, cudaStream_t st);
+                          const CellGrid &cg, float *out, cudaStream_t st, const float *target = nullptr,
+                          float *grad = nullptr, double *loss_out = nullptr, long long n_vox = 0);
 void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab,
                           const CellGrid &cg, const float *grad_out, const float *mean, const float *quat,
                           const float *scale, const float *alpha, long long n, float f64_ratio, float *g_mean,

@@ -135,13 +135,33 @@ struct FwdStage {
 // of its two columns.
 // CELLS: the paper's cell-grid local set; each (record, voxel) term is kept
 // only when the voxel is a member (mgauss.h, MG_LOCAL_CELLS).
-template <bool CELLS>
+// The L1 + L2 slice loss of one voxel (mg_loss_l1l2): r = pred - target,
+// dloss/dpred = (sign(r) + 2 r) / n; adds |r| and r^2 to the FP32 partials.
+__device__ __forceinline__ void l1l2_voxel(float pred, float tgt, float inv_n, float *grad, float &f1, float &f2)
+{
+    const float r = pred - tgt;
+    f1 += fabsf(r);
+    f2 = fmaf(r, r, f2);
+    if (grad) *grad = (copysignf(r != 0.f ? 1.f : 0.f, r) + 2.f * r) * inv_n;
+}
+
+// The fused loss of the forward (LOSS): per-voxel gradient and the tile's
+// FP32 partials of |r| and r^2, written in FP64 to the tile's slot.
+struct FwdLoss {
+    const float *target;
+    float *grad;
+    double2 *tile_part;
+    float inv_n;
+};
+
+template <bool CELLS, bool LOSS>
 __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane, FwdStage &sw, int4 *sgcw,
                                          unsigned *srelw, const unsigned *__restrict__ tile_off,
                                          const unsigned *__restrict__ entries, long long cap_entries,
                                          long long cap_records, const float4 *__restrict__ geo,
                                          const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
-                                         const CellGrid &cg, const int4 *__restrict__ rcell, float *__restrict__ out)
+                                         const CellGrid &cg, const int4 *__restrict__ rcell, float *__restrict__ out,
+                                         const FwdLoss &ls)
 {
     const TileId d = tile_id(tab, t);
     const int grp = lane >> 2, c4 = lane & 3;
@@ -241,10 +261,28 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
         }
     }
     const int px = d.tx * MG_TILE + 2 * c4, py = d.ty * MG_TILE + grp;
+    float f1 = 0.f, f2 = 0.f;
     if (py < d.H) {
-        float *row = out + d.pixbase + (long long)py * d.W;
-        if (px < d.W) row[px] = acc[0].x;
-        if (px + 1 < d.W) row[px + 1] = acc[0].y;
+        const long long o = d.pixbase + (long long)py * d.W;
+        float *row = out + o;
+        if (px < d.W) {
+            row[px] = acc[0].x;
+            if (LOSS) l1l2_voxel(acc[0].x, ls.target[o + px], ls.inv_n, ls.grad ? ls.grad + o + px : nullptr, f1, f2);
+        }
+        if (px + 1 < d.W) {
+            row[px + 1] = acc[0].y;
+            if (LOSS)
+                l1l2_voxel(acc[0].y, ls.target[o + px + 1], ls.inv_n, ls.grad ? ls.grad + o + px + 1 : nullptr, f1, f2);
+        }
+    }
+    if (LOSS) {
+        // the tile's partials by a fixed shuffle tree
+#pragma unroll
+        for (int k = 16; k > 0; k >>= 1) {
+            f1 += __shfl_xor_sync(0xffffffffu, f1, k);
+            f2 += __shfl_xor_sync(0xffffffffu, f2, k);
+        }
+        if (lane == 0) ls.tile_part[t] = make_double2((double)f1, (double)f2);
     }
 }
 
@@ -252,7 +290,9 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
 // warp and step, no dependent loads); then persistent warps pull the tiles
 // with records from a counter (tiles carry very different numbers of
 // records).
-template <bool CELLS>
+// LOSS: the L1 + L2 slice loss and its gradient fused into the writes (the
+// empty tiles' zeros included), one FP64 partial pair per tile.
+template <bool CELLS, bool LOSS>
 __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
@@ -261,7 +301,7 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
                                                           const int4 *__restrict__ rcell,
                                                           const unsigned *__restrict__ tile_list,
                                                           const WsHeader *__restrict__ hdr, float *__restrict__ out,
-                                                          unsigned *counter)
+                                                          FwdLoss ls, unsigned *counter)
 {
     __shared__ FwdStage sg[RW];
     __shared__ int4 sgc[CELLS ? RW : 1][32];
@@ -275,23 +315,48 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
         const TileId d = tile_id(tab, (int)tile_list[n_tiles - 1 - i]);
         const int px0 = d.tx * MG_TILE, py0 = d.ty * MG_TILE;
         const int nx = min(MG_TILE, d.W - px0), ny = min(MG_TILE, d.H - py0);
+        float f1 = 0.f, f2 = 0.f;
         for (int r = 0; r < ny; ++r) {
-            float *row = out + d.pixbase + (long long)(py0 + r) * d.W + px0;
+            const long long o = d.pixbase + (long long)(py0 + r) * d.W + px0;
+            float *row = out + o;
             if (nx == MG_TILE && ((uintptr_t)row & 15) == 0) {
                 ((float4 *)row)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
                 ((float4 *)row)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
                 for (int c = 0; c < nx; ++c) row[c] = 0.f;
             }
+            if (LOSS) {
+                float r1 = 0.f, r2 = 0.f;  // row partials, then added to the tile's
+                float gv[MG_TILE];
+                if (nx == MG_TILE && ((uintptr_t)row & 15) == 0) {
+                    const float4 t0 = ((const float4 *)(ls.target + o))[0], t1 = ((const float4 *)(ls.target + o))[1];
+                    const float tv[MG_TILE] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                    for (int c = 0; c < MG_TILE; ++c) l1l2_voxel(0.f, tv[c], ls.inv_n, &gv[c], r1, r2);
+                    if (ls.grad && ((uintptr_t)(ls.grad + o) & 15) == 0) {
+                        ((float4 *)(ls.grad + o))[0] = make_float4(gv[0], gv[1], gv[2], gv[3]);
+                        ((float4 *)(ls.grad + o))[1] = make_float4(gv[4], gv[5], gv[6], gv[7]);
+                    } else if (ls.grad) {
+#pragma unroll
+                        for (int c = 0; c < MG_TILE; ++c) ls.grad[o + c] = gv[c];
+                    }
+                } else {
+                    for (int c = 0; c < nx; ++c)
+                        l1l2_voxel(0.f, ls.target[o + c], ls.inv_n, ls.grad ? ls.grad + o + c : nullptr, r1, r2);
+                }
+                f1 += r1;
+                f2 += r2;
+            }
         }
+        if (LOSS) ls.tile_part[tile_list[n_tiles - 1 - i]] = make_double2((double)f1, (double)f2);
     }
     for (;;) {
         unsigned i = 0;
         if (lane == 0) i = atomicAdd(counter, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
         if ((long long)i >= n_busy) break;
-        fwd_tile<CELLS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off,
-                        entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, out);
+        fwd_tile<CELLS, LOSS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off,
+                              entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, out, ls);
         __syncwarp();
     }
 }
@@ -985,28 +1050,114 @@ static int resident_grid(const void *kern, int threads)
     return sms * (per > 0 ? per : 1);
 }
 
+// The per-tile loss partials summed in two fixed-order levels (FP64): block
+// b adds the tiles of its contiguous range (thread i: tiles i, i + 256, ...
+// of the range, then a fixed shuffle tree), one block adds the block sums
+// in order; the same bits on every run.
+constexpr int LT_NT = 256;
+
+__device__ __forceinline__ void lt_block_sum(double &s1, double &s2, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = s1;
+        sh[LT_NT / 32 + (threadIdx.x >> 5)] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s1 = s2 = 0.0;
+        for (int k = 0; k < LT_NT / 32; ++k) s1 += sh[k], s2 += sh[LT_NT / 32 + k];
+    }
+}
+
+__global__ void __launch_bounds__(LT_NT) k_loss_tiles_part(const double2 *__restrict__ part, long long n, long long per,
+                                                           double2 *__restrict__ bsum)
+{
+    __shared__ double sh[2 * LT_NT / 32];
+    const long long i0 = (long long)blockIdx.x * per, i1 = min(n, i0 + per);
+    double s1 = 0.0, s2 = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += LT_NT) {
+        const double2 p = part[i];
+        s1 += p.x;
+        s2 += p.y;
+    }
+    lt_block_sum(s1, s2, sh);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = make_double2(s1, s2);
+}
+
+__global__ void __launch_bounds__(LT_NT) k_loss_tiles_final(const double2 *__restrict__ bsum, int nb, double inv_n,
+                                                            double *__restrict__ out)
+{
+    __shared__ double sh[2 * LT_NT / 32];
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < nb; i += LT_NT) {
+        s1 += bsum[i].x;
+        s2 += bsum[i].y;
+    }
+    lt_block_sum(s1, s2, sh);
+    if (threadIdx.x == 0) {
+        out[0] = s1 * inv_n + s2 * inv_n;
+        out[1] = s2;
+    }
+}
+
+template <bool CELLS, bool LOSS>
+static void launch_fwd(const WsLayout &L, char *ws, const StackTable &tab, const SliceDev *slices, const CellGrid &cg,
+                       float *out, const FwdLoss &ls, cudaStream_t st)
+{
+    WsHeader *hdr = (WsHeader *)(ws + L.hdr);
+    int grid = resident_grid((const void *)k_render_fwd<CELLS, LOSS>, 32 * RW);
+    const int nt = tab.n_tiles_total;
+    if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
+    k_render_fwd<CELLS, LOSS><<<grid, 32 * RW, 0, st>>>(
+        tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
+        (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg,
+        cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr, (const unsigned *)(ws + L.tile_list), hdr, out, ls,
+        &hdr->tile_ctr[0]);
+}
+
+// target != NULL: the L1 + L2 slice loss of mg_loss_l1l2 fused into the
+// forward (grad may be NULL), loss_out = {loss, sum r^2} (device doubles)
 void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, const SliceDev *slices,
-                          const CellGrid &cg, float *out, cudaStream_t st)
+                          const CellGrid &cg, float *out, cudaStream_t st, const float *target, float *grad,
+                          double *loss_out, long long n_vox)
 {
     int nt = tab.n_tiles_total;
     if (nt <= 0) return;
     WsHeader *hdr = (WsHeader *)(ws + L.hdr);
     cudaMemsetAsync(&hdr->tile_ctr[0], 0, sizeof(unsigned), st);
-    MG_PROF(MG_ST_RENDER_FWD, st);
-    const void *kern = cg.on ? (const void *)k_render_fwd<true> : (const void *)k_render_fwd<false>;
-    int grid = resident_grid(kern, 32 * RW);
-    if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
-    const int4 *rcell = cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr;
-    if (cg.on)
-        k_render_fwd<true><<<grid, 32 * RW, 0, st>>>(
-            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
-            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
-            (const unsigned *)(ws + L.tile_list), hdr, out, &hdr->tile_ctr[0]);
-    else
-        k_render_fwd<false><<<grid, 32 * RW, 0, st>>>(
-            tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
-            (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
-            (const unsigned *)(ws + L.tile_list), hdr, out, &hdr->tile_ctr[0]);
+    FwdLoss ls;
+    ls.target = target;
+    ls.grad = grad;
+    ls.tile_part = (double2 *)(ws + L.tile_loss);
+    ls.inv_n = n_vox > 0 ? (float)(1.0 / (double)n_vox) : 0.f;
+    {
+        MG_PROF(MG_ST_RENDER_FWD, st);
+        if (target) {
+            if (cg.on)
+                launch_fwd<true, true>(L, ws, tab, slices, cg, out, ls, st);
+            else
+                launch_fwd<false, true>(L, ws, tab, slices, cg, out, ls, st);
+        } else {
+            if (cg.on)
+                launch_fwd<true, false>(L, ws, tab, slices, cg, out, ls, st);
+            else
+                launch_fwd<false, false>(L, ws, tab, slices, cg, out, ls, st);
+        }
+    }
+    if (target) {
+        MG_PROF(MG_ST_LOSS, st);
+        // block sums after the tile partials (the workspace slot holds both)
+        const long long per = 8 * LT_NT;
+        const int nb = (int)((nt + per - 1) / per);
+        double2 *bsum = ls.tile_part + nt;
+        k_loss_tiles_part<<<nb, LT_NT, 0, st>>>(ls.tile_part, nt, per, bsum);
+        k_loss_tiles_final<<<1, LT_NT, 0, st>>>(bsum, nb, n_vox > 0 ? 1.0 / (double)n_vox : 0.0, loss_out);
+    }
 }
 
 // Slice-pose gradient from the moments the last backward left in the workspace.

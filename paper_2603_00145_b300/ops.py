@@ -108,6 +108,23 @@ def mg_render_fwd(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts
     L.check(st, "mg_render_fwd")
 
 
+def mg_render_fwd_l1l2(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, target, out, grad, loss_out,
+                       ws, stream=None):
+    """mg_render_fwd with the L1 + L2 slice loss fused (loss_out: device
+    float64[2] = {loss, sum r^2}; grad may be None)."""
+    g = _gauss(mean, quat, scale, alpha)
+    _dev(target, "target", numel=stacks.n_vox)
+    _dev(out, "out", numel=stacks.n_vox)
+    if grad is not None:
+        _dev(grad, "grad", numel=stacks.n_vox)
+    _dev(loss_out, "loss_out", dtype=torch.float64, numel=2)
+    _dev(ws, "ws", dtype=torch.uint8)
+    st = L.lib().mg_render_fwd_l1l2(ctypes.byref(g), stacks.arr, stacks.n, ctypes.byref(opts), target.data_ptr(),
+                                    out.data_ptr(), grad.data_ptr() if grad is not None else None,
+                                    loss_out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    L.check(st, "mg_render_fwd_l1l2")
+
+
 def mg_render_bwd(mean, quat, scale, alpha, stacks: DeviceStacks, opts: L.MgOpts, grad_out, g_mean, g_quat,
                   g_scale, g_alpha, ws, stream=None, raise_on_error=True) -> int:
     g = _gauss(mean, quat, scale, alpha)
@@ -362,6 +379,26 @@ class SliceRenderer:
             self.caps = (max(self.caps[0], int(st["records"] * 1.25) + 1),
                          max(self.caps[1], int(st["entries"] * 1.25) + 1))
         raise L.MgError(L.MG_ERR_CAPACITY, "mg_render_fwd (after growing the workspace)")
+
+    def forward_l1l2(self, mean, quat, scale, alpha, target, out, grad, loss_out, stream=None):
+        """forward() with the L1 + L2 slice loss and its gradient fused into
+        the evaluation kernel (same growth on capacity overflow)."""
+        n = int(mean.shape[0])
+        for _ in range(4):
+            self._ensure(n)
+            mg_render_fwd_l1l2(mean, quat, scale, alpha, self.dev, self.opts(), target, out, grad, loss_out, self.ws,
+                               stream)
+            if not self.check:
+                return out
+            st = mg_render_stats_get(self.ws, stream)
+            self.last_stats = st
+            if st["status"] == L.MG_OK:
+                return out
+            if st["status"] == L.MG_ERR_NOT_FINITE:
+                raise L.MgError(L.MG_ERR_NOT_FINITE, "mg_render_fwd_l1l2")
+            self.caps = (max(self.caps[0], int(st["records"] * 1.25) + 1),
+                         max(self.caps[1], int(st["entries"] * 1.25) + 1))
+        raise L.MgError(L.MG_ERR_CAPACITY, "mg_render_fwd_l1l2 (after growing the workspace)")
 
     def stats(self, stream=None) -> dict:
         return mg_render_stats_get(self.ws, stream)

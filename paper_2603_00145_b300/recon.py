@@ -181,7 +181,14 @@ class _Trainer:
         with torch.no_grad():
             ops.mg_params_fwd(m.mean_c, m.quat, m.log_scale, self.centre, self.half, cfg.lambda_r, self.mean, self.q,
                               self.s, self.aniso, self.ws_p)
-            pred = self.R.forward(self.mean, self.q, self.s, m.alpha, out=self.pred)
+            fused = cfg.loss != "paper" and self.nrf is None
+            if fused:
+                # the L1 + L2 loss and its gradient fused into the forward's writes
+                grad = torch.empty_like(self.pred)
+                out = torch.empty(2, dtype=torch.float64, device=self.device)
+                pred = self.R.forward_l1l2(self.mean, self.q, self.s, m.alpha, self.target, self.pred, grad, out)
+            else:
+                pred = self.R.forward(self.mean, self.q, self.s, m.alpha, out=self.pred)
             if self.nrf is not None:
                 n_vox = self.target.numel()
                 idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
@@ -190,11 +197,12 @@ class _Trainer:
                 ops.mg_nrf_fwd(self.nrf, xyz, r, self.nrf_params, self.nrf_table)
                 pred.index_add_(0, idx, r)
             # the loss (FP64 sums) and its gradient dL/dpred in one kernel
-            grad = torch.empty_like(pred)
             if cfg.loss == "paper":
+                grad = torch.empty_like(pred)
                 out = torch.empty(3, dtype=torch.float64, device=pred.device)
                 ops.mg_loss_recon(pred, self.target, self.R.dev, cfg.lambda_ssim, grad, out, self.ws)
-            else:
+            elif not fused:
+                grad = torch.empty_like(pred)
                 out = torch.empty(2, dtype=torch.float64, device=pred.device)
                 ops.mg_loss_l1l2(pred, self.target, grad, out, self.ws)
             if self.nrf is not None:
