@@ -46,12 +46,12 @@
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v);  Sww = Lww + sig2;  K2 = K*K;
  *   sig2 = (float)(thickness^2 * 0.18033688011112042) (computed in double);
  *   the record exists iff  w0*w0 <= K2*Sww  (the K-sigma slab test); its pixel box:
- *   r2 = max(K2 - (w0*w0)/Sww, 0);  Cuu = max(Luu - (Luw*Luw)/Sww, 0) + pu2;
- *   Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0) + pv2;  cu = u0 - (Luw*w0)/Sww;  cv = v0 - (Lvw*w0)/Sww;
+ *   iSww = 1/Sww;  r2 = max(K2 - (w0*w0)*iSww, 0);  Cuu = max(Luu - (Luw*Luw)*iSww, 0) + pu2;
+ *   Cvv = max(Lvv - (Lvw*Lvw)*iSww, 0) + pv2;  cu = u0 - (Luw*w0)*iSww;  cv = v0 - (Lvw*w0)*iSww;
  *   pu2 = (float)(psf_u^2 * 0.18033688011112042), pv2 likewise (computed in double);
  *   ru = sqrt(r2*Cuu), rv = sqrt(r2*Cvv);  hx = 0.5*(W-1), hy = 0.5*(H-1);
- *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx),
- *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy);
+ *   idx = 1/dx, idy = 1/dy;  il = ceil((cu-ru)*idx + hx), ih = floor((cu+ru)*idx + hx),
+ *   jl = ceil((cv-rv)*idy + hy), jh = floor((cv+rv)*idy + hy);
  *   the box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0 (NaN: empty);
  *   a non-empty box is clamped (il,jl up to 0, ih,jh down to W-1,H-1) and lists the
  *   tiles [il/8, ih/8] x [jl/8, jh/8]; an empty box lists no tile (stored as the

@@ -42,12 +42,13 @@
  *   Luu = e_u.(Sigma e_u), Lvv = e_v.(Sigma e_v), (Sigma a)_r = (S_r0 a0 + S_r1 a1) + S_r2 a2
  *   Sww = Lww + sig2;  K2 = K*K
  *   the record exists iff  w0*w0 <= K2*Sww  (the K-sigma slab test)
- *   r2 = max(K2 - (w0*w0)/Sww, 0)
- *   Cuu = max(Luu - (Luw*Luw)/Sww, 0) + pu2,  Cvv = max(Lvv - (Lvw*Lvw)/Sww, 0) + pv2
- *   cu = u0 - (Luw*w0)/Sww,  cv = v0 - (Lvw*w0)/Sww
+ *   iSww = 1/Sww;  r2 = max(K2 - (w0*w0)*iSww, 0)
+ *   Cuu = max(Luu - (Luw*Luw)*iSww, 0) + pu2,  Cvv = max(Lvv - (Lvw*Lvw)*iSww, 0) + pv2
+ *   cu = u0 - (Luw*w0)*iSww,  cv = v0 - (Lvw*w0)*iSww
  *   ru = sqrt(r2*Cuu),  rv = sqrt(r2*Cvv)
- *   il = ceil((cu-ru)/dx + hx), ih = floor((cu+ru)/dx + hx), hx = 0.5*(W-1)
- *   jl = ceil((cv-rv)/dy + hy), jh = floor((cv+rv)/dy + hy), hy = 0.5*(H-1)
+ *   idx = 1/dx, idy = 1/dy
+ *   il = ceil((cu-ru)*idx + hx), ih = floor((cu+ru)*idx + hx), hx = 0.5*(W-1)
+ *   jl = ceil((cv-rv)*idy + hy), jh = floor((cv+rv)*idy + hy), hy = 0.5*(H-1)
  *   the pixel box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1,
  *   jh>=0 (false for NaN); a non-empty box has il,jl clamped up to 0 and ih,jh
  *   down to W-1,H-1 and lists the tiles [il/8, ih/8] x [jl/8, jh/8]
@@ -180,24 +181,26 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     float K2 = K * K;
     float ww = w0 * w0;
     if (!(ww <= K2 * Sww)) return 0;
-    float r2 = K2 - ww / Sww;
+    float iSww = 1.0f / Sww;
+    float r2 = K2 - ww * iSww;
     if (r2 < 0.0f) r2 = 0.0f;
     float pu2 = (float)((double)sl->pu * (double)sl->pu * OR_FWHM2VAR);
     float pv2 = (float)((double)sl->pv * (double)sl->pv * OR_FWHM2VAR);
-    float Cuu = Luu - (Luw * Luw) / Sww;
+    float Cuu = Luu - (Luw * Luw) * iSww;
     if (Cuu < 0.0f) Cuu = 0.0f;
     Cuu = Cuu + pu2;
-    float Cvv = Lvv - (Lvw * Lvw) / Sww;
+    float Cvv = Lvv - (Lvw * Lvw) * iSww;
     if (Cvv < 0.0f) Cvv = 0.0f;
     Cvv = Cvv + pv2;
-    float cu = u0 - (Luw * w0) / Sww;
-    float cv = v0 - (Lvw * w0) / Sww;
+    float cu = u0 - (Luw * w0) * iSww;
+    float cv = v0 - (Lvw * w0) * iSww;
     float ru = sqrtf(r2 * Cuu), rv = sqrtf(r2 * Cvv);
     float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
-    float il = ceilf((cu - ru) / sl->dx + hx);
-    float ih = floorf((cu + ru) / sl->dx + hx);
-    float jl = ceilf((cv - rv) / sl->dy + hy);
-    float jh = floorf((cv + rv) / sl->dy + hy);
+    float idx = 1.0f / sl->dx, idy = 1.0f / sl->dy;
+    float il = ceilf((cu - ru) * idx + hx);
+    float ih = floorf((cu + ru) * idx + hx);
+    float jl = ceilf((cv - rv) * idy + hy);
+    float jh = floorf((cv + rv) * idy + hy);
     float Wm1 = (float)(sl->W - 1), Hm1 = (float)(sl->H - 1);
     if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
         rect[0] = 1; rect[1] = 1; rect[2] = 0; rect[3] = 0; /* record without tiles */
@@ -306,10 +309,11 @@ static int record_predicate_cells(const float *mu, const or_slice *sl, const or_
     float ru = c->e * abs_sum3f(eu[0], eu[1], eu[2]) + c->m;
     float rv = c->e * abs_sum3f(ev[0], ev[1], ev[2]) + c->m;
     float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
-    float il = ceilf((uc - ru) / sl->dx + hx);
-    float ih = floorf((uc + ru) / sl->dx + hx);
-    float jl = ceilf((vc - rv) / sl->dy + hy);
-    float jh = floorf((vc + rv) / sl->dy + hy);
+    float idx = 1.0f / sl->dx, idy = 1.0f / sl->dy;
+    float il = ceilf((uc - ru) * idx + hx);
+    float ih = floorf((uc + ru) * idx + hx);
+    float jl = ceilf((vc - rv) * idy + hy);
+    float jh = floorf((vc + rv) * idy + hy);
     float Wm1 = (float)(sl->W - 1), Hm1 = (float)(sl->H - 1);
     if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
         rect[0] = 1; rect[1] = 1; rect[2] = 0; rect[3] = 0;

@@ -305,16 +305,17 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     if (!f.full) frame_full(G, Q, f);
     float u0 = dot3_rn(Q[0], Q[3], Q[6], p0, p1, p2);
     float v0 = dot3_rn(Q[1], Q[4], Q[7], p0, p1, p2);
-    float r2 = __fsub_rn(K2, __fdiv_rn(ww, Sww));
+    const float iSww = __fdiv_rn(1.0f, Sww);
+    float r2 = __fsub_rn(K2, __fmul_rn(ww, iSww));
     if (r2 < 0.0f) r2 = 0.0f;
-    float Cuu = __fsub_rn(f.Luu, __fdiv_rn(__fmul_rn(f.Luw, f.Luw), Sww));
+    float Cuu = __fsub_rn(f.Luu, __fmul_rn(__fmul_rn(f.Luw, f.Luw), iSww));
     if (Cuu < 0.0f) Cuu = 0.0f;
     Cuu = __fadd_rn(Cuu, S.pu2);
-    float Cvv = __fsub_rn(f.Lvv, __fdiv_rn(__fmul_rn(f.Lvw, f.Lvw), Sww));
+    float Cvv = __fsub_rn(f.Lvv, __fmul_rn(__fmul_rn(f.Lvw, f.Lvw), iSww));
     if (Cvv < 0.0f) Cvv = 0.0f;
     Cvv = __fadd_rn(Cvv, S.pv2);
-    float cu = __fsub_rn(u0, __fdiv_rn(__fmul_rn(f.Luw, w0), Sww));
-    float cv = __fsub_rn(v0, __fdiv_rn(__fmul_rn(f.Lvw, w0), Sww));
+    float cu = __fsub_rn(u0, __fmul_rn(__fmul_rn(f.Luw, w0), iSww));
+    float cv = __fsub_rn(v0, __fmul_rn(__fmul_rn(f.Lvw, w0), iSww));
     float ru = __fsqrt_rn(__fmul_rn(r2, Cuu));
     float rv = __fsqrt_rn(__fmul_rn(r2, Cvv));
     pixel_box(S, cu, cv, ru, rv, o);
@@ -325,10 +326,11 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
 // to the image; an empty box is stored as the tile rectangle (1,1,0,0).
 __device__ __forceinline__ void pixel_box(const SliceDev &S, float cu, float cv, float ru, float rv, PredOut &o)
 {
-    float il = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cu, ru), S.dx), S.hx));
-    float ih = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(cu, ru), S.dx), S.hx));
-    float jl = ceilf(__fadd_rn(__fdiv_rn(__fsub_rn(cv, rv), S.dy), S.hy));
-    float jh = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(cv, rv), S.dy), S.hy));
+    const float idx = __fdiv_rn(1.0f, S.dx), idy = __fdiv_rn(1.0f, S.dy);
+    float il = ceilf(__fadd_rn(__fmul_rn(__fsub_rn(cu, ru), idx), S.hx));
+    float ih = floorf(__fadd_rn(__fmul_rn(__fadd_rn(cu, ru), idx), S.hx));
+    float jl = ceilf(__fadd_rn(__fmul_rn(__fsub_rn(cv, rv), idy), S.hy));
+    float jh = floorf(__fadd_rn(__fmul_rn(__fadd_rn(cv, rv), idy), S.hy));
     float Wm1 = (float)(S.W - 1), Hm1 = (float)(S.H - 1);
     if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
         o.il = o.jl = MG_TILE;  // empty box: tile rectangle (1,1,0,0)
