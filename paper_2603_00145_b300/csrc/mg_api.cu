@@ -212,7 +212,7 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.cnt = take(sizeof(unsigned) * (size_t)(S * L.NW + 1));
     L.gcnt = take(sizeof(unsigned) * (size_t)(n + 1));
     L.bits = take(sizeof(unsigned) * (size_t)(L.SW * n + 1));
-    L.scan_part = take(sizeof(unsigned long long) * MG_SCAN_BLOCKS);
+    L.scan_part = take(sizeof(unsigned long long) * 2 * MG_SCAN_BLOCKS);
     L.rec_geo = take(16 * (size_t)L.cap_records);
     L.rec_geo2 = take(8 * (size_t)L.cap_records);
     L.rec_gid = take(4 * (size_t)L.cap_records);

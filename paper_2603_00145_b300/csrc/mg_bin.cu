@@ -112,9 +112,19 @@ __device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigne
 constexpr int SCAN_NT = 512;
 constexpr int SCAN_ITEMS = 4;
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const unsigned *in, long long n,
-                                                         unsigned long long *part)
+// Two independent scans may share the launches: blockIdx.y selects the array.
+struct ScanPair {
+    const unsigned *in[2];
+    unsigned *out[2];
+    long long n[2];
+    unsigned long long *total[2];
+};
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(ScanPair sp, unsigned long long *parts)
 {
+    const unsigned *in = sp.in[blockIdx.y];
+    const long long n = sp.n[blockIdx.y];
+    unsigned long long *part = parts + (size_t)blockIdx.y * gridDim.x;
     long long per = (n + gridDim.x - 1) / gridDim.x;
     long long b0 = (long long)blockIdx.x * per;
     long long b1 = b0 + per < n ? b0 + per : n;
@@ -125,9 +135,10 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const unsigned *in, lon
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_part(unsigned long long *part, int nb,
-                                                       unsigned long long *total_out)
+__global__ void __launch_bounds__(SCAN_NT) k_scan_part(unsigned long long *parts, int nb, ScanPair sp)
 {
+    unsigned long long *part = parts + (size_t)blockIdx.x * nb;
+    unsigned long long *total_out = sp.total[blockIdx.x];
     unsigned long long v = threadIdx.x < nb ? part[threadIdx.x] : 0ull;
     unsigned long long tot;
     unsigned long long pre = block_exclusive_scan<SCAN_NT>(v, &tot);
@@ -135,9 +146,12 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_part(unsigned long long *part,
     if (threadIdx.x == 0 && total_out) *total_out = tot;
 }
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_down(const unsigned *in, unsigned *out, long long n,
-                                                       const unsigned long long *part, int write_end)
+__global__ void __launch_bounds__(SCAN_NT) k_scan_down(ScanPair sp, const unsigned long long *parts, int write_end)
 {
+    const unsigned *in = sp.in[blockIdx.y];
+    unsigned *out = sp.out[blockIdx.y];
+    const long long n = sp.n[blockIdx.y];
+    const unsigned long long *part = parts + (size_t)blockIdx.y * gridDim.x;
     long long per = (n + gridDim.x - 1) / gridDim.x;
     long long b0 = (long long)blockIdx.x * per;
     long long b1 = b0 + per < n ? b0 + per : n;
@@ -168,10 +182,36 @@ void mg_launch_scan_u32(const unsigned *in, unsigned *out, long long n_host, con
                         unsigned long long *part, unsigned long long *total_out, cudaStream_t st)
 {
     (void)n_dev;
+    ScanPair sp;
+    sp.in[0] = sp.in[1] = in;
+    sp.out[0] = sp.out[1] = out;
+    sp.n[0] = sp.n[1] = n_host;
+    sp.total[0] = sp.total[1] = total_out;
     int nb = MG_SCAN_BLOCKS;
-    k_scan_reduce<<<nb, SCAN_NT, 0, st>>>(in, n_host, part);
-    k_scan_part<<<1, SCAN_NT, 0, st>>>(part, nb, total_out);
-    k_scan_down<<<nb, SCAN_NT, 0, st>>>(in, out, n_host, part, 1);
+    k_scan_reduce<<<nb, SCAN_NT, 0, st>>>(sp, part);
+    k_scan_part<<<1, SCAN_NT, 0, st>>>(part, nb, sp);
+    k_scan_down<<<nb, SCAN_NT, 0, st>>>(sp, part, 1);
+}
+
+// two independent exclusive scans in the same three launches (part holds
+// 2 * MG_SCAN_BLOCKS entries)
+void mg_launch_scan2_u32(const unsigned *in0, unsigned *out0, long long n0, unsigned long long *total0,
+                         const unsigned *in1, unsigned *out1, long long n1, unsigned long long *total1,
+                         unsigned long long *part, cudaStream_t st)
+{
+    ScanPair sp;
+    sp.in[0] = in0;
+    sp.out[0] = out0;
+    sp.n[0] = n0;
+    sp.total[0] = total0;
+    sp.in[1] = in1;
+    sp.out[1] = out1;
+    sp.n[1] = n1;
+    sp.total[1] = total1;
+    int nb = MG_SCAN_BLOCKS;
+    k_scan_reduce<<<dim3(nb, 2), SCAN_NT, 0, st>>>(sp, part);
+    k_scan_part<<<2, SCAN_NT, 0, st>>>(part, nb, sp);
+    k_scan_down<<<dim3(nb, 2), SCAN_NT, 0, st>>>(sp, part, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1002,8 +1042,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_SCAN_REC, st);
-        mg_launch_scan_u32(cnt, cnt, (long long)S * NW, nullptr, part, &hdr->n_records, st);
-        mg_launch_scan_u32(gcnt, gcnt, n, nullptr, part, &hdr->scan_total, st);
+        mg_launch_scan2_u32(cnt, cnt, (long long)S * NW, &hdr->n_records, gcnt, gcnt, n, &hdr->scan_total, part, st);
     }
     {
         MG_PROF(MG_ST_K1_EMIT, st);
