@@ -286,10 +286,10 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
     }
 }
 
-// Tiles without records are written with zeros first (32 list entries per
-// warp and step, no dependent loads); then persistent warps pull the tiles
-// with records from a counter (tiles carry very different numbers of
-// records).
+// Persistent warps pull the tiles with records from a counter (tiles carry
+// very different numbers of records); a warp that finds none left pulls the
+// tiles without records 32 at a time from a second counter and writes their
+// zeros (and loss terms) one lane per tile, so that work fills the tail.
 // LOSS: the L1 + L2 slice loss and its gradient fused into the writes (the
 // empty tiles' zeros included), one FP64 partial pair per tile.
 template <bool CELLS, bool LOSS>
@@ -309,47 +309,6 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n_tiles = tab.n_tiles_total;
     const long long n_idle = hdr->n_idle, n_busy = hdr->n_busy;
-    const long long gw = (long long)blockIdx.x * RW + w, nw = (long long)gridDim.x * RW;
-    for (long long i = gw * 32 + lane; i < n_idle; i += nw * 32) {
-        // one lane per empty tile: its rows as two float4 stores where aligned
-        const TileId d = tile_id(tab, (int)tile_list[n_tiles - 1 - i]);
-        const int px0 = d.tx * MG_TILE, py0 = d.ty * MG_TILE;
-        const int nx = min(MG_TILE, d.W - px0), ny = min(MG_TILE, d.H - py0);
-        float f1 = 0.f, f2 = 0.f;
-        for (int r = 0; r < ny; ++r) {
-            const long long o = d.pixbase + (long long)(py0 + r) * d.W + px0;
-            float *row = out + o;
-            if (nx == MG_TILE && ((uintptr_t)row & 15) == 0) {
-                ((float4 *)row)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                ((float4 *)row)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                for (int c = 0; c < nx; ++c) row[c] = 0.f;
-            }
-            if (LOSS) {
-                float r1 = 0.f, r2 = 0.f;  // row partials, then added to the tile's
-                float gv[MG_TILE];
-                if (nx == MG_TILE && ((uintptr_t)row & 15) == 0) {
-                    const float4 t0 = ((const float4 *)(ls.target + o))[0], t1 = ((const float4 *)(ls.target + o))[1];
-                    const float tv[MG_TILE] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-#pragma unroll
-                    for (int c = 0; c < MG_TILE; ++c) l1l2_voxel(0.f, tv[c], ls.inv_n, &gv[c], r1, r2);
-                    if (ls.grad && ((uintptr_t)(ls.grad + o) & 15) == 0) {
-                        ((float4 *)(ls.grad + o))[0] = make_float4(gv[0], gv[1], gv[2], gv[3]);
-                        ((float4 *)(ls.grad + o))[1] = make_float4(gv[4], gv[5], gv[6], gv[7]);
-                    } else if (ls.grad) {
-#pragma unroll
-                        for (int c = 0; c < MG_TILE; ++c) ls.grad[o + c] = gv[c];
-                    }
-                } else {
-                    for (int c = 0; c < nx; ++c)
-                        l1l2_voxel(0.f, ls.target[o + c], ls.inv_n, ls.grad ? ls.grad + o + c : nullptr, r1, r2);
-                }
-                f1 += r1;
-                f2 += r2;
-            }
-        }
-        if (LOSS) ls.tile_part[tile_list[n_tiles - 1 - i]] = make_double2((double)f1, (double)f2);
-    }
     for (;;) {
         unsigned i = 0;
         if (lane == 0) i = atomicAdd(counter, 1u);
@@ -358,6 +317,53 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
         fwd_tile<CELLS, LOSS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off,
                               entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, out, ls);
         __syncwarp();
+    }
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(counter + 2, 32u);
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if ((long long)i0 >= n_idle) break;
+        const long long i = (long long)i0 + lane;
+        if (i < n_idle) {
+            // one lane per empty tile: its rows as two float4 stores where aligned
+            const TileId d = tile_id(tab, (int)tile_list[n_tiles - 1 - i]);
+            const int px0 = d.tx * MG_TILE, py0 = d.ty * MG_TILE;
+            const int nx = min(MG_TILE, d.W - px0), ny = min(MG_TILE, d.H - py0);
+            float f1 = 0.f, f2 = 0.f;
+            for (int r = 0; r < ny; ++r) {
+                const long long o = d.pixbase + (long long)(py0 + r) * d.W + px0;
+                float *row = out + o;
+                if (nx == MG_TILE && ((uintptr_t)row & 15) == 0) {
+                    ((float4 *)row)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    ((float4 *)row)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    for (int c = 0; c < nx; ++c) row[c] = 0.f;
+                }
+                if (LOSS) {
+                    float r1 = 0.f, r2 = 0.f;  // row partials, then added to the tile's
+                    float gv[MG_TILE];
+                    if (nx == MG_TILE && ((uintptr_t)(ls.target + o) & 15) == 0) {
+                        const float4 t0 = ((const float4 *)(ls.target + o))[0], t1 = ((const float4 *)(ls.target + o))[1];
+                        const float tv[MG_TILE] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                        for (int c = 0; c < MG_TILE; ++c) l1l2_voxel(0.f, tv[c], ls.inv_n, &gv[c], r1, r2);
+                        if (ls.grad && ((uintptr_t)(ls.grad + o) & 15) == 0) {
+                            ((float4 *)(ls.grad + o))[0] = make_float4(gv[0], gv[1], gv[2], gv[3]);
+                            ((float4 *)(ls.grad + o))[1] = make_float4(gv[4], gv[5], gv[6], gv[7]);
+                        } else if (ls.grad) {
+#pragma unroll
+                            for (int c = 0; c < MG_TILE; ++c) ls.grad[o + c] = gv[c];
+                        }
+                    } else {
+                        for (int c = 0; c < nx; ++c)
+                            l1l2_voxel(0.f, ls.target[o + c], ls.inv_n, ls.grad ? ls.grad + o + c : nullptr, r1, r2);
+                    }
+                    f1 += r1;
+                    f2 += r2;
+                }
+            }
+            if (LOSS) ls.tile_part[tile_list[n_tiles - 1 - i]] = make_double2((double)f1, (double)f2);
+        }
     }
 }
 
@@ -1129,7 +1135,7 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, co
     int nt = tab.n_tiles_total;
     if (nt <= 0) return;
     WsHeader *hdr = (WsHeader *)(ws + L.hdr);
-    cudaMemsetAsync(&hdr->tile_ctr[0], 0, sizeof(unsigned), st);
+    cudaMemsetAsync(&hdr->tile_ctr[0], 0, 3 * sizeof(unsigned), st);
     FwdLoss ls;
     ls.target = target;
     ls.grad = grad;

@@ -85,3 +85,30 @@ def test_fused_loss_without_gaussians():
     t = target.cpu().numpy().astype(np.float64)
     assert float(out.abs().max()) == 0.0
     np.testing.assert_allclose(loss.cpu().numpy()[0], np.abs(t).mean() + (t * t).mean(), rtol=2e-6)
+
+
+def test_fused_loss_with_unaligned_target_and_grad():
+    """Rows of 64 pixels are 16-byte aligned in `out`, while target and grad
+    start one float past an aligned address: the empty tiles' vector path
+    must check each pointer on its own (results as with aligned buffers)."""
+    from paper_2603_00145_b300 import SliceRenderer
+
+    rng = np.random.default_rng(7)
+    G = ms.random_gaussians(60, 77, box=(-10, 10), sigma=(0.6, 1.5), aniso=2.0)
+    stacks = [ms.make_stack(ms.AXIAL, 4, 64, 64, 1.0, 1.0, 2.0, 2.0)]
+    R = SliceRenderer(stacks)
+    d = to_dev(G)
+    nv = R.dev.n_vox
+    t_host = rng.uniform(0.0, 1.0, nv).astype(np.float32)
+    tgt_a = torch.from_numpy(t_host).cuda()
+    tgt_u = torch.empty(nv + 1, device="cuda")[1:]
+    tgt_u.copy_(tgt_a)
+    outs = []
+    for tgt, off in ((tgt_a, 0), (tgt_u, 1)):
+        out = torch.empty(nv, device="cuda")
+        gbuf = torch.empty(nv + off, device="cuda")[off:]
+        loss = torch.empty(2, dtype=torch.float64, device="cuda")
+        R.forward_l1l2(*d, tgt, out, gbuf, loss)
+        outs.append((out.clone(), gbuf.clone(), loss.cpu().numpy()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
