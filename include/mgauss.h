@@ -355,6 +355,9 @@ mg_status mg_render_pair_count(const mg_gaussians *g, const mg_stack *stacks, in
  * default; enabling affects all threads of the process.
  */
 mg_status mg_profile_enable(int on);
+/* As mg_profile_enable, for the stages whose bit is set in mask only (bit i:
+ * stage i of mg_profile_stage_name); the others launch without events. */
+mg_status mg_profile_stages(uint32_t mask);
 int mg_profile_stage_count(void);
 const char *mg_profile_stage_name(int stage);
 mg_status mg_profile_read(double *ms, int64_t *calls, int reset);

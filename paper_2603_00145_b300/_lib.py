@@ -100,6 +100,7 @@ SIGNATURES = {
                                      c_p, c_sz, c_p]),
     "mg_params_bwd": (ctypes.c_int, [c_i64, c_p, c_p, c_f32, c_f32, c_f32, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "mg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mg_profile_stages": (ctypes.c_int, [ctypes.c_uint32]),
     "mg_profile_stage_count": (ctypes.c_int, []),
     "mg_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
     "mg_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_i64), ctypes.c_int]),

@@ -22,7 +22,7 @@ void mg_launch_sq_diff(const float *a, const float *b, long long n, double *out,
 // per-stage CUDA-event timing
 // ---------------------------------------------------------------------------
 namespace prof {
-std::atomic<bool> on{false};
+std::atomic<unsigned> on{0u};  // bit per stage
 std::mutex mu;
 struct Pending {
     int stage;
@@ -54,7 +54,7 @@ cudaEvent_t get_event()
 
 void mg_prof_begin(int stage, cudaStream_t st)
 {
-    if (!prof::on.load(std::memory_order_relaxed)) return;
+    if (!((prof::on.load(std::memory_order_relaxed) >> stage) & 1u)) return;
     cudaEvent_t e = prof::get_event();
     cudaEventRecord(e, st);
     prof::open_ev[stage] = e;
@@ -62,7 +62,7 @@ void mg_prof_begin(int stage, cudaStream_t st)
 
 void mg_prof_end(int stage, cudaStream_t st)
 {
-    if (!prof::on.load(std::memory_order_relaxed) || !prof::open_ev[stage]) return;
+    if (!((prof::on.load(std::memory_order_relaxed) >> stage) & 1u) || !prof::open_ev[stage]) return;
     cudaEvent_t e = prof::get_event();
     cudaEventRecord(e, st);
     std::lock_guard<std::mutex> lk(prof::mu);
@@ -763,7 +763,13 @@ mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float
 
 mg_status mg_profile_enable(int on)
 {
-    prof::on.store(on != 0);
+    prof::on.store(on != 0 ? (MG_NSTAGES >= 32 ? 0xffffffffu : (1u << MG_NSTAGES) - 1u) : 0u);
+    return MG_OK;
+}
+
+mg_status mg_profile_stages(uint32_t mask)
+{
+    prof::on.store(mask & (MG_NSTAGES >= 32 ? 0xffffffffu : (1u << MG_NSTAGES) - 1u));
     return MG_OK;
 }
 

@@ -300,6 +300,16 @@ def mg_profile_enable(on: bool = True):
     L.check(L.lib().mg_profile_enable(1 if on else 0), "mg_profile_enable")
 
 
+def mg_profile_stages(names):
+    """Time only the named stages (the others launch without events)."""
+    lib = L.lib()
+    all_names = [lib.mg_profile_stage_name(i).decode() for i in range(lib.mg_profile_stage_count())]
+    mask = 0
+    for n in names:
+        mask |= 1 << all_names.index(n)
+    L.check(lib.mg_profile_stages(mask), "mg_profile_stages")
+
+
 def mg_profile_read(reset: bool = True) -> dict:
     """{stage name: (milliseconds, calls)} accumulated since the last reset."""
     lib = L.lib()
