@@ -401,6 +401,18 @@ mg_status mg_nrf_fwd(const mg_nrf *net, const float *xyz, int64_t n, float *out,
  * overwritten. Accumulated with atomics (FP32 summation order varies). */
 mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float *grad_out, float *g_params,
                      float *g_table, mg_stream_t stream);
+/* The residual at a batch of rows of a coordinate table (the NRF's random
+ * voxel batch of a training step, Sec. 3.4, without a gathered copy): for
+ * i < n, acc[idx[i]] += r(coords[idx[i]]). Device buffers: coords [rows,3],
+ * idx int64 [n], acc [rows]; repeated rows each add (atomic adds, so the
+ * summation order of repeats is unspecified). An index outside [0, rows) is
+ * skipped: it adds nothing and reads nothing. mg_nrf_bwd_at: gradients of
+ * sum_i grad_acc[idx[i]] r(coords[idx[i]]) (grad_acc [rows]), outputs and
+ * errors as mg_nrf_bwd. n == 0 is valid (fwd: no work; bwd: zero gradients). */
+mg_status mg_nrf_fwd_at(const mg_nrf *net, const float *coords, int64_t rows, const int64_t *idx, int64_t n,
+                        float *acc, mg_stream_t stream);
+mg_status mg_nrf_bwd_at(const mg_nrf *net, const float *coords, int64_t rows, const int64_t *idx, int64_t n,
+                        const float *grad_acc, float *g_params, float *g_table, mg_stream_t stream);
 
 /*
  * Parameterisation of the fit (Sec. 3.2) and the anisotropy regulariser

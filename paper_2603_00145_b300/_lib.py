@@ -93,6 +93,8 @@ SIGNATURES = {
     "mg_nrf_param_count": (c_i64, [c_i32]),
     "mg_nrf_fwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p]),
     "mg_nrf_bwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p, c_p, c_p]),
+    "mg_nrf_fwd_at": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_i64, c_p, c_p]),
+    "mg_nrf_bwd_at": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, c_p]),
     "mg_adam_step": (ctypes.c_int, [ctypes.POINTER(MgAdamGroup), ctypes.c_int, c_f32, c_f32, c_f32, c_p, c_p,
                                     ctypes.c_uint32, c_p]),
     "mg_params_workspace_size": (c_sz, [c_i64]),

@@ -761,6 +761,44 @@ mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float
     return check_cuda("mg_nrf_bwd");
 }
 
+mg_status mg_nrf_fwd_at(const mg_nrf *net, const float *coords, int64_t rows, const int64_t *idx, int64_t n,
+                        float *acc, mg_stream_t stream)
+{
+    std::string why;
+    if (!valid_nrf(net, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (n < 0 || rows < 0 || (n > 0 && (!coords || !idx || !acc)))
+        return fail(MG_ERR_INVALID_ARG, "bad coords/idx/acc, rows or n");
+    if (n == 0) return MG_OK;
+    MG_PROF(MG_ST_NRF_FWD, (cudaStream_t)stream);
+    cudaError_t e = mg_launch_nrf(net, coords, n, nullptr, acc, nullptr, nullptr, false, (cudaStream_t)stream,
+                                  (const long long *)idx, rows);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("mg_nrf_fwd_at: ") + cudaGetErrorString(e));
+    return MG_OK;
+}
+
+mg_status mg_nrf_bwd_at(const mg_nrf *net, const float *coords, int64_t rows, const int64_t *idx, int64_t n,
+                        const float *grad_acc, float *g_params, float *g_table, mg_stream_t stream)
+{
+    std::string why;
+    if (!valid_nrf(net, why)) return fail(MG_ERR_INVALID_ARG, why);
+    if (n < 0 || rows < 0 || (n > 0 && (!coords || !idx || !grad_acc)) || !g_params)
+        return fail(MG_ERR_INVALID_ARG, "bad pointers or n");
+    if (net->encoding == MG_NRF_GRID && !g_table) return fail(MG_ERR_INVALID_ARG, "grid encoding needs g_table");
+    cudaStream_t st = (cudaStream_t)stream;
+    MG_PROF(MG_ST_NRF_BWD, st);
+    cudaMemsetAsync(g_params, 0, sizeof(float) * (size_t)mg_nrf_param_count_impl(net->encoding), st);
+    if (net->encoding == MG_NRF_GRID) {
+        int lt = net->log2_table > 0 ? net->log2_table : 19;
+        cudaMemsetAsync(g_table, 0, sizeof(float) * 2 * 16 * ((size_t)1 << lt), st);
+    }
+    if (n > 0) {
+        cudaError_t e = mg_launch_nrf(net, coords, n, grad_acc, nullptr, g_params, g_table, true, st,
+                                      (const long long *)idx, rows);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("mg_nrf_bwd_at: ") + cudaGetErrorString(e));
+    }
+    return check_cuda("mg_nrf_bwd_at");
+}
+
 mg_status mg_profile_enable(int on)
 {
     prof::on.store(on != 0 ? (MG_NSTAGES >= 32 ? 0xffffffffu : (1u << MG_NSTAGES) - 1u) : 0u);

@@ -206,7 +206,8 @@ struct MgProfScope {
 // host-side launch helpers (defined in the .cu files)
 int64_t mg_nrf_param_count_impl(int32_t encoding);
 cudaError_t mg_launch_nrf(const mg_nrf *net, const float *xyz, long long n, const float *grad_out, float *out,
-                          float *g_params, float *g_table, bool train, cudaStream_t st);
+                          float *g_params, float *g_table, bool train, cudaStream_t st, const long long *idx = nullptr,
+                          long long rows = 0);
 void mg_launch_pair_count(const WsLayout &L, char *ws, const StackTable &tab, cudaStream_t st);
 void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_t st);
 void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const StackTable &tab, const float *mean,

@@ -95,7 +95,18 @@ struct NrfArgs {
     const float *table;
     float out_scale;
     GridGeom grid;
+    const long long *idx;  // point i is row idx[i] of xyz / out / grad_out (NULL: row i)
+    long long rows;        // with idx: rows of xyz / out / grad_out; other indices are skipped
 };
+
+// Row of point i (-1: past the end or an index outside [0, rows)).
+__device__ __forceinline__ long long nrf_row(const NrfArgs &A, long long i, long long n)
+{
+    if (i >= n) return -1;
+    if (!A.idx) return i;
+    const long long r = A.idx[i];
+    return (r >= 0 && r < A.rows) ? r : -1;
+}
 
 // ---------------------------------------------------------------------------
 // element helpers
@@ -464,7 +475,8 @@ __device__ __forceinline__ void nrf_body(const NrfArgs A, const float *__restric
         // ---- encoding -> H0
         for (int i = tid; i < P * 3; i += NRF_NT) {
             const int p = i / 3, c = i - 3 * p;
-            sPt[p * 4 + c] = (p0 + p < n) ? xyz[(p0 + p) * 3 + c] : 0.f;
+            const long long row = nrf_row(A, p0 + p, n);
+            sPt[p * 4 + c] = row >= 0 ? xyz[row * 3 + c] : 0.f;
         }
         __syncthreads();
         if (ENC == MG_NRF_FOURIER) {
@@ -534,9 +546,15 @@ __device__ __forceinline__ void nrf_body(const NrfArgs A, const float *__restric
             const float o = acc + sWout[WIDTH];
             const float th = tanhf(o);
             if (half == 0) {
-                if (!TRAIN && p0 + p < n) out[p0 + p] = A.out_scale * th;
+                const long long row = nrf_row(A, p0 + p, n);
+                if (!TRAIN && row >= 0) {
+                    if (A.idx)
+                        atomicAdd(&out[row], A.out_scale * th);  // added to the indexed row
+                    else
+                        out[row] = A.out_scale * th;
+                }
                 if (TRAIN) {
-                    const float go = (p0 + p < n) ? grad_out[p0 + p] : 0.f;
+                    const float go = row >= 0 ? grad_out[row] : 0.f;
                     sPt[p * 4 + 3] = go * A.out_scale * (1.f - th * th);  // dL/do
                 }
             }
@@ -704,10 +722,12 @@ GridGeom make_grid(const mg_nrf *net)
 
 template <int ENC, bool BF16, bool TRAIN>
 cudaError_t launch_nrf(const mg_nrf *net, const float *xyz, long long n, const float *grad_out, float *out,
-                       float *g_params, float *g_table, cudaStream_t st)
+                       float *g_params, float *g_table, const long long *idx, long long rows, cudaStream_t st)
 {
     typedef Layout<ENC, BF16, TRAIN> LY;
     NrfArgs A;
+    A.idx = idx;
+    A.rows = rows;
     A.params = net->params;
     A.table = net->table;
     A.out_scale = net->out_scale;
@@ -738,19 +758,20 @@ int64_t mg_nrf_param_count_impl(int32_t encoding)
 }
 
 cudaError_t mg_launch_nrf(const mg_nrf *net, const float *xyz, long long n, const float *grad_out, float *out,
-                          float *g_params, float *g_table, bool train, cudaStream_t st)
+                          float *g_params, float *g_table, bool train, cudaStream_t st, const long long *idx,
+                          long long rows)
 {
     const bool bf = net->precision == MG_NRF_BF16;
     if (net->encoding == MG_NRF_FOURIER) {
         if (train)
-            return bf ? launch_nrf<MG_NRF_FOURIER, true, true>(net, xyz, n, grad_out, out, g_params, g_table, st)
-                      : launch_nrf<MG_NRF_FOURIER, false, true>(net, xyz, n, grad_out, out, g_params, g_table, st);
-        return bf ? launch_nrf<MG_NRF_FOURIER, true, false>(net, xyz, n, grad_out, out, g_params, g_table, st)
-                  : launch_nrf<MG_NRF_FOURIER, false, false>(net, xyz, n, grad_out, out, g_params, g_table, st);
+            return bf ? launch_nrf<MG_NRF_FOURIER, true, true>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st)
+                      : launch_nrf<MG_NRF_FOURIER, false, true>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st);
+        return bf ? launch_nrf<MG_NRF_FOURIER, true, false>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st)
+                  : launch_nrf<MG_NRF_FOURIER, false, false>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st);
     }
     if (train)
-        return bf ? launch_nrf<MG_NRF_GRID, true, true>(net, xyz, n, grad_out, out, g_params, g_table, st)
-                  : launch_nrf<MG_NRF_GRID, false, true>(net, xyz, n, grad_out, out, g_params, g_table, st);
-    return bf ? launch_nrf<MG_NRF_GRID, true, false>(net, xyz, n, grad_out, out, g_params, g_table, st)
-              : launch_nrf<MG_NRF_GRID, false, false>(net, xyz, n, grad_out, out, g_params, g_table, st);
+        return bf ? launch_nrf<MG_NRF_GRID, true, true>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st)
+                  : launch_nrf<MG_NRF_GRID, false, true>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st);
+    return bf ? launch_nrf<MG_NRF_GRID, true, false>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st)
+              : launch_nrf<MG_NRF_GRID, false, false>(net, xyz, n, grad_out, out, g_params, g_table, idx, rows, st);
 }

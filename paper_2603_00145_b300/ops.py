@@ -609,6 +609,39 @@ def mg_nrf_bwd(net: NRF, xyz, grad_out, g_params, g_table=None, params=None, tab
                                _stream_handle(stream)), "mg_nrf_bwd")
 
 
+def mg_nrf_fwd_at(net: NRF, coords, idx, n: int, acc, params=None, table=None, stream=None):
+    """acc[idx[i]] += r(coords[idx[i]]) for i < n (the field at a batch of
+    rows; indices outside [0, rows) are skipped)."""
+    rows = coords.numel() // 3
+    _dev(coords, "coords", numel=3 * rows)
+    _dev(acc, "acc", numel=rows)
+    ip = _dev_idx(idx, n)
+    s = net.struct(params, table)
+    L.check(L.lib().mg_nrf_fwd_at(ctypes.byref(s), coords.data_ptr(), rows, ip, n, acc.data_ptr(),
+                                  _stream_handle(stream)), "mg_nrf_fwd_at")
+
+
+def mg_nrf_bwd_at(net: NRF, coords, idx, n: int, grad_acc, g_params, g_table=None, params=None, table=None,
+                  stream=None):
+    """Gradients of sum_i grad_acc[idx[i]] r(coords[idx[i]]) for the field's parameters (and table)."""
+    rows = coords.numel() // 3
+    _dev(coords, "coords", numel=3 * rows)
+    _dev(grad_acc, "grad_acc", numel=rows)
+    ip = _dev_idx(idx, n)
+    gp = _dev(g_params, "g_params", numel=mg_nrf_param_count(net.encoding))
+    gt = _dev(g_table, "g_table") if g_table is not None else None
+    s = net.struct(params, table)
+    L.check(L.lib().mg_nrf_bwd_at(ctypes.byref(s), coords.data_ptr(), rows, ip, n, grad_acc.data_ptr(), gp, gt,
+                                  _stream_handle(stream)), "mg_nrf_bwd_at")
+
+
+def _dev_idx(idx, n: int) -> int:
+    if not (isinstance(idx, torch.Tensor) and idx.is_cuda and idx.dtype == torch.int64 and idx.is_contiguous()
+            and idx.numel() >= n):
+        raise ValueError(f"idx must be a contiguous CUDA int64 tensor with at least {n} entries")
+    return idx.data_ptr()
+
+
 class NRFFunction(torch.autograd.Function):
     """r = NRF(xyz) with gradients for the parameter vector (and grid table)."""
 

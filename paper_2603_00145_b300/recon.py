@@ -175,8 +175,9 @@ class _Trainer:
             self.nrf_adam.zero_grad()
 
     def iteration(self):
-        """One step, all in this library's kernels except the NRF batch
-        bookkeeping (random voxel indices, gather, index_add)."""
+        """One step, all in this library's kernels; the NRF's random voxel
+        batch (Sec. 3.4) is drawn by torch's generator and passed in as row
+        indices."""
         cfg, m = self.cfg, self.model
         with torch.no_grad():
             ops.mg_params_fwd(m.mean_c, m.quat, m.log_scale, self.centre, self.half, cfg.lambda_r, self.mean, self.q,
@@ -192,10 +193,7 @@ class _Trainer:
             if self.nrf is not None:
                 n_vox = self.target.numel()
                 idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
-                xyz = self.coords[idx]
-                r = torch.empty(idx.numel(), dtype=torch.float32, device=self.device)
-                ops.mg_nrf_fwd(self.nrf, xyz, r, self.nrf_params, self.nrf_table)
-                pred.index_add_(0, idx, r)
+                ops.mg_nrf_fwd_at(self.nrf, self.coords, idx, idx.numel(), pred, self.nrf_params, self.nrf_table)
             # the loss (FP64 sums) and its gradient dL/dpred in one kernel
             if cfg.loss == "paper":
                 grad = torch.empty_like(pred)
@@ -206,10 +204,10 @@ class _Trainer:
                 out = torch.empty(2, dtype=torch.float64, device=pred.device)
                 ops.mg_loss_l1l2(pred, self.target, grad, out, self.ws)
             if self.nrf is not None:
-                g_r = grad[idx]
                 gp = torch.empty_like(self.nrf_params)
                 gt = torch.empty_like(self.nrf_table) if self.nrf_table is not None else None
-                ops.mg_nrf_bwd(self.nrf, xyz, g_r, gp, gt, self.nrf_params, self.nrf_table)
+                ops.mg_nrf_bwd_at(self.nrf, self.coords, idx, idx.numel(), grad, gp, gt, self.nrf_params,
+                                  self.nrf_table)
                 self.nrf_params.grad = gp
                 if gt is not None:
                     self.nrf_table.grad = gt

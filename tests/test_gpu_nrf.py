@@ -147,3 +147,53 @@ def test_nrf_zero_last_layer_gives_zero():
         out = torch.empty(1000, device="cuda")
         mg_nrf_fwd(net, torch.from_numpy(ms.nrf_points(1000, 1)).cuda(), out)
         assert float(out.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("preset", ["paper", "grid"])
+def test_nrf_at_indexed_rows(preset):
+    """The field at a batch of rows of a coordinate table (the training
+    step's random voxel batch, Sec. 3.4): acc[idx[i]] += r(coords[idx[i]])
+    with repeated rows adding, and the gradients of
+    sum_i grad_acc[idx[i]] r(coords[idx[i]]), against the FP64 oracle on the
+    gathered points (FP32 field: forward 1e-5, gradients 1e-4)."""
+    from paper_2603_00145_b300 import mg_nrf_bwd_at, mg_nrf_fwd_at
+
+    net, ref = _nets(preset, "fp32")
+    rows, n = 3001, 4099 + 512  # more indices than rows: repeats; ragged tail
+    coords = _points(rows, 7)
+    idx = np.random.default_rng(8).integers(0, rows, size=n).astype(np.int64)
+    acc0 = np.random.default_rng(9).normal(size=rows).astype(np.float32)
+    acc = torch.from_numpy(acc0.copy()).cuda()
+    cd, idd = torch.from_numpy(coords).cuda(), torch.from_numpy(idx).cuda()
+    mg_nrf_fwd_at(net, cd, idd, n, acc)
+    r = onrf.forward(ref, coords[idx].astype(np.float64))
+    want = acc0.astype(np.float64) + np.bincount(idx, weights=r, minlength=rows)
+    got = acc.cpu().numpy().astype(np.float64)
+    assert _rel(got - acc0, want - acc0) <= 1e-5
+    # n = 0 and a prefix of the index list
+    mg_nrf_fwd_at(net, cd, idd, 0, acc)
+    assert np.array_equal(acc.cpu().numpy().astype(np.float64), got)
+    acc2 = torch.zeros(rows, device="cuda")
+    mg_nrf_fwd_at(net, cd, idd, 100, acc2)
+    want2 = np.bincount(idx[:100], weights=r[:100], minlength=rows)
+    assert _rel(acc2.cpu().numpy(), want2) <= 1e-5
+    ga = np.random.default_rng(10).normal(size=rows).astype(np.float32)
+    gp = torch.empty_like(net.params)
+    gt = torch.empty_like(net.table) if net.table is not None else None
+    mg_nrf_bwd_at(net, cd, idd, n, torch.from_numpy(ga).cuda(), gp, gt)
+    g = onrf.backward(ref, coords[idx].astype(np.float64), ga[idx].astype(np.float64))
+    flat = np.concatenate([np.concatenate([gw.ravel(), gb.ravel()]) for gw, gb in zip(g["weights"], g["biases"])])
+    assert _rel(gp.cpu().numpy(), flat) <= 1e-4
+    if preset == "grid":
+        assert _rel(gt.cpu().numpy().reshape(g["table"].shape), g["table"]) <= 1e-4
+    # indices outside [0, rows) add nothing
+    bad = idd[:64].clone()
+    bad[::3] = -1
+    bad[1::3] = rows
+    acc3 = torch.zeros(rows, device="cuda")
+    mg_nrf_fwd_at(net, cd, bad, 64, acc3)
+    keep = np.arange(64) % 3 == 2
+    want3 = np.bincount(idx[:64][keep], weights=r[:64][keep], minlength=rows)
+    assert _rel(acc3.cpu().numpy(), want3) <= 1e-5
+    with pytest.raises(ValueError):
+        mg_nrf_fwd_at(net, cd, idd.to(torch.int32), n, acc)
