@@ -54,7 +54,7 @@ def lib():
         i64 = ctypes.c_int64
         L.or_make_records.restype = i64
         L.or_make_records.argtypes = [i64, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, ctypes.c_float, i64, p, p,
-                                      p]
+                                      p, p]
         L.or_render.restype = None
         L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, ctypes.c_int, p,
                                 p, p]
@@ -64,7 +64,7 @@ def lib():
         L.or_make_records_cells.restype = i64
         L.or_make_records_cells.argtypes = [i64, p, ctypes.c_int, p, p, p, p, p, p, p, p, p, p, i64, p, p, p]
         L.or_pair_counts.restype = None
-        L.or_pair_counts.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p,
+        L.or_pair_counts.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, p,
                                      ctypes.c_double, p]
         _lib = L
     return _lib
@@ -118,6 +118,7 @@ class Records:
     slice: np.ndarray   # [m] int32 global slice index
     gid: np.ndarray     # [m] int32
     rect: np.ndarray    # [m,4] int32 tile rectangle tx0, ty0, tx1, ty1 (inclusive)
+    inset: np.ndarray | None = None  # [m] uint64 row insets of the rectangle (None: no culling)
 
     @property
     def n(self):
@@ -125,6 +126,19 @@ class Records:
 
     def _args(self):
         return [self.n, _ptr(self.slice), _ptr(self.gid), _ptr(self.rect)]
+
+    def row_tiles(self, r: int):
+        """The (tx, ty) tiles record r lists: its rectangle, each of the first
+        eight tile rows narrowed by the insets (low 4 bits from the left, high
+        4 bits from the right)."""
+        tx0, ty0, tx1, ty1 = (int(v) for v in self.rect[r])
+        ins = 0 if self.inset is None else int(self.inset[r])
+        out = []
+        for ty in range(ty0, ty1 + 1):
+            n = ty - ty0
+            b = (ins >> (8 * n)) & 0xFF if n < 8 else 0
+            out.extend((tx, ty) for tx in range(tx0 + (b & 15), tx1 - (b >> 4) + 1))
+        return out
 
 
 def records(G, stacks, K: float = 3.0, cells=None) -> Records:
@@ -145,12 +159,13 @@ def records(G, stacks, K: float = 3.0, cells=None) -> Records:
         rect = np.zeros((total, 4), dtype=np.int32)
         L.or_make_records_cells(ga[0], ga[1], *a, _ptr(ci), _ptr(cf), total, _ptr(sl), _ptr(gid), _ptr(rect))
         return Records(sl, gid, rect)
-    total = L.or_make_records(*ga[:4], *sa.args(), ctypes.c_float(K), 0, None, None, None)
+    total = L.or_make_records(*ga[:4], *sa.args(), ctypes.c_float(K), 0, None, None, None, None)
     sl = np.zeros(total, dtype=np.int32)
     gid = np.zeros(total, dtype=np.int32)
     rect = np.zeros((total, 4), dtype=np.int32)
-    L.or_make_records(*ga[:4], *sa.args(), ctypes.c_float(K), total, _ptr(sl), _ptr(gid), _ptr(rect))
-    return Records(sl, gid, rect)
+    inset = np.zeros(total, dtype=np.uint64)
+    L.or_make_records(*ga[:4], *sa.args(), ctypes.c_float(K), total, _ptr(sl), _ptr(gid), _ptr(rect), _ptr(inset))
+    return Records(sl, gid, rect, inset)
 
 
 def slice_table(stacks):
@@ -170,16 +185,14 @@ def slice_table(stacks):
 
 def tile_bins(rec: Records, stacks):
     """Per global tile (stacks, slices, then ty*TX+tx): the record count and the
-    sorted record ids (CSR). Brute force over every record's rectangle."""
+    sorted record ids (CSR). Brute force over every record's listed tiles."""
     rows, n_tiles = slice_table(stacks)
     lists = [[] for _ in range(n_tiles)]
     for r in range(rec.n):
         k = int(rec.slice[r])
         _, _, _, TX, _, _, tb = rows[k]
-        tx0, ty0, tx1, ty1 = (int(v) for v in rec.rect[r])
-        for ty in range(ty0, ty1 + 1):
-            for tx in range(tx0, tx1 + 1):
-                lists[tb + ty * TX + tx].append(r)
+        for tx, ty in rec.row_tiles(r):
+            lists[tb + ty * TX + tx].append(r)
     counts = np.array([len(l) for l in lists], dtype=np.int64)
     offs = np.zeros(n_tiles + 1, dtype=np.int64)
     np.cumsum(counts, out=offs[1:])
@@ -293,7 +306,8 @@ def pair_counts(G, stacks, rec: Records, K: float = 3.0):
     sa = _StackArgs(stacks, np.float64)
     keep, ga = _gargs(G, np.float64)
     c = np.zeros(2, dtype=np.int64)
-    L.or_pair_counts(*ga, *sa.args(), *rec._args(), ctypes.c_double(K), _ptr(c))
+    ins = None if rec.inset is None else np.ascontiguousarray(rec.inset, dtype=np.uint64)
+    L.or_pair_counts(*ga, *sa.args(), *rec._args(), None if ins is None else _ptr(ins), ctypes.c_double(K), _ptr(c))
     return int(c[0]), int(c[1])
 
 

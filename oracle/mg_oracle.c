@@ -147,9 +147,79 @@ static float dot3f(const float a[3], const float b[3])
     return t + a[2] * b[2];
 }
 
-/* returns 1 and the tile rectangle if the (Gaussian, slice) record exists */
+/* Row culling of a record's tile rectangle (FP32, each operation rounded, as
+ * the record predicate): for each of the first eight tile rows, the tile
+ * columns that the cut ellipse {(u,v): (u-cu, v-cv) C^-1 (u-cu, v-cv)^T <= r2}
+ * reaches over the row's pixel band v in [va, vb]. The band's leftmost ellipse
+ * point is the ellipse's own leftmost point (cu - ru at v = cv - Cuv sqrt(r2/Cuu))
+ * when that v lies in the band; otherwise, the left boundary being convex in v,
+ * it lies on the band edge nearest to it, where the chord of the ellipse is
+ * centred at cu + (Cuv/Cvv) d with half-width sqrt((r2 - d^2/Cvv)(Cuu - Cuv^2/Cvv)),
+ * d = v - cv; the right side mirrors this. The extents grow by
+ * ru/256 + dx/1024 so that FP32 rounding never drops a tile that holds a voxel
+ * of the ellipse. Returned as 8 bits per row: the tile-column insets from the
+ * rectangle's left (low 4 bits) and right edges, each at most 15. */
+static uint64_t row_insets(const or_slice *sl, float cu, float cv, float Cuu, float Cvv, float Cuv, float r2,
+                           float ru, float il, float ih, float jl, float jh)
+{
+    int tx0 = (int32_t)il / OR_TILE, tx1 = (int32_t)ih / OR_TILE;
+    int ty0 = (int32_t)jl / OR_TILE, ty1 = (int32_t)jh / OR_TILE;
+    if (!(r2 > 0.0f) || !(Cuu > 0.0f) || !(Cvv > 0.0f)) return 0;
+    float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
+    float idx = 1.0f / sl->dx;
+    float e = sqrtf(r2 / Cuu);
+    float g = Cuv / Cvv;
+    float h2 = Cuu - Cuv * g;
+    if (h2 < 0.0f) h2 = 0.0f;
+    float m = ru * 0.00390625f + sl->dx * 0.0009765625f;
+    float vL = cv - Cuv * e, vR = cv + Cuv * e;
+    uint64_t out = 0;
+    int last = ty1 - ty0 < 7 ? ty1 - ty0 : 7;
+    for (int n = 0; n <= last; ++n) {
+        int ty = ty0 + n;
+        int a = (int)jl > OR_TILE * ty ? (int)jl : OR_TILE * ty;
+        int b = (int)jh < OR_TILE * ty + OR_TILE - 1 ? (int)jh : OR_TILE * ty + OR_TILE - 1;
+        float va = ((float)a - hy) * sl->dy, vb = ((float)b - hy) * sl->dy;
+        float left, right;
+        float v = fminf(fmaxf(vL, va), vb);
+        if (v == vL) {
+            left = cu - ru;
+        } else {
+            float d = v - cv;
+            float t = r2 - (d * d) / Cvv;
+            if (t < 0.0f) t = 0.0f;
+            left = (cu + g * d) - sqrtf(t * h2);
+        }
+        v = fminf(fmaxf(vR, va), vb);
+        if (v == vR) {
+            right = cu + ru;
+        } else {
+            float d = v - cv;
+            float t = r2 - (d * d) / Cvv;
+            if (t < 0.0f) t = 0.0f;
+            right = (cu + g * d) + sqrtf(t * h2);
+        }
+        float lo = fmaxf(ceilf((left - m) * idx + hx), il);
+        float hi = fminf(floorf((right + m) * idx + hx), ih);
+        int l, r;
+        if (!(lo <= hi)) { /* no voxel column in this band: the row lists nothing */
+            l = tx1 - tx0 + 1;
+            r = 0;
+        } else {
+            l = (int32_t)lo / OR_TILE - tx0;
+            r = tx1 - (int32_t)hi / OR_TILE;
+        }
+        if (l > 15) l = 15;
+        if (r > 15) r = 15;
+        out |= (uint64_t)(l | (r << 4)) << (8 * n);
+    }
+    return out;
+}
+
+/* returns 1 and the tile rectangle (and the row insets, if asked) if the
+ * (Gaussian, slice) record exists */
 static int record_predicate(const float *mu, const float *q, const float *s, const or_slice *sl, float K,
-                            int32_t rect[4])
+                            int32_t rect[4], uint64_t *inset)
 {
     float R[3][3], M[3][3], Sg[3][3];
     quat_rot_f(q, R);
@@ -175,7 +245,7 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
         sv[r] = dot3f(Sg[r], ev);
     }
     float Lww = dot3f(en, sn), Luw = dot3f(eu, sn), Lvw = dot3f(ev, sn);
-    float Luu = dot3f(eu, su), Lvv = dot3f(ev, sv);
+    float Luu = dot3f(eu, su), Lvv = dot3f(ev, sv), Luv = dot3f(ev, su);
     float sig2 = (float)((double)sl->thk * (double)sl->thk * OR_FWHM2VAR);
     float Sww = Lww + sig2;
     float K2 = K * K;
@@ -202,6 +272,7 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     float jl = ceilf((cv - rv) * idy + hy);
     float jh = floorf((cv + rv) * idy + hy);
     float Wm1 = (float)(sl->W - 1), Hm1 = (float)(sl->H - 1);
+    if (inset) *inset = 0;
     if (!(il <= ih) || !(jl <= jh) || !(il <= Wm1) || !(ih >= 0.0f) || !(jl <= Hm1) || !(jh >= 0.0f)) {
         rect[0] = 1; rect[1] = 1; rect[2] = 0; rect[3] = 0; /* record without tiles */
         return 1;
@@ -214,6 +285,13 @@ static int record_predicate(const float *mu, const float *q, const float *s, con
     rect[1] = (int32_t)jl / OR_TILE;
     rect[2] = (int32_t)ih / OR_TILE;
     rect[3] = (int32_t)jh / OR_TILE;
+    /* rows are culled for Gaussians with max scale <= 64 min scale only: beyond
+     * that, FP32 cancellation in the conditional covariance can exceed the margin */
+    float smax = fmaxf(fmaxf(s[0], s[1]), s[2]), smin = fminf(fminf(s[0], s[1]), s[2]);
+    if (inset && smax <= 64.0f * smin) {
+        float Cuv = Luv - (Luw * Lvw) * iSww;
+        *inset = row_insets(sl, cu, cv, Cuu, Cvv, Cuv, r2, ru, il, ih, jl, jh);
+    }
     return 1;
 }
 
@@ -375,7 +453,7 @@ int64_t or_make_records(int64_t n, const float *mean, const float *quat, const f
                         const int32_t *nsl, const int32_t *H, const int32_t *W, const float *dx, const float *dy,
                         const float *thk, const float *psf, const float *xform, float K, int64_t cap,
                         int32_t *rec_slice,
-                        int32_t *rec_gid, int32_t *rec_rect)
+                        int32_t *rec_gid, int32_t *rec_rect, uint64_t *rec_inset)
 {
     int S;
     or_slice *sl = or_build_slices(n_stacks, nsl, H, W, dx, dy, thk, psf, xform, NULL, NULL, NULL, NULL, NULL, &S);
@@ -385,7 +463,7 @@ int64_t or_make_records(int64_t n, const float *mean, const float *quat, const f
         int64_t c = 0;
         int32_t rect[4];
         for (int64_t g = 0; g < n; ++g)
-            c += record_predicate(mean + 3 * g, quat + 4 * g, scale + 3 * g, &sl[k], K, rect);
+            c += record_predicate(mean + 3 * g, quat + 4 * g, scale + 3 * g, &sl[k], K, rect, NULL);
         cnt[k + 1] = c;
     }
     for (int k = 0; k < S; ++k) cnt[k + 1] += cnt[k];
@@ -396,10 +474,12 @@ int64_t or_make_records(int64_t n, const float *mean, const float *quat, const f
             int64_t pos = cnt[k];
             int32_t rect[4];
             for (int64_t g = 0; g < n && pos < cap; ++g) {
-                if (record_predicate(mean + 3 * g, quat + 4 * g, scale + 3 * g, &sl[k], K, rect)) {
+                uint64_t ins;
+                if (record_predicate(mean + 3 * g, quat + 4 * g, scale + 3 * g, &sl[k], K, rect, &ins)) {
                     rec_slice[pos] = k;
                     rec_gid[pos] = (int32_t)g;
                     memcpy(rec_rect + 4 * pos, rect, sizeof(rect));
+                    if (rec_inset) rec_inset[pos] = ins;
                     ++pos;
                 }
             }
@@ -726,12 +806,14 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
 }
 
 /* counts[0] = pairs (record, pixel in a listed tile) with y^T Sigma'^-1 y <= K^2
- * (FP64), counts[1] = all evaluated pairs (record, pixel in a listed tile). */
+ * (FP64), counts[1] = all evaluated pairs (record, pixel in a listed tile). The
+ * listed tiles are the rectangle's, culled per row by rec_inset (NULL: none). */
 void or_pair_counts(int64_t n_unused, const double *mean, const double *quat, const double *scale, const double *alpha,
                     int n_stacks, const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx,
                     const double *dy, const double *thk, const double *psf, const double *xform, int64_t nrec,
                     const int32_t *rec_slice,
-                    const int32_t *rec_gid, const int32_t *rec_rect, double K, int64_t *counts)
+                    const int32_t *rec_gid, const int32_t *rec_rect, const uint64_t *rec_inset, double K,
+                    int64_t *counts)
 {
     (void)n_unused;
     int S;
@@ -744,11 +826,13 @@ void or_pair_counts(int64_t n_unused, const double *mean, const double *quat, co
         or_term T;
         term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
         const int32_t *rc = rec_rect + 4 * r;
-        int i0 = rc[0] * OR_TILE, j0 = rc[1] * OR_TILE;
-        int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
-        if (i1 > sl[k].W) i1 = sl[k].W;
+        int j0 = rc[1] * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
         if (j1 > sl[k].H) j1 = sl[k].H;
-        for (int j = j0; j < j1; ++j)
+        for (int j = j0; j < j1; ++j) {
+            int n = j / OR_TILE - rc[1];
+            int bits = (rec_inset && n < 8) ? (int)((rec_inset[r] >> (8 * n)) & 0xFF) : 0;
+            int i0 = (rc[0] + (bits & 15)) * OR_TILE, i1 = (rc[2] - (bits >> 4) + 1) * OR_TILE;
+            if (i1 > sl[k].W) i1 = sl[k].W;
             for (int i = i0; i < i1; ++i) {
                 double x[3], y[3], Py[3];
                 pixel_world(&sl[k], i, j, x);
@@ -756,6 +840,7 @@ void or_pair_counts(int64_t n_unused, const double *mean, const double *quat, co
                 inside += (qf <= K * K);
                 evald += 1;
             }
+        }
     }
     counts[0] = inside;
     counts[1] = evald;

@@ -9,7 +9,12 @@ tile rectangle of the cut ellipse) against brute force in FP64.
   quadratic form (a different route from the Schur complement the predicate
   uses), up to an FP32 margin;
 * existence: a record exists exactly when the K-sigma slab test passes; its
-  tile rectangle is empty when the cut ellipse misses the image.
+  tile rectangle is empty when the cut ellipse misses the image;
+* row culling: every tile holding a pixel inside the ellipse stays listed;
+  each listed tile row reaches no further than the FP64 extent of the
+  ellipse over that tile row's pixel band (dense boundary samples plus the
+  band's chords) grown by the stated margin; and the listed tiles number
+  within a few percent of the tiles that hold an inside pixel.
 """
 import numpy as np
 import pytest
@@ -60,6 +65,33 @@ def _fp64_tile_rect(A, b, c, K, st, margin_px):
     return (int(il) // TILE, int(jl) // TILE, int(ih) // TILE, int(jh) // TILE)
 
 
+def _row_extent(A, b, c, K, st, y0, y1):
+    """FP64 pixel-x extent of {q <= K^2} over pixel rows y in [y0, y1]
+    (continuous), or None: boundary samples inside the band plus the chords
+    at its two edges."""
+    ctr = -np.linalg.solve(A, b)
+    r2 = K * K - (c + b @ ctr)
+    if r2 <= 0:
+        return None
+    w, V = np.linalg.eigh(A)
+    th = np.linspace(0, 2 * np.pi, 20001)
+    pts = ctr[:, None] + V @ (np.sqrt(r2 / w)[:, None] * np.stack([np.cos(th), np.sin(th)]))
+    hx, hy = 0.5 * (st.W - 1), 0.5 * (st.H - 1)
+    fx, fy = pts[0] / st.dx + hx, pts[1] / st.dy + hy
+    xs = list(fx[(fy >= y0) & (fy <= y1)])
+    for yb in (y0, y1):
+        v = (yb - hy) * st.dy  # chord: A00 du^2 + 2 A01 du dv + A11 dv^2 = r2, dv = v - ctr_v
+        dv = v - ctr[1]
+        disc = (A[0, 1] * dv) ** 2 - A[0, 0] * (A[1, 1] * dv * dv - r2)
+        if disc >= 0:
+            for sg in (-1.0, 1.0):
+                du = (-A[0, 1] * dv + sg * np.sqrt(disc)) / A[0, 0]
+                xs.append((ctr[0] + du) / st.dx + hx)
+    if not xs:
+        return None
+    return min(xs), max(xs), np.sqrt(r2 / w).max()
+
+
 def _contains(outer, inner):
     if inner is not None and (inner[0] > inner[2] or inner[1] > inner[3]):
         inner = None  # a record whose pixel box is empty lists no tile
@@ -82,6 +114,8 @@ def test_records_vs_brute_force(seed, K):
               ms.make_stack(ms.SAGITTAL, 3, 20, 20, 1.5, 1.5, 0.0, 4.0)]
     rec = orc.records(G, stacks, K)
     have = {(int(k), int(g)): tuple(int(v) for v in r) for k, g, r in zip(rec.slice, rec.gid, rec.rect)}
+    where = {(int(k), int(g)): r for r, (k, g) in enumerate(zip(rec.slice, rec.gid))}
+    n_listed = n_ideal = 0
     # slice-major, ascending Gaussian id
     key = rec.slice.astype(np.int64) * G.n + rec.gid
     assert np.all(np.diff(key) > 0)
@@ -104,6 +138,32 @@ def test_records_vs_brute_force(seed, K):
                     jin, iin = np.nonzero(inside)
                     tx, ty = iin // TILE, jin // TILE
                     assert got[0] <= tx.min() and got[2] >= tx.max() and got[1] <= ty.min() and got[3] >= ty.max()
+                if got is not None:
+                    r = where[(k0 + k, g)]
+                    listed = set(rec.row_tiles(r))
+                    n_listed += len(listed)
+                    # every tile with an inside pixel is listed
+                    need = {(int(a), int(b_)) for a, b_ in zip(*np.nonzero(inside.T))}
+                    need = {(a // TILE, b_ // TILE) for a, b_ in need}
+                    n_ideal += len(need)
+                    assert need <= listed, (k, g, sorted(need - listed))
+                    # each culled row reaches no further than the FP64 extent over the tile band
+                    ins = int(rec.inset[r])
+                    for ty_ in range(got[1], got[3] + 1):
+                        nrow = ty_ - got[1]
+                        bits = (ins >> (8 * nrow)) & 0xFF if nrow < 8 else 0
+                        if nrow >= 8 or (bits & 15) == 15 or (bits >> 4) == 15:
+                            continue
+                        row = sorted(tx_ for tx_, t_ in listed if t_ == ty_)
+                        if not row:
+                            continue
+                        ext = _row_extent(A, b, c, K * (1 + 1e-5), st, TILE * ty_, min(TILE * ty_ + TILE - 1,
+                                                                                         st.H - 1))
+                        assert ext is not None, (k, g, ty_)
+                        lo, hi, rmax = ext
+                        m_px = (rmax / 256 + st.dx / 1024) / st.dx + 1e-3
+                        assert TILE * row[0] + TILE - 1 >= np.ceil(lo - m_px), (k, g, ty_, row, lo)
+                        assert TILE * row[-1] <= np.floor(hi + m_px), (k, g, ty_, row, hi)
                 # slab test in FP64: w0^2 / Sww vs K^2 (margin for FP32 rounding)
                 q_min = c - b @ np.linalg.solve(A, b)  # min over the plane of q
                 # q_min is w0^2/Sww (the plane minimum of the convolved form)
@@ -116,6 +176,9 @@ def test_records_vs_brute_force(seed, K):
                 assert _contains(got, lo), (k, g, got, lo)
                 assert _contains(hi, got), (k, g, got, hi)
         k0 += st.n_slices
+    # the culled lists are close to the ideal tile sets
+    assert n_listed <= 1.03 * n_ideal + 5, (n_listed, n_ideal)
+    assert int(np.count_nonzero(rec.inset)) > 0
 
 
 def test_record_count_and_tile_bins_consistent():
@@ -123,8 +186,9 @@ def test_record_count_and_tile_bins_consistent():
     stacks = [ms.make_stack(ms.CORONAL, 6, 35, 48, 1.0, 1.0, 3.0, 3.0)]
     rec = orc.records(G, stacks, 3.0)
     counts, offs, ids = orc.tile_bins(rec, stacks)
+    assert counts.sum() == sum(len(rec.row_tiles(r)) for r in range(rec.n)) == ids.size
     areas = (rec.rect[:, 2] - rec.rect[:, 0] + 1) * (rec.rect[:, 3] - rec.rect[:, 1] + 1)
-    assert counts.sum() == areas.sum() == ids.size
+    assert counts.sum() <= areas[areas > 0].sum()
     for t in range(counts.size):
         seg = ids[offs[t]:offs[t + 1]]
         assert np.all(np.diff(seg) > 0)
