@@ -53,9 +53,23 @@
  *   idx = 1/dx, idy = 1/dy;  il = ceil((cu-ru)*idx + hx), ih = floor((cu+ru)*idx + hx),
  *   jl = ceil((cv-rv)*idy + hy), jh = floor((cv+rv)*idy + hy);
  *   the box is empty unless il<=ih, jl<=jh, il<=W-1, ih>=0, jl<=H-1, jh>=0 (NaN: empty);
- *   a non-empty box is clamped (il,jl up to 0, ih,jh down to W-1,H-1) and lists the
- *   tiles [il/8, ih/8] x [jl/8, jh/8]; an empty box lists no tile (stored as the
- *   tile rectangle (1,1,0,0)).
+ *   a non-empty box is clamped (il,jl up to 0, ih,jh down to W-1,H-1) and spans the
+ *   tile rectangle [tx0, tx1] x [ty0, ty1] = [il/8, ih/8] x [jl/8, jh/8]; an empty box
+ *   lists no tile (stored as the tile rectangle (1,1,0,0)).
+ *   Row culling: tile row ty0 + n lists the columns [tx0 + l_n, tx1 - r_n]. l_n = r_n = 0
+ *   for n >= 8, and for every row unless max(s) <= 64*min(s) (fmaxf/fminf over the
+ *   three scales), r2 > 0, Cuu > 0, Cvv > 0 and tx1 > tx0. Otherwise, with
+ *   Luv = e_v.(Sigma e_u), Cuv = Luv - (Luw*Lvw)*iSww, e = ru/Cuu, iCvv = 1/Cvv,
+ *   g = Cuv*iCvv, h2 = max(Cuu - Cuv*g, 0),
+ *   m = ru*(1/256) + dx*(1/1024), vL = cv - Cuv*e, vR = cv + Cuv*e, and per row n <= 7:
+ *   a = max(jl, 8ty), b = min(jh, 8ty+7), va = ((float)a - hy)*dy, vb = ((float)b - hy)*dy;
+ *   left: v = fminf(fmaxf(vL, va), vb); if v == vL: left = cu - ru, else d = v - cv,
+ *     t = max(r2 - (d*d)*iCvv, 0), left = (cu + g*d) - sqrt(t*h2);
+ *   right: the same with vR, cu + ru and + sqrt(t*h2);
+ *   lo = fmaxf(ceil((left - m)*idx + hx), il), hi = fminf(floor((right + m)*idx + hx), ih);
+ *   if !(lo <= hi): l_n = tx1 - tx0 + 1, r_n = 0 (the row lists nothing), else
+ *   l_n = (int)lo/8 - tx0, r_n = tx1 - (int)hi/8; both then capped at 15 (a cap only
+ *   lists more). The listed tiles hold every voxel of the cut ellipse with a margin.
  *   Tile (tx,ty) of a slice covers pixels 8tx..8tx+7 x 8ty..8ty+7.
  *   The count of records and of (record, tile) entries is therefore exact
  *   and reproducible bit for bit by any IEEE FP32 implementation.
@@ -243,12 +257,13 @@ mg_status mg_render_pose_grad(const mg_gaussians *g, const mg_stack *stacks, int
  * bins written by mg_render_fwd / mg_sample_volume. Records are ordered by
  * global slice, then ascending Gaussian id (the first `records` entries of
  * each array are valid): rec_gid int32, rec_slice int32, rec_rect uint16x4
- * (tx0, ty0, tx1, ty1). Bins: tile_off uint32 [tiles+1] (exclusive offsets,
+ * (tx0, ty0, tx1, ty1), rec_inset uint64 (byte n: l_n | r_n << 4 of the row
+ * culling above). Bins: tile_off uint32 [tiles+1] (exclusive offsets,
  * global tile order = stacks, slices, ty*TX+tx), entries uint32 (record
  * ids). Returns MG_ERR_INVALID_ARG on bad arguments.
  */
 typedef struct {
-    uint64_t rec_gid, rec_slice, rec_rect, tile_off, entries, total_bytes;
+    uint64_t rec_gid, rec_slice, rec_rect, rec_inset, tile_off, entries, total_bytes;
 } mg_ws_layout;
 mg_status mg_render_ws_layout(const mg_gaussians *g, const mg_stack *stacks, int n_stacks, const mg_opts *opts,
                               mg_ws_layout *out);

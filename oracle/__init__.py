@@ -56,11 +56,11 @@ def lib():
         L.or_make_records.argtypes = [i64, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, ctypes.c_float, i64, p, p,
                                       p, p]
         L.or_render.restype = None
-        L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, ctypes.c_int, p,
-                                p, p]
+        L.or_render.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, p, ctypes.c_int,
+                                p, p, p]
         L.or_grad.restype = None
         L.or_grad.argtypes = [i64, p, p, p, p, ctypes.c_int, p, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p,
-                              p, p]
+                              p, p, p]
         L.or_make_records_cells.restype = i64
         L.or_make_records_cells.argtypes = [i64, p, ctypes.c_int, p, p, p, p, p, p, p, p, p, p, i64, p, p, p]
         L.or_pair_counts.restype = None
@@ -125,7 +125,10 @@ class Records:
         return int(self.slice.shape[0])
 
     def _args(self):
-        return [self.n, _ptr(self.slice), _ptr(self.gid), _ptr(self.rect)]
+        if self.inset is not None:
+            self.inset = np.ascontiguousarray(self.inset, dtype=np.uint64)
+        return [self.n, _ptr(self.slice), _ptr(self.gid), _ptr(self.rect),
+                None if self.inset is None else _ptr(self.inset)]
 
     def row_tiles(self, r: int):
         """The (tx, ty) tiles record r lists: its rectangle, each of the first
@@ -158,7 +161,7 @@ def records(G, stacks, K: float = 3.0, cells=None) -> Records:
         gid = np.zeros(total, dtype=np.int32)
         rect = np.zeros((total, 4), dtype=np.int32)
         L.or_make_records_cells(ga[0], ga[1], *a, _ptr(ci), _ptr(cf), total, _ptr(sl), _ptr(gid), _ptr(rect))
-        return Records(sl, gid, rect)
+        return Records(sl, gid, rect, np.zeros(total, dtype=np.uint64))  # no row culling for cells
     total = L.or_make_records(*ga[:4], *sa.args(), ctypes.c_float(K), 0, None, None, None, None)
     sl = np.zeros(total, dtype=np.int32)
     gid = np.zeros(total, dtype=np.int32)
@@ -281,7 +284,8 @@ def pose_grad(G, stacks, rec: Records, gout: np.ndarray, cells=None) -> np.ndarr
                                         psf_u=getattr(s, "psf_u", 0.0), psf_v=getattr(s, "psf_v", 0.0),
                                         xform=xf[None, :].copy(), n_vox=npx)
             sel = rec.slice == k
-            rk = Records(np.zeros(int(sel.sum()), np.int32), rec.gid[sel].copy(), rec.rect[sel].copy())
+            rk = Records(np.zeros(int(sel.sum()), np.int32), rec.gid[sel].copy(), rec.rect[sel].copy(),
+                         None if rec.inset is None else rec.inset[sel].copy())
             gr = grad(G, [sub], rk, go[off:off + npx], cells)
             R = xf[:9].reshape(3, 3)
             t = xf[9:]
@@ -306,8 +310,7 @@ def pair_counts(G, stacks, rec: Records, K: float = 3.0):
     sa = _StackArgs(stacks, np.float64)
     keep, ga = _gargs(G, np.float64)
     c = np.zeros(2, dtype=np.int64)
-    ins = None if rec.inset is None else np.ascontiguousarray(rec.inset, dtype=np.uint64)
-    L.or_pair_counts(*ga, *sa.args(), *rec._args(), None if ins is None else _ptr(ins), ctypes.c_double(K), _ptr(c))
+    L.or_pair_counts(*ga, *sa.args(), *rec._args(), ctypes.c_double(K), _ptr(c))
     return int(c[0]), int(c[1])
 
 

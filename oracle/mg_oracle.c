@@ -151,11 +151,12 @@ static float dot3f(const float a[3], const float b[3])
  * the record predicate): for each of the first eight tile rows, the tile
  * columns that the cut ellipse {(u,v): (u-cu, v-cv) C^-1 (u-cu, v-cv)^T <= r2}
  * reaches over the row's pixel band v in [va, vb]. The band's leftmost ellipse
- * point is the ellipse's own leftmost point (cu - ru at v = cv - Cuv sqrt(r2/Cuu))
- * when that v lies in the band; otherwise, the left boundary being convex in v,
- * it lies on the band edge nearest to it, where the chord of the ellipse is
- * centred at cu + (Cuv/Cvv) d with half-width sqrt((r2 - d^2/Cvv)(Cuu - Cuv^2/Cvv)),
- * d = v - cv; the right side mirrors this. The extents grow by
+ * point is the ellipse's own leftmost point (cu - ru at v = cv - Cuv ru/Cuu,
+ * ru = sqrt(r2 Cuu)) when that v lies in the band; otherwise, the left boundary
+ * being convex in v, it lies on the band edge nearest to it, where the chord of
+ * the ellipse is centred at cu + (Cuv/Cvv) d with half-width
+ * sqrt((r2 - d^2/Cvv)(Cuu - Cuv^2/Cvv)), d = v - cv; the right side mirrors
+ * this. A rectangle one tile wide is not culled. The extents grow by
  * ru/256 + dx/1024 so that FP32 rounding never drops a tile that holds a voxel
  * of the ellipse. Returned as 8 bits per row: the tile-column insets from the
  * rectangle's left (low 4 bits) and right edges, each at most 15. */
@@ -164,11 +165,12 @@ static uint64_t row_insets(const or_slice *sl, float cu, float cv, float Cuu, fl
 {
     int tx0 = (int32_t)il / OR_TILE, tx1 = (int32_t)ih / OR_TILE;
     int ty0 = (int32_t)jl / OR_TILE, ty1 = (int32_t)jh / OR_TILE;
-    if (!(r2 > 0.0f) || !(Cuu > 0.0f) || !(Cvv > 0.0f)) return 0;
+    if (!(r2 > 0.0f) || !(Cuu > 0.0f) || !(Cvv > 0.0f) || tx1 == tx0) return 0;
     float hx = 0.5f * (float)(sl->W - 1), hy = 0.5f * (float)(sl->H - 1);
     float idx = 1.0f / sl->dx;
-    float e = sqrtf(r2 / Cuu);
-    float g = Cuv / Cvv;
+    float e = ru / Cuu;
+    float iCvv = 1.0f / Cvv;
+    float g = Cuv * iCvv;
     float h2 = Cuu - Cuv * g;
     if (h2 < 0.0f) h2 = 0.0f;
     float m = ru * 0.00390625f + sl->dx * 0.0009765625f;
@@ -186,7 +188,7 @@ static uint64_t row_insets(const or_slice *sl, float cu, float cv, float Cuu, fl
             left = cu - ru;
         } else {
             float d = v - cv;
-            float t = r2 - (d * d) / Cvv;
+            float t = r2 - (d * d) * iCvv;
             if (t < 0.0f) t = 0.0f;
             left = (cu + g * d) - sqrtf(t * h2);
         }
@@ -195,7 +197,7 @@ static uint64_t row_insets(const or_slice *sl, float cu, float cv, float Cuu, fl
             right = cu + ru;
         } else {
             float d = v - cv;
-            float t = r2 - (d * d) / Cvv;
+            float t = r2 - (d * d) * iCvv;
             if (t < 0.0f) t = 0.0f;
             right = (cu + g * d) + sqrtf(t * h2);
         }
@@ -214,6 +216,17 @@ static uint64_t row_insets(const or_slice *sl, float cu, float cv, float Cuu, fl
         out |= (uint64_t)(l | (r << 4)) << (8 * n);
     }
     return out;
+}
+
+/* The pixel columns [*i0, *i1) that record r lists in pixel row j: its
+ * rectangle's tiles, narrowed by the row insets (NULL: none). */
+static void listed_cols(const int32_t *rc, const uint64_t *rec_inset, int64_t r, int j, int W, int *i0, int *i1)
+{
+    int n = j / OR_TILE - rc[1];
+    int bits = (rec_inset && n < 8) ? (int)((rec_inset[r] >> (8 * n)) & 0xFF) : 0;
+    *i0 = (rc[0] + (bits & 15)) * OR_TILE;
+    *i1 = (rc[2] - (bits >> 4) + 1) * OR_TILE;
+    if (*i1 > W) *i1 = W;
 }
 
 /* returns 1 and the tile rectangle (and the row insets, if asked) if the
@@ -624,8 +637,8 @@ static double quad_form(const or_term *T, const double x[3], double y[3], double
 void or_render(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
                const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy,
                const double *thk, const double *psf, const double *xform, int64_t nrec, const int32_t *rec_slice,
-               const int32_t *rec_gid, const int32_t *rec_rect, int exact, double *out, const int32_t *cells_i,
-               const float *cells_f)
+               const int32_t *rec_gid, const int32_t *rec_rect, const uint64_t *rec_inset, int exact, double *out,
+               const int32_t *cells_i, const float *cells_f)
 {
     int S;
     or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
@@ -666,9 +679,7 @@ void or_render(int64_t n, const double *mean, const double *quat, const double *
                 or_term T;
                 term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
                 const int32_t *rc = rec_rect + 4 * r;
-                int i0 = rc[0] * OR_TILE, j0 = rc[1] * OR_TILE;
-                int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
-                if (i1 > sl[k].W) i1 = sl[k].W;
+                int j0 = rc[1] * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
                 if (j1 > sl[k].H) j1 = sl[k].H;
                 int gcell[3];
                 if (cells_i) {
@@ -676,7 +687,9 @@ void or_render(int64_t n, const double *mean, const double *quat, const double *
                     float b[3];
                     gauss_cell_f(muf, &cc, gcell, b);
                 }
-                for (int j = j0; j < j1; ++j)
+                for (int j = j0; j < j1; ++j) {
+                    int i0, i1;
+                    listed_cols(rc, rec_inset, r, j, sl[k].W, &i0, &i1);
                     for (int i = i0; i < i1; ++i) {
                         if (cells_i) {
                             int vcell[3];
@@ -688,6 +701,7 @@ void or_render(int64_t n, const double *mean, const double *quat, const double *
                         double qf = quad_form(&T, x, y, Py);
                         img[(int64_t)j * sl[k].W + i] += T.alpha * T.c * exp(-0.5 * qf);
                     }
+                }
             }
         }
         free(first);
@@ -710,8 +724,8 @@ void or_render(int64_t n, const double *mean, const double *quat, const double *
 void or_grad(int64_t n, const double *mean, const double *quat, const double *scale, const double *alpha, int n_stacks,
              const int32_t *nsl, const int32_t *H, const int32_t *W, const double *dx, const double *dy, const double *thk,
              const double *psf, const double *xform, int64_t nrec, const int32_t *rec_slice, const int32_t *rec_gid,
-             const int32_t *rec_rect, const double *gout, double *gmean, double *gquat, double *gscale,
-             double *galpha, const int32_t *cells_i, const float *cells_f)
+             const int32_t *rec_rect, const uint64_t *rec_inset, const double *gout, double *gmean, double *gquat,
+             double *gscale, double *galpha, const int32_t *cells_i, const float *cells_f)
 {
     int S;
     or_slice *sl = or_build_slices(n_stacks, nsl, H, W, NULL, NULL, NULL, NULL, NULL, dx, dy, thk, psf, xform, &S);
@@ -726,9 +740,7 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
         term_setup(mean + 3 * g, quat + 4 * g, scale + 3 * g, alpha[g], &sl[k], &T);
         const double *go = gout + sl[k].out_base;
         const int32_t *rc = rec_rect + 4 * r;
-        int i0 = rc[0] * OR_TILE, j0 = rc[1] * OR_TILE;
-        int i1 = (rc[2] + 1) * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
-        if (i1 > sl[k].W) i1 = sl[k].W;
+        int j0 = rc[1] * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
         if (j1 > sl[k].H) j1 = sl[k].H;
         double ga = 0, gmu[3] = {0, 0, 0}, GS[3][3];
         memset(GS, 0, sizeof(GS));
@@ -738,7 +750,9 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
             float b[3];
             gauss_cell_f(muf, &cc, gcell, b);
         }
-        for (int j = j0; j < j1; ++j)
+        for (int j = j0; j < j1; ++j) {
+            int i0, i1;
+            listed_cols(rc, rec_inset, r, j, sl[k].W, &i0, &i1);
             for (int i = i0; i < i1; ++i) {
                 double G = go[(int64_t)j * sl[k].W + i];
                 if (G == 0.0) continue;
@@ -758,6 +772,7 @@ void or_grad(int64_t n, const double *mean, const double *quat, const double *sc
                     for (int b = 0; b < 3; ++b)
                         GS[a][b] += G * f * 0.5 * (T.Sgi[a][b] - T.P[a][b] + Py[a] * Py[b]);
             }
+        }
         /* chain Sigma -> R, s -> q */
         const double *s = scale + 3 * g;
         double dLdR[3][3];
@@ -829,10 +844,8 @@ void or_pair_counts(int64_t n_unused, const double *mean, const double *quat, co
         int j0 = rc[1] * OR_TILE, j1 = (rc[3] + 1) * OR_TILE;
         if (j1 > sl[k].H) j1 = sl[k].H;
         for (int j = j0; j < j1; ++j) {
-            int n = j / OR_TILE - rc[1];
-            int bits = (rec_inset && n < 8) ? (int)((rec_inset[r] >> (8 * n)) & 0xFF) : 0;
-            int i0 = (rc[0] + (bits & 15)) * OR_TILE, i1 = (rc[2] - (bits >> 4) + 1) * OR_TILE;
-            if (i1 > sl[k].W) i1 = sl[k].W;
+            int i0, i1;
+            listed_cols(rc, rec_inset, r, j, sl[k].W, &i0, &i1);
             for (int i = i0; i < i1; ++i) {
                 double x[3], y[3], Py[3];
                 pixel_world(&sl[k], i, j, x);

@@ -38,7 +38,8 @@ class MgRenderStats(ctypes.Structure):
 
 class MgWsLayout(ctypes.Structure):
     _fields_ = [("rec_gid", ctypes.c_uint64), ("rec_slice", ctypes.c_uint64), ("rec_rect", ctypes.c_uint64),
-                ("tile_off", ctypes.c_uint64), ("entries", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
+                ("rec_inset", ctypes.c_uint64), ("tile_off", ctypes.c_uint64), ("entries", ctypes.c_uint64),
+                ("total_bytes", ctypes.c_uint64)]
 
 
 class MgNrf(ctypes.Structure):

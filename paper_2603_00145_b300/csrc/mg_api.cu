@@ -218,6 +218,7 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.rec_gid = take(4 * (size_t)L.cap_records);
     L.rec_slice = take(4 * (size_t)L.cap_records);
     L.rec_rect = take(8 * (size_t)L.cap_records);
+    L.rec_inset = take(8 * (size_t)L.cap_records);
     L.rec_mom = take(32 * (size_t)L.cap_records);
     L.rec_thr = take(4 * (size_t)L.cap_records);
     L.chunk_base = take(sizeof(unsigned) * 2 * (size_t)(S + 1));
@@ -559,6 +560,7 @@ static mg_status fill_layout(const WsLayout &L, mg_ws_layout *out)
     out->rec_gid = L.rec_gid;
     out->rec_slice = L.rec_slice;
     out->rec_rect = L.rec_rect;
+    out->rec_inset = L.rec_inset;
     out->tile_off = L.tile_off;
     out->entries = L.entries;
     out->total_bytes = L.total;

@@ -1,11 +1,12 @@
 // mg_bin.cu -- record pass and tile binning (count, exclusive scan, stable scatter).
 //
 // Sec. 3.3.1 of the paper restricts each voxel's sum to a local Gaussian set;
-// here that set is decided per (Gaussian, slice) record and per 16x16 tile:
-//   K1  k1_count / k1_emit : per (Gaussian, slice) K-sigma slab test of the
-//       profile-convolved covariance and the tile rectangle of the cut
-//       ellipse (the FP32 record predicate of mgauss.h, bit-exact), then the
-//       record's evaluation geometry (2D centre, conic, amplitude).
+// here that set is decided per (Gaussian, slice) record and per 8x8 tile:
+//   K1  k1_count / k1_emit / k_rec_fill : per (Gaussian, slice) K-sigma slab
+//       test of the profile-convolved covariance, the tile rectangle of the
+//       cut ellipse and its per-row culling (the FP32 record predicate of
+//       mgauss.h, bit-exact), then the record's evaluation geometry (2D
+//       centre, conic, amplitude).
 //   K2  three-phase exclusive scans (no inter-block waiting).
 //   K3  bin_hist / bin_colscan / bin_scatter : a counting sort of (record,
 //       tile) entries by tile, chunked per slice, with warp-level ranking by
@@ -275,6 +276,7 @@ __device__ bool load_gauss_pred(const float *mean, const float *quat, const floa
 
 struct PredOut {
     int il, ih, jl, jh;  // clamped pixel box
+    float cu, cv, Cuu, Cvv, Cuv, r2, ru;  // the cut ellipse (slice mm) for the row culling
 };
 
 // The terms of the predicate that depend on the Gaussian's covariance and the
@@ -283,8 +285,8 @@ struct FrameTerms {
     float Lww;
     float wmu;  // e_n . mu
     float k2sww;  // K2 * (Lww + sig2) of the frame's profile (slab test)
-    float Luw, Lvw, Luu, Lvv;
-    bool full;  // Luw..Lvv computed
+    float Luw, Lvw, Luu, Lvv, Luv;
+    bool full;  // Luw..Luv computed
 };
 
 __device__ __forceinline__ void frame_slab(const GaussPred &G, const float *Q, FrameTerms &f)
@@ -318,6 +320,7 @@ __device__ __forceinline__ void frame_full(const GaussPred &G, const float *Q, F
     float sv1 = dot3_rn(G.Sg[1][0], G.Sg[1][1], G.Sg[1][2], ev0, ev1, ev2);
     float sv2 = dot3_rn(G.Sg[2][0], G.Sg[2][1], G.Sg[2][2], ev0, ev1, ev2);
     f.Lvv = dot3_rn(ev0, ev1, ev2, sv0, sv1, sv2);
+    f.Luv = dot3_rn(ev0, ev1, ev2, su0, su1, su2);
     f.full = true;
 }
 
@@ -359,7 +362,81 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
     float ru = __fsqrt_rn(__fmul_rn(r2, Cuu));
     float rv = __fsqrt_rn(__fmul_rn(r2, Cvv));
     pixel_box(S, cu, cv, ru, rv, o);
+    o.cu = cu;
+    o.cv = cv;
+    o.Cuu = Cuu;
+    o.Cvv = Cvv;
+    o.Cuv = __fsub_rn(f.Luv, __fmul_rn(__fmul_rn(f.Luw, f.Lvw), iSww));
+    o.r2 = r2;
+    o.ru = ru;
     return true;
+}
+
+// Per-row culling of the tile rectangle (the FP32 rule of mgauss.h): for each
+// of the first eight tile rows, the tile columns that the cut ellipse reaches
+// over the row's pixel band. The band's extreme ellipse point on each side is
+// the ellipse's own (at v = cv -/+ Cuv ru/Cuu) when it lies in the band, else
+// on the band edge nearest to it (the boundary is convex in v), where the
+// chord is centred at cu + (Cuv/Cvv) d with half-width
+// sqrt((r2 - d^2/Cvv)(Cuu - Cuv^2/Cvv)). Extents grow by ru/256 + dx/1024.
+// Rectangles one tile wide are not culled. 8 bits per row: insets from the
+// rectangle's left (low nibble) and right edges, each at most 15.
+__device__ __forceinline__ float row_edge(float vext, float va, float vb, const PredOut &o, float g, float h2,
+                                          float iCvv, float sgn)
+{
+    const float v = fminf(fmaxf(vext, va), vb);
+    if (v == vext) return sgn > 0.f ? __fadd_rn(o.cu, o.ru) : __fsub_rn(o.cu, o.ru);
+    const float d = __fsub_rn(v, o.cv);
+    const float t = fmaxf(__fsub_rn(o.r2, __fmul_rn(__fmul_rn(d, d), iCvv)), 0.f);
+    const float c = __fadd_rn(o.cu, __fmul_rn(g, d)), hw = __fsqrt_rn(__fmul_rn(t, h2));
+    return sgn > 0.f ? __fadd_rn(c, hw) : __fsub_rn(c, hw);
+}
+
+__device__ __forceinline__ unsigned long long row_insets(const SliceDev &S, const PredOut &o)
+{
+    if (!(o.r2 > 0.f) || !(o.Cuu > 0.f) || !(o.Cvv > 0.f) || o.il > o.ih) return 0ull;
+    const int tx0 = o.il / MG_TILE, tx1 = o.ih / MG_TILE, ty0 = o.jl / MG_TILE, ty1 = o.jh / MG_TILE;
+    if (tx1 == tx0) return 0ull;
+    const float idx = __fdiv_rn(1.0f, S.dx);
+    const float e = __fdiv_rn(o.ru, o.Cuu);
+    const float iCvv = __fdiv_rn(1.0f, o.Cvv);
+    const float g = __fmul_rn(o.Cuv, iCvv);
+    const float h2 = fmaxf(__fsub_rn(o.Cuu, __fmul_rn(o.Cuv, g)), 0.f);
+    const float m = __fadd_rn(__fmul_rn(o.ru, 0.00390625f), __fmul_rn(S.dx, 0.0009765625f));
+    const float ce = __fmul_rn(o.Cuv, e);
+    const float vL = __fsub_rn(o.cv, ce), vR = __fadd_rn(o.cv, ce);
+    const float fil = (float)o.il, fih = (float)o.ih;
+    unsigned long long out = 0ull;
+    const int last = min(ty1 - ty0, 7);
+    for (int n = 0; n <= last; ++n) {
+        const int ty = ty0 + n;
+        const int a = max(o.jl, MG_TILE * ty), b = min(o.jh, MG_TILE * ty + MG_TILE - 1);
+        const float va = __fmul_rn(__fsub_rn((float)a, S.hy), S.dy);
+        const float vb = __fmul_rn(__fsub_rn((float)b, S.hy), S.dy);
+        const float left = row_edge(vL, va, vb, o, g, h2, iCvv, -1.f);
+        const float right = row_edge(vR, va, vb, o, g, h2, iCvv, 1.f);
+        const float lo = fmaxf(ceilf(__fadd_rn(__fmul_rn(__fsub_rn(left, m), idx), S.hx)), fil);
+        const float hi = fminf(floorf(__fadd_rn(__fmul_rn(__fadd_rn(right, m), idx), S.hx)), fih);
+        int l, r;
+        if (!(lo <= hi)) {  // no voxel column of the band: the row lists nothing
+            l = tx1 - tx0 + 1;
+            r = 0;
+        } else {
+            l = (int)lo / MG_TILE - tx0;
+            r = tx1 - (int)hi / MG_TILE;
+        }
+        l = min(l, 15);
+        r = min(r, 15);
+        out |= (unsigned long long)(l | (r << 4)) << (8 * n);
+    }
+    return out;
+}
+
+// the tile columns [first, last] that record row n (0-based in its rectangle) lists
+__device__ __forceinline__ int2 row_span(const ushort4 &rc, unsigned long long ins, int n)
+{
+    const unsigned b = n < 8 ? (unsigned)(ins >> (8 * n)) & 0xFFu : 0u;
+    return make_int2((int)rc.x + (int)(b & 15u), (int)rc.z - (int)(b >> 4));
 }
 
 // The pixel box of [cu - ru, cu + ru] x [cv - rv, cv + rv] (slice mm), clamped
@@ -684,9 +761,9 @@ __global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsig
 // slab test passed in k1_count) and the FP32 evaluation geometry (FP64 for
 // near-degenerate Gaussians in k_rec_geom_f64)
 template <bool CELLS>
-__global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ slices, const float *mean,
-                           const float *quat, const float *scale, const float *alpha, float K2, float f64_ratio,
-                           CellGrid cg, Records rec)
+__global__ void __launch_bounds__(256, 4)
+    k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ slices, const float *mean, const float *quat,
+               const float *scale, const float *alpha, float K2, float f64_ratio, CellGrid cg, Records rec)
 {
     long long nr = (long long)hdr->n_records;
     if (nr > rec.cap) nr = rec.cap;
@@ -716,11 +793,17 @@ __global__ void k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ sli
         }
         rec.rect[r] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
                                    (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        // rows are culled for max scale <= 64 min scale only (beyond, FP32
+        // cancellation in the conditional covariance can exceed the margin)
+        unsigned long long ins = 0ull;
+        if (!CELLS && fmaxf(fmaxf(sc[0], sc[1]), sc[2]) <= 64.0f * fminf(fminf(sc[0], sc[1]), sc[2]))
+            ins = row_insets(Sd, po);
+        rec.inset[r] = ins;
         // the backward's moment slots start at zero (it accumulates into them);
         // near-degenerate Gaussians accumulate in FP64
         ((float4 *)rec.mom)[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
         ((float4 *)rec.mom)[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
         const bool dg = is_degenerate(sc, f64_ratio);
         rec.f64[r] = dg ? 1 : 0;
         if (dg) {
@@ -844,7 +927,8 @@ constexpr size_t BIN_SMEM_MAX = 200 * 1024;
 
 __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *slices, int S, const unsigned *slice_rs,
                                                              const unsigned *chunk_base, const ushort4 *rect,
-                                                             unsigned *hist, int Tmax, long long cap_chunks)
+                                                             const unsigned long long *inset, unsigned *hist,
+                                                             int Tmax, long long cap_chunks)
 {
     extern __shared__ unsigned smem_u[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -860,9 +944,12 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
         for (int t = lane; t < Tk; t += 32) hs[t] = 0;
         __syncwarp();
         for (unsigned r = r0 + lane; r < r1; r += 32) {
-            ushort4 rc = rect[r];
-            for (int ty = rc.y; ty <= rc.w; ++ty)
-                for (int tx = rc.x; tx <= rc.z; ++tx) atomicAdd(&hs[ty * TX + tx], 1u);
+            const ushort4 rc = rect[r];
+            const unsigned long long ins = inset[r];
+            for (int ty = rc.y; ty <= rc.w; ++ty) {
+                const int2 sp = row_span(rc, ins, ty - rc.y);
+                for (int tx = sp.x; tx <= sp.y; ++tx) atomicAdd(&hs[ty * TX + tx], 1u);
+            }
         }
         __syncwarp();
         unsigned *hout = hist + (size_t)c * Tmax;
@@ -927,7 +1014,9 @@ __global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chu
 
 __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *slices, int S,
                                                                 const unsigned *slice_rs, const unsigned *chunk_base,
-                                                                const ushort4 *rect, const unsigned *hist, int Tmax,
+                                                                const ushort4 *rect,
+                                                                const unsigned long long *inset, const unsigned *hist,
+                                                                int Tmax,
                                                                 long long cap_chunks, const unsigned *tile_off,
                                                                 unsigned *entries, long long cap_entries,
                                                                 WsHeader *hdr)
@@ -963,18 +1052,30 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
         for (unsigned base = r0; base < r1; base += 32) {
             unsigned r = base + lane;
             bool have = r < r1;
-            ushort4 rc = have ? rect[r] : make_ushort4(0, 0, 0, 0);
-            int wdt = rc.z - rc.x + 1;
-            int area = have ? wdt * (rc.w - rc.y + 1) : 0;
+            const ushort4 rc = have ? rect[r] : make_ushort4(1, 1, 0, 0);
+            const unsigned long long ins = have ? inset[r] : 0ull;
+            int area = 0;
+            for (int ty = rc.y; ty <= rc.w; ++ty) {
+                const int2 sp = row_span(rc, ins, ty - rc.y);
+                area += max(sp.y - sp.x + 1, 0);
+            }
             int maxa = __reduce_max_sync(0xffffffffu, area);
-            int jx = rc.x, jy = rc.y;  // the rectangle's tiles in row-major order
+            // the listed tiles in row-major order: (jx, jy) with the row's last column xe
+            int jy = rc.y;
+            int2 sp = row_span(rc, ins, 0);
+            while (sp.x > sp.y && jy < (int)rc.w) sp = row_span(rc, ins, ++jy - rc.y);
+            int jx = sp.x, xe = sp.y;
             for (int j = 0; j < maxa; ++j) {
                 bool act = j < area;
                 unsigned t = 0xffffffffu;
                 if (act) t = (unsigned)(jy * TX + jx);
-                if (++jx > (int)rc.z) {
-                    jx = rc.x;
-                    ++jy;
+                if (act && ++jx > xe) {
+                    do {
+                        if (++jy > (int)rc.w) break;
+                        sp = row_span(rc, ins, jy - rc.y);
+                    } while (sp.x > sp.y);
+                    jx = sp.x;
+                    xe = sp.y;
                 }
                 unsigned peers = __match_any_sync(0xffffffffu, t);
                 unsigned before = peers & lt;
@@ -1008,6 +1109,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     rec.gid = (int *)(ws + L.rec_gid);
     rec.slice = (int *)(ws + L.rec_slice);
     rec.rect = (ushort4 *)(ws + L.rec_rect);
+    rec.inset = (unsigned long long *)(ws + L.rec_inset);
     rec.mom = (float *)(ws + L.rec_mom);
     rec.f64 = (unsigned char *)(ws + L.rec_f64);
     rec.mom64 = (double *)(ws + L.rec_mom64);
@@ -1078,7 +1180,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     int gb = (int)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
     {
         MG_PROF(MG_ST_BIN_HIST, st);
-        k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+        k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, rec.inset, hist, Tmax,
                                                      L.cap_chunks);
     }
     long long tot = (long long)S * Tmax;
@@ -1094,7 +1196,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_BIN_SCATTER, st);
-        k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, hist, Tmax,
+        k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, rec.inset, hist, Tmax,
                                                         L.cap_chunks, tile_off, entries, L.cap_entries, hdr);
     }
 }

@@ -136,6 +136,7 @@ struct Records {
     int *gid;           // Gaussian id
     int *slice;         // global slice id
     ushort4 *rect;      // tile rectangle (tx0, ty0, tx1, ty1)
+    unsigned long long *inset;  // per tile row (first 8): tile-column insets, left (low nibble) and right
     float *mom;         // [cap][8] backward moments (6 used)
     float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
     int4 *cell;         // MG_LOCAL_CELLS: the Gaussian's cell (x, y, z, 0); else unused
@@ -147,7 +148,7 @@ struct Records {
 // Workspace layout, computed identically on the host for fwd, bwd and the
 // size query.
 struct WsLayout {
-    size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_mom, rec_thr;
+    size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_inset, rec_mom, rec_thr;
     size_t chunk_base, hist, tile_cnt, tile_off, tile_list, tile_loss, entries, gcnt, bits, gmap, rec_grad, rec_cell, rec_f64,
         rec_mom64, total;
     long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;

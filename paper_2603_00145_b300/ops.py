@@ -162,16 +162,17 @@ def mg_sample_ws_layout(n: int, G: int, opts: L.MgOpts) -> dict:
 
 
 def read_bins(ws, layout: dict, n_records: int, n_tiles: int, n_entries: int):
-    """Copies of the records (gid, slice, rect) and tile bins from a workspace."""
+    """Copies of the records (gid, slice, rect, row insets) and tile bins from a workspace."""
     def view(off, count, dtype, width=1):
         nbytes = count * width * torch.tensor([], dtype=dtype).element_size()
         return ws[off:off + nbytes].view(dtype).reshape(count, width).cpu()
     gid = view(layout["rec_gid"], n_records, torch.int32)[:, 0]
     sl = view(layout["rec_slice"], n_records, torch.int32)[:, 0]
     rect = view(layout["rec_rect"], n_records, torch.int16, 4).to(torch.int32) & 0xFFFF
+    inset = view(layout["rec_inset"], n_records, torch.int64)[:, 0]
     toff = view(layout["tile_off"], n_tiles + 1, torch.int32)[:, 0].to(torch.int64) & 0xFFFFFFFF
     ent = view(layout["entries"], n_entries, torch.int32)[:, 0].to(torch.int64) & 0xFFFFFFFF
-    return gid, sl, rect, toff, ent
+    return gid, sl, rect, inset, toff, ent
 
 
 def mg_render_stats_get(ws, stream=None) -> dict:

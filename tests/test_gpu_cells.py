@@ -33,10 +33,11 @@ def test_cells_records_render_and_gradients(seed, res, radius):
     out = R.forward(m, q, s, a)
     torch.cuda.synchronize()
     rec = orc.records(G, stacks, cells=cells)
-    st, (gid, sl, rect, toff, ent) = gpu_bins(R, G.n)
+    st, (gid, sl, rect, inset, toff, ent) = gpu_bins(R, G.n)
     assert st["status"] == 0 and st["records"] == rec.n
     assert np.array_equal(gid.numpy(), rec.gid) and np.array_equal(sl.numpy(), rec.slice)
     assert np.array_equal(rect.numpy(), rec.rect)
+    assert np.array_equal(inset.numpy().view(np.uint64), rec.inset)
     want = orc.render(G, stacks, rec, cells=cells)
     assert_render_close(out.cpu().numpy(), want, "cells fwd")
     gout = np.random.default_rng(seed).normal(size=want.size).astype(np.float32)

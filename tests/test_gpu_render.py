@@ -28,13 +28,14 @@ def _mixed_case(seed, n=300, neg=0.1):
 
 def _check_bins(G, stacks, R, K=3.0):
     rec = orc.records(G, stacks, K)
-    st, (gid, sl, rect, toff, ent) = gpu_bins(R, G.n)
+    st, (gid, sl, rect, inset, toff, ent) = gpu_bins(R, G.n)
     assert st["status"] == 0
     assert st["tiles"] == R.dev.n_tiles == sum(
         s.n_slices * -(-s.W // orc.TILE) * -(-s.H // orc.TILE) for s in stacks)
     assert st["records"] == rec.n
     assert np.array_equal(gid.numpy(), rec.gid) and np.array_equal(sl.numpy(), rec.slice)
     assert np.array_equal(rect.numpy(), rec.rect)
+    assert np.array_equal(inset.numpy().view(np.uint64), rec.inset)
     counts, offs, ids = orc.tile_bins(rec, stacks)
     assert st["entries"] == ids.size
     assert np.array_equal(toff.numpy(), offs)

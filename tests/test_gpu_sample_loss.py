@@ -32,10 +32,11 @@ def test_sampler_parity(Gd, h):
 
     st = S.last_stats
     lay = mg_sample_ws_layout(G.n, Gd, _opts(3.0, 100.0, *S.caps))
-    gid, sl, rect, toff, ent = read_bins(S.ws, lay, st["records"], st["tiles"], st["entries"])
+    gid, sl, rect, inset, toff, ent = read_bins(S.ws, lay, st["records"], st["tiles"], st["entries"])
     rec = orc.records(G, [orc.volume_planes(Gd, h, centre)])
     assert np.array_equal(gid.numpy(), rec.gid) and np.array_equal(sl.numpy(), rec.slice)
     assert np.array_equal(rect.numpy(), rec.rect)
+    assert np.array_equal(inset.numpy().view(np.uint64), rec.inset)
 
 
 def test_sampler_is_e7_and_conserves_mass():
