@@ -256,9 +256,10 @@ mg_status mg_render_pose_grad(const mg_gaussians *g, const mg_stack *stacks, int
  * offsets, inside the workspace, of the per-record arrays and of the tile
  * bins written by mg_render_fwd / mg_sample_volume. Records are ordered by
  * global slice, then ascending Gaussian id (the first `records` entries of
- * each array are valid): rec_gid int32, rec_slice int32, rec_rect uint16x4
- * (tx0, ty0, tx1, ty1), rec_inset uint64 (byte n: l_n | r_n << 4 of the row
- * culling above). Bins: tile_off uint32 [tiles+1] (exclusive offsets,
+ * each array are valid): rec_gid int32, rec_slice int32; rec_rect: 16-byte
+ * records of uint16x4 (tx0, ty0, tx1, ty1) followed by a uint64 of row insets
+ * (byte n: l_n | r_n << 4 of the row culling above), rec_inset = rec_rect + 8
+ * (same 16-byte stride). Bins: tile_off uint32 [tiles+1] (exclusive offsets,
  * global tile order = stacks, slices, ty*TX+tx), entries uint32 (record
  * ids). Returns MG_ERR_INVALID_ARG on bad arguments.
  */

@@ -217,8 +217,8 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.rec_geo2 = take(8 * (size_t)L.cap_records);
     L.rec_gid = take(4 * (size_t)L.cap_records);
     L.rec_slice = take(4 * (size_t)L.cap_records);
-    L.rec_rect = take(8 * (size_t)L.cap_records);
-    L.rec_inset = take(8 * (size_t)L.cap_records);
+    L.rec_rect = take(16 * (size_t)L.cap_records);  // RecTiles: rect, then the row insets
+    L.rec_inset = L.rec_rect + 8;
     L.rec_mom = take(32 * (size_t)L.cap_records);
     L.rec_thr = take(4 * (size_t)L.cap_records);
     L.chunk_base = take(sizeof(unsigned) * 2 * (size_t)(S + 1));

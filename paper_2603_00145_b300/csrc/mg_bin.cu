@@ -381,15 +381,12 @@ __device__ __forceinline__ bool record_predicate(const GaussPred &G, const Slice
 // sqrt((r2 - d^2/Cvv)(Cuu - Cuv^2/Cvv)). Extents grow by ru/256 + dx/1024.
 // Rectangles one tile wide are not culled. 8 bits per row: insets from the
 // rectangle's left (low nibble) and right edges, each at most 15.
-__device__ __forceinline__ float row_edge(float vext, float va, float vb, const PredOut &o, float g, float h2,
-                                          float iCvv, float sgn)
+// the chord of the cut ellipse at v (v != the side's extreme): centre and half-width
+__device__ __forceinline__ float2 row_chord(float v, const PredOut &o, float g, float h2, float iCvv)
 {
-    const float v = fminf(fmaxf(vext, va), vb);
-    if (v == vext) return sgn > 0.f ? __fadd_rn(o.cu, o.ru) : __fsub_rn(o.cu, o.ru);
     const float d = __fsub_rn(v, o.cv);
     const float t = fmaxf(__fsub_rn(o.r2, __fmul_rn(__fmul_rn(d, d), iCvv)), 0.f);
-    const float c = __fadd_rn(o.cu, __fmul_rn(g, d)), hw = __fsqrt_rn(__fmul_rn(t, h2));
-    return sgn > 0.f ? __fadd_rn(c, hw) : __fsub_rn(c, hw);
+    return make_float2(__fadd_rn(o.cu, __fmul_rn(g, d)), __fsqrt_rn(__fmul_rn(t, h2)));
 }
 
 __device__ __forceinline__ unsigned long long row_insets(const SliceDev &S, const PredOut &o)
@@ -413,8 +410,14 @@ __device__ __forceinline__ unsigned long long row_insets(const SliceDev &S, cons
         const int a = max(o.jl, MG_TILE * ty), b = min(o.jh, MG_TILE * ty + MG_TILE - 1);
         const float va = __fmul_rn(__fsub_rn((float)a, S.hy), S.dy);
         const float vb = __fmul_rn(__fsub_rn((float)b, S.hy), S.dy);
-        const float left = row_edge(vL, va, vb, o, g, h2, iCvv, -1.f);
-        const float right = row_edge(vR, va, vb, o, g, h2, iCvv, 1.f);
+        // both sides usually clamp to the same band edge: one chord serves both
+        const float wl = fminf(fmaxf(vL, va), vb), wr = fminf(fmaxf(vR, va), vb);
+        const bool el = wl == vL, er = wr == vR;
+        float2 cl = make_float2(0.f, 0.f), cr = make_float2(0.f, 0.f);
+        if (!el) cl = row_chord(wl, o, g, h2, iCvv);
+        if (!er) cr = (!el && wr == wl) ? cl : row_chord(wr, o, g, h2, iCvv);
+        const float left = el ? __fsub_rn(o.cu, o.ru) : __fsub_rn(cl.x, cl.y);
+        const float right = er ? __fadd_rn(o.cu, o.ru) : __fadd_rn(cr.x, cr.y);
         const float lo = fmaxf(ceilf(__fadd_rn(__fmul_rn(__fsub_rn(left, m), idx), S.hx)), fil);
         const float hi = fminf(floorf(__fadd_rn(__fmul_rn(__fadd_rn(right, m), idx), S.hx)), fih);
         int l, r;
@@ -430,6 +433,17 @@ __device__ __forceinline__ unsigned long long row_insets(const SliceDev &S, cons
         out |= (unsigned long long)(l | (r << 4)) << (8 * n);
     }
     return out;
+}
+
+// one 16-byte load of a record's listed tiles
+__device__ __forceinline__ RecTiles load_tiles(const RecTiles *p)
+{
+    const uint4 u = __ldg((const uint4 *)p);
+    RecTiles t;
+    t.rect = make_ushort4((unsigned short)(u.x & 0xFFFFu), (unsigned short)(u.x >> 16),
+                          (unsigned short)(u.y & 0xFFFFu), (unsigned short)(u.y >> 16));
+    t.inset = (unsigned long long)u.z | ((unsigned long long)u.w << 32);
+    return t;
 }
 
 // the tile columns [first, last] that record row n (0-based in its rectangle) lists
@@ -791,15 +805,17 @@ __global__ void __launch_bounds__(256, 4)
             frame_slab(G, Sd.Q, ft);
             record_predicate(G, Sd, K2, ft, po);  // true: the slab test of k1_count
         }
-        rec.rect[r] = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
-                                   (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
+        RecTiles rt;
+        rt.rect = make_ushort4((unsigned short)(po.il / MG_TILE), (unsigned short)(po.jl / MG_TILE),
+                               (unsigned short)(po.ih / MG_TILE), (unsigned short)(po.jh / MG_TILE));
         float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
         // rows are culled for max scale <= 64 min scale only (beyond, FP32
         // cancellation in the conditional covariance can exceed the margin)
         unsigned long long ins = 0ull;
         if (!CELLS && fmaxf(fmaxf(sc[0], sc[1]), sc[2]) <= 64.0f * fminf(fminf(sc[0], sc[1]), sc[2]))
             ins = row_insets(Sd, po);
-        rec.inset[r] = ins;
+        rt.inset = ins;
+        rec.tiles[r] = rt;
         // the backward's moment slots start at zero (it accumulates into them);
         // near-degenerate Gaussians accumulate in FP64
         ((float4 *)rec.mom)[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -926,8 +942,8 @@ constexpr int BIN_WARPS = 4;
 constexpr size_t BIN_SMEM_MAX = 200 * 1024;
 
 __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *slices, int S, const unsigned *slice_rs,
-                                                             const unsigned *chunk_base, const ushort4 *rect,
-                                                             const unsigned long long *inset, unsigned *hist,
+                                                             const unsigned *chunk_base, const RecTiles *tiles,
+                                                             unsigned *hist,
                                                              int Tmax, long long cap_chunks)
 {
     extern __shared__ unsigned smem_u[];
@@ -944,8 +960,9 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
         for (int t = lane; t < Tk; t += 32) hs[t] = 0;
         __syncwarp();
         for (unsigned r = r0 + lane; r < r1; r += 32) {
-            const ushort4 rc = rect[r];
-            const unsigned long long ins = inset[r];
+            const RecTiles rt = load_tiles(tiles + r);
+            const ushort4 rc = rt.rect;
+            const unsigned long long ins = rt.inset;
             for (int ty = rc.y; ty <= rc.w; ++ty) {
                 const int2 sp = row_span(rc, ins, ty - rc.y);
                 for (int tx = sp.x; tx <= sp.y; ++tx) atomicAdd(&hs[ty * TX + tx], 1u);
@@ -1014,8 +1031,7 @@ __global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chu
 
 __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *slices, int S,
                                                                 const unsigned *slice_rs, const unsigned *chunk_base,
-                                                                const ushort4 *rect,
-                                                                const unsigned long long *inset, const unsigned *hist,
+                                                                const RecTiles *tiles, const unsigned *hist,
                                                                 int Tmax,
                                                                 long long cap_chunks, const unsigned *tile_off,
                                                                 unsigned *entries, long long cap_entries,
@@ -1052,8 +1068,12 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
         for (unsigned base = r0; base < r1; base += 32) {
             unsigned r = base + lane;
             bool have = r < r1;
-            const ushort4 rc = have ? rect[r] : make_ushort4(1, 1, 0, 0);
-            const unsigned long long ins = have ? inset[r] : 0ull;
+            RecTiles rt;
+            rt.rect = make_ushort4(1, 1, 0, 0);
+            rt.inset = 0ull;
+            if (have) rt = load_tiles(tiles + r);
+            const ushort4 rc = rt.rect;
+            const unsigned long long ins = rt.inset;
             int area = 0;
             for (int ty = rc.y; ty <= rc.w; ++ty) {
                 const int2 sp = row_span(rc, ins, ty - rc.y);
@@ -1108,8 +1128,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     rec.geo2 = (float2 *)(ws + L.rec_geo2);
     rec.gid = (int *)(ws + L.rec_gid);
     rec.slice = (int *)(ws + L.rec_slice);
-    rec.rect = (ushort4 *)(ws + L.rec_rect);
-    rec.inset = (unsigned long long *)(ws + L.rec_inset);
+    rec.tiles = (RecTiles *)(ws + L.rec_rect);
     rec.mom = (float *)(ws + L.rec_mom);
     rec.f64 = (unsigned char *)(ws + L.rec_f64);
     rec.mom64 = (double *)(ws + L.rec_mom64);
@@ -1180,7 +1199,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     int gb = (int)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
     {
         MG_PROF(MG_ST_BIN_HIST, st);
-        k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, rec.inset, hist, Tmax,
+        k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
                                                      L.cap_chunks);
     }
     long long tot = (long long)S * Tmax;
@@ -1196,7 +1215,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_BIN_SCATTER, st);
-        k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.rect, rec.inset, hist, Tmax,
+        k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
                                                         L.cap_chunks, tile_off, entries, L.cap_entries, hdr);
     }
 }

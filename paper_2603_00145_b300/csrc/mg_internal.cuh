@@ -130,13 +130,19 @@ struct WsHeader {
 };
 
 // Records are stored as structure-of-arrays.
+// a record's listed tiles: the tile rectangle (tx0, ty0, tx1, ty1) and, per
+// tile row (first 8), the tile-column insets, left (low nibble) and right
+struct __align__(16) RecTiles {
+    ushort4 rect;
+    unsigned long long inset;
+};
+
 struct Records {
     float4 *geo;        // (pcx, pcy, A, B2): centre in pixels, conic (log2 units)
     float2 *geo2;       // (C, amp)
     int *gid;           // Gaussian id
     int *slice;         // global slice id
-    ushort4 *rect;      // tile rectangle (tx0, ty0, tx1, ty1)
-    unsigned long long *inset;  // per tile row (first 8): tile-column insets, left (low nibble) and right
+    RecTiles *tiles;    // listed tiles
     float *mom;         // [cap][8] backward moments (6 used)
     float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
     int4 *cell;         // MG_LOCAL_CELLS: the Gaussian's cell (x, y, z, 0); else unused

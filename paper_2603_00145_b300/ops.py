@@ -168,8 +168,9 @@ def read_bins(ws, layout: dict, n_records: int, n_tiles: int, n_entries: int):
         return ws[off:off + nbytes].view(dtype).reshape(count, width).cpu()
     gid = view(layout["rec_gid"], n_records, torch.int32)[:, 0]
     sl = view(layout["rec_slice"], n_records, torch.int32)[:, 0]
-    rect = view(layout["rec_rect"], n_records, torch.int16, 4).to(torch.int32) & 0xFFFF
-    inset = view(layout["rec_inset"], n_records, torch.int64)[:, 0]
+    tiles = view(layout["rec_rect"], n_records, torch.int16, 8)  # 16-byte records: rect, row insets
+    rect = tiles[:, :4].to(torch.int32) & 0xFFFF
+    inset = tiles[:, 4:].contiguous().view(torch.int64)[:, 0]
     toff = view(layout["tile_off"], n_tiles + 1, torch.int32)[:, 0].to(torch.int64) & 0xFFFFFFFF
     ent = view(layout["entries"], n_entries, torch.int32)[:, 0].to(torch.int64) & 0xFFFFFFFF
     return gid, sl, rect, inset, toff, ent
