@@ -7,7 +7,7 @@
 //       cut ellipse and its per-row culling (the FP32 record predicate of
 //       mgauss.h, bit-exact), then the record's evaluation geometry (2D
 //       centre, conic, amplitude).
-//   K2  three-phase exclusive scans (no inter-block waiting).
+//   K2  two-phase exclusive scans (no inter-block waiting).
 //   K3  bin_hist / bin_colscan / bin_scatter : a counting sort of (record,
 //       tile) entries by tile, chunked per slice, with warp-level ranking by
 //       __match_any_sync so the order inside each tile list is reproducible.
@@ -79,7 +79,8 @@ void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_
 }
 
 // ---------------------------------------------------------------------------
-// three-phase exclusive scan of uint32 (totals in uint64, outputs saturate)
+// two-phase exclusive scan of uint32 (block totals, then each block sums the
+// totals before it and scans its range; totals in uint64, outputs saturate)
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long *total)
@@ -136,17 +137,6 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(ScanPair sp, unsigned l
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_part(unsigned long long *parts, int nb, ScanPair sp)
-{
-    unsigned long long *part = parts + (size_t)blockIdx.x * nb;
-    unsigned long long *total_out = sp.total[blockIdx.x];
-    unsigned long long v = threadIdx.x < nb ? part[threadIdx.x] : 0ull;
-    unsigned long long tot;
-    unsigned long long pre = block_exclusive_scan<SCAN_NT>(v, &tot);
-    if (threadIdx.x < nb) part[threadIdx.x] = pre;
-    if (threadIdx.x == 0 && total_out) *total_out = tot;
-}
-
 __global__ void __launch_bounds__(SCAN_NT) k_scan_down(ScanPair sp, const unsigned long long *parts, int write_end)
 {
     const unsigned *in = sp.in[blockIdx.y];
@@ -156,7 +146,13 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_down(ScanPair sp, const unsign
     long long per = (n + gridDim.x - 1) / gridDim.x;
     long long b0 = (long long)blockIdx.x * per;
     long long b1 = b0 + per < n ? b0 + per : n;
-    unsigned long long run = part[blockIdx.x];
+    // this block's offset: the totals of the blocks before it (at most MG_SCAN_BLOCKS)
+    unsigned long long run;
+    {
+        unsigned long long v = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += SCAN_NT) v += part[i];
+        block_exclusive_scan<SCAN_NT>(v, &run);
+    }
     for (long long base = b0; base < b1; base += (long long)SCAN_NT * SCAN_ITEMS) {
         unsigned v[SCAN_ITEMS];
         unsigned long long s = 0;
@@ -175,8 +171,10 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_down(ScanPair sp, const unsign
         }
         run += tot;
     }
-    if (write_end && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
-        out[n] = run > 0xffffffffull ? 0xffffffffu : (unsigned)run;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        if (write_end) out[n] = run > 0xffffffffull ? 0xffffffffu : (unsigned)run;
+        if (sp.total[blockIdx.y]) *sp.total[blockIdx.y] = run;
+    }
 }
 
 void mg_launch_scan_u32(const unsigned *in, unsigned *out, long long n_host, const unsigned long long *n_dev,
@@ -190,11 +188,10 @@ void mg_launch_scan_u32(const unsigned *in, unsigned *out, long long n_host, con
     sp.total[0] = sp.total[1] = total_out;
     int nb = MG_SCAN_BLOCKS;
     k_scan_reduce<<<nb, SCAN_NT, 0, st>>>(sp, part);
-    k_scan_part<<<1, SCAN_NT, 0, st>>>(part, nb, sp);
     k_scan_down<<<nb, SCAN_NT, 0, st>>>(sp, part, 1);
 }
 
-// two independent exclusive scans in the same three launches (part holds
+// two independent exclusive scans in the same two launches (part holds
 // 2 * MG_SCAN_BLOCKS entries)
 void mg_launch_scan2_u32(const unsigned *in0, unsigned *out0, long long n0, unsigned long long *total0,
                          const unsigned *in1, unsigned *out1, long long n1, unsigned long long *total1,
@@ -211,7 +208,6 @@ void mg_launch_scan2_u32(const unsigned *in0, unsigned *out0, long long n0, unsi
     sp.total[1] = total1;
     int nb = MG_SCAN_BLOCKS;
     k_scan_reduce<<<dim3(nb, 2), SCAN_NT, 0, st>>>(sp, part);
-    k_scan_part<<<2, SCAN_NT, 0, st>>>(part, nb, sp);
     k_scan_down<<<dim3(nb, 2), SCAN_NT, 0, st>>>(sp, part, 1);
 }
 
@@ -1047,20 +1043,30 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
 
 // per (slice, tile): exclusive prefix over the slice's chunks; tile totals;
 // and the tile list of the render kernels: tiles with records appended at
-// the front, tiles without at the back (warp-aggregated atomics; the order
-// within each part is arbitrary and does not change any result)
-__global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chunk_base, unsigned *hist, int Tmax,
-                              long long cap_chunks, unsigned *tile_cnt, unsigned *tile_list, long long n_tiles,
-                              WsHeader *hdr)
+// the front, tiles without at the back (counts aggregated per block, one
+// atomic per block and part; the order within each part is arbitrary and
+// does not change any result)
+constexpr int COLSCAN_NT = 256;
+__global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slices, int S, const unsigned *chunk_base,
+                                                            unsigned *hist, int Tmax, long long cap_chunks,
+                                                            unsigned *tile_cnt, unsigned *tile_list,
+                                                            long long n_tiles, WsHeader *hdr)
 {
-    long long total = (long long)S * Tmax;
+    __shared__ unsigned wb[COLSCAN_NT / 32], wi[COLSCAN_NT / 32];
+    __shared__ unsigned base_b, base_i;
+    const long long total = (long long)S * Tmax;
     const unsigned lt = lanemask_lt();
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        int k = (int)(idx / Tmax), t = (int)(idx % Tmax);
-        const int Tk = slices[k].TX * slices[k].TY;
-        const bool real = t < Tk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long blk = (long long)blockIdx.x * COLSCAN_NT; blk < total; blk += (long long)gridDim.x * COLSCAN_NT) {
+        const long long idx = blk + threadIdx.x;
+        int k = 0, t = 0;
+        bool real = false;
         unsigned run = 0;
+        if (idx < total) {
+            k = (int)(idx / Tmax);
+            t = (int)(idx % Tmax);
+            real = t < slices[k].TX * slices[k].TY;
+        }
         if (real) {
             unsigned c0 = chunk_base[k], c1 = chunk_base[k + 1];
             if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
@@ -1083,19 +1089,31 @@ __global__ void k_bin_colscan(const SliceDev *slices, int S, const unsigned *chu
             }
             tile_cnt[slices[k].tile_base + t] = run;
         }
-        const unsigned am = __activemask();
         const bool busy = real && run > 0, idle = real && run == 0;
-        const unsigned bb = __ballot_sync(am, busy), ib = __ballot_sync(am, idle);
-        const int leader = __ffs(am) - 1;
-        unsigned pb = 0, pi = 0;
-        if ((int)(threadIdx.x & 31) == leader) {
-            if (bb) pb = atomicAdd(&hdr->n_busy, (unsigned)__popc(bb));
-            if (ib) pi = atomicAdd(&hdr->n_idle, (unsigned)__popc(ib));
+        const unsigned bb = __ballot_sync(0xffffffffu, busy), ib = __ballot_sync(0xffffffffu, idle);
+        if (lane == 0) {
+            wb[w] = __popc(bb);
+            wi[w] = __popc(ib);
         }
-        pb = __shfl_sync(am, pb, leader);
-        pi = __shfl_sync(am, pi, leader);
-        if (busy) tile_list[pb + __popc(bb & lt)] = (unsigned)(slices[k].tile_base + t);
-        if (idle) tile_list[n_tiles - 1 - (long long)(pi + __popc(ib & lt))] = (unsigned)(slices[k].tile_base + t);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned sb = 0, si = 0;
+            for (int i = 0; i < COLSCAN_NT / 32; ++i) {
+                const unsigned a = wb[i], b = wi[i];
+                wb[i] = sb;
+                wi[i] = si;
+                sb += a;
+                si += b;
+            }
+            base_b = sb ? atomicAdd(&hdr->n_busy, sb) : 0u;
+            base_i = si ? atomicAdd(&hdr->n_idle, si) : 0u;
+        }
+        __syncthreads();
+        if (busy) tile_list[base_b + wb[w] + __popc(bb & lt)] = (unsigned)(slices[k].tile_base + t);
+        if (idle)
+            tile_list[n_tiles - 1 - (long long)(base_i + wi[w] + __popc(ib & lt))] =
+                (unsigned)(slices[k].tile_base + t);
+        __syncthreads();  // wb, wi and the bases are rewritten by the next round
     }
 }
 
@@ -1275,7 +1293,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     int gc = (int)((tot + 255) / 256 < 148 * 32 ? (tot + 255) / 256 : 148 * 32);
     {
         MG_PROF(MG_ST_BIN_COLSCAN, st);
-        k_bin_colscan<<<gc, 256, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt,
+        k_bin_colscan<<<gc, COLSCAN_NT, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt,
                                           (unsigned *)(ws + L.tile_list), L.n_tiles, hdr);
     }
     {

@@ -10,7 +10,7 @@
 #define MG_MAX_STACKS 32
 #define MG_MAX_TILES_SLICE 16384 // 1024 x 1024 pixels
 #define MG_CHUNK 512           // records per binning chunk (one warp each)
-#define MG_SCAN_BLOCKS 256     // blocks of the three-phase scan
+#define MG_SCAN_BLOCKS 256     // blocks of the two-phase scan
 
 // device status flags (workspace header)
 #define MG_FLAG_CAP_RECORDS 1u
