@@ -1070,22 +1070,17 @@ __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slic
         if (real) {
             unsigned c0 = chunk_base[k], c1 = chunk_base[k + 1];
             if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
-            unsigned c = c0;
-            // eight independent loads in flight per thread before the dependent stores
-            for (; c + 8 <= c1; c += 8) {
-                unsigned v[8];
+            // sixteen independent (guarded) loads in flight per thread before the
+            // dependent stores: a slice's column of chunk counts in one or two rounds
+            for (unsigned c = c0; c < c1; c += 16) {
+                unsigned v[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = __ldcg(&hist[(size_t)(c + u) * Tmax + t]);
+                for (int u = 0; u < 16; ++u) v[u] = (c + u < c1) ? __ldcg(&hist[(size_t)(c + u) * Tmax + t]) : 0u;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    hist[(size_t)(c + u) * Tmax + t] = run;
+                for (int u = 0; u < 16; ++u) {
+                    if (c + u < c1) hist[(size_t)(c + u) * Tmax + t] = run;
                     run += v[u];
                 }
-            }
-            for (; c < c1; ++c) {
-                unsigned v = hist[(size_t)c * Tmax + t];
-                hist[(size_t)c * Tmax + t] = run;
-                run += v;
             }
             tile_cnt[slices[k].tile_base + t] = run;
         }
