@@ -615,9 +615,11 @@ __device__ __forceinline__ bool is_degenerate(const float *s, float ratio)
 constexpr int K1_NT = 256;
 constexpr int K1_SMEM_SLICES = 256;  // slices staged in shared memory at a time
 
-// One thread per Gaussian walks the slices in windows of 32 (staged in shared
-// memory); the frame terms are formed at the first slice of each run of
-// slices sharing a frame and carried across windows while it continues.
+// One thread per (Gaussian, window of 32 slices): blockIdx.y is the window
+// (staged in shared memory), so the tests of one Gaussian run in parallel
+// over the windows; the frame terms are formed at the first slice of each run
+// of slices sharing a frame. gcnt must be zero on entry (summed over the
+// windows with one atomic per thread).
 // Within a window, slices form runs that share a frame; along a run whose
 // plane offsets e_n . t are monotone, the slab test can only pass on the
 // contiguous range of slices whose offset lies within the slab's half-width
@@ -634,23 +636,24 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
     __shared__ SliceDev ssl[32];
     __shared__ float sent[32];
     __shared__ int run_end[32], run_dir[32];  // at a run's first slice: its last slice, +1/-1 monotone, 0 not
+    __shared__ float sig2max;                  // the largest profile variance in the window
     const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
     const long long wg = g >> 5;
     const int lane = threadIdx.x & 31;
+    const int wd = blockIdx.y, k0 = wd * 32, nk = min(32, S - k0);
     GaussPred G;
     bool valid = false;
     if (g < n) {
         valid = load_gauss_pred(mean, quat, scale, alpha, g, G);
-        if (!valid) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
-        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
-        if (valid && is_degenerate(sc, f64_ratio)) atomicOr(&hdr->flags, MG_FLAG_DEGENERATE);
+        if (wd == 0) {
+            if (!valid) atomicOr(&hdr->flags, MG_FLAG_NOT_FINITE);
+            float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+            if (valid && is_degenerate(sc, f64_ratio)) atomicOr(&hdr->flags, MG_FLAG_DEGENERATE);
+        }
     }
     FrameTerms f;
     f.full = false;
-    unsigned total = 0;
-    for (int k0 = 0, wd = 0; k0 < S; k0 += 32, ++wd) {
-        const int nk = min(32, S - k0);
-        __syncthreads();
+    {
         for (int i = threadIdx.x; i < nk; i += K1_NT) {
             ssl[i] = slices[k0 + i];
             sent[i] = slices[k0 + i].ent;
@@ -671,56 +674,85 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
                 run_end[l] = e;
                 run_dir[l] = (inc & steps) == steps ? 1 : ((dec & steps) == steps ? -1 : 0);
             }
+            const float m = __reduce_max_sync(0xffffffffu, in ? __float_as_uint(ssl[l].sig2) : 0u);
+            if (l == 0) sig2max = __uint_as_float(m);  // variances are >= 0: their bits order as they do
         }
         __syncthreads();
+        // cheap screen for slices tested one by one: |e_n . mu - e_n . t| beyond
+        // K sqrt(s_max^2 + sig2max), grown by 2^-8 of it plus 2^-18 |mu|_1 (far more
+        // than the FP32 rounding of the exact test and of this bound), fails the
+        // exact test, since e_n . Sigma e_n <= s_max^2
+        float bnd = 0.f;
+        if (valid) {
+            const float sm = fmaxf(fmaxf(scale[3 * g], scale[3 * g + 1]), scale[3 * g + 2]);
+            bnd = sqrtf(K2 * (sm * sm + sig2max)) * 1.00390625f +
+                  (fabsf(G.mu[0]) + fabsf(G.mu[1]) + fabsf(G.mu[2])) * 3.814697265625e-6f;
+        }
         unsigned word = 0, myc = 0;  // myc: the warp's count at slice k0 + lane
         for (int a = 0; a < nk;) {
             const int e = run_end[a], dir = run_dir[a];
-            int lo = a, hi = e;  // this lane's candidate slices in the run
-            if (valid) {
-                // the frame terms carry over from the previous window's last run
-                // when its first slice continues that frame
-                if (!(a == 0 && k0 > 0 && ssl[0].same_frame)) {
-                    frame_slab(G, ssl[a].Q, f);
-                    f.k2sww = __fmul_rn(K2, __fadd_rn(f.Lww, ssl[a].sig2));
-                }
-                if (dir != 0) {
-                    // offsets within R of e_n . mu: R exceeds the test's sqrt(K2 Sww) by 2^-9
-                    // of it plus 2^-20 |e_n . mu|, more than the FP32 rounding of the test
-                    // and of the bounds below
-                    const float R = sqrtf(f.k2sww) * 1.001953125f + fabsf(f.wmu) * 9.5367431640625e-7f;
-                    const float olo = f.wmu - R, ohi = f.wmu + R;
-                    int b0 = a, b1 = e + 1;
-                    if (dir > 0) {
-                        while (b0 < b1) {  // first offset >= olo
-                            const int m = (b0 + b1) >> 1;
-                            if (sent[m] < olo) b0 = m + 1; else b1 = m;
-                        }
-                        lo = b0;
-                        b1 = e + 1;
-                        while (b0 < b1) {  // first offset > ohi
-                            const int m = (b0 + b1) >> 1;
-                            if (sent[m] <= ohi) b0 = m + 1; else b1 = m;
-                        }
-                        hi = b0 - 1;
-                    } else {
-                        while (b0 < b1) {  // first offset <= ohi
-                            const int m = (b0 + b1) >> 1;
-                            if (sent[m] > ohi) b0 = m + 1; else b1 = m;
-                        }
-                        lo = b0;
-                        b1 = e + 1;
-                        while (b0 < b1) {  // first offset < olo
-                            const int m = (b0 + b1) >> 1;
-                            if (sent[m] >= olo) b0 = m + 1; else b1 = m;
-                        }
-                        hi = b0 - 1;
+            if (!(dir != 0 && e - a >= 7)) {
+                // short runs (moving slices): the screen, then the exact test slice by slice
+                bool cand = false;
+                if (valid) {
+                    const float *Q = ssl[a].Q;
+                    const float wm = fmaf(Q[2], G.mu[0], fmaf(Q[5], G.mu[1], Q[8] * G.mu[2]));
+                    for (int kk = a; kk <= e; ++kk) cand |= fabsf(wm - sent[kk]) <= bnd;
+                    if (cand) {
+                        frame_slab(G, Q, f);
+                        f.k2sww = __fmul_rn(K2, __fadd_rn(f.Lww, ssl[a].sig2));
                     }
                 }
+                if (__any_sync(0xffffffffu, cand)) {  // else every lane fails every slice of the run
+                    for (int kk = a; kk <= e; ++kk) {
+                        const bool ex = cand && slab_test(f, ssl[kk]);  // off the screen: fails the test
+                        const unsigned c = __popc(__ballot_sync(0xffffffffu, ex));
+                        if (lane == kk) myc = c;
+                        word |= (unsigned)ex << kk;
+                    }
+                }
+                a = e + 1;
+                continue;
             }
-            if (!valid || lo > hi) {  // nothing to test: neutral in the warp's union
-                lo = e + 1;
-                hi = a - 1;
+            int lo = e + 1, hi = a - 1;  // this lane's candidate slices in the run (none)
+            if (valid) {
+                frame_slab(G, ssl[a].Q, f);
+                f.k2sww = __fmul_rn(K2, __fadd_rn(f.Lww, ssl[a].sig2));
+                // offsets within R of e_n . mu: R exceeds the test's sqrt(K2 Sww) by 2^-9
+                // of it plus 2^-20 |e_n . mu|, more than the FP32 rounding of the test
+                // and of the bounds below
+                const float R = sqrtf(f.k2sww) * 1.001953125f + fabsf(f.wmu) * 9.5367431640625e-7f;
+                const float olo = f.wmu - R, ohi = f.wmu + R;
+                int b0 = a, b1 = e + 1;
+                if (dir > 0) {
+                    while (b0 < b1) {  // first offset >= olo
+                        const int m = (b0 + b1) >> 1;
+                        if (sent[m] < olo) b0 = m + 1; else b1 = m;
+                    }
+                    lo = b0;
+                    b1 = e + 1;
+                    while (b0 < b1) {  // first offset > ohi
+                        const int m = (b0 + b1) >> 1;
+                        if (sent[m] <= ohi) b0 = m + 1; else b1 = m;
+                    }
+                    hi = b0 - 1;
+                } else {
+                    while (b0 < b1) {  // first offset <= ohi
+                        const int m = (b0 + b1) >> 1;
+                        if (sent[m] > ohi) b0 = m + 1; else b1 = m;
+                    }
+                    lo = b0;
+                    b1 = e + 1;
+                    while (b0 < b1) {  // first offset < olo
+                        const int m = (b0 + b1) >> 1;
+                        if (sent[m] >= olo) b0 = m + 1; else b1 = m;
+                    }
+                    hi = b0 - 1;
+                }
+                if (lo > hi) {  // nothing to test: neutral in the warp's union
+                    lo = e + 1;
+                    hi = a - 1;
+                }
             }
             const int ulo = __reduce_min_sync(0xffffffffu, lo), uhi = __reduce_max_sync(0xffffffffu, hi);
             for (int kk = ulo; kk <= uhi; ++kk) {
@@ -732,10 +764,11 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
             a = e + 1;
         }
         if (wg < NW && lane < nk) cnt[(long long)(k0 + lane) * NW + wg] = myc;
-        if (g < n) bits[(long long)wd * n + g] = word;
-        total += __popc(word);
+        if (g < n) {
+            bits[(long long)wd * n + g] = word;
+            if (word) atomicAdd(&gcnt[g], (unsigned)__popc(word));
+        }
     }
-    if (g < n) gcnt[g] = total;
 }
 
 // ---------------------------------------------------------------------------
@@ -1239,8 +1272,9 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
             k1_count_cells<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, f64_ratio, cg, cnt, NW, gcnt,
                                                  bits, hdr);
         } else {
-            k1_count<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio, cnt, NW, gcnt, bits,
-                                           hdr);
+            cudaMemsetAsync(gcnt, 0, sizeof(unsigned) * (size_t)n, st);
+            k1_count<<<dim3(g1, (unsigned)L.SW), K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio,
+                                                                 cnt, NW, gcnt, bits, hdr);
         }
     }
     {
