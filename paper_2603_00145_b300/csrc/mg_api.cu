@@ -115,7 +115,7 @@ mg_opts resolve_opts(const mg_opts *o, long long n, long long S)
 
 // The kernels' view of the MG_LOCAL_CELLS options (cg.on = 0 for the K-sigma
 // set). max_px: the largest pixel spacing of the stacks (mm), for the check
-// that a 16x16 tile spans at most 250 cells per axis.
+// that a tile (MG_TILE pixels square) spans at most 250 cells per axis.
 bool make_cellgrid(const mg_opts &o, float max_px, CellGrid &cg, std::string &why)
 {
     memset(&cg, 0, sizeof(cg));
