@@ -945,8 +945,9 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
             gauss_frame<float>(qv, sc, F);
             float gmu[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             float gs[3] = {0.f, 0.f, 0.f}, ga = 0.f;
-            // the next record's data, loaded one record ahead
+            // record ids are loaded two records ahead, their data one record ahead
             unsigned nr = j0 < j1 ? gmap[j0] : 0xffffffffu;
+            unsigned nr2 = j0 + 1 < j1 ? gmap[j0 + 1] : 0xffffffffu;
             float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nm0 = na;
             float2 nb = make_float2(0.f, 0.f), nm1 = nb;
             int ns = 0;
@@ -962,7 +963,8 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
                 const float4 a = na, m0 = nm0;
                 const float2 b = nb, m1 = nm1;
                 const int sl = ns;
-                nr = j + 1 < j1 ? gmap[j + 1] : 0xffffffffu;
+                nr = nr2;
+                nr2 = j + 2 < j1 ? gmap[j + 2] : 0xffffffffu;
                 if ((long long)nr < cap_records) {
                     na = geo[nr];
                     nb = geo2[nr];
