@@ -39,7 +39,7 @@ UNIT = "pairs/s"
 # kernels per library stage (the scans are two kernels each)
 KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 2, "k1_emit": 1, "chunks": 1, "bin_hist": 1,
                      "bin_colscan": 1, "scan_tiles": 2, "bin_scatter": 1, "render_fwd": 1, "zero_moments": 1,
-                     "render_bwd": 1, "chain": 1, "loss": 2, "pair_count": 1, "nrf_fwd": 1, "nrf_bwd": 1, "rec_geom": 1, "rec_fill": 1}
+                     "render_bwd": 1, "chain": 1, "loss": 1, "pair_count": 1, "nrf_fwd": 1, "nrf_bwd": 1, "rec_geom": 1, "rec_fill": 1}
 # Algorithmic per-pair work of the evaluation kernels (SIMT FP32 pipe ops,
 # MUFU ex2 ops): forward q (2 FMA) + accumulate (1 FMA) + 1 ex2; backward q
 # (2 FMA) + w = g 2^q (1 MUL) + three moment accumulations (3) + 1 ex2.

@@ -123,7 +123,7 @@ struct WsHeader {
     unsigned long long scan_total;
     unsigned long long pairs_inside;     // mg_render_pair_count
     unsigned long long pairs_evaluated;
-    unsigned int tile_ctr[4];  // work counters: forward busy, backward, forward empty tiles, spare
+    unsigned int tile_ctr[4];  // work counters: forward busy, backward, forward empty tiles, loss ticket
     unsigned int n_busy;       // tiles with records (front of the tile list)
     unsigned int n_idle;       // tiles without records (back of the tile list)
     unsigned long long reserved[22];

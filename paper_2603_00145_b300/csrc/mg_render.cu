@@ -1082,10 +1082,15 @@ __device__ __forceinline__ void lt_block_sum(double &s1, double &s2, double *sh)
     }
 }
 
-__global__ void __launch_bounds__(LT_NT) k_loss_tiles_part(const double2 *__restrict__ part, long long n, long long per,
-                                                           double2 *__restrict__ bsum)
+// The per-tile loss partials in two fixed-order FP64 levels, one launch: each
+// block sums its range of tiles, and the block that finishes last (a ticket
+// counter, no waiting) sums the block sums in block order and writes the loss.
+__global__ void __launch_bounds__(LT_NT) k_loss_tiles(const double2 *__restrict__ part, long long n, long long per,
+                                                      double2 *__restrict__ bsum, unsigned *ticket, double inv_n,
+                                                      double *__restrict__ out)
 {
     __shared__ double sh[2 * LT_NT / 32];
+    __shared__ bool last;
     const long long i0 = (long long)blockIdx.x * per, i1 = min(n, i0 + per);
     double s1 = 0.0, s2 = 0.0;
     for (long long i = i0 + threadIdx.x; i < i1; i += LT_NT) {
@@ -1094,22 +1099,26 @@ __global__ void __launch_bounds__(LT_NT) k_loss_tiles_part(const double2 *__rest
         s2 += p.y;
     }
     lt_block_sum(s1, s2, sh);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = make_double2(s1, s2);
-}
-
-__global__ void __launch_bounds__(LT_NT) k_loss_tiles_final(const double2 *__restrict__ bsum, int nb, double inv_n,
-                                                            double *__restrict__ out)
-{
-    __shared__ double sh[2 * LT_NT / 32];
-    double s1 = 0.0, s2 = 0.0;
-    for (int i = threadIdx.x; i < nb; i += LT_NT) {
-        s1 += bsum[i].x;
-        s2 += bsum[i].y;
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = make_double2(s1, s2);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    s1 = 0.0;
+    s2 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += LT_NT) {
+        const double2 b = __ldcg(&bsum[i]);
+        s1 += b.x;
+        s2 += b.y;
     }
     lt_block_sum(s1, s2, sh);
     if (threadIdx.x == 0) {
         out[0] = s1 * inv_n + s2 * inv_n;
         out[1] = s2;
+        *ticket = 0u;  // ready for the next launch
     }
 }
 
@@ -1137,7 +1146,8 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, co
     int nt = tab.n_tiles_total;
     if (nt <= 0) return;
     WsHeader *hdr = (WsHeader *)(ws + L.hdr);
-    cudaMemsetAsync(&hdr->tile_ctr[0], 0, 3 * sizeof(unsigned), st);
+    // the work counters (tile_ctr) start at zero: the bin pass that precedes
+    // every forward clears the workspace header
     FwdLoss ls;
     ls.target = target;
     ls.grad = grad;
@@ -1163,8 +1173,8 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, co
         const long long per = 8 * LT_NT;
         const int nb = (int)((nt + per - 1) / per);
         double2 *bsum = ls.tile_part + nt;
-        k_loss_tiles_part<<<nb, LT_NT, 0, st>>>(ls.tile_part, nt, per, bsum);
-        k_loss_tiles_final<<<1, LT_NT, 0, st>>>(bsum, nb, n_vox > 0 ? 1.0 / (double)n_vox : 0.0, loss_out);
+        k_loss_tiles<<<nb, LT_NT, 0, st>>>(ls.tile_part, nt, per, bsum, &hdr->tile_ctr[3],
+                                           n_vox > 0 ? 1.0 / (double)n_vox : 0.0, loss_out);
     }
 }
 
