@@ -1296,7 +1296,8 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     if (f64_ratio > 0.f) {
         MG_PROF(MG_ST_REC_GEOM, st);
-        int gg = (int)((n + 255) / 256 < 148 * 8 ? (n + 255) / 256 : 148 * 8);
+        // grid-strided: two blocks per SM; most steps have no near-degenerate Gaussian and every block returns at once
+        int gg = (int)((n + 255) / 256 < 148 * 2 ? (n + 255) / 256 : 148 * 2);
         k_rec_geom_f64<<<gg, 256, 0, st>>>(hdr, n, slices, mean, quat, scale, alpha, K2, f64_ratio, gcnt, gmap, rec);
     }
     {
