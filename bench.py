@@ -204,27 +204,45 @@ def run_mgauss(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step(m, q, s, a)
     torch.cuda.synchronize()
+    # the step's launches captured once as a CUDA graph (the library's stage
+    # events off) and replayed in the timed region
+    mg_profile_enable(False)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        step(m, q, s, a)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step(m, q, s, a)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
-    # the timed steps carry events around the two evaluation kernels only (the
-    # roofline's live kernel times); events around every stage cost about 5 %
-    # of the step, so the per-stage breakdown comes from a second, identical
-    # set of steps after the timed ones
-    mg_profile_read(reset=True)
-    mg_profile_stages(["render_fwd", "render_bwd"])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record()
-        step(m, q, s, a)
+        graph.replay()
         ev[k][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    # the roofline's live kernel times: the same steps launched one by one with
+    # events around the two evaluation kernels only; the per-stage breakdown
+    # from a third set with events around every stage (they cost about 5 % of
+    # the step)
+    mg_profile_read(reset=True)
+    mg_profile_stages(["render_fwd", "render_bwd"])
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        step(m, q, s, a)
     torch.cuda.synchronize()
     mg_profile_enable(False)
     prof_eval = mg_profile_read(reset=True)
-    clk = clocks.stop()
     mg_profile_enable(True)
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -328,7 +346,8 @@ def run_mgauss(args, rank, world, local_rank):
                        "records": st["records"], "entries": st["entries"],
                        "pairs_inside_per_step": pairs_inside, "pairs_evaluated_per_step": pairs_eval,
                        "binning_efficiency": pairs_inside / max(pairs_eval, 1),
-                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between timed steps (256 MiB write)", "launch": "CUDA graph of the step, replayed",
+                       "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms / args.steps,
@@ -336,8 +355,9 @@ def run_mgauss(args, rank, world, local_rank):
                                "copied and gradients read back on the compute stream; host sync every step"},
             "gpu_launches": launches,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-            "stages_note": "render_fwd and render_bwd timed with events inside the timed steps; the other "
-                           "stages from an identical set of steps with events around every stage",
+            "stages_note": "the timed steps replay a CUDA graph of the step; render_fwd and render_bwd timed "
+                           "with events in the same steps launched one by one (events around those two kernels "
+                           "only), the other stages in a third set with events around every stage",
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(G, wl, args.cpu_seconds)
