@@ -449,6 +449,58 @@ __device__ __forceinline__ int2 row_span(const ushort4 &rc, unsigned long long i
     return make_int2((int)rc.x + (int)(b & 15u), (int)rc.z - (int)(b >> 4));
 }
 
+// The tile (index ty * TX + tx in its slice) of a record's i-th listed tile
+// in row-major order (i below the record's listed count): the first eight
+// rows by their insets, the rows after them whole.
+__device__ __forceinline__ int nth_listed_tile(const ushort4 &rc, unsigned long long ins, unsigned i, int TX)
+{
+    int n = 0;
+    const int h = (int)rc.w - (int)rc.y + 1;
+    for (; n < 8 && n < h; ++n) {
+        const int2 sp = row_span(rc, ins, n);
+        const unsigned w = sp.y >= sp.x ? (unsigned)(sp.y - sp.x + 1) : 0u;
+        if (i < w) return ((int)rc.y + n) * TX + sp.x + (int)i;
+        i -= w;
+    }
+    const unsigned W = (unsigned)((int)rc.z - (int)rc.x + 1);
+    return ((int)rc.y + n + (int)(i / W)) * TX + (int)rc.x + (int)(i % W);
+}
+
+// lane j's record tiles, fetched by every lane of the warp
+__device__ __forceinline__ void shfl_tiles(const ushort4 &rc, unsigned long long ins, int j, ushort4 &rj,
+                                           unsigned long long &ij)
+{
+    const unsigned a0 = __shfl_sync(0xffffffffu, (unsigned)rc.x | ((unsigned)rc.y << 16), j);
+    const unsigned a1 = __shfl_sync(0xffffffffu, (unsigned)rc.z | ((unsigned)rc.w << 16), j);
+    const unsigned b0 = __shfl_sync(0xffffffffu, (unsigned)ins, j);
+    const unsigned b1 = __shfl_sync(0xffffffffu, (unsigned)(ins >> 32), j);
+    rj = make_ushort4((unsigned short)(a0 & 0xFFFFu), (unsigned short)(a0 >> 16), (unsigned short)(a1 & 0xFFFFu),
+                      (unsigned short)(a1 >> 16));
+    ij = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
+}
+
+// A batch of 32 records is flattened (one entry per lane per round, in
+// record-major order) when its largest record holds well over the mean: a
+// lane walking its own record's tiles would keep the warp for the largest one.
+__device__ __forceinline__ bool flatten_batch(int maxa, unsigned total)
+{
+    const unsigned rounds = (total + 31u) / 32u;
+    return (unsigned)maxa > rounds + rounds / 2u + 2u;
+}
+
+// The batch lane that owns flattened entry e: the first lane whose inclusive
+// prefix of listed-tile counts exceeds e (e below the batch total).
+__device__ __forceinline__ int entry_owner(unsigned incl, unsigned e)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const unsigned v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+        if (v <= e) lo += step;
+    }
+    return lo;
+}
+
 // The pixel box of [cu - ru, cu + ru] x [cv - rv, cv + rv] (slice mm), clamped
 // to the image; an empty box is stored as the tile rectangle (1,1,0,0).
 __device__ __forceinline__ void pixel_box(const SliceDev &S, float cu, float cv, float ru, float rv, PredOut &o)
@@ -1196,6 +1248,38 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
                 area += max(sp.y - sp.x + 1, 0);
             }
             int maxa = __reduce_max_sync(0xffffffffu, area);
+            unsigned incl = (unsigned)area;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+            if (flatten_batch(maxa, total)) {
+                // one entry per lane per round, record-major: the ranks within a tile
+                // follow record order (a deterministic order, like the loop below)
+                for (unsigned eb = 0; eb < total; eb += 32) {
+                    const unsigned e = eb + lane;
+                    const bool act = e < total;
+                    const int j = entry_owner(incl, act ? e : total - 1);
+                    ushort4 rj;
+                    unsigned long long ij;
+                    shfl_tiles(rc, ins, j, rj, ij);
+                    const unsigned excl = __shfl_sync(0xffffffffu, incl, j) - __shfl_sync(0xffffffffu, (unsigned)area, j);
+                    const unsigned t = act ? (unsigned)nth_listed_tile(rj, ij, e - excl, TX) : 0xffffffffu;
+                    const unsigned peers = __match_any_sync(0xffffffffu, t);
+                    const unsigned before = peers & lt;
+                    unsigned pos = 0;
+                    if (act) pos = cur[t] + __popc(before);
+                    __syncwarp();
+                    if (act) {
+                        if ((long long)pos < cap_entries) entries[pos] = base + (unsigned)j;
+                        if (before == 0) cur[t] += __popc(peers);
+                    }
+                    __syncwarp();
+                }
+                continue;
+            }
             // the listed tiles in row-major order: (jx, jy) with the row's last column xe
             int jy = rc.y;
             int2 sp = row_span(rc, ins, 0);
