@@ -908,14 +908,50 @@ __device__ __noinline__ void chain_gaussian_f64(const float *mu, const float *q,
     o[10] = (float)ga;
 }
 
+// One record's moments chained into the Gaussian's dL/d(mean, R, scale, alpha).
+__device__ __forceinline__ void chain_record(const GaussFrame<float> &F, const float *mu, float al, const float4 &a,
+                                             const float2 &b, const float4 &m0, const float2 &m1, const SliceDev &S,
+                                             float *gmu, float (*gR)[3], float *gs, float &ga)
+{
+    const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
+    const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
+    const float la = amp * 0.69314718055994531f;
+    const float gpx = -la * (2.f * A * Sx + B2 * Sy);
+    const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
+    record_adjoint<float>(F, mu, al, S, la * Sxx, la * Sxy, la * Syy, gpx, gpy, S0, gmu, gR, gs, ga);
+}
+
+// The Gaussian's gradients; the quaternion's on the unit sphere: its component
+// along q dropped (the normalisation q = q_raw/|q_raw| removes it, and the
+// rotation formula is only a rotation for unit q).
+__device__ __forceinline__ void write_gaussian_grads(long long g, const float *o, const float *qv, float *g_mean,
+                                                     float *g_quat, float *g_scale, float *g_alpha)
+{
+    const float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+    const float rad = qq > 0.f ? (o[3] * qv[0] + o[4] * qv[1] + o[5] * qv[2] + o[6] * qv[3]) / qq : 0.f;
+    g_mean[3 * g] = o[0];
+    g_mean[3 * g + 1] = o[1];
+    g_mean[3 * g + 2] = o[2];
+    for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = o[3 + i] - rad * qv[i];
+    g_scale[3 * g] = o[7];
+    g_scale[3 * g + 1] = o[8];
+    g_scale[3 * g + 2] = o[9];
+    g_alpha[g] = o[10];
+}
+
 // K6 fused: one thread per Gaussian visits its records in slice order (the
 // Gaussian-major list), turns each record's moments into dL/d(centre, conic,
 // amplitude) and chains them through the record geometry (FP64 for
 // near-degenerate Gaussians), summing in that fixed order; the Gaussian's
 // frame (rotation, scales) is formed once, the records add to dL/d(mean,
 // R, scale, alpha), and dL/dq follows from dL/dR once. The next record's
-// data is loaded while the current one is chained. Nothing per record is
-// written.
+// data is loaded while the current one is chained. A Gaussian with more than
+// 64 records (a fitted model grows a few that span many slices) is summed by
+// its whole warp instead, lane l taking records l, l + 32, ..., then a fixed
+// shuffle tree: one thread would hold the warp for all of them. Nothing per
+// record is written.
+constexpr unsigned CHAIN_WARP_RECORDS = 64;
+
 __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsigned *__restrict__ goff,
                                                      const unsigned *__restrict__ gmap, long long cap_records,
                                                      const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
@@ -927,44 +963,37 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
                                                      float f64_ratio, float *g_mean, float *g_quat, float *g_scale,
                                                      float *g_alpha)
 {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
-        unsigned long long j0 = goff[g], j1 = goff[g + 1];
+    const int lane = threadIdx.x & 31;
+    for (long long gb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); gb < n;
+         gb += (long long)gridDim.x * blockDim.x) {
+        const long long g = gb + lane;
+        const bool valid = g < n;
+        const long long gl = valid ? g : gb;  // lanes past n read a valid Gaussian and write nothing
+        unsigned long long j0 = goff[gl], j1 = goff[gl + 1];
         if ((long long)j1 > cap_records) j1 = cap_records;
         if (j0 > j1) j0 = j1;
-        float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
-        float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
-        float qv[4] = {quat[4 * g], quat[4 * g + 1], quat[4 * g + 2], quat[4 * g + 3]};
-        const float al = alpha[g];
+        float sc[3] = {scale[3 * gl], scale[3 * gl + 1], scale[3 * gl + 2]};
+        float mu[3] = {mean[3 * gl], mean[3 * gl + 1], mean[3 * gl + 2]};
+        float qv[4] = {quat[4 * gl], quat[4 * gl + 1], quat[4 * gl + 2], quat[4 * gl + 3]};
+        const float al = alpha[gl];
         const float mx = fmaxf(fmaxf(sc[0], sc[1]), sc[2]), mn = fminf(fminf(sc[0], sc[1]), sc[2]);
         const bool dbl = f64_ratio > 0.f && mx > f64_ratio * mn;
-        float o[11];
-        if (dbl) {
-            chain_gaussian_f64(mu, qv, sc, al, j0, j1, gmap, cap_records, geo, geo2, rslice, mom64, slices, o);
-        } else {
-            GaussFrame<float> F;
-            gauss_frame<float>(qv, sc, F);
-            float gmu[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-            float gs[3] = {0.f, 0.f, 0.f}, ga = 0.f;
-            // record ids are loaded two records ahead, their data one record ahead
-            unsigned nr = j0 < j1 ? gmap[j0] : 0xffffffffu;
-            unsigned nr2 = j0 + 1 < j1 ? gmap[j0 + 1] : 0xffffffffu;
-            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nm0 = na;
-            float2 nb = make_float2(0.f, 0.f), nm1 = nb;
-            int ns = 0;
-            if ((long long)nr < cap_records) {
-                na = geo[nr];
-                nb = geo2[nr];
-                nm0 = *(const float4 *)(mom + (size_t)nr * 8);
-                nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
-                ns = rslice[nr];
-            }
-            for (unsigned long long j = j0; j < j1; ++j) {
-                const unsigned r = nr;
-                const float4 a = na, m0 = nm0;
-                const float2 b = nb, m1 = nm1;
-                const int sl = ns;
-                nr = nr2;
-                nr2 = j + 2 < j1 ? gmap[j + 2] : 0xffffffffu;
+        const bool many = valid && !dbl && j1 - j0 > CHAIN_WARP_RECORDS;
+        if (valid && !many) {
+            float o[11];
+            if (dbl) {
+                chain_gaussian_f64(mu, qv, sc, al, j0, j1, gmap, cap_records, geo, geo2, rslice, mom64, slices, o);
+            } else {
+                GaussFrame<float> F;
+                gauss_frame<float>(qv, sc, F);
+                float gmu[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+                float gs[3] = {0.f, 0.f, 0.f}, ga = 0.f;
+                // record ids are loaded two records ahead, their data one record ahead
+                unsigned nr = j0 < j1 ? gmap[j0] : 0xffffffffu;
+                unsigned nr2 = j0 + 1 < j1 ? gmap[j0 + 1] : 0xffffffffu;
+                float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nm0 = na;
+                float2 nb = make_float2(0.f, 0.f), nm1 = nb;
+                int ns = 0;
                 if ((long long)nr < cap_records) {
                     na = geo[nr];
                     nb = geo2[nr];
@@ -972,34 +1001,67 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
                     nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
                     ns = rslice[nr];
                 }
-                if ((long long)r >= cap_records) continue;
-                const float A = a.z, B2 = a.w, C = b.x, amp = b.y;
-                const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
-                const float la = amp * 0.69314718055994531f;
-                const float gpx = -la * (2.f * A * Sx + B2 * Sy);
-                const float gpy = -la * (B2 * Sx + 2.f * C * Sy);
-                record_adjoint<float>(F, mu, al, slices[sl], la * Sxx, la * Sxy, la * Syy, gpx, gpy, S0, gmu, gR, gs,
-                                      ga);
+                for (unsigned long long j = j0; j < j1; ++j) {
+                    const unsigned r = nr;
+                    const float4 a = na, m0 = nm0;
+                    const float2 b = nb, m1 = nm1;
+                    const int sl = ns;
+                    nr = nr2;
+                    nr2 = j + 2 < j1 ? gmap[j + 2] : 0xffffffffu;
+                    if ((long long)nr < cap_records) {
+                        na = geo[nr];
+                        nb = geo2[nr];
+                        nm0 = *(const float4 *)(mom + (size_t)nr * 8);
+                        nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
+                        ns = rslice[nr];
+                    }
+                    if ((long long)r >= cap_records) continue;
+                    chain_record(F, mu, al, a, b, m0, m1, slices[sl], gmu, gR, gs, ga);
+                }
+                float gq[4];
+                quat_adjoint<float>(qv, gR, gq);
+                for (int i = 0; i < 3; ++i) o[i] = gmu[i], o[7 + i] = gs[i];
+                for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
+                o[10] = ga;
             }
-            float gq[4];
-            quat_adjoint<float>(qv, gR, gq);
-            for (int i = 0; i < 3; ++i) o[i] = gmu[i], o[7 + i] = gs[i];
-            for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
-            o[10] = ga;
+            write_gaussian_grads(g, o, qv, g_mean, g_quat, g_scale, g_alpha);
         }
-        // gradient on the unit sphere: drop the component along q (the
-        // normalisation q = q_raw/|q_raw| removes it, and the rotation formula
-        // is only a rotation for unit q)
-        const float qq = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-        const float rad = qq > 0.f ? (o[3] * qv[0] + o[4] * qv[1] + o[5] * qv[2] + o[6] * qv[3]) / qq : 0.f;
-        g_mean[3 * g] = o[0];
-        g_mean[3 * g + 1] = o[1];
-        g_mean[3 * g + 2] = o[2];
-        for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = o[3 + i] - rad * qv[i];
-        g_scale[3 * g] = o[7];
-        g_scale[3 * g + 1] = o[8];
-        g_scale[3 * g + 2] = o[9];
-        g_alpha[g] = o[10];
+        // the warp's Gaussians with many records, one at a time
+        unsigned lm = __ballot_sync(0xffffffffu, many);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const long long gg = gb + src;
+            const unsigned long long k0 = __shfl_sync(0xffffffffu, j0, src), k1 = __shfl_sync(0xffffffffu, j1, src);
+            const float sg[3] = {scale[3 * gg], scale[3 * gg + 1], scale[3 * gg + 2]};
+            const float mg[3] = {mean[3 * gg], mean[3 * gg + 1], mean[3 * gg + 2]};
+            const float qg[4] = {quat[4 * gg], quat[4 * gg + 1], quat[4 * gg + 2], quat[4 * gg + 3]};
+            const float ag = alpha[gg];
+            GaussFrame<float> F;
+            gauss_frame<float>(qg, sg, F);
+            float acc[16];  // dL/d mean (3), R (9), scale (3), alpha
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+            for (unsigned long long j = k0 + lane; j < k1; j += 32) {
+                const unsigned r = gmap[j];
+                if ((long long)r >= cap_records) continue;
+                const float4 a = geo[r], m0 = *(const float4 *)(mom + (size_t)r * 8);
+                const float2 b = geo2[r], m1 = *(const float2 *)(mom + (size_t)r * 8 + 4);
+                chain_record(F, mg, ag, a, b, m0, m1, slices[rslice[r]], acc, (float(*)[3])(acc + 3), acc + 12,
+                             acc[15]);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+            if (lane == src) {
+                float gq[4], o[11];
+                quat_adjoint<float>(qg, (float(*)[3])(acc + 3), gq);
+                for (int i = 0; i < 3; ++i) o[i] = acc[i], o[7 + i] = acc[12 + i];
+                for (int i = 0; i < 4; ++i) o[3 + i] = gq[i];
+                o[10] = acc[15];
+                write_gaussian_grads(gg, o, qg, g_mean, g_quat, g_scale, g_alpha);
+            }
+        }
     }
 }
 

@@ -48,3 +48,34 @@ def test_runs_bins_bit_exact(name, stacks):
     for t in np.nonzero(counts)[0]:
         assert np.array_equal(np.sort(e[offs[t]:offs[t + 1]]), ids[offs[t]:offs[t + 1]]), t
     assert_render_close(out.cpu().numpy(), orc.render(G, stacks, rec), name)
+
+
+def test_many_records_per_gaussian_gradients():
+    """Gaussians elongated along the normal of an 80-slice stack have a record
+    in nearly every slice (more than 64: the chain sums them with the whole
+    warp, lane-strided, in a fixed shuffle tree); slices and gradients against
+    the oracle (the moments themselves sum by FP32 atomics, so gradients are not
+    compared between runs)."""
+    from gpu_util import assert_grads_close
+
+    rng = np.random.default_rng(12)
+    st = [ms.make_stack(ms.AXIAL, 80, 24, 22, 1.0, 1.0, 1.0, 0.5)]
+    n_long = 5
+    quat = np.tile(np.array([[1.0, 0.0, 0.0, 0.0]]), (n_long, 1)) + rng.normal(scale=0.05, size=(n_long, 4))
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)
+    longs = ms.Gaussians(rng.uniform(-4, 4, size=(n_long, 3)), quat,
+                         np.column_stack([rng.uniform(1.5, 3.0, n_long), rng.uniform(1.5, 3.0, n_long),
+                                          np.full(n_long, 12.0)]), rng.uniform(0.3, 1.0, n_long))
+    short = ms.random_gaussians(60, 13, box=(-10, 10), sigma=(0.6, 2.0), aniso=2.0)
+    G = ms.Gaussians(*(np.concatenate([getattr(p, f) for p in (longs, short)]) for f in ("mean", "quat", "scale",
+                                                                                         "alpha")))
+    R, out, dev = render_gpu(G, st)
+    rec = orc.records(G, st, 3.0)
+    per_g = np.bincount(rec.gid, minlength=G.n)
+    assert (per_g[:n_long] > 64).all(), per_g[:n_long]
+    want = orc.render(G, st, rec)
+    assert_render_close(out.cpu().numpy(), want, "many records")
+    gout = np.random.default_rng(14).normal(size=want.size).astype(np.float32)
+    g1 = R.backward(*dev, torch.from_numpy(gout).cuda())
+    ref = orc.grad(G, st, rec, gout.astype(np.float64))
+    assert_grads_close(g1, ref, G, "many records")
