@@ -193,3 +193,48 @@ def test_record_count_and_tile_bins_consistent():
     for t in range(counts.size):
         seg = ids[offs[t]:offs[t + 1]]
         assert np.all(np.diff(seg) > 0)
+
+
+@pytest.mark.parametrize("seed,K", [(0, 3.0), (5, 2.5)])
+def test_pair_counts_vs_brute_force(seed, K):
+    """Pin of ``pair_counts`` (the metric's numerator P and the evaluated
+    pairs): the inside count equals the number of (record, pixel) pairs with
+    y^T Sigma'^-1 y <= K^2 found here over EVERY pixel of every slice by the
+    scipy-rotation plane quadratic (another route than the oracle's 3x3
+    inverse), up to the pixels in the 1e-5 boundary band; the evaluated count
+    equals the pixels of the listed tiles, counted tile by tile with the image
+    border clipping them."""
+    rng = np.random.default_rng(100 + seed)
+    G = ms.random_gaussians(60, 300 + seed, box=(-20, 20), sigma=(0.6, 3.5), aniso=4.0, negative_frac=0.2)
+    stacks = [ms.make_stack(ms.AXIAL, 4, 37, 30, 1.0, 1.2, 3.0, 2.5),
+              ms.make_stack(ms.random_rotations(1, rng)[0], 4, 29, 41, 0.8, 0.9, 2.0, 3.0,
+                            rng=rng, max_rot_deg=5.0, max_trans_mm=1.0, psf_u=1.4, psf_v=0.7),
+              ms.make_stack(ms.CORONAL, 3, 21, 19, 1.5, 1.5, 0.0, 4.0)]
+    rec = orc.records(G, stacks, K)
+    got_in, got_ev = orc.pair_counts(G, stacks, rec, K)
+    where = {(int(k), int(g)): r for r, (k, g) in enumerate(zip(rec.slice, rec.gid))}
+    lo = hi = ev = 0
+    k0 = 0
+    for st in stacks:
+        psf_var = np.array([st.psf_u ** 2, st.psf_v ** 2, st.thickness ** 2]) * FWHM2VAR
+        ii, jj = np.meshgrid(np.arange(st.W), np.arange(st.H), indexing="xy")
+        uv = np.stack([(ii - 0.5 * (st.W - 1)) * st.dx, (jj - 0.5 * (st.H - 1)) * st.dy], axis=-1)
+        for k in range(st.n_slices):
+            xf = st.xform[k].astype(np.float64)
+            for g in range(G.n):
+                r = where.get((k0 + k, g))
+                if r is None:
+                    continue
+                q = G.quat[g].astype(np.float64)
+                q /= np.linalg.norm(q)
+                A, b, c = _plane_quadratic(G.mean[g].astype(np.float64), q, G.scale[g], xf, psf_var)
+                qv = np.einsum("hwi,ij,hwj->hw", uv, A, uv) + 2 * uv @ b + c
+                lo += int(np.count_nonzero(qv <= K * K * (1 - 1e-5)))
+                hi += int(np.count_nonzero(qv <= K * K * (1 + 1e-5)))
+                for tx, ty in rec.row_tiles(r):
+                    ev += min(TILE, st.W - TILE * tx) * min(TILE, st.H - TILE * ty)
+        k0 += st.n_slices
+    assert lo <= got_in <= hi, (lo, got_in, hi)
+    assert hi - lo <= max(3, 1e-3 * lo)  # the band is thin: the count is pinned, not merely bracketed
+    assert got_ev == ev, (got_ev, ev)
+    assert 0 < got_in < got_ev
