@@ -650,6 +650,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.fitted and args.impl == "reference":
+        ap.error("--fitted needs the GPU fit; the reference arm times the oracle on the initial Gaussians only")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

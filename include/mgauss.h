@@ -309,9 +309,12 @@ mg_status mg_loss_l1l2(const float *pred, const float *target, int64_t n, float 
  * no cudaMalloc, cudaFree or other allocating routine.
  *   Limit: n <= 33554432 (8192 partial blocks of 4096 voxels); larger n
  *   returns MG_ERR_INVALID_ARG with nothing launched.
- *   Set-up: the first call on each device looks up the array's device
- *   address with that device current; make that first call before any
- *   stream capture.
+ *   Set-up: each call made outside a stream capture looks up the array's
+ *   device address with the device current (no allocation), so the address
+ *   stays right across a cudaDeviceReset; a call inside a capture uses the
+ *   address found by the last call outside one. So the first call on each
+ *   device, and the first after a reset, must come before any stream
+ *   capture (inside one it returns MG_ERR_INVALID_ARG, nothing launched).
  *   Sharing: every call uses the same array. Calls that overlap on the GPU
  *   (other streams, other host threads) race on it; serialise them. Each
  *   call writes every slot it reads, so nothing needs clearing between calls.

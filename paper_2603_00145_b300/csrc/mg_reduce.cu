@@ -168,17 +168,32 @@ extern "C" mg_status mg_loss_l1l2_noalloc(const float *pred, const float *target
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MG_NOALLOC_MAX_DEVICES)
         return mg_set_error(MG_ERR_CUDA, "mg_loss_l1l2_noalloc: no usable current device");
+    cudaStream_t st = (cudaStream_t)stream;
+    // Is the stream being captured into a graph? A query that fails (the
+    // legacy stream while another stream captures) counts as capturing.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
     double *part = nullptr;
     {
-        // set-up, once per device, with that device current: the device
-        // address of the array (its name is only a host-side stand-in)
+        // The device address of the array (its name is only a host-side
+        // stand-in), looked up with the device current. Outside a capture it
+        // is looked up on every call (no allocation), so it stays right after
+        // a cudaDeviceReset reloads the module; inside a capture the address
+        // of the last call outside one is used.
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
             if (e != cudaSuccess || !p)
                 return mg_set_error(MG_ERR_CUDA, "mg_loss_l1l2_noalloc: cudaGetSymbolAddress failed");
             g_noalloc_ptr[dev] = (double *)p;
+        } else if (!g_noalloc_ptr[dev]) {
+            return mg_set_error(MG_ERR_INVALID_ARG,
+                                "mg_loss_l1l2_noalloc: first call on this device inside a stream capture; make one "
+                                "call outside any capture first");
         }
         part = g_noalloc_ptr[dev];
     }
@@ -186,7 +201,6 @@ extern "C" mg_status mg_loss_l1l2_noalloc(const float *pred, const float *target
     int nb = (int)((leaves + RED_NT - 1) / RED_NT);
     if (nb < 1) nb = 1;
     double inv_n = n > 0 ? 1.0 / (double)n : 0.0;
-    cudaStream_t st = (cudaStream_t)stream;
     // every partial slot the final pass reads is written by the first pass,
     // so nothing left in the array by an earlier call is used
     k_reduce_leaf<0><<<nb, RED_NT, 0, st>>>(pred, target, n, grad, inv_n, part);

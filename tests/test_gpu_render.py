@@ -183,19 +183,49 @@ def test_degenerate_gaussians_fp64_geometry():
     assert_render_close(out.cpu().numpy(), orc.render(G, stacks, rec), "degenerate fwd")
 
 
-def test_bench_config_sampled_slices():
-    """The FeTA-shaped fit at full size (200k Gaussians; 3 x 64 slices of
-    256^2): the GPU renders everything; the oracle checks one slice per stack,
+def _needles(G, every, factor, seed):
+    """Every ``every``-th Gaussian stretched by ``factor`` along one axis: a
+    scale ratio above the FP64 threshold (near-degenerate covariance)."""
+    rng = np.random.default_rng(seed)
+    sc = G.scale.copy()
+    idx = np.arange(0, G.n, every)
+    sc[idx, rng.integers(3, size=idx.size)] *= factor
+    return ms.Gaussians(G.mean, G.quat, sc, G.alpha)
+
+
+def _anisotropic(G, seed):
+    """The workload's isotropic initial Gaussians given random orientations and
+    per-axis scale factors in [0.6, 1.6] (a fitted model's shapes): the
+    quaternion gradient of an isotropic Gaussian is identically zero, so it
+    would check nothing."""
+    rng = np.random.default_rng(seed)
+    q = ms.random_unit_quats(G.n, rng).astype(np.float32)
+    sc = (G.scale * rng.uniform(0.6, 1.6, size=G.scale.shape)).astype(np.float32)
+    return ms.Gaussians(G.mean, q, sc, G.alpha)
+
+
+@pytest.mark.parametrize("name", ["feta", "motion", "stress"])
+def test_bench_config_sampled_slices(name):
+    """The workloads at full size, in the bench's launch configuration:
+    FeTA-shaped (200k Gaussians; 3 x 64 slices of 256^2), motion (500k
+    Gaussians; 4 stacks of 64 x 256^2, one oblique, per-slice motion <= 3 deg)
+    and stress (2M Gaussians; 5 stacks of 96 x 384^2 at random orientations,
+    motion <= 5 deg, one Gaussian in 500 stretched 150x onto the FP64
+    geometry path), each Gaussian given a random orientation and per-axis
+    scales. The GPU renders everything; the oracle checks one slice per stack,
     and the adjoint with dL/dI non-zero on those slices only."""
-    wl = ms.feta_workload(0)
-    G = ms.phantom_init_gaussians(wl, seed=0)
+    maker = {"feta": ms.feta_workload, "motion": ms.motion_workload, "stress": ms.stress_workload}[name]
+    wl = maker(0)
+    G = _anisotropic(ms.phantom_init_gaussians(wl, seed=0), 3)
+    if name == "stress":
+        G = _needles(G, 500, 150.0, 5)
     R, out, dev = render_gpu(G, wl.stacks)
-    picks = [(0, 20), (1, 33), (2, 47)]
+    picks = [(i, (17 + 13 * i) % s.n_slices) for i, s in enumerate(wl.stacks)]
     sub, ranges = sub_stacks(wl.stacks, picks)
     rec = orc.records(G, sub)
     want = orc.render(G, sub, rec)
     got = np.concatenate([out[a:b].cpu().numpy() for a, b in ranges])
-    assert_render_close(got, want, "feta slices")
+    r, m = assert_render_close(got, want, f"{name} slices")
     gout_sub = np.random.default_rng(2).normal(size=want.size).astype(np.float32)
     gout = torch.zeros(R.dev.n_vox, device="cuda")
     o = 0
@@ -204,7 +234,31 @@ def test_bench_config_sampled_slices():
         o += b - a
     g = R.backward(*dev, gout)
     ref = orc.grad(G, sub, rec, gout_sub.astype(np.float64))
-    assert_grads_close(g, ref, G, "feta slices")
+    ge = assert_grads_close(g, ref, G, f"{name} slices")
+    print(f"{name}: slices rel-L2 {r:.2e} max-abs {m:.2e}; grads " +
+          " ".join(f"{k} {v:.2e}" for k, v in ge.items()))
+
+
+def test_k6_slices_equal_untruncated_sum():
+    """At K = 6 every omitted term is below exp(-18) ~ 1.5e-8 of its
+    Gaussian's peak, so the slices must equal the untruncated profile-integrated
+    sum over every Gaussian at every pixel (the oracle's ``exact`` render:
+    no records, tiles or culling rule involved), within the render tolerance.
+    Thick-profile, in-plane PSF, zero-thickness and an oblique stack with
+    per-slice motion; a quarter of the Gaussians take the FP64 geometry."""
+    rng = np.random.default_rng(61)
+    G = ms.random_gaussians(320, 610, box=(-20, 20), sigma=(0.5, 2.5), aniso=3.0, negative_frac=0.1)
+    G = _needles(G, 4, 130.0, 62)
+    stacks = [ms.make_stack(ms.AXIAL, 7, 37, 45, 1.0, 1.1, 3.0, 3.0, psf_u=1.2, psf_v=0.8),
+              ms.make_stack(ms.random_rotations(1, rng)[0], 6, 40, 34, 0.9, 0.9, 2.0, 2.5, rng=rng,
+                            max_rot_deg=3.0, max_trans_mm=1.0),
+              ms.make_stack(ms.axis_angle_matrix([1, 0, 0], np.deg2rad(30.0)) @ ms.CORONAL, 5, 29, 41, 1.0, 1.0,
+                            2.0, 2.0, rng=rng, max_rot_deg=3.0, max_trans_mm=1.0, psf_u=0.0, psf_v=1.5),
+              ms.make_stack(ms.SAGITTAL, 4, 30, 18, 1.3, 1.2, 0.0, 4.0)]
+    R, out, dev = render_gpu(G, stacks, K=6.0)
+    want = orc.render(G, stacks, exact=True)
+    r, m = assert_render_close(out.cpu().numpy(), want, "K=6 vs untruncated")
+    print(f"K=6 vs untruncated: rel-L2 {r:.2e} max-abs {m:.2e}")
 
 
 def test_pair_counts_vs_oracle():
