@@ -234,7 +234,7 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.rec_grad = take(32 * (size_t)L.cap_records);  // slice-pose shares: 2 float4 per record
     L.rec_cell = o.local_set == MG_LOCAL_CELLS ? take(16 * (size_t)L.cap_records) : 0;
     L.rec_f64 = take((size_t)L.cap_records);
-    L.rec_mom64 = take(48 * (size_t)L.cap_records);
+    L.rec_mom64 = take(sizeof(double) * MOM64_STRIDE * (size_t)L.cap_records);
     L.total = off;
     return L;
 }

@@ -974,7 +974,7 @@ __global__ void __launch_bounds__(256, 4)
         const bool dg = is_degenerate(sc, f64_ratio);
         rec.f64[r] = dg ? 1 : 0;
         if (dg) {
-            double2 *m2 = (double2 *)(rec.mom64 + 6 * r);
+            double2 *m2 = (double2 *)(rec.mom64 + MOM64_STRIDE * r);
             m2[0] = m2[1] = m2[2] = make_double2(0.0, 0.0);
             continue;
         }
@@ -1011,6 +1011,14 @@ __global__ void k_rec_geom_f64(const WsHeader *hdr, long long n, const SliceDev 
             rec.geo[r] = make_float4((float)o.pcx, (float)o.pcy, (float)o.A, (float)o.B2);
             rec.geo2[r] = make_float2((float)o.C, (float)o.amp);
             rec.thr[r] = (float)o.thr;
+            // the FP64 centre and conic: rounded to FP32, the conic of a needle
+            // far along its axis moves the exponent by ~ 2^-24 (max/min scale)^2
+            double *g64 = rec.mom64 + MOM64_STRIDE * r + MOM64_GEO;
+            g64[0] = o.pcx;
+            g64[1] = o.pcy;
+            g64[2] = o.A;
+            g64[3] = o.B2;
+            g64[4] = o.C;
         }
     }
 }
@@ -1257,7 +1265,9 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
             const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
             if (flatten_batch(maxa, total)) {
                 // one entry per lane per round, record-major: the ranks within a tile
-                // follow record order (a deterministic order, like the loop below)
+                // follow record order. The per-lane loop below orders a tile's entries
+                // by (round, lane) instead; both orders are deterministic, but they
+                // differ, so a tile's summation order depends on which path its batch took
                 for (unsigned eb = 0; eb < total; eb += 32) {
                     const unsigned e = eb + lane;
                     const bool act = e < total;

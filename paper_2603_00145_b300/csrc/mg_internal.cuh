@@ -147,7 +147,8 @@ struct Records {
     float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
     int4 *cell;         // MG_LOCAL_CELLS: the Gaussian's cell (x, y, z, 0); else unused
     unsigned char *f64; // 1: near-degenerate Gaussian (FP64 geometry and FP64 moments)
-    double *mom64;      // [cap][6] backward moments of the FP64 records (FP64 accumulation)
+    double *mom64;      // [cap][12] of the FP64 records: [0..5] backward moments (FP64
+                        // accumulation), [6..10] FP64 geometry (pcx, pcy, A, B2, C)
     long long cap;
 };
 
@@ -163,6 +164,10 @@ struct WsLayout {
 // -------------------------------------------------------------------------
 // small device helpers
 // -------------------------------------------------------------------------
+// FP64 slots of a near-degenerate record: moments, then its FP64 geometry
+constexpr int MOM64_STRIDE = 12;
+constexpr int MOM64_GEO = 6;
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;

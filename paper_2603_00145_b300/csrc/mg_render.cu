@@ -8,7 +8,8 @@
 //     I += amp * 2^q.
 // K5 k_render_bwd : lane = record; each lane sweeps the tile's 64 voxels
 //     and forms six moments of w = g 2^q (sum w, w dx, w dy, w dx^2, w dx dy,
-//     w dy^2); two vector atomics per (record, tile). Nothing per pair is
+//     w dy^2); two vector atomics per (record, tile). A batch of <= 16
+//     records shares each record's rows among 2-8 lanes. Nothing per pair is
 //     stored.
 // K6 k_chain_fused : per Gaussian, its records' moments -> dL/d(centre,
 //     conic, amp) -> adjoint of the record geometry -> dL/d(mean, quat,
@@ -91,6 +92,23 @@ __device__ __forceinline__ TileQuad tile_quad(float A, float B, float C, float d
     return t;
 }
 
+// The same coefficients D, E, F for a near-degenerate record, from its FP64
+// centre and conic (g64 = pcx, pcy, A, B2, C), in FP64: for a needle the
+// three terms of F are large and cancel, and its FP32 conic alone is off by
+// ~ 2^-24 (max/min scale)^2 in the exponent far along its axis.
+// (Out of line: the caller tests a warp-uniform flag first, so the FP64 work
+// never runs predicated off for ordinary records.)
+__device__ __noinline__ TileQuad tile_quad_f64(const double *__restrict__ g64, float x0c, float y0c)
+{
+    const double dx0 = (double)x0c - g64[0], dy0 = (double)y0c - g64[1];
+    const double A = g64[2], B = g64[3], C = g64[4];
+    TileQuad t;
+    t.D = (float)fma(2.0 * A, dx0, B * dy0);
+    t.E = (float)fma(B, dx0, 2.0 * C * dy0);
+    t.F = (float)fma(fma(A, dx0, B * dy0), dx0, C * dy0 * dy0);
+    return t;
+}
+
 // CELLS: the tile's voxel cells packed relative to its smallest cell (one
 // word per voxel, row-major), and that smallest cell
 __device__ __forceinline__ void tile_cells(const SliceDev &Sd, const CellGrid &cg, int tx, int ty, int lane,
@@ -160,8 +178,9 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
                                          const unsigned *__restrict__ entries, long long cap_entries,
                                          long long cap_records, const float4 *__restrict__ geo,
                                          const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
-                                         const CellGrid &cg, const int4 *__restrict__ rcell, float *__restrict__ out,
-                                         const FwdLoss &ls)
+                                         const CellGrid &cg, const int4 *__restrict__ rcell,
+                                         const unsigned char *__restrict__ f64, const double *__restrict__ mom64,
+                                         float *__restrict__ out, const FwdLoss &ls)
 {
     const TileId d = tile_id(tab, t);
     const int grp = lane >> 2, c4 = lane & 3;
@@ -191,18 +210,22 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 nc = make_int4(0, 0, 0, 0);
+    unsigned nr = 0xffffffffu;  // the staged record's id when it takes the FP64 geometry
     unsigned er = (e0 + lane < e1) ? entries[e0 + lane] : 0xffffffffu;
     if ((long long)er < cap_records) {
         na = geo[er];
         nb = geo2[er];
         if (CELLS) nc = rcell[er];
+        if (f64[er]) nr = er;
     }
     er = (e0 + 32 + lane < e1) ? entries[e0 + 32 + lane] : 0xffffffffu;
     for (unsigned base = e0; base < e1; base += 32) {
         {
             // stage this lane's record in the tile frame (a zero record past the end)
             const float A = na.z, B = na.w, C = nb.x;
-            const TileQuad tq = tile_quad(A, B, C, x0c - na.x, y0c - na.y);
+            TileQuad tq = tile_quad(A, B, C, x0c - na.x, y0c - na.y);
+            if (__any_sync(0xffffffffu, nr != 0xffffffffu) && nr != 0xffffffffu)
+                tq = tile_quad_f64(mom64 + (size_t)nr * MOM64_STRIDE + MOM64_GEO, x0c, y0c);
             sw.ab[lane] = make_float4(A, A, B, B);
             sw.cd[lane] = make_float4(C, C, tq.D, tq.D);
             sw.ef[lane] = make_float4(tq.E, tq.E, tq.F, tq.F);
@@ -212,10 +235,12 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
         __syncwarp();
         na = make_float4(0.f, 0.f, 0.f, 0.f);
         nb = make_float2(0.f, 0.f);
+        nr = 0xffffffffu;
         if ((long long)er < cap_records) {
             na = geo[er];
             nb = geo2[er];
             if (CELLS) nc = rcell[er];
+            if (f64[er]) nr = er;
         }
         er = (base + 64 + lane < e1) ? entries[base + 64 + lane] : 0xffffffffu;
         const int m = (int)min(32u, e1 - base);
@@ -300,7 +325,9 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
                                                           const SliceDev *__restrict__ slices, CellGrid cg,
                                                           const int4 *__restrict__ rcell,
                                                           const unsigned *__restrict__ tile_list,
-                                                          const WsHeader *__restrict__ hdr, float *__restrict__ out,
+                                                          const WsHeader *__restrict__ hdr,
+                                                          const unsigned char *__restrict__ f64,
+                                                          const double *__restrict__ mom64, float *__restrict__ out,
                                                           FwdLoss ls, unsigned *counter)
 {
     __shared__ FwdStage sg[RW];
@@ -315,7 +342,7 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
         i = __shfl_sync(0xffffffffu, i, 0);
         if ((long long)i >= n_busy) break;
         fwd_tile<CELLS, LOSS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off,
-                              entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, out, ls);
+                              entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64, mom64, out, ls);
         __syncwarp();
     }
     for (;;) {
@@ -371,11 +398,14 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
 // entries and sweeps all 64 voxels of the tile, reading dL/dI from shared
 // memory by broadcast. Per row y: b1 = B y + D, b0 = (C y + E) y + F; per
 // column pair q = (A x + b1) x + b0 with packed FP32x2 FMAs, w = g 2^q, and
-// three row sums (w, x w, x^2 w) from the tile's products g, g x, g x^2; per
-// row the row sums fold into six moment accumulators with y. Moments are
-// taken about the tile centre and moved to the record centre at the end, so
-// no cross-lane reduction is needed; each lane then adds its record's six
-// moments with a float4 and a float2 atomic.
+// three row sums (w, x w, x^2 w) with x and x^2 held in registers (only g is
+// read from shared memory: broadcasting g x and g x^2 as well made the
+// shared-memory path, at 12 bytes per pair and lane, the limit); per row the
+// row sums fold into six moment accumulators with y. Moments are
+// taken about the tile centre and moved to the record centre at the end; a
+// lane then adds its record's six moments with a float4 and a float2 atomic.
+// A batch of at most 16 records (a tile's last, or only, batch) splits each
+// record's rows over 2, 4 or 8 lanes and sums their moments by shuffles first.
 template <bool CELLS>
 __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane, float *sgvw, unsigned *srelw,
                                          const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
@@ -389,15 +419,10 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
     unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
     if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 >= e1) return;
-    // dL/dI of the tile and its products with the column offset x and x^2
-    // (shared by all records of the tile)
+    // dL/dI of the tile (shared by all records of the tile)
     for (int i = lane; i < NV; i += 32) {
         const int px = d.tx * MG_TILE + (i % MG_TILE), py = d.ty * MG_TILE + (i / MG_TILE);
-        const float gval = (px < d.W && py < d.H) ? grad_out[d.pixbase + (long long)py * d.W + px] : 0.f;
-        const float x = (float)(i % MG_TILE) - TC;
-        sgvw[i] = gval;
-        sgvw[NV + i] = gval * x;
-        sgvw[2 * NV + i] = gval * x * x;
+        sgvw[i] = (px < d.W && py < d.H) ? grad_out[d.pixbase + (long long)py * d.W + px] : 0.f;
     }
     int cb0 = 0, cb1 = 0, cb2 = 0;
     if (CELLS) tile_cells(slices[tab.slice_base[d.s] + d.kk], cg, d.tx, d.ty, lane, srelw, cb0, cb1, cb2);
@@ -406,9 +431,13 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
     // column offsets as register pairs, formed once per tile (an opaque zero
     // added so that they stay in registers)
     const float rz = __uint_as_float(e1 & 0x80000000u);
-    float2 xp[MG_TILE / 2];
+    float2 xp[MG_TILE / 2], xq[MG_TILE / 2];
 #pragma unroll
-    for (int c = 0; c < MG_TILE / 2; ++c) xp[c] = make_float2((float)(2 * c) - TC + rz, (float)(2 * c + 1) - TC + rz);
+    for (int c = 0; c < MG_TILE / 2; ++c) {
+        xp[c] = make_float2((float)(2 * c) - TC + rz, (float)(2 * c + 1) - TC + rz);
+        xq[c] = make_float2(((float)(2 * c) - TC) * ((float)(2 * c) - TC) + rz,
+                            ((float)(2 * c + 1) - TC) * ((float)(2 * c + 1) - TC) + rz);
+    }
     // the next batch of 32 records is fetched while the current one is swept
     // loads run two steps ahead: record ids two batches ahead, their
     // geometry one batch ahead
@@ -416,7 +445,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 nb = make_float2(0.f, 0.f);
     int4 ncl = make_int4(0, 0, 0, 0);
-    unsigned char nf = 0;
+    int nf = 0;
     unsigned er = (e0 + lane < e1) ? entries[e0 + lane] : 0xffffffffu;
     if ((long long)er < cap_records) {
         nr = er;
@@ -428,10 +457,10 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
     er = (e0 + 32 + lane < e1) ? entries[e0 + 32 + lane] : 0xffffffffu;
     for (unsigned base = e0; base < e1; base += 32) {
         unsigned r = nr;
-        const float4 a = na;
-        const float2 b = nb;
-        const int4 cl = ncl;
-        const bool dbl = nf != 0;
+        float4 a = na;
+        float2 b = nb;
+        int4 cl = ncl;
+        int dbl = nf;
         nr = 0xffffffffu;
         na = make_float4(0.f, 0.f, 0.f, 0.f);
         nb = make_float2(0.f, 0.f);
@@ -444,30 +473,55 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             if (CELLS) ncl = rcell[er];
         }
         er = (base + 64 + lane < e1) ? entries[base + 64 + lane] : 0xffffffffu;
+        // A batch of m <= 16 records splits each record's 8 rows over L = 2,
+        // 4 or 8 lanes (lane l: record l mod 32/L, rows (l div 32/L) 8/L ..),
+        // so that a sparse tile does not leave most lanes idle; the L partial
+        // moment sets are summed by shuffles before the atomics.
+        const unsigned m = min(32u, e1 - base);
+        const int lg = m > 16u ? 0 : m > 8u ? 1 : m > 4u ? 2 : 3;  // log2 L (warp-uniform)
+        const int P = 32 >> lg;                                 // records per pass
+        int j0 = 0;
+        if (lg) {
+            const int src = lane & (P - 1);
+            r = __shfl_sync(0xffffffffu, r, src);
+            a.x = __shfl_sync(0xffffffffu, a.x, src);
+            a.y = __shfl_sync(0xffffffffu, a.y, src);
+            a.z = __shfl_sync(0xffffffffu, a.z, src);
+            a.w = __shfl_sync(0xffffffffu, a.w, src);
+            b.x = __shfl_sync(0xffffffffu, b.x, src);
+            dbl = __shfl_sync(0xffffffffu, dbl, src);
+            if (CELLS) {
+                cl.x = __shfl_sync(0xffffffffu, cl.x, src);
+                cl.y = __shfl_sync(0xffffffffu, cl.y, src);
+                cl.z = __shfl_sync(0xffffffffu, cl.z, src);
+                cl.w = __shfl_sync(0xffffffffu, cl.w, src);
+            }
+            j0 = (lane >> (5 - lg)) << (3 - lg);
+        }
         unsigned clo = 0u, chi = 0u;
         if (CELLS && r != 0xffffffffu && !cell_range(cl, cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
         const float A = a.z, B = a.w, C = b.x;
         const float dx0 = x0c - a.x;  // the tile centre's offset from the record centre
         const float dy0 = y0c - a.y;
-        const TileQuad tq = tile_quad(A, B, C, dx0, dy0);
+        TileQuad tq = tile_quad(A, B, C, dx0, dy0);
+        const bool tdbl = dbl && r != 0xffffffffu;
+        const double *g64 = mom64 + (size_t)(tdbl ? r : 0u) * MOM64_STRIDE;
+        if (__any_sync(0xffffffffu, tdbl) && tdbl) tq = tile_quad_f64(g64 + MOM64_GEO, x0c, y0c);
         const float2 A2 = make_float2(A, A);
         float T0 = 0.f, T1 = 0.f, T2 = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
-        float y = -TC;
-#pragma unroll 2
-        for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
+        // one row y of the record: three row sums, folded into the six moments
+        auto row = [&](int j, float y) {
             const float b1 = fmaf(B, y, tq.D);
             const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
-            const float4 *g0r = (const float4 *)&sgvw[j * MG_TILE];
-            const float4 *g1r = g0r + NV / 4;
-            const float4 *g2r = g1r + NV / 4;
+            const float4 *gr = (const float4 *)&sgvw[j * MG_TILE];
             const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
-            // column pairs (i, i+1) with packed FP32x2 arithmetic:
-            // P0 += g e, P1 += (g x) e, P2 += (g x^2) e
+            // column pairs (i, i+1) with packed FP32x2 arithmetic: w = g e,
+            // P0 += w, P1 += x w, P2 += x^2 w
             const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
             float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
             for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
-                const float4 u0 = g0r[i4], u1 = g1r[i4], u2 = g2r[i4];
+                const float4 u = gr[i4];
                 uint4 rl = make_uint4(0u, 0u, 0u, 0u);
                 if (CELLS) rl = relr[i4];
 #pragma unroll
@@ -479,9 +533,10 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
                         if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
                         if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
                     }
-                    P0 = __ffma2_rn(h ? make_float2(u0.z, u0.w) : make_float2(u0.x, u0.y), e, P0);
-                    P1 = __ffma2_rn(h ? make_float2(u1.z, u1.w) : make_float2(u1.x, u1.y), e, P1);
-                    P2 = __ffma2_rn(h ? make_float2(u2.z, u2.w) : make_float2(u2.x, u2.y), e, P2);
+                    const float2 w = __fmul2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e);
+                    P0 = __fadd2_rn(P0, w);
+                    P1 = __ffma2_rn(x, w, P1);
+                    P2 = __ffma2_rn(xq[i4 * 2 + h], w, P2);
                 }
             }
             const float R0 = P0.x + P0.y, R1 = P1.x + P1.y, R2 = P2.x + P2.y;
@@ -491,15 +546,34 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             Y0 = fmaf(y, R0, Y0);
             Y1 = fmaf(y, R1, Y1);
             Y2 = fmaf(y * y, R0, Y2);
+        };
+        if (lg == 0) {
+            float y = -TC;
+#pragma unroll 2
+            for (int j = 0; j < MG_TILE; ++j, y += 1.f) row(j, y);
+        } else {
+            const int nrow = MG_TILE >> lg;
+            float y = (float)j0 - TC;
+            for (int j = j0; j < j0 + nrow; ++j, y += 1.f) row(j, y);
+            // the L partial sets of each record, summed over lanes src + k P
+            for (int o = P; o < 32; o <<= 1) {
+                T0 += __shfl_xor_sync(0xffffffffu, T0, o);
+                T1 += __shfl_xor_sync(0xffffffffu, T1, o);
+                T2 += __shfl_xor_sync(0xffffffffu, T2, o);
+                Y0 += __shfl_xor_sync(0xffffffffu, Y0, o);
+                Y1 += __shfl_xor_sync(0xffffffffu, Y1, o);
+                Y2 += __shfl_xor_sync(0xffffffffu, Y2, o);
+            }
+            if (lane >= P) r = 0xffffffffu;  // one lane per record adds it
         }
         if (r != 0xffffffffu) {
             if (dbl) {
                 // near-degenerate Gaussian: the moments about its centre are
                 // small differences of large terms, so the shift from the tile
                 // centre (exact offsets) and the sum over tiles are in FP64
-                const double X = (double)x0c - (double)a.x, Y = (double)y0c - (double)a.y;
+                const double X = (double)x0c - g64[MOM64_GEO], Y = (double)y0c - g64[MOM64_GEO + 1];
                 const double t0 = T0, t1 = T1, t2 = T2, y0 = Y0, y1 = Y1, y2 = Y2;
-                double *mr = mom64 + (size_t)r * 6;
+                double *mr = mom64 + (size_t)r * MOM64_STRIDE;
                 atomicAdd(mr + 0, t0);
                 atomicAdd(mr + 1, fma(X, t0, t1));
                 atomicAdd(mr + 2, fma(Y, t0, y0));
@@ -530,7 +604,7 @@ __global__ void __launch_bounds__(32 * RW, 4) k_render_bwd(StackTable tab, const
                                                           const float *__restrict__ grad_out, float *__restrict__ mom,
                                                           double *__restrict__ mom64, unsigned *counter)
 {
-    __shared__ __align__(16) float sgv[RW][3 * NV];
+    __shared__ __align__(16) float sgv[RW][NV];
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n_busy = hdr->n_busy;  // tiles without records contribute nothing
@@ -813,7 +887,10 @@ __global__ void k_zero_mom(float4 *mom, const unsigned char *__restrict__ f64, d
     if (n > cap_records) n = cap_records;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         mom[2 * r] = mom[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);  // 8 floats per record
-        if (f64[r]) mom64[3 * r] = mom64[3 * r + 1] = mom64[3 * r + 2] = make_double2(0.0, 0.0);
+        if (f64[r]) {
+            double2 *m2 = mom64 + (MOM64_STRIDE / 2) * r;
+            m2[0] = m2[1] = m2[2] = make_double2(0.0, 0.0);
+        }
     }
 }
 
@@ -849,11 +926,12 @@ __global__ void k_pose_rec(const WsHeader *hdr, long long cap_records, const flo
         float o6[6];
         if (DBL) {
             // the FP64 moments of a near-degenerate Gaussian, chained in FP64
-            const double *m = mom64 + (size_t)r * 6;
+            const double *m = mom64 + (size_t)r * MOM64_STRIDE;
             const double S0 = m[0], Sx = m[1], Sy = m[2], Sxx = m[3], Sxy = m[4], Syy = m[5];
+            const double A64 = m[MOM64_GEO + 2], B64 = m[MOM64_GEO + 3], C64 = m[MOM64_GEO + 4];
             const double la = (double)amp * 0.6931471805599453;
-            const double gpx = -la * (2.0 * A * Sx + (double)B2 * Sy);
-            const double gpy = -la * ((double)B2 * Sx + 2.0 * C * Sy);
+            const double gpx = -la * (2.0 * A64 * Sx + B64 * Sy);
+            const double gpy = -la * (B64 * Sx + 2.0 * C64 * Sy);
             double dm[3], dq[4], ds[3], da, dp[6];
             geometry_adjoint<double, true>(mu, qv, sc, al, Sd, la * Sxx, la * Sxy, la * Syy, gpx, gpy, S0, dm, dq,
                                            ds, da, dp);
@@ -891,10 +969,9 @@ __device__ __noinline__ void chain_gaussian_f64(const float *mu, const float *q,
     for (unsigned long long j = j0; j < j1; ++j) {
         const unsigned r = gmap[j];
         if ((long long)r >= cap_records) continue;
-        const float4 a = geo[r];
         const float2 b = geo2[r];
-        const double A = a.z, B2 = a.w, C = b.x;
-        const double *m = mom64 + (size_t)r * 6;
+        const double *m = mom64 + (size_t)r * MOM64_STRIDE;
+        const double A = m[MOM64_GEO + 2], B2 = m[MOM64_GEO + 3], C = m[MOM64_GEO + 4];
         const double la = (double)b.y * 0.6931471805599453;
         const double gpx = -la * (2.0 * A * m[1] + B2 * m[2]);
         const double gpy = -la * (B2 * m[1] + 2.0 * C * m[2]);
@@ -1195,8 +1272,8 @@ static void launch_fwd(const WsLayout &L, char *ws, const StackTable &tab, const
     k_render_fwd<CELLS, LOSS><<<grid, 32 * RW, 0, st>>>(
         tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
         (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg,
-        cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr, (const unsigned *)(ws + L.tile_list), hdr, out, ls,
-        &hdr->tile_ctr[0]);
+        cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr, (const unsigned *)(ws + L.tile_list), hdr,
+        (const unsigned char *)(ws + L.rec_f64), (const double *)(ws + L.rec_mom64), out, ls, &hdr->tile_ctr[0]);
 }
 
 // target != NULL: the L1 + L2 slice loss of mg_loss_l1l2 fused into the
