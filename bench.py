@@ -13,6 +13,9 @@ slice voxel) pairs inside the K = 3 ellipsoid of the profile-convolved
 covariance, counted on the device by mg_render_pair_count for the step's
 input. The evaluated (tile-level) pair count is reported beside it.
 
+The line's "fitted" sub-record times the same step on the Gaussians after a
+2000-iteration L1+L2 fit (the state a reconstruction spends its iterations in).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgauss|reference]
 Under torchrun each rank renders its own independent replica (seed = rank):
 weak scaling, no collective on the data path (the step does not shard).
@@ -47,7 +50,7 @@ PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (6, 1)}
 # DRAM bytes (read + write) per launch of the evaluation kernels on this
 # workload, from one ncu capture of the current kernels
 # (profiles/k_render_fwd_bwd_feta256_full.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"render_fwd": (187.3 + 55.6) * 1e6, "render_bwd": (245.3 + 63.1) * 1e6}
+PROFILED_TRAFFIC = {"render_fwd": None, "render_bwd": None}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).
@@ -185,22 +188,18 @@ def fitted_gaussians(wl, G, target, dev, iterations: int = 2000):
 # ---------------------------------------------------------------------------
 # the mgauss arm
 # ---------------------------------------------------------------------------
-def run_mgauss(args, rank, world, local_rank):
+def device_step_timing(G, wl, target, dev, args, dist=None):
+    """The device-resident step on Gaussians G: record pass + binning + forward
+    with the fused L1 + L2 loss + adjoint, captured once as a CUDA graph and
+    replayed ``args.steps`` times (L2 flushed between steps, CUDA events on
+    the launching stream), then the same steps launched one by one for the
+    evaluation kernels' live times and the per-stage breakdown. Returns a dict
+    with the renderer, buffers and all figures."""
     import torch
 
     from paper_2603_00145_b300 import SliceRenderer
     from paper_2603_00145_b300.ops import mg_profile_enable, mg_profile_read, mg_profile_stages
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-    wl, G, target = build_workload(args.workload, args.seed + rank, dev)
-    if args.fitted:
-        G = fitted_gaussians(wl, G, target, dev)
     m, q, s, a = (torch.from_numpy(x).to(dev) for x in (G.mean, G.quat, G.scale, G.alpha))
     R = SliceRenderer(wl.stacks, device=dev, check=True)
     out = R.forward(m, q, s, a)  # sizes the workspace (grows on overflow)
@@ -238,7 +237,7 @@ def run_mgauss(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -273,6 +272,55 @@ def run_mgauss(args, rank, world, local_rank):
     value, ms_step, pairs_job = job_throughput(pairs_inside, ms_total, args.steps, dist, dev)
     st = R.stats()
     assert st["status"] == 0, f"device status {st['status']} during the timed steps"
+    stages = {k: v for k, v in prof.items() if v[1] > 0}
+    roof = roofline(stages, pairs_eval, traffic=PROFILED_TRAFFIC if args.workload == "feta" and not args.fitted else None)
+    del flush, graph
+    return {"R": R, "out": out, "grad": grad, "loss": loss, "dev_in": (m, q, s, a), "value": value,
+            "ms_step": ms_step, "pairs_inside": pairs_inside, "pairs_eval": pairs_eval, "stats": st, "stages": stages,
+            "roofline": roof, "clocks": clk}
+
+
+def roofline(stages, pairs_eval, traffic=None):
+    """Roofline of the dominant evaluation kernel from its live CUDA-event time."""
+    dom = max(("render_fwd", "render_bwd"), key=lambda k: stages.get(k, (0, 0))[0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    achieved = pairs_eval / (dom_ms / 1e3)
+    peak = alu_peak_pairs(dom)
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": (traffic or {}).get(dom),
+            "traffic_unit": "bytes per launch (ncu capture)",
+            "peak_basis": (f"{N_SM} SMs x min({FP32_LANES}/{PAIR_OPS[dom][0]} FP32, {MUFU_LANES}/{PAIR_OPS[dom][1]} "
+                           f"MUFU) pairs/clk x {SM_MHZ:.0f} MHz (nominal unit counts)"),
+            "units_per_launch": pairs_eval, "ms_per_launch": dom_ms}
+    other = {}
+    for k in ("render_fwd", "render_bwd"):
+        if k in stages and k != dom:
+            t_ = stages[k][0] / stages[k][1]
+            other[k] = {"ms": t_, "Gpair_s": pairs_eval / (t_ / 1e3) / 1e9,
+                        "frac": pairs_eval / (t_ / 1e3) / alu_peak_pairs(k)}
+    roof["other"] = other
+    return roof
+
+
+def run_mgauss(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    wl, G, target = build_workload(args.workload, args.seed + rank, dev)
+    if args.fitted:
+        G = fitted_gaussians(wl, G, target, dev)
+    T = device_step_timing(G, wl, target, dev, args, dist)
+    R, out, grad, loss = T["R"], T["out"], T["grad"], T["loss"]
+    value, ms_step, pairs_inside, pairs_eval = T["value"], T["ms_step"], T["pairs_inside"], T["pairs_eval"]
+    stages, roof, clk, st = T["stages"], T["roofline"], T["clocks"], T["stats"]
+    nv = target.numel()
+    from paper_2603_00145_b300.ops import mg_profile_enable
 
     # end to end through the C ABI with host buffers: every step copies its
     # inputs (Gaussian parameters and target slices) from pinned memory, runs,
@@ -347,25 +395,6 @@ def run_mgauss(args, rank, world, local_rank):
     e2e_value, e2e_ms_step, _ = job_throughput(pairs_inside, e2e_ms, args.steps, dist, dev)
     e2e_ms = e2e_ms_step * args.steps
 
-    # roofline of the dominant evaluation kernel, timed live with CUDA events
-    stages = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(("render_fwd", "render_bwd"), key=lambda k: stages.get(k, (0, 0))[0])
-    dom_ms = stages[dom][0] / stages[dom][1]
-    achieved = pairs_eval / (dom_ms / 1e3)
-    peak = alu_peak_pairs(dom)
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(dom) if args.workload == "feta" else None,
-            "traffic_unit": "bytes per launch (ncu capture)",
-            "peak_basis": (f"{N_SM} SMs x min({FP32_LANES}/{PAIR_OPS[dom][0]} FP32, {MUFU_LANES}/{PAIR_OPS[dom][1]} "
-                           f"MUFU) pairs/clk x {SM_MHZ:.0f} MHz (nominal unit counts)"),
-            "units_per_launch": pairs_eval}
-    other = {}
-    for k in ("render_fwd", "render_bwd"):
-        if k in stages and k != dom:
-            t_ = stages[k][0] / stages[k][1]
-            other[k] = {"ms": t_, "Gpair_s": pairs_eval / (t_ / 1e3) / 1e9,
-                        "frac": pairs_eval / (t_ / 1e3) / alu_peak_pairs(k)}
-    roof["other"] = other
     launches = sum(KERNELS_PER_STAGE.get(k, 1) * v[1] for k, v in stages.items())
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -393,9 +422,26 @@ def run_mgauss(args, rank, world, local_rank):
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(G, wl, args.cpu_seconds)
-    if rank == 0 and world == 1 and args.recon_iters > 0:
-        del R, out, grad, flush
+    del T, R, out, grad, e2e_graphs, e2e_outs
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.fitted and args.fit_iters > 0:
+        # the same step on the Gaussians after an L1 + L2 fit: the state a
+        # reconstruction spends its iterations in (a few Gaussians grown over
+        # whole slices, many tiles with few records)
+        t0 = time.perf_counter()
+        Gf = fitted_gaussians(wl, G, target, dev, iterations=args.fit_iters)
+        fit_s = time.perf_counter() - t0
+        F = device_step_timing(Gf, wl, target, dev, args, None)
+        line["fitted"] = {"state": f"after {args.fit_iters} L1+L2 Adam iterations ({fit_s:.1f} s incl. set-up)",
+                          "value": F["value"], "unit": UNIT, "ms_per_step": F["ms_step"],
+                          "records": F["stats"]["records"], "entries": F["stats"]["entries"],
+                          "pairs_inside_per_step": F["pairs_inside"], "pairs_evaluated_per_step": F["pairs_eval"],
+                          "roofline": F["roofline"],
+                          "stages_ms_per_step": {k: v[0] / args.steps for k, v in F["stages"].items()},
+                          "clocks": F["clocks"]}
+        del F
         torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.recon_iters > 0:
         line["recon"] = run_recon(args, dev)
         if args.radius_sweep:
             line["radius_sweep"] = run_radius_sweep(args, dev)
@@ -639,6 +685,8 @@ def main():
     ap.add_argument("--workload", default="feta", choices=["feta", "tiny", "motion", "stress"])
     ap.add_argument("--fitted", action="store_true",
                     help="time the step on the Gaussians after a 2000-iteration L1+L2 fit instead of the initial ones")
+    ap.add_argument("--fit-iters", type=int, default=2000,
+                    help="iterations of the fit whose Gaussians the 'fitted' sub-record times (0: skip it)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

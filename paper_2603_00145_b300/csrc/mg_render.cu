@@ -336,14 +336,22 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n_tiles = tab.n_tiles_total;
     const long long n_idle = hdr->n_idle, n_busy = hdr->n_busy;
-    for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(counter, 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if ((long long)i >= n_busy) break;
-        fwd_tile<CELLS, LOSS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off,
-                              entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64, mom64, out, ls);
-        __syncwarp();
+    const long long n_bulk = max(0ll, n_busy - (long long)TILE_RESERVE * gridDim.x * RW);
+    for (unsigned part = 0; part < 2; ++part) {
+        const long long lo = part ? n_bulk : 0, hi = part ? n_busy : n_bulk;
+        const unsigned step = part ? 1u : TILE_CLAIM;
+        for (;;) {
+            unsigned i0 = 0;
+            if (lane == 0) i0 = atomicAdd(part ? counter + 5 : counter, step);  // tile_ctr[0], tile_ctr[5]
+            i0 = __shfl_sync(0xffffffffu, i0, 0);
+            if (lo + (long long)i0 >= hi) break;
+            for (long long i = lo + i0; i < lo + i0 + step && i < hi; ++i) {
+                fwd_tile<CELLS, LOSS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0],
+                                      tile_off, entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64,
+                                      mom64, out, ls);
+                __syncwarp();
+            }
+        }
     }
     for (;;) {
         unsigned i0 = 0;
@@ -608,14 +616,21 @@ __global__ void __launch_bounds__(32 * RW, 4) k_render_bwd(StackTable tab, const
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n_busy = hdr->n_busy;  // tiles without records contribute nothing
-    for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(counter, 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if ((long long)i >= n_busy) break;
-        bwd_tile<CELLS>(tab, (int)tile_list[i], lane, sgv[w], srel[CELLS ? w : 0], tile_off, entries, cap_entries,
-                        cap_records, geo, geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
-        __syncwarp();
+    const long long n_bulk = max(0ll, n_busy - (long long)TILE_RESERVE * gridDim.x * RW);
+    for (unsigned part = 0; part < 2; ++part) {
+        const long long lo = part ? n_bulk : 0, hi = part ? n_busy : n_bulk;
+        const unsigned step = part ? 1u : TILE_CLAIM;
+        for (;;) {
+            unsigned i0 = 0;
+            if (lane == 0) i0 = atomicAdd(part ? counter + 3 : counter, step);  // tile_ctr[1], tile_ctr[4]
+            i0 = __shfl_sync(0xffffffffu, i0, 0);
+            if (lo + (long long)i0 >= hi) break;
+            for (long long i = lo + i0; i < lo + i0 + step && i < hi; ++i) {
+                bwd_tile<CELLS>(tab, (int)tile_list[i], lane, sgv[w], srel[CELLS ? w : 0], tile_off, entries,
+                                cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
+                __syncwarp();
+            }
+        }
     }
 }
 
@@ -1358,7 +1373,9 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     }
     int nt = tab.n_tiles_total;
     if (nt > 0) {
-        cudaMemsetAsync((void *)&hdr->tile_ctr[1], 0, sizeof(unsigned), st);
+        // the backward's two work counters, tile_ctr[1] and tile_ctr[4] (the
+        // forward's counters in between are spent by now)
+        cudaMemsetAsync((void *)&hdr->tile_ctr[1], 0, 4 * sizeof(unsigned), st);
         MG_PROF(MG_ST_RENDER_BWD, st);
         const void *kern = cg.on ? (const void *)k_render_bwd<true> : (const void *)k_render_bwd<false>;
         int grid = resident_grid(kern, 32 * RW);
