@@ -49,8 +49,8 @@ KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 2, "k1_emit": 1
 PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (6, 1)}
 # DRAM bytes (read + write) per launch of the evaluation kernels on this
 # workload, from one ncu capture of the current kernels
-# (profiles/k_render_fwd_bwd_feta256_full.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"render_fwd": None, "render_bwd": None}
+# (profiles/render_step_feta256_launches.md); None once a kernel changes.
+PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": (230.38 + 51.42) * 1e6}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).

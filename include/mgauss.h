@@ -409,7 +409,23 @@ typedef struct {
     const float *table; /* MG_NRF_GRID: device FP32 [16][2^log2_table][2]; else unused */
     int32_t log2_table, n_min, n_max; /* MG_NRF_GRID geometry; 0 = 19, 16, 512 */
     float out_scale;    /* bound of |r|; the paper's 0.1 */
+    /* Encoding cache (MG_NRF_GRID; ignored for MG_NRF_FOURIER): a device buffer
+     * of mg_nrf_enc_bytes(net, n) bytes holding, for batch position i < n, the
+     * 32 encoded features of point i in the precision's element type (BF16 or
+     * FP32), caller-owned. enc_mode MG_NRF_ENC_STORE: a forward call (mg_nrf_fwd,
+     * mg_nrf_fwd_at) also writes the features; MG_NRF_ENC_LOAD: a backward call
+     * reads them instead of gathering the table again (the training step runs
+     * the forward and then the backward on the same points: the backward's grid
+     * gathers were 82M L2 requests per 2^20 points). The features read back
+     * are the bits the gathers would give, so results are unchanged. With
+     * LOAD the buffer must hold a STORE call's features for the same points,
+     * table and geometry. MG_NRF_ENC_NONE (0): no cache. */
+    void *enc;
+    int32_t enc_mode;
 } mg_nrf;
+enum { MG_NRF_ENC_NONE = 0, MG_NRF_ENC_STORE = 1, MG_NRF_ENC_LOAD = 2 };
+/* Bytes of the encoding cache for n points (0 for MG_NRF_FOURIER or bad args). */
+size_t mg_nrf_enc_bytes(const mg_nrf *net, int64_t n);
 
 /* Number of FP32 parameters of an encoding's MLP (-1 for an unknown one). */
 int64_t mg_nrf_param_count(int32_t encoding);

@@ -44,7 +44,10 @@ class MgWsLayout(ctypes.Structure):
 
 class MgNrf(ctypes.Structure):
     _fields_ = [("encoding", c_i32), ("precision", c_i32), ("params", c_p), ("table", c_p), ("log2_table", c_i32),
-                ("n_min", c_i32), ("n_max", c_i32), ("out_scale", c_f32)]
+                ("n_min", c_i32), ("n_max", c_i32), ("out_scale", c_f32), ("enc", c_p), ("enc_mode", c_i32)]
+
+
+MG_NRF_ENC_NONE, MG_NRF_ENC_STORE, MG_NRF_ENC_LOAD = 0, 1, 2
 
 
 class MgAdamGroup(ctypes.Structure):
@@ -92,6 +95,7 @@ SIGNATURES = {
     "mg_render_pair_count": (ctypes.c_int, [ctypes.POINTER(MgGaussians), ctypes.POINTER(MgStack), ctypes.c_int,
                                             ctypes.POINTER(MgOpts), c_p, c_sz, ctypes.POINTER(c_i64), c_p]),
     "mg_nrf_param_count": (c_i64, [c_i32]),
+    "mg_nrf_enc_bytes": (ctypes.c_size_t, [c_p, c_i64]),
     "mg_nrf_fwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p]),
     "mg_nrf_bwd": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_p, c_p, c_p]),
     "mg_nrf_fwd_at": (ctypes.c_int, [ctypes.POINTER(MgNrf), c_p, c_i64, c_p, c_i64, c_p, c_p]),

@@ -693,6 +693,7 @@ mg_status mg_render_pair_count(const mg_gaussians *g, const mg_stack *stacks, in
 }
 
 int64_t mg_nrf_param_count(int32_t encoding) { return mg_nrf_param_count_impl(encoding); }
+size_t mg_nrf_enc_bytes(const mg_nrf *net, int64_t n) { return mg_nrf_enc_bytes_impl(net, n); }
 
 static bool valid_nrf(const mg_nrf *net, std::string &why)
 {
@@ -725,6 +726,14 @@ static bool valid_nrf(const mg_nrf *net, std::string &why)
     }
     if (!(net->out_scale > 0.f) || !isfinite(net->out_scale)) {
         why = "out_scale must be positive";
+        return false;
+    }
+    if (net->enc_mode != MG_NRF_ENC_NONE && net->enc_mode != MG_NRF_ENC_STORE && net->enc_mode != MG_NRF_ENC_LOAD) {
+        why = "unknown enc_mode";
+        return false;
+    }
+    if (net->encoding == MG_NRF_GRID && net->enc_mode != MG_NRF_ENC_NONE && !net->enc) {
+        why = "enc_mode needs an encoding cache";
         return false;
     }
     return true;

@@ -230,6 +230,7 @@ struct MgProfScope {
 
 // host-side launch helpers (defined in the .cu files)
 int64_t mg_nrf_param_count_impl(int32_t encoding);
+size_t mg_nrf_enc_bytes_impl(const mg_nrf *net, long long n);
 cudaError_t mg_launch_nrf(const mg_nrf *net, const float *xyz, long long n, const float *grad_out, float *out,
                           float *g_params, float *g_table, bool train, cudaStream_t st, const long long *idx = nullptr,
                           long long rows = 0);

@@ -97,6 +97,8 @@ struct NrfArgs {
     GridGeom grid;
     const long long *idx;  // point i is row idx[i] of xyz / out / grad_out (NULL: row i)
     long long rows;        // with idx: rows of xyz / out / grad_out; other indices are skipped
+    void *enc;             // grid encoding cache [n][32] (element type of the precision)
+    int enc_mode;          // MG_NRF_ENC_NONE / _STORE / _LOAD
 };
 
 // Row of point i (-1: past the end or an index outside [0, rows)).
@@ -490,7 +492,15 @@ __device__ __forceinline__ void nrf_body(const NrfArgs A, const float *__restric
                 const int p = i / PADD, k = Preset<ENC>::K0 + i % PADD;
                 sH0[p * LY::LDH0 + k] = to_e<E>(0.f);
             }
+        } else if (A.enc_mode == MG_NRF_ENC_LOAD) {
+            // the features a forward call stored for these points (coalesced)
+            const E *ec = (const E *)A.enc;
+            for (int i = tid; i < P * 2 * GRID_LEVELS; i += NRF_NT) {
+                const int p = i / (2 * GRID_LEVELS), k = i - p * (2 * GRID_LEVELS);
+                sH0[p * LY::LDH0 + k] = (p0 + p < n) ? ec[(p0 + p) * (2 * GRID_LEVELS) + k] : to_e<E>(0.f);
+            }
         } else {
+            E *ec = A.enc_mode == MG_NRF_ENC_STORE ? (E *)A.enc : nullptr;
             for (int i = tid; i < P * GRID_LEVELS; i += NRF_NT) {
                 const int p = i / GRID_LEVELS, lv = i - p * GRID_LEVELS;
                 const float x[3] = {sPt[p * 4], sPt[p * 4 + 1], sPt[p * 4 + 2]};
@@ -504,8 +514,13 @@ __device__ __forceinline__ void nrf_body(const NrfArgs A, const float *__restric
                     f0 = fmaf(cr.wt[c], v.x, f0);
                     f1 = fmaf(cr.wt[c], v.y, f1);
                 }
-                sH0[p * LY::LDH0 + 2 * lv] = to_e<E>(f0);
-                sH0[p * LY::LDH0 + 2 * lv + 1] = to_e<E>(f1);
+                const E e0 = to_e<E>(f0), e1 = to_e<E>(f1);
+                sH0[p * LY::LDH0 + 2 * lv] = e0;
+                sH0[p * LY::LDH0 + 2 * lv + 1] = e1;
+                if (ec && p0 + p < n) {
+                    ec[(p0 + p) * (2 * GRID_LEVELS) + 2 * lv] = e0;
+                    ec[(p0 + p) * (2 * GRID_LEVELS) + 2 * lv + 1] = e1;
+                }
             }
         }
         __syncthreads();
@@ -732,6 +747,8 @@ cudaError_t launch_nrf(const mg_nrf *net, const float *xyz, long long n, const f
     A.table = net->table;
     A.out_scale = net->out_scale;
     A.grid = make_grid(net);
+    A.enc = ENC == MG_NRF_GRID ? net->enc : nullptr;
+    A.enc_mode = (ENC == MG_NRF_GRID && net->enc) ? net->enc_mode : MG_NRF_ENC_NONE;
     auto kern = TRAIN ? k_nrf<ENC, BF16, TRAIN> : k_nrf4<ENC, BF16, TRAIN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::bytes);
     if (e != cudaSuccess) return e;
@@ -749,6 +766,12 @@ cudaError_t launch_nrf(const mg_nrf *net, const float *xyz, long long n, const f
 }
 
 }  // namespace
+
+size_t mg_nrf_enc_bytes_impl(const mg_nrf *net, long long n)
+{
+    if (!net || n < 0 || net->encoding != MG_NRF_GRID) return 0;
+    return (size_t)n * 2 * GRID_LEVELS * (net->precision == MG_NRF_BF16 ? 2 : 4);
+}
 
 int64_t mg_nrf_param_count_impl(int32_t encoding)
 {

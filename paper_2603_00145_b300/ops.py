@@ -583,12 +583,24 @@ class NRF:
                 raise ValueError("table must be [16, 2^log2_table, 2]")
         self.log2_table, self.n_min, self.n_max, self.out_scale = log2_table, n_min, n_max, out_scale
 
-    def struct(self, params=None, table=None) -> L.MgNrf:
+    def struct(self, params=None, table=None, enc=None, enc_mode: int = 0) -> L.MgNrf:
         p = self.params if params is None else params
         t = self.table if table is None else table
         return L.MgNrf(ENCODINGS[self.encoding], PRECISIONS[self.precision], _dev(p, "params"),
                        _dev(t, "table") if t is not None else None, self.log2_table, self.n_min, self.n_max,
-                       float(self.out_scale))
+                       float(self.out_scale), _dev(enc, "enc", torch.uint8) if enc is not None else None,
+                       enc_mode if enc is not None else L.MG_NRF_ENC_NONE)
+
+    def enc_cache(self, n: int, device=None):
+        """A device buffer for the grid encoding of n points (None for the
+        Fourier encoding): a forward call at rows stores the features into it,
+        the backward call at the same rows reads them back instead of
+        gathering the table again (mg_nrf.enc / enc_mode)."""
+        s = self.struct()
+        nb = int(L.lib().mg_nrf_enc_bytes(ctypes.byref(s), int(n)))
+        if nb == 0:
+            return None
+        return torch.empty(nb, dtype=torch.uint8, device=device or self.params.device)
 
 
 def mg_nrf_fwd(net: NRF, xyz, out, params=None, table=None, stream=None):
@@ -611,28 +623,40 @@ def mg_nrf_bwd(net: NRF, xyz, grad_out, g_params, g_table=None, params=None, tab
                                _stream_handle(stream)), "mg_nrf_bwd")
 
 
-def mg_nrf_fwd_at(net: NRF, coords, idx, n: int, acc, params=None, table=None, stream=None):
+def _check_enc(net: NRF, enc, n: int):
+    if enc is not None:
+        need = int(L.lib().mg_nrf_enc_bytes(ctypes.byref(net.struct()), int(n)))
+        if enc.numel() * enc.element_size() < need:
+            raise ValueError(f"encoding cache holds {enc.numel() * enc.element_size()} bytes, {need} needed")
+
+
+def mg_nrf_fwd_at(net: NRF, coords, idx, n: int, acc, params=None, table=None, stream=None, enc=None):
     """acc[idx[i]] += r(coords[idx[i]]) for i < n (the field at a batch of
-    rows; indices outside [0, rows) are skipped)."""
+    rows; indices outside [0, rows) are skipped). ``enc`` (NRF.enc_cache):
+    the points' grid encoding is also stored there for mg_nrf_bwd_at."""
     rows = coords.numel() // 3
     _dev(coords, "coords", numel=3 * rows)
     _dev(acc, "acc", numel=rows)
     ip = _dev_idx(idx, n)
-    s = net.struct(params, table)
+    _check_enc(net, enc, n)
+    s = net.struct(params, table, enc, L.MG_NRF_ENC_STORE)
     L.check(L.lib().mg_nrf_fwd_at(ctypes.byref(s), coords.data_ptr(), rows, ip, n, acc.data_ptr(),
                                   _stream_handle(stream)), "mg_nrf_fwd_at")
 
 
 def mg_nrf_bwd_at(net: NRF, coords, idx, n: int, grad_acc, g_params, g_table=None, params=None, table=None,
-                  stream=None):
-    """Gradients of sum_i grad_acc[idx[i]] r(coords[idx[i]]) for the field's parameters (and table)."""
+                  stream=None, enc=None):
+    """Gradients of sum_i grad_acc[idx[i]] r(coords[idx[i]]) for the field's
+    parameters (and table). ``enc``: the encoding a mg_nrf_fwd_at call stored
+    for the same rows, read instead of gathering the table again."""
     rows = coords.numel() // 3
     _dev(coords, "coords", numel=3 * rows)
     _dev(grad_acc, "grad_acc", numel=rows)
     ip = _dev_idx(idx, n)
     gp = _dev(g_params, "g_params", numel=mg_nrf_param_count(net.encoding))
     gt = _dev(g_table, "g_table") if g_table is not None else None
-    s = net.struct(params, table)
+    _check_enc(net, enc, n)
+    s = net.struct(params, table, enc, L.MG_NRF_ENC_LOAD)
     L.check(L.lib().mg_nrf_bwd_at(ctypes.byref(s), coords.data_ptr(), rows, ip, n, grad_acc.data_ptr(), gp, gt,
                                   _stream_handle(stream)), "mg_nrf_bwd_at")
 

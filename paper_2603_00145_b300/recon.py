@@ -148,6 +148,7 @@ class _Trainer:
             self.ws = torch.empty(ops.mg_reduce_workspace_size(target.numel()), dtype=torch.uint8, device=device)
         self.nrf = self.nrf_adam = self.coords = None
         self.nrf_params = self.nrf_table = None
+        self.nrf_enc = None  # grid encoding of the current NRF batch (forward stores, backward reads)
         # device buffers of the parameterisation (mg_params_fwd / _bwd)
         n = m.mean_c.shape[0]
         f32 = dict(dtype=torch.float32, device=device)
@@ -193,7 +194,10 @@ class _Trainer:
             if self.nrf is not None:
                 n_vox = self.target.numel()
                 idx = torch.randint(0, n_vox, (min(cfg.nrf_batch, n_vox),), device=self.device)
-                ops.mg_nrf_fwd_at(self.nrf, self.coords, idx, idx.numel(), pred, self.nrf_params, self.nrf_table)
+                if self.nrf_enc is None:
+                    self.nrf_enc = self.nrf.enc_cache(idx.numel())
+                ops.mg_nrf_fwd_at(self.nrf, self.coords, idx, idx.numel(), pred, self.nrf_params, self.nrf_table,
+                                  enc=self.nrf_enc)
             # the loss (FP64 sums) and its gradient dL/dpred in one kernel
             if cfg.loss == "paper":
                 grad = torch.empty_like(pred)
@@ -207,7 +211,7 @@ class _Trainer:
                 gp = torch.empty_like(self.nrf_params)
                 gt = torch.empty_like(self.nrf_table) if self.nrf_table is not None else None
                 ops.mg_nrf_bwd_at(self.nrf, self.coords, idx, idx.numel(), grad, gp, gt, self.nrf_params,
-                                  self.nrf_table)
+                                  self.nrf_table, enc=self.nrf_enc)
                 self.nrf_params.grad = gp
                 if gt is not None:
                     self.nrf_table.grad = gt

@@ -199,3 +199,35 @@ def test_nrf_at_indexed_rows(preset):
     assert _rel(acc3.cpu().numpy(), want3) <= 1e-5
     with pytest.raises(ValueError):
         mg_nrf_fwd_at(net, cd, idd.to(torch.int32), n, acc)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_nrf_encoding_cache(precision):
+    """The training pair with the grid-encoding cache (mg_nrf.enc): the forward
+    at rows stores each point's features, the backward at the same rows reads
+    them instead of gathering the table. The field is bit-identical, the
+    gradients equal the uncached ones up to the atomic summation order."""
+    from paper_2603_00145_b300 import mg_nrf_bwd_at, mg_nrf_fwd_at
+
+    net, ref = _nets("grid", precision)
+    rows, n = 2500, 3000 + 7
+    coords = torch.from_numpy(_points(rows, 11)).cuda()
+    idx = torch.from_numpy(np.random.default_rng(12).integers(-3, rows + 3, size=n).astype(np.int64)).cuda()
+    enc = net.enc_cache(n)
+    assert enc is not None and enc.numel() == n * 32 * (2 if precision == "bf16" else 4)
+    acc0, acc1 = torch.zeros(rows, device="cuda"), torch.zeros(rows, device="cuda")
+    mg_nrf_fwd_at(net, coords, idx, n, acc0)
+    mg_nrf_fwd_at(net, coords, idx, n, acc1, enc=enc)
+    torch.cuda.synchronize()
+    ga = torch.from_numpy(np.random.default_rng(13).normal(size=rows).astype(np.float32)).cuda()
+    gp0, gp1 = torch.empty_like(net.params), torch.empty_like(net.params)
+    gt0, gt1 = torch.empty_like(net.table), torch.empty_like(net.table)
+    mg_nrf_bwd_at(net, coords, idx, n, ga, gp0, gt0)
+    mg_nrf_bwd_at(net, coords, idx, n, ga, gp1, gt1, enc=enc)
+    torch.cuda.synchronize()
+    # the forward adds per point with atomics: compare per row within FP32 order
+    assert _rel(acc1.cpu().numpy(), acc0.cpu().numpy()) <= 1e-6
+    assert _rel(gp1.cpu().numpy(), gp0.cpu().numpy()) <= 1e-6
+    assert _rel(gt1.cpu().numpy(), gt0.cpu().numpy()) <= 1e-6
+    with pytest.raises(ValueError):
+        mg_nrf_bwd_at(net, coords, idx, n, ga, gp1, gt1, enc=enc[:100])
