@@ -302,6 +302,69 @@ def roofline(stages, pairs_eval, traffic=None):
     return roof
 
 
+# Tensor-core work of the hash-grid NRF per point (BF16 mma, FP32 accumulate):
+# layers 32->64, 64->64, 64->1 = 6208 MAC forward; the training backward
+# recomputes the forward, forms dW (6208 MAC) and the deltas of the hidden
+# layers and the features (4096 + 2048 MAC).
+NRF_FLOPS_FWD = 2 * (32 * 64 + 64 * 64 + 64)
+NRF_FLOPS_BWD = NRF_FLOPS_FWD + 2 * (32 * 64 + 64 * 64 + 64) + 2 * (64 * 64 + 64 * 32)
+# L2 requests per 2^20 points from one ncu capture of the BF16 grid kernels
+# (profiles/nrf_grid_bf16.md): table gathers (forward) and table-gradient
+# atomics (backward); None once a kernel changes.
+NRF_PROFILED = {"fwd_gather_requests": 83115931, "bwd_red_requests": 201154922, "bwd_gather_requests": 3116625}
+
+
+def nrf_pair_timing(wl, dev, steps: int, warmup: int, n: int = 1 << 20):
+    """The neural residual field's training pair as the reconstruction runs it
+    once the field is on: mg_nrf_fwd_at (BF16 hash grid, adds r at 2^20 random
+    slice voxels, storing the points' encoding) then mg_nrf_bwd_at (gradients
+    of the parameters and the table, reading the encoding back), on the
+    workload's voxel coordinates; CUDA events around each call."""
+    import torch
+
+    import mg_synth as ms
+    from paper_2603_00145_b300 import recon
+    from paper_2603_00145_b300.ops import NRF, mg_nrf_bwd_at, mg_nrf_fwd_at
+
+    coords = recon.voxel_coords(wl.stacks, (0.0, 0.0, 0.0), wl.phantom.fov_mm / 2, device=dev)
+    rows = coords.numel() // 3
+    W, b, t = ms.nrf_init("grid", 0, bf16=True, last_gain=0.1)
+    net = NRF("grid", "bf16", W, b, t, device=dev)
+    acc = torch.zeros(rows, device=dev)
+    ga = torch.randn(rows, device=dev)
+    gp, gt = torch.empty_like(net.params), torch.empty_like(net.table)
+    enc = net.enc_cache(n)
+    tf = tb = 0.0
+    for k in range(warmup + steps):
+        idx = torch.randint(0, rows, (n,), device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        mg_nrf_fwd_at(net, coords, idx, n, acc, enc=enc)
+        ev[1].record()
+        mg_nrf_bwd_at(net, coords, idx, n, ga, gp, gt, enc=enc)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if k >= warmup:
+            tf += ev[0].elapsed_time(ev[1])
+            tb += ev[1].elapsed_time(ev[2])
+    fwd_ms, bwd_ms = tf / steps, tb / steps
+    peaks = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1800.0))
+    ach_f = NRF_FLOPS_FWD * n / (fwd_ms * 1e-3) / 1e12
+    ach_b = NRF_FLOPS_BWD * n / (bwd_ms * 1e-3) / 1e12
+    dom = "nrf_bwd" if bwd_ms >= fwd_ms else "nrf_fwd"
+    ach = ach_b if dom == "nrf_bwd" else ach_f
+    return {"points": n, "encoding": "hash grid 16 x 2, 2 x 64 ReLU, BF16 mma.sync, FP32 accumulation",
+            "fwd_at_ms": fwd_ms, "bwd_at_ms": bwd_ms, "pair_ms": fwd_ms + bwd_ms,
+            "roofline": {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "peak_basis": "bf16_tflops of MEASURED_PEAKS.json (measured, burst)"
+                         if "bf16_tflops" in peaks else "fallback 1.8 PFLOP/s",
+                         "traffic": None,
+                         "note": "the MLP is 64 wide; the kernels are bound by L2 requests (hash-table "
+                                 "gathers forward, table-gradient atomics backward), not by the tensor pipe"},
+            "l2_requests_profiled": NRF_PROFILED}
+
+
 def run_mgauss(args, rank, world, local_rank):
     import torch
 
@@ -440,6 +503,9 @@ def run_mgauss(args, rank, world, local_rank):
                           "stages_ms_per_step": {k: v[0] / args.steps for k, v in F["stages"].items()},
                           "clocks": F["clocks"]}
         del F
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.nrf:
+        line["nrf"] = nrf_pair_timing(wl, dev, args.steps, args.warmup)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.recon_iters > 0:
         line["recon"] = run_recon(args, dev)
@@ -687,6 +753,7 @@ def main():
                     help="time the step on the Gaussians after a 2000-iteration L1+L2 fit instead of the initial ones")
     ap.add_argument("--fit-iters", type=int, default=2000,
                     help="iterations of the fit whose Gaussians the 'fitted' sub-record times (0: skip it)")
+    ap.add_argument("--nrf", type=int, default=1, help="time the NRF training pair (1) or not (0)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
