@@ -376,8 +376,20 @@ def run_mgauss(args, rank, world, local_rank):
 
         dist.init_process_group("nccl", device_id=dev)
     wl, G, target = build_workload(args.workload, args.seed + rank, dev)
-    if args.fitted:
+    if args.only == "nrf":
+        if rank == 0:
+            print(json.dumps({"metric": "NRF training pair ms per 2^20 points", "workload": wl.name,
+                              "nrf": nrf_pair_timing(wl, dev, args.steps, args.warmup)}), flush=True)
+        return
+    if args.gaussians:
+        import mg_synth as ms
+
+        z = np.load(args.gaussians)
+        G = ms.Gaussians(z["mean"], z["quat"], z["scale"], z["alpha"])
+    elif args.fitted:
         G = fitted_gaussians(wl, G, target, dev)
+    if args.save_gaussians and rank == 0:
+        np.savez(args.save_gaussians, mean=G.mean, quat=G.quat, scale=G.scale, alpha=G.alpha)
     T = device_step_timing(G, wl, target, dev, args, dist)
     R, out, grad, loss = T["R"], T["out"], T["grad"], T["loss"]
     value, ms_step, pairs_inside, pairs_eval = T["value"], T["ms_step"], T["pairs_inside"], T["pairs_eval"]
@@ -463,7 +475,8 @@ def run_mgauss(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ellipsoid phantom, simulated stacks)",
-            "config": {"workload": wl.name + ("-fitted" if args.fitted else ""), "gaussians": G.n,
+            "config": {"workload": wl.name + ("-fitted" if args.fitted else "") +
+                       ("-" + os.path.basename(args.gaussians) if args.gaussians else ""), "gaussians": G.n,
                        "stacks": len(wl.stacks),
                        "slices": sum(s_.n_slices for s_ in wl.stacks), "voxels": nv, "cutoff_k": 3.0,
                        "records": st["records"], "entries": st["entries"],
@@ -754,6 +767,12 @@ def main():
     ap.add_argument("--fit-iters", type=int, default=2000,
                     help="iterations of the fit whose Gaussians the 'fitted' sub-record times (0: skip it)")
     ap.add_argument("--nrf", type=int, default=1, help="time the NRF training pair (1) or not (0)")
+    ap.add_argument("--only", choices=["nrf"], default=None,
+                    help="nrf: time only the NRF training pair and print its line")
+    ap.add_argument("--gaussians", default=None,
+                    help="time the step on the Gaussians of this .npz (mean, quat, scale, alpha) instead")
+    ap.add_argument("--save-gaussians", default=None,
+                    help="write the Gaussians the step is timed on (initial, fitted or loaded) to this .npz")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -765,8 +784,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.fitted and args.impl == "reference":
-        ap.error("--fitted needs the GPU fit; the reference arm times the oracle on the initial Gaussians only")
+    if (args.fitted or args.gaussians or args.only) and args.impl == "reference":
+        ap.error("--fitted, --gaussians and --only concern the GPU arm; the reference arm times the oracle on the "
+                 "initial Gaussians only")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
