@@ -235,6 +235,10 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.rec_cell = o.local_set == MG_LOCAL_CELLS ? take(16 * (size_t)L.cap_records) : 0;
     L.rec_f64 = take((size_t)L.cap_records);
     L.rec_mom64 = take(sizeof(double) * MOM64_STRIDE * (size_t)L.cap_records);
+    L.big_n = take(sizeof(unsigned) * (size_t)L.cap_chunks);
+    L.big_list = take(sizeof(unsigned) * BIG_MAX * (size_t)L.cap_chunks);
+    L.tile_small = take(sizeof(unsigned) * (size_t)tiles);
+    L.tile_big = take(sizeof(unsigned) * (size_t)tiles);
     L.total = off;
     return L;
 }

@@ -466,6 +466,41 @@ __device__ __forceinline__ int nth_listed_tile(const ushort4 &rc, unsigned long 
     return ((int)rc.y + n + (int)(i / W)) * TX + (int)rc.x + (int)(i % W);
 }
 
+// the number of tiles a record lists (its rectangle less the first eight
+// rows' insets)
+__device__ __forceinline__ int listed_count(const ushort4 &rc, unsigned long long ins)
+{
+    if (rc.x > rc.z || rc.y > rc.w) return 0;
+    const int h = (int)rc.w - (int)rc.y + 1, W = (int)rc.z - (int)rc.x + 1;
+    int a = 0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        const unsigned b = (unsigned)(ins >> (8 * n)) & 0xFFu;
+        if (n < h) a += max(W - (int)(b & 15u) - (int)(b >> 4), 0);
+    }
+    return a + max(h - 8, 0) * W;
+}
+
+// does the record list tile (tx, ty)?
+__device__ __forceinline__ bool lists_tile(const ushort4 &rc, unsigned long long ins, int tx, int ty)
+{
+    if (ty < (int)rc.y || ty > (int)rc.w) return false;
+    const int2 sp = row_span(rc, ins, ty - (int)rc.y);
+    return tx >= sp.x && tx <= sp.y;
+}
+
+// A batch's records listed apart (large, while the chunk's list has room):
+// the same rule in the histogram and the scatter. nbig: the chunk's list
+// length so far (updated); returns the lane's slot, or -1.
+__device__ __forceinline__ int big_slot(int area, unsigned &nbig, unsigned lt)
+{
+    const bool big = area > BIG_AREA;
+    const unsigned bm = __ballot_sync(0xffffffffu, big);
+    const unsigned slot = nbig + __popc(bm & lt);
+    nbig = min(nbig + (unsigned)__popc(bm), (unsigned)BIG_MAX);
+    return big && slot < (unsigned)BIG_MAX ? (int)slot : -1;
+}
+
 // lane j's record tiles, fetched by every lane of the warp
 __device__ __forceinline__ void shfl_tiles(const ushort4 &rc, unsigned long long ins, int j, ushort4 &rj,
                                            unsigned long long &ij)
@@ -892,8 +927,14 @@ __global__ void __launch_bounds__(K1_NT) k1_count_cells(const SliceDev *__restri
 
 __global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsigned *__restrict__ bits,
                                                  const unsigned *__restrict__ off, long long NW,
-                                                 const unsigned *__restrict__ goff, Records rec, unsigned *gmap)
+                                                 const unsigned *__restrict__ goff, Records rec, unsigned *gmap,
+                                                 const SliceDev *__restrict__ slices, WsHeader *hdr)
 {
+    // block 0 also marks the stacks whose slices do not all share one rotation
+    if (blockIdx.x == 0)
+        for (int k = 1 + threadIdx.x; k < S; k += K1_NT)
+            if (slices[k].stack == slices[k - 1].stack && !slices[k].same_frame)
+                atomicOr(&hdr->moving, 1u << slices[k].stack);
     const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
     const long long wg = g >> 5;
     const bool valid = g < n;
@@ -1102,11 +1143,12 @@ constexpr size_t BIN_SMEM_MAX = 200 * 1024;
 
 __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *slices, int S, const unsigned *slice_rs,
                                                              const unsigned *chunk_base, const RecTiles *tiles,
-                                                             unsigned *hist,
-                                                             int Tmax, long long cap_chunks)
+                                                             unsigned *hist, int Tmax, long long cap_chunks,
+                                                             unsigned *big_n, unsigned *big_list, WsHeader *hdr)
 {
     extern __shared__ unsigned smem_u[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
     unsigned *hs = smem_u + w * Tmax;
     unsigned n_chunks = chunk_base[S];
     if ((long long)n_chunks > cap_chunks) n_chunks = (unsigned)cap_chunks;
@@ -1118,10 +1160,23 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
         unsigned r1 = min(r0 + MG_CHUNK, slice_rs[k + 1]);
         for (int t = lane; t < Tk; t += 32) hs[t] = 0;
         __syncwarp();
-        for (unsigned r = r0 + lane; r < r1; r += 32) {
-            const RecTiles rt = load_tiles(tiles + r);
+        unsigned nbig = 0;
+        for (unsigned base = r0; base < r1; base += 32) {
+            const unsigned r = base + lane;
+            RecTiles rt;
+            rt.rect = make_ushort4(1, 1, 0, 0);
+            rt.inset = 0ull;
+            if (r < r1) rt = load_tiles(tiles + r);
             const ushort4 rc = rt.rect;
             const unsigned long long ins = rt.inset;
+            // a rectangle of at most BIG_AREA tiles lists at most that many
+            const bool wide = rc.x <= rc.z && rc.y <= rc.w && ((int)rc.z - rc.x + 1) * ((int)rc.w - rc.y + 1) > BIG_AREA;
+            const int area = wide ? listed_count(rc, ins) : 0;
+            const int slot = big_slot(area, nbig, lt);
+            if (slot >= 0) {
+                big_list[(size_t)c * BIG_MAX + slot] = r;  // counted and placed by k_bin_big
+                continue;
+            }
             for (int ty = rc.y; ty <= rc.w; ++ty) {
                 const int2 sp = row_span(rc, ins, ty - rc.y);
                 for (int tx = sp.x; tx <= sp.y; ++tx) atomicAdd(&hs[ty * TX + tx], 1u);
@@ -1130,6 +1185,10 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
         __syncwarp();
         unsigned *hout = hist + (size_t)c * Tmax;
         for (int t = lane; t < Tk; t += 32) hout[t] = hs[t];
+        if (lane == 0) {
+            big_n[c] = nbig;
+            if (nbig) atomicAdd(&hdr->n_big, (unsigned long long)nbig);
+        }
         __syncwarp();
     }
 }
@@ -1143,8 +1202,10 @@ constexpr int COLSCAN_NT = 256;
 __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slices, int S, const unsigned *chunk_base,
                                                             unsigned *hist, int Tmax, long long cap_chunks,
                                                             unsigned *tile_cnt, unsigned *tile_list,
-                                                            long long n_tiles, WsHeader *hdr)
+                                                            long long n_tiles, WsHeader *hdr,
+                                                            const unsigned *tile_big, unsigned *tile_small)
 {
+    const bool any_big = hdr->n_big > 0;  // tile_big is written only then
     __shared__ unsigned wb[COLSCAN_NT / 32], wi[COLSCAN_NT / 32];
     __shared__ unsigned base_b, base_i;
     const long long total = (long long)S * Tmax;
@@ -1175,7 +1236,11 @@ __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slic
                     run += v[u];
                 }
             }
-            tile_cnt[slices[k].tile_base + t] = run;
+            // the large records listed apart follow the tile's other entries
+            const int tile = slices[k].tile_base + t;
+            tile_small[tile] = run;
+            if (any_big) run += tile_big[tile];
+            tile_cnt[tile] = run;
         }
         const bool busy = real && run > 0, idle = real && run == 0;
         const unsigned bb = __ballot_sync(0xffffffffu, busy), ib = __ballot_sync(0xffffffffu, idle);
@@ -1205,7 +1270,7 @@ __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slic
     }
 }
 
-__global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *slices, int S,
+__global__ void __launch_bounds__(32 * BIN_WARPS, 12) k_bin_scatter(const SliceDev *slices, int S,
                                                                 const unsigned *slice_rs, const unsigned *chunk_base,
                                                                 const RecTiles *tiles, const unsigned *hist,
                                                                 int Tmax,
@@ -1241,6 +1306,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
             for (; t < Tk; t += 32) cur[t] = tile_off[tb + t] + hin[t];
         }
         __syncwarp();
+        unsigned nbig = 0;
         for (unsigned base = r0; base < r1; base += 32) {
             unsigned r = base + lane;
             bool have = r < r1;
@@ -1250,11 +1316,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
             if (have) rt = load_tiles(tiles + r);
             const ushort4 rc = rt.rect;
             const unsigned long long ins = rt.inset;
-            int area = 0;
-            for (int ty = rc.y; ty <= rc.w; ++ty) {
-                const int2 sp = row_span(rc, ins, ty - rc.y);
-                area += max(sp.y - sp.x + 1, 0);
-            }
+            int area = listed_count(rc, ins);
+            if (big_slot(area, nbig, lt) >= 0) area = 0;  // listed apart: placed by k_bin_big_place
             int maxa = __reduce_max_sync(0xffffffffu, area);
             unsigned incl = (unsigned)area;
 #pragma unroll
@@ -1323,6 +1386,96 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_scatter(const SliceDev *
     }
 }
 
+// The records listed apart (large records), one thread per tile of a slice:
+// COUNT writes how many list the tile (tile_big); PLACE writes them after the
+// tile's other entries, in chunk order and each chunk's list order. The
+// slice's listed records are staged in shared memory (their chunks' list
+// lengths scanned, then the records loaded in parallel) and every tile thread
+// tests them in order.
+constexpr int BIG_NT = 256;
+constexpr int BIG_STAGE = 512;
+template <bool PLACE>
+__global__ void __launch_bounds__(BIG_NT) k_bin_big(const SliceDev *__restrict__ slices, int S, int Tmax,
+                                                    const unsigned *__restrict__ chunk_base, long long cap_chunks,
+                                                    const unsigned *__restrict__ big_n,
+                                                    const unsigned *__restrict__ big_list,
+                                                    const RecTiles *__restrict__ tiles, unsigned *tile_big,
+                                                    const unsigned *__restrict__ tile_off,
+                                                    const unsigned *__restrict__ tile_small, unsigned *entries,
+                                                    long long cap_entries, const WsHeader *hdr)
+{
+    __shared__ unsigned offs[BIG_NT + 1];
+    __shared__ unsigned wsum[BIG_NT / 32];
+    __shared__ uint4 srt[BIG_STAGE];
+    __shared__ unsigned srid[BIG_STAGE];
+    if (hdr->n_big == 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per = (Tmax + BIG_NT - 1) / BIG_NT;  // blocks of tiles per slice
+    for (long long job = blockIdx.x; job < (long long)S * per; job += gridDim.x) {
+        const int k = (int)(job / per), t = (int)(job % per) * BIG_NT + threadIdx.x;
+        const int TX = slices[k].TX;
+        const bool act = t < TX * slices[k].TY;
+        const int tile = slices[k].tile_base + (act ? t : 0), tx = t % TX, ty = t / TX;
+        unsigned long long pos = PLACE && act ? (unsigned long long)tile_off[tile] + tile_small[tile] : 0ull;
+        const unsigned c0 = chunk_base[k];
+        unsigned c1 = chunk_base[k + 1];
+        if ((long long)c1 > cap_chunks) c1 = (unsigned)cap_chunks;
+        for (unsigned cg = c0; cg < c1; cg += BIG_NT) {
+            const unsigned nch = min((unsigned)BIG_NT, c1 - cg);
+            // exclusive offsets of the group's list lengths
+            const unsigned m = threadIdx.x < nch ? big_n[cg + threadIdx.x] : 0u;
+            unsigned x = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += v;
+            }
+            if (lane == 31) wsum[w] = x;
+            __syncthreads();
+            unsigned before = 0, total = 0;
+            for (int i = 0; i < BIG_NT / 32; ++i) {
+                before += i < w ? wsum[i] : 0u;
+                total += wsum[i];
+            }
+            offs[threadIdx.x] = before + x - m;
+            if (threadIdx.x == 0) offs[BIG_NT] = total;
+            __syncthreads();
+            for (unsigned s0 = 0; s0 < total; s0 += BIG_STAGE) {
+                const unsigned ns = min((unsigned)BIG_STAGE, total - s0);
+                for (unsigned i = threadIdx.x; i < ns; i += BIG_NT) {
+                    // the chunk of element s0 + i: the last q with offs[q] <= s0 + i
+                    const unsigned e = s0 + i;
+                    int lo = 0, hi = (int)nch - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (offs[mid] <= e)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    const unsigned r = big_list[(size_t)(cg + lo) * BIG_MAX + (e - offs[lo])];
+                    srid[i] = r;
+                    srt[i] = __ldg((const uint4 *)(tiles + r));
+                }
+                __syncthreads();
+                if (act) {
+                    for (unsigned i = 0; i < ns; ++i) {
+                        const uint4 u = srt[i];
+                        const ushort4 rc = make_ushort4((unsigned short)(u.x & 0xFFFFu), (unsigned short)(u.x >> 16),
+                                                        (unsigned short)(u.y & 0xFFFFu), (unsigned short)(u.y >> 16));
+                        if (lists_tile(rc, (unsigned long long)u.z | ((unsigned long long)u.w << 32), tx, ty)) {
+                            if (PLACE && (long long)pos < cap_entries) entries[pos] = srid[i];
+                            ++pos;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!PLACE && act) tile_big[tile] = (unsigned)pos;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the whole record + binning pass
 // ---------------------------------------------------------------------------
@@ -1351,6 +1504,10 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     unsigned *tile_cnt = (unsigned *)(ws + L.tile_cnt);
     unsigned *tile_off = (unsigned *)(ws + L.tile_off);
     unsigned *entries = (unsigned *)(ws + L.entries);
+    unsigned *big_n = (unsigned *)(ws + L.big_n);
+    unsigned *big_list = (unsigned *)(ws + L.big_list);
+    unsigned *tile_small = (unsigned *)(ws + L.tile_small);
+    unsigned *tile_big = (unsigned *)(ws + L.tile_big);
     const int S = (int)L.S;
     const float K2 = K * K;  // one FP32 multiply, rounded once (as in the predicate)
 
@@ -1377,7 +1534,7 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_K1_EMIT, st);
-        k1_emit<<<g1, K1_NT, 0, st>>>(S, n, bits, cnt, NW, gcnt, rec, gmap);
+        k1_emit<<<g1, K1_NT, 0, st>>>(S, n, bits, cnt, NW, gcnt, rec, gmap, slices, hdr);
     }
     {
         MG_PROF(MG_ST_REC_FILL, st);
@@ -1411,14 +1568,20 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     {
         MG_PROF(MG_ST_BIN_HIST, st);
         k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
-                                                     L.cap_chunks);
+                                                     L.cap_chunks, big_n, big_list, hdr);
     }
+    // the large records' tile counts: jobs of 256 tiles of a slice over two
+    // blocks per SM (every block returns at once when no record was listed apart)
+    const long long big_jobs = (long long)S * ((Tmax + BIG_NT - 1) / BIG_NT);
+    const int gbig = (int)(big_jobs < 148 * 2 ? (big_jobs > 0 ? big_jobs : 1) : 148 * 2);
+    k_bin_big<false><<<gbig, BIG_NT, 0, st>>>(slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
+                                              tile_big, tile_off, tile_small, entries, L.cap_entries, hdr);
     long long tot = (long long)S * Tmax;
     int gc = (int)((tot + 255) / 256 < 148 * 32 ? (tot + 255) / 256 : 148 * 32);
     {
         MG_PROF(MG_ST_BIN_COLSCAN, st);
         k_bin_colscan<<<gc, COLSCAN_NT, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt,
-                                          (unsigned *)(ws + L.tile_list), L.n_tiles, hdr);
+                                          (unsigned *)(ws + L.tile_list), L.n_tiles, hdr, tile_big, tile_small);
     }
     {
         MG_PROF(MG_ST_SCAN_TILES, st);
@@ -1429,4 +1592,6 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
         k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
                                                         L.cap_chunks, tile_off, entries, L.cap_entries, hdr);
     }
+    k_bin_big<true><<<gbig, BIG_NT, 0, st>>>(slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
+                                             tile_big, tile_off, tile_small, entries, L.cap_entries, hdr);
 }

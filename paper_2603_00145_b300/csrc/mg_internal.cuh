@@ -128,7 +128,10 @@ struct WsHeader {
                                // [5] forward busy tiles (reserve)
     unsigned int n_busy;       // tiles with records (front of the tile list)
     unsigned int n_idle;       // tiles without records (back of the tile list)
-    unsigned long long reserved[21];
+    unsigned long long n_big;  // records listed apart from their chunks (large records)
+    unsigned int moving;       // bit s: stack s has slices of different rotations (set by k1_emit)
+    unsigned int pad1;
+    unsigned long long reserved[19];
 };
 
 static_assert(sizeof(WsHeader) == 256, "the workspace header is 256 bytes");
@@ -170,13 +173,20 @@ struct Records {
 struct WsLayout {
     size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_inset, rec_mom, rec_thr;
     size_t chunk_base, hist, tile_cnt, tile_off, tile_list, tile_loss, entries, gcnt, bits, gmap, rec_grad, rec_cell, rec_f64,
-        rec_mom64, total;
+        rec_mom64, big_n, big_list, tile_small, tile_big, total;
     long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
 
 // -------------------------------------------------------------------------
 // small device helpers
 // -------------------------------------------------------------------------
+// Binning of large records: a record listing more than BIG_AREA tiles is
+// listed apart from its chunk (up to BIG_MAX per chunk, in record order) and
+// placed after the tile's other entries by one thread per tile, so that a
+// chunk holding a few records that span whole slices does not hold its warp.
+constexpr int BIG_AREA = 16;
+constexpr int BIG_MAX = 64;
+
 // FP64 slots of a near-degenerate record: moments, then its FP64 geometry
 constexpr int MOM64_STRIDE = 12;
 constexpr int MOM64_GEO = 6;

@@ -1013,6 +1013,154 @@ __device__ __forceinline__ void chain_record(const GaussFrame<float> &F, const f
     record_adjoint<float>(F, mu, al, S, la * Sxx, la * Sxy, la * Syy, gpx, gpy, S0, gmu, gR, gs, ga);
 }
 
+// The chain of a Gaussian's records, grouped by slice frame. A record's
+// conic, determinant factor and the regression of its centre on the slab
+// offset depend only on the Gaussian and on the slice's frame (rotation,
+// profile, spacing, PSF; the stack's slices share one unless they move), not
+// on the slice's offset w0. The adjoint of record_adjoint is linear in nine
+// frame-level gradients (of H = Sigma_L^-1 and of Sigma_L's uw, vw, ww entries)
+// and in the offset gradients (du, dv, dw0), each record adding terms formed
+// from its own w0, exp factor and moments; so a record adds those twelve
+// sums, and the 3x3 part (through the frame to R and the scales) runs once per
+// run of records in one frame. Same formulas as record_adjoint, summed in a
+// different order.
+struct ChainFrame {
+    // frame constants (rotation, spacing, profile and PSF variances are read from the slice)
+    float iSww, rD, iD, f, Suw, Svw, Huw, Hvw;
+    float Kpuu, Kpuv, Kpvv, im, rm, K0uu, K0uv, K0vv;
+    // sums over the frame's records
+    float aHuu, aHuv, aHvv, aHuw, aHvw, aHww, aSuw, aSvw, aSww, adu, adv, adw;
+};
+
+__device__ __forceinline__ void chain_frame_begin(const float *qv, const float *sc, const SliceDev &S, ChainFrame &C)
+{
+    GaussFrame<float> F;
+    gauss_frame<float>(qv, sc, F);
+    float g[3][3], Lm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float P = S.Q[a] * F.R[0][c] + S.Q[3 + a] * F.R[1][c] + S.Q[6 + a] * F.R[2][c];
+            g[a][c] = P * F.isc[c];
+            Lm[a][c] = P * F.sc[c];
+        }
+    C.Huw = g[0][0] * g[2][0] + g[0][1] * g[2][1] + g[0][2] * g[2][2];
+    C.Hvw = g[1][0] * g[2][0] + g[1][1] * g[2][1] + g[1][2] * g[2][2];
+    const float Hww = g[2][0] * g[2][0] + g[2][1] * g[2][1] + g[2][2] * g[2][2];
+    C.Suw = Lm[0][0] * Lm[2][0] + Lm[0][1] * Lm[2][1] + Lm[0][2] * Lm[2][2];
+    C.Svw = Lm[1][0] * Lm[2][0] + Lm[1][1] * Lm[2][1] + Lm[1][2] * Lm[2][2];
+    const float Sww = Lm[2][0] * Lm[2][0] + Lm[2][1] * Lm[2][1] + Lm[2][2] * Lm[2][2] + S.sig2;
+    C.iSww = c_rcp<float>(Sww);
+    const float D = 1.f + S.sig2 * Hww;
+    C.rD = c_rsqrt<float>(D);
+    C.iD = C.rD * C.rD;
+    C.f = S.sig2 * C.iD;
+    if (S.pu2 > 0.f || S.pv2 > 0.f) {
+        const float Huu = g[0][0] * g[0][0] + g[0][1] * g[0][1] + g[0][2] * g[0][2];
+        const float Huv = g[0][0] * g[1][0] + g[0][1] * g[1][1] + g[0][2] * g[1][2];
+        const float Hvv = g[1][0] * g[1][0] + g[1][1] * g[1][1] + g[1][2] * g[1][2];
+        C.K0uu = Huu - C.f * C.Huw * C.Huw;
+        C.K0uv = Huv - C.f * C.Huw * C.Hvw;
+        C.K0vv = Hvv - C.f * C.Hvw * C.Hvw;
+        const float pu2 = S.pu2, pv2 = S.pv2;
+        const float dK = C.K0uu * C.K0vv - C.K0uv * C.K0uv;
+        const float m = 1.f + pu2 * C.K0uu + pv2 * C.K0vv + pu2 * pv2 * dK;
+        C.im = c_rcp<float>(m);
+        C.rm = c_rsqrt<float>(m);
+        C.Kpuu = (C.K0uu + pv2 * dK) * C.im;
+        C.Kpuv = C.K0uv * C.im;
+        C.Kpvv = (C.K0vv + pu2 * dK) * C.im;
+    }
+    C.aHuu = C.aHuv = C.aHvv = C.aHuw = C.aHvw = C.aHww = 0.f;
+    C.aSuw = C.aSvw = C.aSww = C.adu = C.adv = C.adw = 0.f;
+}
+
+// One record's terms (its moments a, b, m0, m1 as the backward left them).
+__device__ __forceinline__ void chain_frame_record(ChainFrame &C, const float *mu, float alpha, const SliceDev &S,
+                                                   const float4 &a, const float2 &b, const float4 &m0,
+                                                   const float2 &m1, float &galpha)
+{
+    const float A = a.z, B2 = a.w, Cc = b.x, ampr = b.y;
+    const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
+    const float la = ampr * 0.69314718055994531f;
+    const float gpx = -la * (2.f * A * Sx + B2 * Sy);
+    const float gpy = -la * (B2 * Sx + 2.f * Cc * Sy);
+    float gamp = S0;
+    const float p0 = mu[0] - S.t[0], p1 = mu[1] - S.t[1], p2 = mu[2] - S.t[2];
+    const float w0 = S.Q[2] * p0 + S.Q[5] * p1 + S.Q[8] * p2;
+    const float wS = w0 * C.iSww;
+    const float E = c_exp<float>(-0.5f * w0 * wS);
+    const float amp = alpha * C.rD * E;
+    const float kap = -0.72134752044448170368f, dx = S.dx, dy = S.dy;
+    float gKuu = la * Sxx * (kap * dx * dx), gKuv = la * Sxy * (2.f * kap * dx * dy), gKvv = la * Syy * (kap * dy * dy);
+    const float gcu = gpx * c_rcp<float>(dx), gcv = gpy * c_rcp<float>(dy);
+    const float pu2 = S.pu2, pv2 = S.pv2;
+    if (pu2 > 0.f || pv2 > 0.f) {
+        const float gm = -(gKuu * C.Kpuu + gKuv * C.Kpuv + gKvv * C.Kpvv) * C.im - 0.5f * gamp * amp * C.rm * C.im;
+        const float gNuu = gKuu * C.im, gNuv = gKuv * C.im, gNvv = gKvv * C.im;
+        const float gdK = pv2 * gNuu + pu2 * gNvv + gm * pu2 * pv2;
+        gKuu = gNuu + gm * pu2 + gdK * C.K0vv;
+        gKvv = gNvv + gm * pv2 + gdK * C.K0uu;
+        gKuv = gNuv - 2.f * gdK * C.K0uv;
+        gamp = gamp * C.rm;
+    }
+    galpha += gamp * C.rD * E;
+    const float ga = gamp * amp;
+    float gD = -0.5f * ga * C.iD;
+    float gw0 = -ga * wS;
+    float gSww = 0.5f * ga * wS * wS;
+    const float cs = gcu * C.Suw + gcv * C.Svw;
+    gw0 -= cs * C.iSww;
+    gSww += cs * wS * C.iSww;
+    gD += C.f * C.iD * (gKuu * C.Huw * C.Huw + gKuv * C.Huw * C.Hvw + gKvv * C.Hvw * C.Hvw);
+    C.aHuu += gKuu;
+    C.aHvv += gKvv;
+    C.aHuv += gKuv;
+    C.aHuw += -C.f * (2.f * gKuu * C.Huw + gKuv * C.Hvw);
+    C.aHvw += -C.f * (2.f * gKvv * C.Hvw + gKuv * C.Huw);
+    C.aHww += S.sig2 * gD;
+    C.aSuw += -gcu * wS;
+    C.aSvw += -gcv * wS;
+    C.aSww += gSww;
+    C.adu += gcu;
+    C.adv += gcv;
+    C.adw += gw0;
+}
+
+// The frame's sums through Sigma_L = P diag(s^2) P^T and H = g g^T (P = Q^T R)
+// to R and the scales, and the offsets to the mean: added to gmu, gR, gs.
+__device__ __forceinline__ void chain_frame_end(const float *qv, const float *sc, const ChainFrame &C,
+                                                const float *Q, float gmu[3], float gR[3][3], float gs[3])
+{
+    GaussFrame<float> F;
+    gauss_frame<float>(qv, sc, F);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float P[3], g[3], Lm[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            P[a] = Q[a] * F.R[0][c] + Q[3 + a] * F.R[1][c] + Q[6 + a] * F.R[2][c];
+            g[a] = P[a] * F.isc[c];
+            Lm[a] = P[a] * F.sc[c];
+        }
+        const float gg0 = 2.f * C.aHuu * g[0] + C.aHuv * g[1] + C.aHuw * g[2];
+        const float gg1 = 2.f * C.aHvv * g[1] + C.aHuv * g[0] + C.aHvw * g[2];
+        const float gg2 = 2.f * C.aHww * g[2] + C.aHuw * g[0] + C.aHvw * g[1];
+        const float gL0 = C.aSuw * Lm[2];
+        const float gL1 = C.aSvw * Lm[2];
+        const float gL2 = C.aSuw * Lm[0] + C.aSvw * Lm[1] + 2.f * C.aSww * Lm[2];
+        const float gP0 = gg0 * F.isc[c] + gL0 * F.sc[c];
+        const float gP1 = gg1 * F.isc[c] + gL1 * F.sc[c];
+        const float gP2 = gg2 * F.isc[c] + gL2 * F.sc[c];
+        gs[c] += -(gg0 * g[0] + gg1 * g[1] + gg2 * g[2]) * F.isc[c] + (gL0 * P[0] + gL1 * P[1] + gL2 * P[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gR[r][c] += Q[3 * r] * gP0 + Q[3 * r + 1] * gP1 + Q[3 * r + 2] * gP2;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) gmu[r] += Q[3 * r] * C.adu + Q[3 * r + 1] * C.adv + Q[3 * r + 2] * C.adw;
+}
+
 // The Gaussian's gradients; the quaternion's on the unit sphere: its component
 // along q dropped (the normalisation q = q_raw/|q_raw| removes it, and the
 // rotation formula is only a rotation for unit q).
@@ -1034,17 +1182,22 @@ __device__ __forceinline__ void write_gaussian_grads(long long g, const float *o
 // K6 fused: one thread per Gaussian visits its records in slice order (the
 // Gaussian-major list), turns each record's moments into dL/d(centre, conic,
 // amplitude) and chains them through the record geometry (FP64 for
-// near-degenerate Gaussians), summing in that fixed order; the Gaussian's
-// frame (rotation, scales) is formed once, the records add to dL/d(mean,
-// R, scale, alpha), and dL/dq follows from dL/dR once. The next record's
-// data is loaded while the current one is chained. A Gaussian with more than
-// 64 records (a fitted model grows a few that span many slices) is summed by
-// its whole warp instead, lane l taking records l, l + 32, ..., then a fixed
-// shuffle tree: one thread would hold the warp for all of them. Nothing per
-// record is written.
+// near-degenerate Gaussians), summing in that fixed order; the records add to
+// dL/d(mean, R, scale, alpha), and dL/dq follows from dL/dR once. The warp
+// walks the stacks together: in a stack whose slices share one rotation (no
+// motion) a record only adds its terms to the frame sums (ChainFrame) and the
+// 3x3 part runs once per (Gaussian, stack); in a moving stack every record is
+// chained whole. Walking the stacks in step keeps the lanes' frame set-ups
+// aligned (per-lane frame changes would run the set-up divergently on almost
+// every record). The next record's data is loaded while the current one is
+// chained. A Gaussian with more than 64 records (a fitted model grows a few
+// that span many slices) is summed by its whole warp instead, record by record,
+// lane l taking records l, l + 32, ..., then a fixed shuffle tree: one thread
+// would hold the warp for all of them. Nothing per record is written.
 constexpr unsigned CHAIN_WARP_RECORDS = 64;
 
-__global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsigned *__restrict__ goff,
+__global__ void __launch_bounds__(128, 4) k_chain_fused(StackTable tab, const WsHeader *__restrict__ hdr, long long n,
+                                                     const unsigned *__restrict__ goff,
                                                      const unsigned *__restrict__ gmap, long long cap_records,
                                                      const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
                                                      const int *__restrict__ rslice, const float *__restrict__ mom,
@@ -1056,6 +1209,7 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
                                                      float *g_alpha)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned moving = hdr->moving;  // bit s: the slices of stack s do not share one rotation
     for (long long gb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); gb < n;
          gb += (long long)gridDim.x * blockDim.x) {
         const long long g = gb + lane;
@@ -1076,11 +1230,10 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
             if (dbl) {
                 chain_gaussian_f64(mu, qv, sc, al, j0, j1, gmap, cap_records, geo, geo2, rslice, mom64, slices, o);
             } else {
-                GaussFrame<float> F;
-                gauss_frame<float>(qv, sc, F);
                 float gmu[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
                 float gs[3] = {0.f, 0.f, 0.f}, ga = 0.f;
-                // record ids are loaded two records ahead, their data one record ahead
+                // record ids are loaded two records ahead, their data one record
+                // ahead (an id past the capacity reads as slice 0 and is skipped)
                 unsigned nr = j0 < j1 ? gmap[j0] : 0xffffffffu;
                 unsigned nr2 = j0 + 1 < j1 ? gmap[j0 + 1] : 0xffffffffu;
                 float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nm0 = na;
@@ -1093,13 +1246,17 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
                     nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
                     ns = rslice[nr];
                 }
-                for (unsigned long long j = j0; j < j1; ++j) {
-                    const unsigned r = nr;
-                    const float4 a = na, m0 = nm0;
-                    const float2 b = nb, m1 = nm1;
-                    const int sl = ns;
+                unsigned long long j = j0;
+                auto advance = [&](unsigned &r, float4 &a, float2 &b, float4 &m0, float2 &m1, int &sl) {
+                    r = nr;
+                    a = na;
+                    m0 = nm0;
+                    b = nb;
+                    m1 = nm1;
+                    sl = ns;
                     nr = nr2;
                     nr2 = j + 2 < j1 ? gmap[j + 2] : 0xffffffffu;
+                    ns = 0;
                     if ((long long)nr < cap_records) {
                         na = geo[nr];
                         nb = geo2[nr];
@@ -1107,8 +1264,38 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(long long n, const unsig
                         nm1 = *(const float2 *)(mom + (size_t)nr * 8 + 4);
                         ns = rslice[nr];
                     }
-                    if ((long long)r >= cap_records) continue;
-                    chain_record(F, mu, al, a, b, m0, m1, slices[sl], gmu, gR, gs, ga);
+                    ++j;
+                };
+                // stack by stack (the records are in slice order), the same
+                // stack for every lane of the warp at a time
+                for (int s = 0; s < tab.n_stacks; ++s) {
+                    const int sb = tab.slice_base[s], se = tab.slice_base[s + 1];
+                    const bool has = j < j1 && ns < se;
+                    if (!(moving >> s & 1u)) {
+                        // one rotation for the whole stack: one frame
+                        ChainFrame C;
+                        if (has) chain_frame_begin(qv, sc, slices[sb], C);
+                        while (j < j1 && ns < se) {
+                            unsigned r;
+                            float4 a, m0;
+                            float2 b, m1;
+                            int sl;
+                            advance(r, a, b, m0, m1, sl);
+                            if ((long long)r < cap_records) chain_frame_record(C, mu, al, slices[sl], a, b, m0, m1, ga);
+                        }
+                        if (has) chain_frame_end(qv, sc, C, slices[sb].Q, gmu, gR, gs);
+                    } else if (has) {
+                        GaussFrame<float> F;
+                        gauss_frame<float>(qv, sc, F);
+                        while (j < j1 && ns < se) {
+                            unsigned r;
+                            float4 a, m0;
+                            float2 b, m1;
+                            int sl;
+                            advance(r, a, b, m0, m1, sl);
+                            if ((long long)r < cap_records) chain_record(F, mu, al, a, b, m0, m1, slices[sl], gmu, gR, gs, ga);
+                        }
+                    }
                 }
                 float gq[4];
                 quat_adjoint<float>(qv, gR, gq);
@@ -1397,7 +1584,7 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     MG_PROF(MG_ST_CHAIN, st);
     long long wg = (n + 127) / 128;
     int gc = (int)(wg < 148 * 32 ? (wg > 0 ? wg : 1) : 148 * 32);
-    k_chain_fused<<<gc, 128, 0, st>>>(n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
+    k_chain_fused<<<gc, 128, 0, st>>>(tab, hdr, n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
                                       L.cap_records, (const float4 *)(ws + L.rec_geo),
                                       (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_slice),
                                       (const float *)(ws + L.rec_mom), (const double *)(ws + L.rec_mom64), slices,

@@ -98,6 +98,41 @@ def test_deterministic_and_repeatable():
         assert torch.equal(x, y)
 
 
+def test_large_records_listed_apart():
+    """Records listing more than 16 tiles are binned apart from their chunks
+    (at most 64 per chunk of 512 records; the rest stay in the chunk): a mix of
+    large and small Gaussians on 96x112 slices, so that some chunks list fewer
+    than 64 large records and others overflow. Bins, slices and gradients
+    against the oracle; the tile lists repeat bit for bit."""
+    rng = np.random.default_rng(11)
+    big = ms.random_gaussians(700, 31, box=(-30, 30), sigma=(5.0, 12.0), aniso=2.0, alpha=(0.05, 0.3))
+    small = ms.random_gaussians(1300, 32, box=(-40, 40), sigma=(0.6, 2.0), aniso=2.0, alpha=(0.1, 1.0),
+                                negative_frac=0.1)
+    order = rng.permutation(2000)
+    G = ms.Gaussians(*(np.concatenate([getattr(big, f), getattr(small, f)])[order]
+                       for f in ("mean", "quat", "scale", "alpha")))
+    stacks = [ms.make_stack(ms.AXIAL, 6, 96, 112, 1.0, 1.0, 2.0, 6.0),
+              ms.make_stack(ms.random_rotations(1, rng)[0], 5, 90, 96, 1.1, 1.0, 3.0, 7.0, rng=rng,
+                            max_rot_deg=4.0, max_trans_mm=1.0)]
+    R, out, dev = render_gpu(G, stacks)
+    rec = _check_bins(G, stacks, R)
+    area = np.array([len(rec.row_tiles(r)) for r in range(rec.n)])
+    per_chunk = [np.count_nonzero(a[c:c + 512] > 16) for a in (area[rec.slice == k] for k in np.unique(rec.slice))
+                 for c in range(0, a.size, 512)]
+    assert 0 < min(per_chunk) < 64 < max(per_chunk), per_chunk  # both sides of the per-chunk list limit
+    want = orc.render(G, stacks, rec)
+    assert_render_close(out.cpu().numpy(), want, "large records fwd")
+    gout = np.random.default_rng(12).normal(size=want.size).astype(np.float32)
+    g = R.backward(*dev, torch.from_numpy(gout).cuda())
+    ref = orc.grad(G, stacks, rec, gout.astype(np.float64))
+    assert_grads_close(g, ref, G, "large records")
+    _, b1 = gpu_bins(R, G.n)
+    R.forward(*dev)
+    _, b2 = gpu_bins(R, G.n)
+    for x, y in zip(b1, b2):
+        assert torch.equal(x, y)
+
+
 def test_capacity_overflow_then_growth():
     from paper_2603_00145_b300 import SliceRenderer
     from paper_2603_00145_b300.ops import mg_render_fwd, mg_render_stats_get
