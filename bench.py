@@ -40,17 +40,19 @@ import numpy as np  # noqa: E402
 METRIC = "fwd+bwd Gaussian-voxel pairs/s"
 UNIT = "pairs/s"
 # kernels per library stage (the scans are two kernels each)
-KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 2, "k1_emit": 1, "chunks": 1, "bin_hist": 1,
-                     "bin_colscan": 1, "scan_tiles": 2, "bin_scatter": 1, "render_fwd": 1, "zero_moments": 1,
+KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 2, "k1_emit": 1, "chunks": 1, "bin_hist": 2,
+                     "bin_colscan": 1, "scan_tiles": 2, "bin_scatter": 2, "render_fwd": 1, "zero_moments": 1,
                      "render_bwd": 1, "chain": 1, "loss": 1, "pair_count": 1, "nrf_fwd": 1, "nrf_bwd": 1, "rec_geom": 1, "rec_fill": 1}
 # Algorithmic per-pair work of the evaluation kernels (SIMT FP32 pipe ops,
 # MUFU ex2 ops): forward q (2 FMA) + accumulate (1 FMA) + 1 ex2; backward q
-# (2 FMA) + w = g 2^q (1 MUL) + three moment accumulations (3) + 1 ex2.
-PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (6, 1)}
+# (2 FMA) + the running column sums a += g 2^q (1 FMA), z += a, zz += z (2
+# adds) + 1 ex2 (batches of more than 16 records; smaller batches split rows
+# over lanes and take one more FP32 op per pair).
+PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (5, 1)}
 # DRAM bytes (read + write) per launch of the evaluation kernels on this
 # workload, from one ncu capture of the current kernels
 # (profiles/render_step_feta256_launches.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": (230.38 + 51.42) * 1e6}
+PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": None}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).

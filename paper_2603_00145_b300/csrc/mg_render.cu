@@ -556,9 +556,63 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             Y2 = fmaf(y * y, R0, Y2);
         };
         if (lg == 0) {
+            // all eight rows in order, per column pair running sums over the
+            // rows so far: a = sum w (one packed FMA with g, so w is never
+            // formed), z += a, zz += z. After row 7, with n = 8 - j the
+            // distance of row j from the end: a = sum w, z = sum n w,
+            // zz = sum n (n + 1) / 2 w; with y = 4.5 - n the six moments
+            // follow once per record (two adds per voxel instead of the three
+            // row sums, and no per-row fold).
+            float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
+#pragma unroll
+            for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
             float y = -TC;
 #pragma unroll 2
-            for (int j = 0; j < MG_TILE; ++j, y += 1.f) row(j, y);
+            for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
+                const float b1 = fmaf(B, y, tq.D);
+                const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
+                const float4 *gr = (const float4 *)&sgvw[j * MG_TILE];
+                const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
+                const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
+#pragma unroll
+                for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
+                    const float4 u = gr[i4];
+                    uint4 rl = make_uint4(0u, 0u, 0u, 0u);
+                    if (CELLS) rl = relr[i4];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = i4 * 2 + h;
+                        const float2 x = xp[c];
+                        const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
+                        float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                        if (CELLS) {
+                            if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
+                            if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
+                        }
+                        ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
+                        zc[c] = __fadd2_rn(zc[c], ac[c]);
+                        zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+                    }
+                }
+            }
+            float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
+#pragma unroll
+            for (int c = 0; c < MG_TILE / 2; ++c) {
+                sa = __fadd2_rn(sa, ac[c]);
+                sxa = __ffma2_rn(xp[c], ac[c], sxa);
+                sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
+                sz = __fadd2_rn(sz, zc[c]);
+                sxz = __ffma2_rn(xp[c], zc[c], sxz);
+                szz = __fadd2_rn(szz, zzc[c]);
+            }
+            const float SA = sa.x + sa.y, SXA = sxa.x + sxa.y, SZ = sz.x + sz.y, SXZ = sxz.x + sxz.y;
+            const float Yc = (float)MG_TILE - TC;  // y = Yc - n
+            T0 = SA;
+            T1 = SXA;
+            T2 = sxxa.x + sxxa.y;
+            Y0 = fmaf(Yc, SA, -SZ);                                               // sum y w
+            Y1 = fmaf(Yc, SXA, -SXZ);                                             // sum x y w
+            Y2 = fmaf(Yc * Yc, SA, fmaf(-(2.f * Yc + 1.f), SZ, 2.f * (szz.x + szz.y)));  // sum y^2 w
         } else {
             const int nrow = MG_TILE >> lg;
             float y = (float)j0 - TC;
