@@ -44,6 +44,8 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
     d.stack = s;
     d.dx = in.dx[s];
     d.dy = in.dy[s];
+    d.idx = __fdiv_rn(1.0f, d.dx);
+    d.idy = __fdiv_rn(1.0f, d.dy);
     d.sig2 = in.sig2[s];
     d.pu2 = in.planes ? 0.f : in.pu2[s];
     d.pv2 = in.planes ? 0.f : in.pv2[s];
@@ -390,7 +392,7 @@ __device__ __forceinline__ unsigned long long row_insets(const SliceDev &S, cons
     if (!(o.r2 > 0.f) || !(o.Cuu > 0.f) || !(o.Cvv > 0.f) || o.il > o.ih) return 0ull;
     const int tx0 = o.il / MG_TILE, tx1 = o.ih / MG_TILE, ty0 = o.jl / MG_TILE, ty1 = o.jh / MG_TILE;
     if (tx1 == tx0) return 0ull;
-    const float idx = __fdiv_rn(1.0f, S.dx);
+    const float idx = S.idx;
     const float e = __fdiv_rn(o.ru, o.Cuu);
     const float iCvv = __fdiv_rn(1.0f, o.Cvv);
     const float g = __fmul_rn(o.Cuv, iCvv);
@@ -540,7 +542,7 @@ __device__ __forceinline__ int entry_owner(unsigned incl, unsigned e)
 // to the image; an empty box is stored as the tile rectangle (1,1,0,0).
 __device__ __forceinline__ void pixel_box(const SliceDev &S, float cu, float cv, float ru, float rv, PredOut &o)
 {
-    const float idx = __fdiv_rn(1.0f, S.dx), idy = __fdiv_rn(1.0f, S.dy);
+    const float idx = S.idx, idy = S.idy;  // the correctly rounded 1/dx, 1/dy
     float il = ceilf(__fadd_rn(__fmul_rn(__fsub_rn(cu, ru), idx), S.hx));
     float ih = floorf(__fadd_rn(__fmul_rn(__fadd_rn(cu, ru), idx), S.hx));
     float jl = ceilf(__fadd_rn(__fmul_rn(__fsub_rn(cv, rv), idy), S.hy));
@@ -651,8 +653,10 @@ __device__ void record_geometry(const float *mu, const float *q, const float *s,
     T cv = dv - Svw * wS;
     const T kap = (T)(-0.72134752044448170368);  // -log2(e)/2
     T dx = S.dx, dy = S.dy;
-    o.pcx = cu * t_rcp<T>(dx) + (T)S.hx;
-    o.pcy = cv * t_rcp<T>(dy) + (T)S.hy;
+    // FP32: the slice's correctly rounded reciprocals (what t_rcp gives)
+    const T idx = sizeof(T) == 4 ? (T)S.idx : t_rcp<T>(dx), idy = sizeof(T) == 4 ? (T)S.idy : t_rcp<T>(dy);
+    o.pcx = cu * idx + (T)S.hx;
+    o.pcy = cv * idy + (T)S.hy;
     o.A = kap * Kuu * dx * dx;
     o.B2 = 2 * kap * Kuv * dx * dy;
     o.C = kap * Kvv * dy * dy;

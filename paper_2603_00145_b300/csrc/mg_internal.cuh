@@ -27,12 +27,18 @@ struct SliceDev {
     float ent;   // e_n . t in FP32 (record predicate: w0 = e_n . mu - e_n . t)
     float pu2, pv2;  // FP32 in-plane PSF variances along e_u, e_v (0: none)
     float dx, dy, hx, hy;  // spacing, 0.5*(W-1), 0.5*(H-1)
+    float idx, idy;        // 1/dx, 1/dy rounded once (FP32 division)
     int W, H, TX, TY;
     int tile_base;  // global index of tile (0,0)
     int stack;
     int same_frame;  // 1: rotation and profile bitwise equal to the previous slice's
+    int pad[2];
     long long pix_base;  // offset of pixel (0,0) in the output
 };
+// Kernels gather one field of 32 different slices per warp (and stage slices
+// in shared memory one per thread): a size that is a multiple of 128 bytes
+// would put every lane's word in the same bank.
+static_assert(sizeof(SliceDev) % 128 != 0, "the slice table's stride must not be a multiple of 128 bytes");
 
 // Per-stack table passed by value: maps a global tile to its slice.
 struct StackTable {

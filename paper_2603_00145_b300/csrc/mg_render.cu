@@ -654,7 +654,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
 }
 
 template <bool CELLS>
-__global__ void __launch_bounds__(32 * RW, 4) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
+__global__ void __launch_bounds__(32 * RW, 5) k_render_bwd(StackTable tab, const unsigned *__restrict__ tile_off,
                                                           const unsigned *__restrict__ entries, long long cap_entries,
                                                           long long cap_records, const float4 *__restrict__ geo,
                                                           const float2 *__restrict__ geo2,
