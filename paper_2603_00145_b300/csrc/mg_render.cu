@@ -402,6 +402,99 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
     }
 }
 
+// One record's six moments over the eight rows of its tile (w = g 2^q, g the
+// tile's dL/dI in shared memory), rows in order with per column pair running
+// sums over the rows so far: a = sum w (one packed FMA with g, so w is never
+// formed), z += a, zz += z. After row 7, with n = 8 - j the distance of row j
+// from the end: a = sum w, z = sum n w, zz = sum n (n + 1) / 2 w; with
+// y = 4.5 - n the six moments follow once per record (two adds per voxel
+// instead of three weighted sums, and no per-row fold).
+template <bool CELLS>
+__device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C, const TileQuad &tq,
+                                             const float *gt, const unsigned *srelw, unsigned clo, unsigned chi,
+                                             const float2 *xp, const float2 *xq, float &T0, float &T1, float &T2,
+                                             float &Y0, float &Y1, float &Y2)
+{
+    float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
+#pragma unroll
+    for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
+    float y = -TC;
+#pragma unroll 2
+    for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
+        const float b1 = fmaf(B, y, tq.D);
+        const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
+        const float4 *gr = (const float4 *)&gt[j * MG_TILE];
+        const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
+        const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
+#pragma unroll
+        for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
+            const float4 u = gr[i4];
+            uint4 rl = make_uint4(0u, 0u, 0u, 0u);
+            if (CELLS) rl = relr[i4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = i4 * 2 + h;
+                const float2 x = xp[c];
+                const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
+                float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                if (CELLS) {
+                    if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
+                    if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
+                }
+                ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
+                zc[c] = __fadd2_rn(zc[c], ac[c]);
+                zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+            }
+        }
+    }
+    float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
+#pragma unroll
+    for (int c = 0; c < MG_TILE / 2; ++c) {
+        sa = __fadd2_rn(sa, ac[c]);
+        sxa = __ffma2_rn(xp[c], ac[c], sxa);
+        sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
+        sz = __fadd2_rn(sz, zc[c]);
+        sxz = __ffma2_rn(xp[c], zc[c], sxz);
+        szz = __fadd2_rn(szz, zzc[c]);
+    }
+    const float SA = sa.x + sa.y, SXA = sxa.x + sxa.y, SZ = sz.x + sz.y, SXZ = sxz.x + sxz.y;
+    const float Yc = (float)MG_TILE - TC;  // y = Yc - n
+    T0 = SA;
+    T1 = SXA;
+    T2 = sxxa.x + sxxa.y;
+    Y0 = fmaf(Yc, SA, -SZ);                                                      // sum y w
+    Y1 = fmaf(Yc, SXA, -SXZ);                                                    // sum x y w
+    Y2 = fmaf(Yc * Yc, SA, fmaf(-(2.f * Yc + 1.f), SZ, 2.f * (szz.x + szz.y)));  // sum y^2 w
+}
+
+// A record's moments about the tile centre moved to the record centre and
+// added to its slot: a float4 and a float2 atomic; near-degenerate records in
+// FP64 (their moments about the centre are small differences of large terms,
+// so the shift from the tile centre, by exact offsets, and the sum over tiles
+// are in FP64).
+__device__ __forceinline__ void record_add(unsigned r, int dbl, const double *g64, float x0c, float y0c, float dx0,
+                                           float dy0, float T0, float T1, float T2, float Y0, float Y1, float Y2,
+                                           float *__restrict__ mom, double *__restrict__ mom64)
+{
+    if (dbl) {
+        const double X = (double)x0c - g64[MOM64_GEO], Y = (double)y0c - g64[MOM64_GEO + 1];
+        const double t0 = T0, t1 = T1, t2 = T2, y0 = Y0, y1 = Y1, y2 = Y2;
+        double *mr = mom64 + (size_t)r * MOM64_STRIDE;
+        atomicAdd(mr + 0, t0);
+        atomicAdd(mr + 1, fma(X, t0, t1));
+        atomicAdd(mr + 2, fma(Y, t0, y0));
+        atomicAdd(mr + 3, fma(X, fma(X, t0, t1 + t1), t2));
+        atomicAdd(mr + 4, fma(X, fma(Y, t0, y0), fma(Y, t1, y1)));
+        atomicAdd(mr + 5, fma(Y, fma(Y, t0, y0 + y0), y2));
+    } else {
+        float *mr = mom + (size_t)r * 8;
+        atomicAdd((float4 *)mr, make_float4(T0, fmaf(dx0, T0, T1), fmaf(dy0, T0, Y0),
+                                            fmaf(dx0, fmaf(dx0, T0, T1 + T1), T2)));
+        atomicAdd((float2 *)(mr + 4), make_float2(fmaf(dx0, fmaf(dy0, T0, Y0), fmaf(dy0, T1, Y1)),
+                                                  fmaf(dy0, fmaf(dy0, T0, Y0 + Y0), Y2)));
+    }
+}
+
 // K5, "one lane per record": lane l takes record l of the tile's next 32
 // entries and sweeps all 64 voxels of the tile, reading dL/dI from shared
 // memory by broadcast. Per row y: b1 = B y + D, b0 = (C y + E) y + F; per
@@ -415,18 +508,16 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
 // A batch of at most 16 records (a tile's last, or only, batch) splits each
 // record's rows over 2, 4 or 8 lanes and sums their moments by shuffles first.
 template <bool CELLS>
-__device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane, float *sgvw, unsigned *srelw,
-                                         const unsigned *__restrict__ tile_off, const unsigned *__restrict__ entries,
-                                         long long cap_entries, long long cap_records, const float4 *__restrict__ geo,
+__device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, unsigned e0, unsigned e1, int lane, float *sgvw,
+                                         unsigned *srelw, const unsigned *__restrict__ entries,
+                                         long long cap_records, const float4 *__restrict__ geo,
                                          const float2 *__restrict__ geo2, const SliceDev *__restrict__ slices,
                                          const CellGrid &cg, const int4 *__restrict__ rcell,
                                          const unsigned char *__restrict__ f64, const float *__restrict__ grad_out,
                                          float *__restrict__ mom, double *__restrict__ mom64)
 {
-    const TileId d = tile_id(tab, t);
-    unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
-    if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
     if (e0 >= e1) return;
+    const TileId d = tile_id(tab, t);
     // dL/dI of the tile (shared by all records of the tile)
     for (int i = lane; i < NV; i += 32) {
         const int px = d.tx * MG_TILE + (i % MG_TILE), py = d.ty * MG_TILE + (i / MG_TILE);
@@ -556,63 +647,7 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             Y2 = fmaf(y * y, R0, Y2);
         };
         if (lg == 0) {
-            // all eight rows in order, per column pair running sums over the
-            // rows so far: a = sum w (one packed FMA with g, so w is never
-            // formed), z += a, zz += z. After row 7, with n = 8 - j the
-            // distance of row j from the end: a = sum w, z = sum n w,
-            // zz = sum n (n + 1) / 2 w; with y = 4.5 - n the six moments
-            // follow once per record (two adds per voxel instead of the three
-            // row sums, and no per-row fold).
-            float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
-#pragma unroll
-            for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
-            float y = -TC;
-#pragma unroll 2
-            for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
-                const float b1 = fmaf(B, y, tq.D);
-                const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
-                const float4 *gr = (const float4 *)&sgvw[j * MG_TILE];
-                const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
-                const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
-#pragma unroll
-                for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
-                    const float4 u = gr[i4];
-                    uint4 rl = make_uint4(0u, 0u, 0u, 0u);
-                    if (CELLS) rl = relr[i4];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int c = i4 * 2 + h;
-                        const float2 x = xp[c];
-                        const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
-                        float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
-                        if (CELLS) {
-                            if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
-                            if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
-                        }
-                        ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
-                        zc[c] = __fadd2_rn(zc[c], ac[c]);
-                        zzc[c] = __fadd2_rn(zzc[c], zc[c]);
-                    }
-                }
-            }
-            float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
-#pragma unroll
-            for (int c = 0; c < MG_TILE / 2; ++c) {
-                sa = __fadd2_rn(sa, ac[c]);
-                sxa = __ffma2_rn(xp[c], ac[c], sxa);
-                sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
-                sz = __fadd2_rn(sz, zc[c]);
-                sxz = __ffma2_rn(xp[c], zc[c], sxz);
-                szz = __fadd2_rn(szz, zzc[c]);
-            }
-            const float SA = sa.x + sa.y, SXA = sxa.x + sxa.y, SZ = sz.x + sz.y, SXZ = sxz.x + sxz.y;
-            const float Yc = (float)MG_TILE - TC;  // y = Yc - n
-            T0 = SA;
-            T1 = SXA;
-            T2 = sxxa.x + sxxa.y;
-            Y0 = fmaf(Yc, SA, -SZ);                                               // sum y w
-            Y1 = fmaf(Yc, SXA, -SXZ);                                             // sum x y w
-            Y2 = fmaf(Yc * Yc, SA, fmaf(-(2.f * Yc + 1.f), SZ, 2.f * (szz.x + szz.y)));  // sum y^2 w
+            record_rows8<CELLS>(A2, B, C, tq, sgvw, srelw, clo, chi, xp, xq, T0, T1, T2, Y0, Y1, Y2);
         } else {
             const int nrow = MG_TILE >> lg;
             float y = (float)j0 - TC;
@@ -628,29 +663,67 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, int lane,
             }
             if (lane >= P) r = 0xffffffffu;  // one lane per record adds it
         }
-        if (r != 0xffffffffu) {
-            if (dbl) {
-                // near-degenerate Gaussian: the moments about its centre are
-                // small differences of large terms, so the shift from the tile
-                // centre (exact offsets) and the sum over tiles are in FP64
-                const double X = (double)x0c - g64[MOM64_GEO], Y = (double)y0c - g64[MOM64_GEO + 1];
-                const double t0 = T0, t1 = T1, t2 = T2, y0 = Y0, y1 = Y1, y2 = Y2;
-                double *mr = mom64 + (size_t)r * MOM64_STRIDE;
-                atomicAdd(mr + 0, t0);
-                atomicAdd(mr + 1, fma(X, t0, t1));
-                atomicAdd(mr + 2, fma(Y, t0, y0));
-                atomicAdd(mr + 3, fma(X, fma(X, t0, t1 + t1), t2));
-                atomicAdd(mr + 4, fma(X, fma(Y, t0, y0), fma(Y, t1, y1)));
-                atomicAdd(mr + 5, fma(Y, fma(Y, t0, y0 + y0), y2));
-            } else {
-                float *mr = mom + (size_t)r * 8;
-                atomicAdd((float4 *)mr, make_float4(T0, fmaf(dx0, T0, T1), fmaf(dy0, T0, Y0),
-                                                    fmaf(dx0, fmaf(dx0, T0, T1 + T1), T2)));
-                atomicAdd((float2 *)(mr + 4), make_float2(fmaf(dx0, fmaf(dy0, T0, Y0), fmaf(dy0, T1, Y1)),
-                                                          fmaf(dy0, fmaf(dy0, T0, Y0 + Y0), Y2)));
-            }
-        }
+        if (r != 0xffffffffu) record_add(r, dbl, g64, x0c, y0c, dx0, dy0, T0, T1, T2, Y0, Y1, Y2, mom, mom64);
     }
+}
+
+// Two tiles whose records fit one batch (at most 32 together; a fitted model
+// turns most tiles busy with a handful of records): lane l takes record l of
+// the first tile or record l - n0 of the second, each over all eight rows of
+// its own tile, so that the two tiles' loads overlap and no rows are split.
+// The second tile's dL/dI lies 4 words past the first's end in shared memory,
+// so that the two tiles' rows fall in different banks.
+constexpr int NV2 = 2 * NV + 4;
+__device__ __forceinline__ void bwd_pair(const StackTable &tab, int t0, unsigned e0a, unsigned e1a, int t1,
+                                         unsigned e0b, unsigned e1b, int lane, float *sgvw,
+                                         const unsigned *__restrict__ entries, long long cap_records,
+                                         const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
+                                         const unsigned char *__restrict__ f64, const float *__restrict__ grad_out,
+                                         float *__restrict__ mom, double *__restrict__ mom64)
+{
+    const unsigned n0 = e1a - e0a, n1 = e1b - e0b;
+    const bool in0 = (unsigned)lane < n0, in1 = !in0 && (unsigned)lane < n0 + n1;
+    unsigned r = 0xffffffffu;
+    if (in0) r = entries[e0a + lane];
+    if (in1) r = entries[e0b + (lane - n0)];
+    const TileId d0 = tile_id(tab, t0), d1 = tile_id(tab, t1);
+    for (int i = lane; i < 2 * NV; i += 32) {
+        const TileId &d = i < NV ? d0 : d1;
+        const int v = i & (NV - 1);
+        const int px = d.tx * MG_TILE + (v % MG_TILE), py = d.ty * MG_TILE + (v / MG_TILE);
+        sgvw[i < NV ? v : NV + 4 + v] = (px < d.W && py < d.H) ? grad_out[d.pixbase + (long long)py * d.W + px] : 0.f;
+    }
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 b = make_float2(0.f, 0.f);
+    int dbl = 0;
+    if ((long long)r < cap_records) {
+        a = geo[r];
+        b = geo2[r];
+        dbl = f64[r];
+    } else {
+        r = 0xffffffffu;
+    }
+    __syncwarp();
+    const TileId &d = in1 ? d1 : d0;
+    const float x0c = (float)(d.tx * MG_TILE) + TC, y0c = (float)(d.ty * MG_TILE) + TC;
+    const float rz = __uint_as_float(e1a & 0x80000000u);
+    float2 xp[MG_TILE / 2], xq[MG_TILE / 2];
+#pragma unroll
+    for (int c = 0; c < MG_TILE / 2; ++c) {
+        xp[c] = make_float2((float)(2 * c) - TC + rz, (float)(2 * c + 1) - TC + rz);
+        xq[c] = make_float2(((float)(2 * c) - TC) * ((float)(2 * c) - TC) + rz,
+                            ((float)(2 * c + 1) - TC) * ((float)(2 * c + 1) - TC) + rz);
+    }
+    const float A = a.z, B = a.w, C = b.x;
+    const float dx0 = x0c - a.x, dy0 = y0c - a.y;
+    TileQuad tq = tile_quad(A, B, C, dx0, dy0);
+    const bool tdbl = dbl && r != 0xffffffffu;
+    const double *g64 = mom64 + (size_t)(tdbl ? r : 0u) * MOM64_STRIDE;
+    if (__any_sync(0xffffffffu, tdbl) && tdbl) tq = tile_quad_f64(g64 + MOM64_GEO, x0c, y0c);
+    float T0, T1, T2, Y0, Y1, Y2;
+    record_rows8<false>(make_float2(A, A), B, C, tq, sgvw + (in1 ? NV + 4 : 0), nullptr, 0u, 0u, xp, xq, T0, T1, T2,
+                        Y0, Y1, Y2);
+    if (r != 0xffffffffu) record_add(r, dbl, g64, x0c, y0c, dx0, dy0, T0, T1, T2, Y0, Y1, Y2, mom, mom64);
 }
 
 template <bool CELLS>
@@ -666,11 +739,17 @@ __global__ void __launch_bounds__(32 * RW, 5) k_render_bwd(StackTable tab, const
                                                           const float *__restrict__ grad_out, float *__restrict__ mom,
                                                           double *__restrict__ mom64, unsigned *counter)
 {
-    __shared__ __align__(16) float sgv[RW][NV];
+    __shared__ __align__(16) float sgv[RW][NV2];
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n_busy = hdr->n_busy;  // tiles without records contribute nothing
     const long long n_bulk = max(0ll, n_busy - (long long)TILE_RESERVE * gridDim.x * RW);
+    auto range = [&](int t, unsigned &e0, unsigned &e1) {
+        e0 = tile_off[t];
+        e1 = tile_off[t + 1];
+        if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
+        if (e0 > e1) e0 = e1;
+    };
     for (unsigned part = 0; part < 2; ++part) {
         const long long lo = part ? n_bulk : 0, hi = part ? n_busy : n_bulk;
         const unsigned step = part ? 1u : TILE_CLAIM;
@@ -679,9 +758,31 @@ __global__ void __launch_bounds__(32 * RW, 5) k_render_bwd(StackTable tab, const
             if (lane == 0) i0 = atomicAdd(part ? counter + 3 : counter, step);  // tile_ctr[1], tile_ctr[4]
             i0 = __shfl_sync(0xffffffffu, i0, 0);
             if (lo + (long long)i0 >= hi) break;
-            for (long long i = lo + i0; i < lo + i0 + step && i < hi; ++i) {
-                bwd_tile<CELLS>(tab, (int)tile_list[i], lane, sgv[w], srel[CELLS ? w : 0], tile_off, entries,
-                                cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
+            const long long ia = lo + i0;
+            if (step == 2 && ia + 1 < hi) {
+                const int ta = (int)tile_list[ia], tb = (int)tile_list[ia + 1];
+                unsigned a0, a1, b0, b1;
+                range(ta, a0, a1);
+                range(tb, b0, b1);
+                if (!CELLS && (a1 - a0) + (b1 - b0) <= 32u) {
+                    bwd_pair(tab, ta, a0, a1, tb, b0, b1, lane, sgv[w], entries, cap_records, geo, geo2, f64,
+                             grad_out, mom, mom64);
+                } else {
+                    bwd_tile<CELLS>(tab, ta, a0, a1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo,
+                                    geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
+                    __syncwarp();
+                    bwd_tile<CELLS>(tab, tb, b0, b1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo,
+                                    geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
+                }
+                __syncwarp();
+                continue;
+            }
+            for (long long i = ia; i < ia + step && i < hi; ++i) {
+                const int t = (int)tile_list[i];
+                unsigned e0, e1;
+                range(t, e0, e1);
+                bwd_tile<CELLS>(tab, t, e0, e1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo, geo2,
+                                slices, cg, rcell, f64, grad_out, mom, mom64);
                 __syncwarp();
             }
         }
