@@ -948,14 +948,18 @@ __global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsig
     for (int wd = 0; wd < SW; ++wd) {
         unsigned word = valid ? bits[(long long)wd * n + g] : 0u;
         unsigned uni = __reduce_or_sync(0xffffffffu, word);
+        // lane j loads the warp's output offset for slice 32 wd + j when some
+        // lane has a record there (all of the word's loads in flight at once)
+        const unsigned offl = (uni >> (threadIdx.x & 31)) & 1u ? off[(long long)(wd * 32 + (threadIdx.x & 31)) * NW + wg] : 0u;
         while (uni) {
             const int b = __ffs(uni) - 1;
             uni &= uni - 1;
             const int k = wd * 32 + b;
             const bool f = (word >> b) & 1u;
             const unsigned bal = __ballot_sync(0xffffffffu, f);
+            const unsigned ob = __shfl_sync(0xffffffffu, offl, b);
             if (f) {
-                const unsigned long long pos = (unsigned long long)off[(long long)k * NW + wg] + __popc(bal & lt);
+                const unsigned long long pos = (unsigned long long)ob + __popc(bal & lt);
                 if ((long long)pos < rec.cap) {
                     rec.gid[pos] = (int)g;
                     rec.slice[pos] = k;
@@ -1396,8 +1400,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 12) k_bin_scatter(const SliceD
 // slice's listed records are staged in shared memory (their chunks' list
 // lengths scanned, then the records loaded in parallel) and every tile thread
 // tests them in order.
-constexpr int BIG_NT = 256;
-constexpr int BIG_STAGE = 512;
+constexpr int BIG_NT = 1024;  // a slice's tiles per job (all of a 256x256 slice's)
+constexpr int BIG_STAGE = 1024;
 template <bool PLACE>
 __global__ void __launch_bounds__(BIG_NT) k_bin_big(const SliceDev *__restrict__ slices, int S, int Tmax,
                                                     const unsigned *__restrict__ chunk_base, long long cap_chunks,
@@ -1574,8 +1578,9 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
         k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
                                                      L.cap_chunks, big_n, big_list, hdr);
     }
-    // the large records' tile counts: jobs of 256 tiles of a slice over two
-    // blocks per SM (every block returns at once when no record was listed apart)
+    // the large records' tile counts: jobs of 1024 tiles of a slice (the
+    // slice's listed records staged once per job), at most two blocks per SM
+    // (every block returns at once when no record was listed apart)
     const long long big_jobs = (long long)S * ((Tmax + BIG_NT - 1) / BIG_NT);
     const int gbig = (int)(big_jobs < 148 * 2 ? (big_jobs > 0 ? big_jobs : 1) : 148 * 2);
     k_bin_big<false><<<gbig, BIG_NT, 0, st>>>(slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
