@@ -404,9 +404,11 @@ def run_mgauss(args, rank, world, local_rank):
     # and reads the loss and the gradients back. The target slices do not
     # depend on the previous step, so step k+1's copy runs on a second stream
     # (copy engine) while step k computes, into the other of two device
-    # buffers; the Gaussians are copied on the compute stream at the start of
-    # their step (a fit would update them on the host in between). The timed
-    # window holds exactly K steps: the first timed step copies its own
+    # buffers. The Gaussians (a fit would update them on the host in between)
+    # are copied at the start of their step on that same copy stream, ahead
+    # of the next step's target: on the compute stream their copy could queue
+    # behind the 50 MB target copy in the copy engine and hold the step. The
+    # timed window holds exactly K steps: the first timed step copies its own
     # target, the last issues no copy for a step after it.
     host_in = [torch.from_numpy(x).pin_memory() for x in (G.mean, G.quat, G.scale, G.alpha)]
     host_tgt = target.cpu().pin_memory()
@@ -421,6 +423,7 @@ def run_mgauss(args, rank, world, local_rank):
     side = torch.cuda.Stream(dev)
     ev_tgt = [torch.cuda.Event() for _ in range(2)]
     ev_free = [torch.cuda.Event() for _ in range(2)]
+    ev_in = torch.cuda.Event()
 
     def e2e_step(mm, qq, ss, aa, tgt):
         R.forward_l1l2(mm, qq, ss, aa, tgt, out, grad, loss)
@@ -446,9 +449,14 @@ def run_mgauss(args, rank, world, local_rank):
         ev_tgt[0].record(side)
         for k in range(n_steps):
             b = k % 2
+            # the previous step is done (host synchronisation below): its
+            # inputs may be overwritten
+            with torch.cuda.stream(side):
+                for d_, h_ in zip(dev_in, host_in):
+                    d_.copy_(h_, non_blocking=True)
+            ev_in.record(side)
             main.wait_event(ev_tgt[b])
-            for d_, h_ in zip(dev_in, host_in):
-                d_.copy_(h_, non_blocking=True)
+            main.wait_event(ev_in)
             if k + 1 < n_steps:
                 if k >= 1:
                     side.wait_event(ev_free[1 - b])  # step k-1 is done with that buffer
@@ -489,9 +497,9 @@ def run_mgauss(args, rank, world, local_rank):
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms / args.steps,
-                    "overlap": "target slices of step k+1 copied on a second stream during step k; Gaussians "
-                               "copied and gradients read back on the compute stream; host sync every step; the "
-                               "compute replayed as a CUDA graph"},
+                    "overlap": "target slices of step k+1 copied on a second stream during step k; each step's "
+                               "Gaussians copied on that stream ahead of the next target, gradients read back on "
+                               "the compute stream; host sync every step; the compute replayed as a CUDA graph"},
             "gpu_launches": launches,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "stages_note": "the timed steps replay a CUDA graph of the step; render_fwd and render_bwd timed "

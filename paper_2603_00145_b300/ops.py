@@ -424,10 +424,19 @@ class SliceRenderer:
         """(pairs inside the K-sigma ellipsoid, evaluated pairs) of the last forward."""
         return mg_render_pair_count(mean, quat, scale, alpha, self.dev, self.opts(), self.ws, stream)
 
-    def backward(self, mean, quat, scale, alpha, grad_out, stream=None):
+    def backward(self, mean, quat, scale, alpha, grad_out, stream=None, out=None):
+        """dL/d(mean, quat, scale, alpha) for dL/dI = grad_out; ``out``: four
+        contiguous FP32 tensors of shapes [n,3], [n,4], [n,3], [n] to write
+        into (for example views of one flat buffer), else new ones."""
         n = int(mean.shape[0])
-        g = [torch.empty(n, 3, dtype=_F32, device=mean.device), torch.empty(n, 4, dtype=_F32, device=mean.device),
-             torch.empty(n, 3, dtype=_F32, device=mean.device), torch.empty(n, dtype=_F32, device=mean.device)]
+        if out is None:
+            g = [torch.empty(n, 3, dtype=_F32, device=mean.device), torch.empty(n, 4, dtype=_F32, device=mean.device),
+                 torch.empty(n, 3, dtype=_F32, device=mean.device), torch.empty(n, dtype=_F32, device=mean.device)]
+        else:
+            g = list(out)
+            for t_, shp in zip(g, ((n, 3), (n, 4), (n, 3), (n,))):
+                if tuple(t_.shape) != shp or t_.dtype != _F32 or not t_.is_contiguous() or t_.device != mean.device:
+                    raise ValueError(f"backward(out=...): expected contiguous float32 {shp} on {mean.device}")
         st = mg_render_bwd(mean, quat, scale, alpha, self.dev, self.opts(), grad_out.contiguous(), *g, self.ws,
                            stream, raise_on_error=False)
         if st == L.MG_ERR_STALE_WORKSPACE:
