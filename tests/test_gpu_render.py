@@ -159,6 +159,27 @@ def test_sparse_tiles_paired_backward():
     assert_grads_close(g, ref, G, "sparse tiles")
 
 
+def test_backward_into_caller_buffers():
+    """backward(out=...) writes the gradients into given tensors (here views of
+    one flat buffer, as a host round trip would use) and matches the default
+    call (up to the FP32 order of the moment atomics); a tensor of the wrong
+    shape is refused."""
+    G, stacks = _mixed_case(4)
+    R, out, dev = render_gpu(G, stacks)
+    gout = torch.from_numpy(np.random.default_rng(4).normal(size=out.numel()).astype(np.float32)).cuda()
+    g = R.backward(*dev, gout)
+    n = G.n
+    flat = torch.full((11 * n,), float("nan"), dtype=torch.float32, device="cuda")
+    views = [flat[0:3 * n].view(n, 3), flat[3 * n:7 * n].view(n, 4), flat[7 * n:10 * n].view(n, 3), flat[10 * n:]]
+    g2 = R.backward(*dev, gout, out=views)
+    for a, b in zip(g, g2):
+        assert torch.isfinite(b).all()
+        assert (a - b).abs().max() <= 1e-5 * a.abs().max()
+    assert g2[0].data_ptr() == flat.data_ptr()
+    with pytest.raises(ValueError):
+        R.backward(*dev, gout, out=[views[1], views[0], views[2], views[3]])
+
+
 def test_capacity_overflow_then_growth():
     from paper_2603_00145_b300 import SliceRenderer
     from paper_2603_00145_b300.ops import mg_render_fwd, mg_render_stats_get
