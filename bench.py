@@ -401,76 +401,66 @@ def run_mgauss(args, rank, world, local_rank):
 
     # end to end through the C ABI with host buffers: every step copies its
     # inputs (Gaussian parameters and target slices) from pinned memory, runs,
-    # and reads the loss and the gradients back. The target slices do not
-    # depend on the previous step, so step k+1's copy runs on a second stream
-    # (copy engine) while step k computes, into the other of two device
-    # buffers. The Gaussians (a fit would update them on the host in between)
-    # are copied at the start of their step on that same copy stream, ahead
-    # of the next step's target: on the compute stream their copy could queue
-    # behind the 50 MB target copy in the copy engine and hold the step. The
-    # timed window holds exactly K steps: the first timed step copies its own
-    # target, the last issues no copy for a step after it.
+    # and reads the loss and the gradients back, and the host waits for them.
+    # Each step is one CUDA graph holding its copies and its compute: on a
+    # copy stream forked from the graph's stream, the step's Gaussians (a fit
+    # would update them on the host in between), then the NEXT step's target
+    # slices into the other of two device buffers (they do not depend on this
+    # step, so that 50 MB copy overlaps this step's compute); on the graph's
+    # stream the compute, then the gradients and the loss copied back. The
+    # Gaussians go ahead of the target on the copy stream (behind it they
+    # would hold the step). The timed window holds exactly K steps: the first
+    # step's own target is copied before its graph, the last step's graph
+    # copies no target for a step after it.
+    loss_ref = loss.cpu()  # the device-resident step's loss (a fixed-order reduction)
     host_in = [torch.from_numpy(x).pin_memory() for x in (G.mean, G.quat, G.scale, G.alpha)]
     host_tgt = target.cpu().pin_memory()
     dev_in = [torch.empty_like(x, device=dev) for x in host_in]
+    for d_, h_ in zip(dev_in, host_in):
+        d_.copy_(h_)
     host_out = [torch.empty((G.n, w), dtype=torch.float32).pin_memory() for w in (3, 4, 3)] + \
         [torch.empty(G.n, dtype=torch.float32).pin_memory()]
+    dev_gout = [torch.empty(h_.shape, dtype=torch.float32, device=dev) for h_ in host_out]
     host_loss = torch.empty(2, dtype=torch.float64).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in host_in) + host_tgt.numel() * 4
     d2h = sum(x.numel() * x.element_size() for x in host_out) + 16
     tgt_buf = [target, torch.empty_like(target)]
     main = torch.cuda.current_stream(dev)
     side = torch.cuda.Stream(dev)
-    ev_tgt = [torch.cuda.Event() for _ in range(2)]
-    ev_free = [torch.cuda.Event() for _ in range(2)]
-    ev_in = torch.cuda.Event()
-
-    def e2e_step(mm, qq, ss, aa, tgt):
-        R.forward_l1l2(mm, qq, ss, aa, tgt, out, grad, loss)
-        return R.backward(mm, qq, ss, aa, grad)
-
-    # the compute of an e2e step captured as a CUDA graph, one per target
-    # buffer; the copies and the host synchronisation stay per step
     mg_profile_enable(False)
-    e2e_graphs, e2e_outs = [], []
-    for b in range(2):
+
+    def capture_step(b, copy_next):
         gr_ = torch.cuda.CUDAGraph()
         with torch.cuda.graph(gr_):
-            e2e_outs.append(e2e_step(*dev_in, tgt_buf[b]))
-        e2e_graphs.append(gr_)
+            cap = torch.cuda.current_stream(dev)
+            side.wait_stream(cap)
+            with torch.cuda.stream(side):
+                for d_, h_ in zip(dev_in, host_in):
+                    d_.copy_(h_, non_blocking=True)
+            cap.wait_stream(side)  # the compute waits for the Gaussians only
+            if copy_next:
+                with torch.cuda.stream(side):
+                    tgt_buf[1 - b].copy_(host_tgt, non_blocking=True)
+            R.forward_l1l2(*dev_in, tgt_buf[b], out, grad, loss)
+            R.backward(*dev_in, grad, out=dev_gout)
+            for h_, g_ in zip(host_out, dev_gout):
+                h_.copy_(g_, non_blocking=True)
+            host_loss.copy_(loss, non_blocking=True)
+            cap.wait_stream(side)  # the next target's copy joins the graph's end
+        return gr_
+
+    # [parity][copies the next target]
+    e2e_graphs = [[capture_step(b, c) for c in (False, True)] for b in range(2)]
     torch.cuda.synchronize()
 
     def run_e2e(n_steps):
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         t0.record(main)
-        with torch.cuda.stream(side):
-            tgt_buf[0].copy_(host_tgt, non_blocking=True)
-        ev_tgt[0].record(side)
+        tgt_buf[0].copy_(host_tgt, non_blocking=True)
         for k in range(n_steps):
-            b = k % 2
-            # the previous step is done (host synchronisation below): its
-            # inputs may be overwritten
-            with torch.cuda.stream(side):
-                for d_, h_ in zip(dev_in, host_in):
-                    d_.copy_(h_, non_blocking=True)
-            ev_in.record(side)
-            main.wait_event(ev_tgt[b])
-            main.wait_event(ev_in)
-            if k + 1 < n_steps:
-                if k >= 1:
-                    side.wait_event(ev_free[1 - b])  # step k-1 is done with that buffer
-                with torch.cuda.stream(side):
-                    tgt_buf[1 - b].copy_(host_tgt, non_blocking=True)
-                ev_tgt[1 - b].record(side)
-            e2e_graphs[b].replay()
-            gs = e2e_outs[b]
-            ev_free[b].record(main)
-            for h_, g_ in zip(host_out, gs):
-                h_.copy_(g_, non_blocking=True)
-            host_loss.copy_(loss, non_blocking=True)
+            e2e_graphs[k % 2][k + 1 < n_steps].replay()
             main.synchronize()  # the host reads this step's loss and gradients
-        main.wait_stream(side)
         t1.record(main)
         torch.cuda.synchronize()
         return t0.elapsed_time(t1)
@@ -497,9 +487,10 @@ def run_mgauss(args, rank, world, local_rank):
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms / args.steps,
-                    "overlap": "target slices of step k+1 copied on a second stream during step k; each step's "
-                               "Gaussians copied on that stream ahead of the next target, gradients read back on "
-                               "the compute stream; host sync every step; the compute replayed as a CUDA graph"},
+                    "loss_equals_device_step": bool(torch.equal(host_loss, loss_ref)),
+                    "overlap": "each step one CUDA graph: its Gaussians, then step k+1's target slices, copied "
+                               "on a forked copy stream (the target copy overlaps the compute), the compute, the "
+                               "gradients and loss copied back; host sync every step"},
             "gpu_launches": launches,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "stages_note": "the timed steps replay a CUDA graph of the step; render_fwd and render_bwd timed "
@@ -508,7 +499,7 @@ def run_mgauss(args, rank, world, local_rank):
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(G, wl, args.cpu_seconds)
-    del T, R, out, grad, e2e_graphs, e2e_outs
+    del T, R, out, grad, e2e_graphs, dev_gout
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.fitted and args.fit_iters > 0:
         # the same step on the Gaussians after an L1 + L2 fit: the state a

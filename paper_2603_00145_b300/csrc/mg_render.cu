@@ -419,7 +419,7 @@ __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C,
 #pragma unroll
     for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
     float y = -TC;
-#pragma unroll 2
+#pragma unroll
     for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
         const float b1 = fmaf(B, y, tq.D);
         const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
