@@ -52,7 +52,7 @@ PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (5, 1)}
 # DRAM bytes (read + write) per launch of the evaluation kernels on this
 # workload, from one ncu capture of the current kernels
 # (profiles/render_step_feta256_launches.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": (230.51 + 55.14) * 1e6}
+PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": None}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).
