@@ -226,6 +226,8 @@ WsLayout make_layout(long long n, const std::vector<StackDesc> &st, const mg_opt
     L.tile_cnt = take(sizeof(unsigned) * (size_t)tiles);
     L.tile_off = take(sizeof(unsigned) * (size_t)(tiles + 1));
     L.tile_list = take(sizeof(unsigned) * (size_t)tiles);
+    L.dense_list = take(sizeof(unsigned) * (size_t)tiles);
+    L.sparse_list = take(sizeof(unsigned) * (size_t)tiles);
     // loss partials: per tile and per block of 2048 tiles (fused forward), or per
     // reduction block (no Gaussians)
     L.tile_loss = take(16 * (size_t)(tiles + tiles / 2048 + 1 > 148 * 8 ? tiles + tiles / 2048 + 1 : 148 * 8));

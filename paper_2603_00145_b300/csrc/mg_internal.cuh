@@ -129,15 +129,17 @@ struct WsHeader {
     unsigned long long scan_total;
     unsigned long long pairs_inside;     // mg_render_pair_count
     unsigned long long pairs_evaluated;
-    unsigned int tile_ctr[6];  // work counters: [0] forward busy tiles (bulk), [1] backward (bulk),
-                               // [2] forward empty tiles, [3] loss ticket, [4] backward (reserve),
-                               // [5] forward busy tiles (reserve)
+    unsigned int tile_ctr[6];  // work counters: [0] forward busy tiles (bulk), [1] backward dense tiles
+                               // (bulk), [2] forward empty tiles, then backward sparse tiles, [3] loss
+                               // ticket, [4] backward dense tiles (reserve), [5] forward busy tiles (reserve)
     unsigned int n_busy;       // tiles with records (front of the tile list)
     unsigned int n_idle;       // tiles without records (back of the tile list)
     unsigned long long n_big;  // records listed apart from their chunks (large records)
     unsigned int moving;       // bit s: stack s has slices of different rotations (set by k1_emit)
     unsigned int pad1;
-    unsigned long long reserved[19];
+    unsigned int n_dense;      // tiles with more than SPARSE_MAX records (dense list)
+    unsigned int n_sparse;     // tiles with 1..SPARSE_MAX records (sparse list)
+    unsigned long long reserved[18];
 };
 
 static_assert(sizeof(WsHeader) == 256, "the workspace header is 256 bytes");
@@ -179,13 +181,20 @@ struct Records {
 struct WsLayout {
     size_t hdr, slices, cnt, scan_part, rec_geo, rec_geo2, rec_gid, rec_slice, rec_rect, rec_inset, rec_mom, rec_thr;
     size_t chunk_base, hist, tile_cnt, tile_off, tile_list, tile_loss, entries, gcnt, bits, gmap, rec_grad, rec_cell, rec_f64,
-        rec_mom64, big_n, big_list, tile_small, tile_big, total;
+        rec_mom64, big_n, big_list, tile_small, tile_big, dense_list, sparse_list, total;
     long long S, NB, NW, SW, cap_records, cap_entries, cap_chunks, n_tiles, max_tiles;
 };
 
 // -------------------------------------------------------------------------
 // small device helpers
 // -------------------------------------------------------------------------
+// The backward takes the tiles with more than SPARSE_MAX records (the dense
+// list) with two-tile claims, then the others (the sparse list, a fitted
+// model's background) SPARSE_CLAIM at a time, their records packed into
+// batches of up to 32 lanes, each lane over all rows of its own tile.
+constexpr unsigned SPARSE_MAX = 16;
+constexpr unsigned SPARSE_CLAIM = 8;
+
 // Binning of large records: a record listing more than BIG_AREA tiles is
 // listed apart from its chunk (up to BIG_MAX per chunk, in record order) and
 // placed after the tile's other entries by one thread per tile, so that a

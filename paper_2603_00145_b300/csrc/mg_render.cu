@@ -403,68 +403,76 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
 }
 
 // One record's six moments over the eight rows of its tile (w = g 2^q, g the
-// tile's dL/dI in shared memory), rows in order with per column pair running
-// sums over the rows so far: a = sum w (one packed FMA with g, so w is never
-// formed), z += a, zz += z. After row 7, with n = 8 - j the distance of row j
-// from the end: a = sum w, z = sum n w, zz = sum n (n + 1) / 2 w; with
-// y = 4.5 - n the six moments follow once per record (two adds per voxel
-// instead of three weighted sums, and no per-row fold).
+// tile's dL/dI in shared memory). Each half of the tile is swept towards the
+// centre (rows 0..3, then rows 7..4) with per column pair running sums over
+// the half's rows so far: a += g 2^q (one packed FMA, so w is never formed),
+// zz += z, then z += a. At the end of a half, with n = 1..4 a row's distance
+// from the half's end (n = 1 next to the centre, y = -/+(n - 1/2)):
+// a = sum w, z = sum n w, zz = sum n (n - 1) / 2 w, so that
+// sum y w = -/+(z - a/2) and sum y^2 w = 2 zz + a/4 (no cancellation in the
+// even moments, at most 3x in the odd ones). Two adds per voxel instead of
+// three weighted sums, and no per-row fold.
 template <bool CELLS>
 __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C, const TileQuad &tq,
                                              const float *gt, const unsigned *srelw, unsigned clo, unsigned chi,
                                              const float2 *xp, const float2 *xq, float &T0, float &T1, float &T2,
                                              float &Y0, float &Y1, float &Y2)
 {
-    float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
+    T0 = T1 = T2 = Y0 = Y1 = Y2 = 0.f;
 #pragma unroll
-    for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
-    float y = -TC;
+    for (int half = 0; half < 2; ++half) {
+        float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
 #pragma unroll
-    for (int j = 0; j < MG_TILE; ++j, y += 1.f) {
-        const float b1 = fmaf(B, y, tq.D);
-        const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
-        const float4 *gr = (const float4 *)&gt[j * MG_TILE];
-        const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
-        const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
+        for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
-            const float4 u = gr[i4];
-            uint4 rl = make_uint4(0u, 0u, 0u, 0u);
-            if (CELLS) rl = relr[i4];
+        for (int i = 0; i < MG_TILE / 2; ++i) {
+            const int j = half ? MG_TILE - 1 - i : i;  // towards the centre
+            const float y = (float)j - TC;
+            const float b1 = fmaf(B, y, tq.D);
+            const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
+            const float4 *gr = (const float4 *)&gt[j * MG_TILE];
+            const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
+            const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = i4 * 2 + h;
-                const float2 x = xp[c];
-                const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
-                float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
-                if (CELLS) {
-                    if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
-                    if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
+            for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
+                const float4 u = gr[i4];
+                uint4 rl = make_uint4(0u, 0u, 0u, 0u);
+                if (CELLS) rl = relr[i4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = i4 * 2 + h;
+                    const float2 x = xp[c];
+                    const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
+                    float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                    if (CELLS) {
+                        if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
+                        if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
+                    }
+                    ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
+                    zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+                    zc[c] = __fadd2_rn(zc[c], ac[c]);
                 }
-                ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
-                zc[c] = __fadd2_rn(zc[c], ac[c]);
-                zzc[c] = __fadd2_rn(zzc[c], zc[c]);
             }
         }
-    }
-    float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
+        float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
 #pragma unroll
-    for (int c = 0; c < MG_TILE / 2; ++c) {
-        sa = __fadd2_rn(sa, ac[c]);
-        sxa = __ffma2_rn(xp[c], ac[c], sxa);
-        sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
-        sz = __fadd2_rn(sz, zc[c]);
-        sxz = __ffma2_rn(xp[c], zc[c], sxz);
-        szz = __fadd2_rn(szz, zzc[c]);
+        for (int c = 0; c < MG_TILE / 2; ++c) {
+            sa = __fadd2_rn(sa, ac[c]);
+            sxa = __ffma2_rn(xp[c], ac[c], sxa);
+            sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
+            sz = __fadd2_rn(sz, zc[c]);
+            sxz = __ffma2_rn(xp[c], zc[c], sxz);
+            szz = __fadd2_rn(szz, zzc[c]);
+        }
+        const float SA = sa.x + sa.y, SXA = sxa.x + sxa.y, SZ = sz.x + sz.y, SXZ = sxz.x + sxz.y;
+        const float sgn = half ? 1.f : -1.f;  // y = sgn (n - 1/2)
+        T0 += SA;
+        T1 += SXA;
+        T2 += sxxa.x + sxxa.y;
+        Y0 = fmaf(sgn, fmaf(-0.5f, SA, SZ), Y0);                         // sum y w
+        Y1 = fmaf(sgn, fmaf(-0.5f, SXA, SXZ), Y1);                       // sum x y w
+        Y2 += fmaf(2.f, szz.x + szz.y, 0.25f * SA);                      // sum y^2 w
     }
-    const float SA = sa.x + sa.y, SXA = sxa.x + sxa.y, SZ = sz.x + sz.y, SXZ = sxz.x + sxz.y;
-    const float Yc = (float)MG_TILE - TC;  // y = Yc - n
-    T0 = SA;
-    T1 = SXA;
-    T2 = sxxa.x + sxxa.y;
-    Y0 = fmaf(Yc, SA, -SZ);                                                      // sum y w
-    Y1 = fmaf(Yc, SXA, -SXZ);                                                    // sum x y w
-    Y2 = fmaf(Yc * Yc, SA, fmaf(-(2.f * Yc + 1.f), SZ, 2.f * (szz.x + szz.y)));  // sum y^2 w
 }
 
 // A record's moments about the tile centre moved to the record centre and
@@ -667,46 +675,63 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, unsigned 
     }
 }
 
-// Two tiles whose records fit one batch (at most 32 together; a fitted model
-// turns most tiles busy with a handful of records): lane l takes record l of
-// the first tile or record l - n0 of the second, each over all eight rows of
-// its own tile, so that the two tiles' loads overlap and no rows are split.
-// The second tile's dL/dI lies 4 words past the first's end in shared memory,
-// so that the two tiles' rows fall in different banks.
-constexpr int NV2 = 2 * NV + 4;
-__device__ __forceinline__ void bwd_pair(const StackTable &tab, int t0, unsigned e0a, unsigned e1a, int t1,
-                                         unsigned e0b, unsigned e1b, int lane, float *sgvw,
-                                         const unsigned *__restrict__ entries, long long cap_records,
-                                         const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
-                                         const unsigned char *__restrict__ f64, const float *__restrict__ grad_out,
-                                         float *__restrict__ mom, double *__restrict__ mom64)
+// Up to SPARSE_CLAIM tiles of at most SPARSE_MAX records each (a fitted
+// model's background: most tiles hold a handful of records), their records
+// packed into batches of up to 32 lanes (tiles whole), each lane over all
+// eight rows of its own tile: the tiles' loads overlap and no rows are split
+// over lanes. The tiles' dL/dI is staged once, tile k at 68 k words, so that
+// the tiles' rows fall in different banks.
+constexpr int SG = NV + 4;
+__device__ __forceinline__ void bwd_sparse(const StackTable &tab, const unsigned *__restrict__ sparse_list,
+                                           unsigned i0, unsigned nt, int lane, float *sgvw,
+                                           const unsigned *__restrict__ tile_off, long long cap_entries,
+                                           const unsigned *__restrict__ entries, long long cap_records,
+                                           const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
+                                           const unsigned char *__restrict__ f64, const float *__restrict__ grad_out,
+                                           float *__restrict__ mom, double *__restrict__ mom64)
 {
-    const unsigned n0 = e1a - e0a, n1 = e1b - e0b;
-    const bool in0 = (unsigned)lane < n0, in1 = !in0 && (unsigned)lane < n0 + n1;
-    unsigned r = 0xffffffffu;
-    if (in0) r = entries[e0a + lane];
-    if (in1) r = entries[e0b + (lane - n0)];
-    const TileId d0 = tile_id(tab, t0), d1 = tile_id(tab, t1);
-    for (int i = lane; i < 2 * NV; i += 32) {
-        const TileId &d = i < NV ? d0 : d1;
-        const int v = i & (NV - 1);
-        const int px = d.tx * MG_TILE + (v % MG_TILE), py = d.ty * MG_TILE + (v / MG_TILE);
-        sgvw[i < NV ? v : NV + 4 + v] = (px < d.W && py < d.H) ? grad_out[d.pixbase + (long long)py * d.W + px] : 0.f;
+    // lane k < nt: tile k's entry range and position
+    unsigned e0 = 0, e1 = 0;
+    int tx = 0, ty = 0, W = 0, H = 0;
+    long long pb = 0;
+    if ((unsigned)lane < nt) {
+        const int t = (int)sparse_list[i0 + lane];
+        e0 = tile_off[t];
+        e1 = tile_off[t + 1];
+        if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
+        if (e0 > e1) e0 = e1;
+        const TileId d = tile_id(tab, t);
+        tx = d.tx;
+        ty = d.ty;
+        W = d.W;
+        H = d.H;
+        pb = d.pixbase;
     }
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 b = make_float2(0.f, 0.f);
-    int dbl = 0;
-    if ((long long)r < cap_records) {
-        a = geo[r];
-        b = geo2[r];
-        dbl = f64[r];
-    } else {
-        r = 0xffffffffu;
+    // the tiles' dL/dI, all loads in flight before the stores: half-tile j of tile j / 2
+    float gv[2 * SPARSE_CLAIM];
+#pragma unroll
+    for (int j = 0; j < 2 * (int)SPARSE_CLAIM; ++j) {
+        const int k = j >> 1, v = (j & 1) * 32 + lane;
+        const int kx = __shfl_sync(0xffffffffu, tx, k), ky = __shfl_sync(0xffffffffu, ty, k);
+        const int kW = __shfl_sync(0xffffffffu, W, k), kH = __shfl_sync(0xffffffffu, H, k);
+        const long long kp = __shfl_sync(0xffffffffu, pb, k);
+        const int px = kx * MG_TILE + (v % MG_TILE), py = ky * MG_TILE + (v / MG_TILE);
+        gv[j] = (j < 2 * (int)nt && px < kW && py < kH) ? grad_out[kp + (long long)py * kW + px] : 0.f;
     }
+#pragma unroll
+    for (int j = 0; j < 2 * (int)SPARSE_CLAIM; ++j)
+        if (j < 2 * (int)nt) sgvw[(j >> 1) * SG + (j & 1) * 32 + lane] = gv[j];
     __syncwarp();
-    const TileId &d = in1 ? d1 : d0;
-    const float x0c = (float)(d.tx * MG_TILE) + TC, y0c = (float)(d.ty * MG_TILE) + TC;
-    const float rz = __uint_as_float(e1a & 0x80000000u);
+    // inclusive prefix of the tiles' record counts
+    const unsigned cnt = e1 - e0;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned excl = incl - cnt;
+    const float rz = __uint_as_float(e1 & 0x80000000u);
     float2 xp[MG_TILE / 2], xq[MG_TILE / 2];
 #pragma unroll
     for (int c = 0; c < MG_TILE / 2; ++c) {
@@ -714,16 +739,49 @@ __device__ __forceinline__ void bwd_pair(const StackTable &tab, int t0, unsigned
         xq[c] = make_float2(((float)(2 * c) - TC) * ((float)(2 * c) - TC) + rz,
                             ((float)(2 * c + 1) - TC) * ((float)(2 * c + 1) - TC) + rz);
     }
-    const float A = a.z, B = a.w, C = b.x;
-    const float dx0 = x0c - a.x, dy0 = y0c - a.y;
-    TileQuad tq = tile_quad(A, B, C, dx0, dy0);
-    const bool tdbl = dbl && r != 0xffffffffu;
-    const double *g64 = mom64 + (size_t)(tdbl ? r : 0u) * MOM64_STRIDE;
-    if (__any_sync(0xffffffffu, tdbl) && tdbl) tq = tile_quad_f64(g64 + MOM64_GEO, x0c, y0c);
-    float T0, T1, T2, Y0, Y1, Y2;
-    record_rows8<false>(make_float2(A, A), B, C, tq, sgvw + (in1 ? NV + 4 : 0), nullptr, 0u, 0u, xp, xq, T0, T1, T2,
-                        Y0, Y1, Y2);
-    if (r != 0xffffffffu) record_add(r, dbl, g64, x0c, y0c, dx0, dy0, T0, T1, T2, Y0, Y1, Y2, mom, mom64);
+    unsigned lem;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(lem));
+    for (unsigned s = 0; s < nt;) {
+        // the batch: tiles s..e whole, at most 32 records (each tile holds at most SPARSE_MAX)
+        const unsigned base = __shfl_sync(0xffffffffu, excl, s);
+        const bool in = (unsigned)lane >= s && (unsigned)lane < nt && incl - base <= 32u;
+        const unsigned fit = __ballot_sync(0xffffffffu, in);
+        const unsigned e = 31u - __clz(fit);
+        const unsigned end = __shfl_sync(0xffffffffu, incl, e);
+        // lane l takes record base + l: its tile is the last tile of the batch starting at or before l
+        // (a tile left without entries by a capacity overflow starts where the
+        // next does; the count check below keeps every read inside its tile)
+        const unsigned starts = __reduce_or_sync(0xffffffffu, in && excl - base < 32u ? 1u << (excl - base) : 0u);
+        const unsigned gi = base + lane;
+        const int k = (int)s + __popc(starts & lem) - 1;
+        const unsigned ek = __shfl_sync(0xffffffffu, e0, k), xk = __shfl_sync(0xffffffffu, excl, k);
+        const unsigned ck = __shfl_sync(0xffffffffu, cnt, k);
+        const int kx = __shfl_sync(0xffffffffu, tx, k), ky = __shfl_sync(0xffffffffu, ty, k);
+        const bool act = gi < end && k >= (int)s && gi - xk < ck;
+        unsigned r = act ? entries[ek + (gi - xk)] : 0xffffffffu;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 b = make_float2(0.f, 0.f);
+        int dbl = 0;
+        if ((long long)r < cap_records) {
+            a = geo[r];
+            b = geo2[r];
+            dbl = f64[r];
+        } else {
+            r = 0xffffffffu;
+        }
+        const float x0c = (float)(kx * MG_TILE) + TC, y0c = (float)(ky * MG_TILE) + TC;
+        const float A = a.z, B = a.w, C = b.x;
+        const float dx0 = x0c - a.x, dy0 = y0c - a.y;
+        TileQuad tq = tile_quad(A, B, C, dx0, dy0);
+        const bool tdbl = dbl && r != 0xffffffffu;
+        const double *g64 = mom64 + (size_t)(tdbl ? r : 0u) * MOM64_STRIDE;
+        if (__any_sync(0xffffffffu, tdbl) && tdbl) tq = tile_quad_f64(g64 + MOM64_GEO, x0c, y0c);
+        float T0, T1, T2, Y0, Y1, Y2;
+        record_rows8<false>(make_float2(A, A), B, C, tq, sgvw + (act ? k : 0) * SG, nullptr, 0u, 0u, xp, xq, T0, T1,
+                            T2, Y0, Y1, Y2);
+        if (r != 0xffffffffu) record_add(r, dbl, g64, x0c, y0c, dx0, dy0, T0, T1, T2, Y0, Y1, Y2, mom, mom64);
+        s = e + 1;
+    }
 }
 
 template <bool CELLS>
@@ -733,61 +791,54 @@ __global__ void __launch_bounds__(32 * RW, 5) k_render_bwd(StackTable tab, const
                                                           const float2 *__restrict__ geo2,
                                                           const SliceDev *__restrict__ slices, CellGrid cg,
                                                           const int4 *__restrict__ rcell,
-                                                          const unsigned *__restrict__ tile_list,
+                                                          const unsigned *__restrict__ dense_list,
+                                                          const unsigned *__restrict__ sparse_list,
                                                           const WsHeader *__restrict__ hdr,
                                                           const unsigned char *__restrict__ f64,
                                                           const float *__restrict__ grad_out, float *__restrict__ mom,
                                                           double *__restrict__ mom64, unsigned *counter)
 {
-    __shared__ __align__(16) float sgv[RW][NV2];
+    __shared__ __align__(16) float sgv[RW][SPARSE_CLAIM * SG];
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long n_busy = hdr->n_busy;  // tiles without records contribute nothing
-    const long long n_bulk = max(0ll, n_busy - (long long)TILE_RESERVE * gridDim.x * RW);
-    auto range = [&](int t, unsigned &e0, unsigned &e1) {
-        e0 = tile_off[t];
-        e1 = tile_off[t + 1];
+    const long long n_dense = hdr->n_dense, n_sparse = hdr->n_sparse;
+    const long long n_bulk = max(0ll, n_dense - (long long)TILE_RESERVE * gridDim.x * RW);
+    auto tile = [&](int t) {
+        unsigned e0 = tile_off[t], e1 = tile_off[t + 1];
         if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
         if (e0 > e1) e0 = e1;
+        bwd_tile<CELLS>(tab, t, e0, e1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo, geo2, slices,
+                        cg, rcell, f64, grad_out, mom, mom64);
+        __syncwarp();
     };
+    // the dense tiles: claims of two, then a reserve of single tiles
     for (unsigned part = 0; part < 2; ++part) {
-        const long long lo = part ? n_bulk : 0, hi = part ? n_busy : n_bulk;
+        const long long lo = part ? n_bulk : 0, hi = part ? n_dense : n_bulk;
         const unsigned step = part ? 1u : TILE_CLAIM;
         for (;;) {
             unsigned i0 = 0;
             if (lane == 0) i0 = atomicAdd(part ? counter + 3 : counter, step);  // tile_ctr[1], tile_ctr[4]
             i0 = __shfl_sync(0xffffffffu, i0, 0);
             if (lo + (long long)i0 >= hi) break;
-            const long long ia = lo + i0;
-            if (step == 2 && ia + 1 < hi) {
-                const int ta = (int)tile_list[ia], tb = (int)tile_list[ia + 1];
-                unsigned a0, a1, b0, b1;
-                range(ta, a0, a1);
-                range(tb, b0, b1);
-                if (!CELLS && (a1 - a0) + (b1 - b0) <= 32u) {
-                    bwd_pair(tab, ta, a0, a1, tb, b0, b1, lane, sgv[w], entries, cap_records, geo, geo2, f64,
-                             grad_out, mom, mom64);
-                } else {
-                    bwd_tile<CELLS>(tab, ta, a0, a1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo,
-                                    geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
-                    __syncwarp();
-                    bwd_tile<CELLS>(tab, tb, b0, b1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo,
-                                    geo2, slices, cg, rcell, f64, grad_out, mom, mom64);
-                }
-                __syncwarp();
-                continue;
-            }
-            for (long long i = ia; i < ia + step && i < hi; ++i) {
-                const int t = (int)tile_list[i];
-                unsigned e0, e1;
-                range(t, e0, e1);
-                bwd_tile<CELLS>(tab, t, e0, e1, lane, sgv[w], srel[CELLS ? w : 0], entries, cap_records, geo, geo2,
-                                slices, cg, rcell, f64, grad_out, mom, mom64);
-                __syncwarp();
-            }
+            for (long long i = lo + i0; i < lo + i0 + step && i < hi; ++i) tile((int)dense_list[i]);
+        }
+    }
+    // the sparse tiles, SPARSE_CLAIM at a time (the cell-grid form one at a time)
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(counter + 1, CELLS ? 1u : SPARSE_CLAIM);  // tile_ctr[2]
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if ((long long)i0 >= n_sparse) break;
+        if (CELLS) {
+            tile((int)sparse_list[i0]);
+        } else {
+            bwd_sparse(tab, sparse_list, i0, (unsigned)min((long long)SPARSE_CLAIM, n_sparse - (long long)i0), lane,
+                       sgv[w], tile_off, cap_entries, entries, cap_records, geo, geo2, f64, grad_out, mom, mom64);
+            __syncwarp();
         }
     }
 }
+
 
 // Pair statistics over the bins: evaluated (record, in-image voxel) pairs and
 // those inside the record's K-sigma ellipsoid (q >= thr in log2 units).
@@ -1715,8 +1766,9 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     }
     int nt = tab.n_tiles_total;
     if (nt > 0) {
-        // the backward's two work counters, tile_ctr[1] and tile_ctr[4] (the
-        // forward's counters in between are spent by now)
+        // the backward's work counters: tile_ctr[1] and [4] (dense tiles) and
+        // tile_ctr[2] (sparse tiles; the forward's counters [2] and [3] are
+        // spent by now)
         cudaMemsetAsync((void *)&hdr->tile_ctr[1], 0, 4 * sizeof(unsigned), st);
         MG_PROF(MG_ST_RENDER_BWD, st);
         const void *kern = cg.on ? (const void *)k_render_bwd<true> : (const void *)k_render_bwd<false>;
@@ -1727,14 +1779,16 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
             k_render_bwd<true><<<grid, 32 * RW, 0, st>>>(
                 tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
-                (const unsigned *)(ws + L.tile_list), hdr, (const unsigned char *)(ws + L.rec_f64), grad_out,
-                (float *)(ws + L.rec_mom), (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
+                (const unsigned *)(ws + L.dense_list), (const unsigned *)(ws + L.sparse_list), hdr,
+                (const unsigned char *)(ws + L.rec_f64), grad_out, (float *)(ws + L.rec_mom),
+                (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
         else
             k_render_bwd<false><<<grid, 32 * RW, 0, st>>>(
                 tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
-                (const unsigned *)(ws + L.tile_list), hdr, (const unsigned char *)(ws + L.rec_f64), grad_out,
-                (float *)(ws + L.rec_mom), (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
+                (const unsigned *)(ws + L.dense_list), (const unsigned *)(ws + L.sparse_list), hdr,
+                (const unsigned char *)(ws + L.rec_f64), grad_out, (float *)(ws + L.rec_mom),
+                (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
     }
     MG_PROF(MG_ST_CHAIN, st);
     long long wg = (n + 127) / 128;

@@ -133,12 +133,11 @@ def test_large_records_listed_apart():
         assert torch.equal(x, y)
 
 
-def test_sparse_tiles_paired_backward():
+def test_sparse_tiles_packed_backward():
     """Tiles holding a handful of records (a fitted model's background): the
-    backward takes two claimed tiles whose records fit one batch together, each
-    lane over all rows of its own tile. 16k busy tiles with at most 16 records
-    each (more than the single-tile reserve of 2 tiles per resident warp on a
-    148-SM GPU, so most are claimed in pairs); bins, slices and gradients
+    backward takes the tiles of at most 16 records eight at a time and packs
+    their records into batches of up to 32 lanes, each lane over all rows of
+    its own tile. 16k busy tiles, all sparse; bins, slices and gradients
     against the oracle."""
     G = ms.random_gaussians(6000, 41, box=(-60, 60), sigma=(0.5, 1.6), aniso=2.0, alpha=(0.1, 1.0),
                             negative_frac=0.1)
