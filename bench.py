@@ -313,7 +313,7 @@ NRF_FLOPS_BWD = NRF_FLOPS_FWD + 2 * (32 * 64 + 64 * 64 + 64) + 2 * (64 * 64 + 64
 # L2 requests per 2^20 points from one ncu capture of the BF16 grid kernels
 # (profiles/nrf_grid_bf16.md): table gathers (forward) and table-gradient
 # atomics (backward); None once a kernel changes.
-NRF_PROFILED = {"fwd_gather_requests": 83115931, "bwd_red_requests": 201154922, "bwd_gather_requests": 3116625}
+NRF_PROFILED = {"fwd_gather_requests": 83115931, "bwd_red_requests": None, "bwd_gather_requests": None}
 
 
 def nrf_pair_timing(wl, dev, steps: int, warmup: int, n: int = 1 << 20):

@@ -406,7 +406,8 @@ typedef struct {
     int32_t encoding;   /* mg_nrf_encoding */
     int32_t precision;  /* mg_nrf_precision */
     const float *params;
-    const float *table; /* MG_NRF_GRID: device FP32 [16][2^log2_table][2]; else unused */
+    const float *table; /* MG_NRF_GRID: device FP32 [16][2^log2_table][2], 8-byte aligned (an
+                           entry's two features are one 8-byte word); else unused */
     int32_t log2_table, n_min, n_max; /* MG_NRF_GRID geometry; 0 = 19, 16, 512 */
     float out_scale;    /* bound of |r|; the paper's 0.1 */
     /* Encoding cache (MG_NRF_GRID; ignored for MG_NRF_FOURIER): a device buffer
@@ -432,8 +433,10 @@ int64_t mg_nrf_param_count(int32_t encoding);
 /* out[i] = r(xyz[i]) for n points (device xyz [n,3], out [n]). */
 mg_status mg_nrf_fwd(const mg_nrf *net, const float *xyz, int64_t n, float *out, mg_stream_t stream);
 /* Gradients of sum_i grad_out[i] r(xyz[i]): g_params (device, param_count
- * floats) and, for MG_NRF_GRID, g_table (device, same shape as table) are
- * overwritten. Accumulated with atomics (FP32 summation order varies). */
+ * floats) and, for MG_NRF_GRID, g_table (device, same shape as table,
+ * 16-byte aligned: two neighbouring entries that share a 16-byte word take
+ * one atomic; MG_ERR_INVALID_ARG otherwise) are overwritten. Accumulated with
+ * atomics (FP32 summation order varies). */
 mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float *grad_out, float *g_params,
                      float *g_table, mg_stream_t stream);
 /* The residual at a batch of rows of a coordinate table (the NRF's random

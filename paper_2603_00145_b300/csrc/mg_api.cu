@@ -724,6 +724,10 @@ static bool valid_nrf(const mg_nrf *net, std::string &why)
             why = "grid encoding needs a table";
             return false;
         }
+        if ((uintptr_t)net->table & 7u) {
+            why = "the grid table must be 8-byte aligned";
+            return false;
+        }
         if (net->log2_table < 0 || net->log2_table > 24 || net->n_min < 0 || net->n_max < 0 ||
             (net->n_min > 0 && net->n_max > 0 && net->n_max < net->n_min)) {
             why = "bad grid geometry";
@@ -763,7 +767,8 @@ mg_status mg_nrf_bwd(const mg_nrf *net, const float *xyz, int64_t n, const float
     std::string why;
     if (!valid_nrf(net, why)) return fail(MG_ERR_INVALID_ARG, why);
     if (n < 0 || (n > 0 && (!xyz || !grad_out)) || !g_params) return fail(MG_ERR_INVALID_ARG, "bad pointers or n");
-    if (net->encoding == MG_NRF_GRID && !g_table) return fail(MG_ERR_INVALID_ARG, "grid encoding needs g_table");
+    if (net->encoding == MG_NRF_GRID && (!g_table || ((uintptr_t)g_table & 15u)))
+        return fail(MG_ERR_INVALID_ARG, "grid encoding needs a 16-byte aligned g_table");
     cudaStream_t st = (cudaStream_t)stream;
     MG_PROF(MG_ST_NRF_BWD, st);
     cudaMemsetAsync(g_params, 0, sizeof(float) * (size_t)mg_nrf_param_count_impl(net->encoding), st);
@@ -800,7 +805,8 @@ mg_status mg_nrf_bwd_at(const mg_nrf *net, const float *coords, int64_t rows, co
     if (!valid_nrf(net, why)) return fail(MG_ERR_INVALID_ARG, why);
     if (n < 0 || rows < 0 || (n > 0 && (!coords || !idx || !grad_acc)) || !g_params)
         return fail(MG_ERR_INVALID_ARG, "bad pointers or n");
-    if (net->encoding == MG_NRF_GRID && !g_table) return fail(MG_ERR_INVALID_ARG, "grid encoding needs g_table");
+    if (net->encoding == MG_NRF_GRID && (!g_table || ((uintptr_t)g_table & 15u)))
+        return fail(MG_ERR_INVALID_ARG, "grid encoding needs a 16-byte aligned g_table");
     cudaStream_t st = (cudaStream_t)stream;
     MG_PROF(MG_ST_NRF_BWD, st);
     cudaMemsetAsync(g_params, 0, sizeof(float) * (size_t)mg_nrf_param_count_impl(net->encoding), st);

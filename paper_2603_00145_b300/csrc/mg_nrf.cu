@@ -676,8 +676,21 @@ __device__ __forceinline__ void nrf_body(const NrfArgs A, const float *__restric
                     Corner8 cr;
                     grid_corners(x, lv, sGrid, cr);
                     float2 *tg = (float2 *)g_table + ((size_t)lv << sGrid.log2T);
+                    // corners x, x + 1 in one 16-byte slot (indices differing in the
+                    // lowest bit only) take one float4 atomic, else one float2 each
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) atomicAdd(&tg[cr.idx[c]], make_float2(cr.wt[c] * v0, cr.wt[c] * v1));
+                    for (int c = 0; c < 8; c += 2) {
+                        const unsigned ia = cr.idx[c], ib = cr.idx[c + 1];
+                        const float2 ga = make_float2(cr.wt[c] * v0, cr.wt[c] * v1);
+                        const float2 gb = make_float2(cr.wt[c + 1] * v0, cr.wt[c + 1] * v1);
+                        if ((ia ^ ib) == 1u) {
+                            atomicAdd((float4 *)&tg[ia & ~1u], (ia & 1u) ? make_float4(gb.x, gb.y, ga.x, ga.y)
+                                                                          : make_float4(ga.x, ga.y, gb.x, gb.y));
+                        } else {
+                            atomicAdd(&tg[ia], ga);
+                            atomicAdd(&tg[ib], gb);
+                        }
+                    }
                 };
                 if (BF16)
                     gemm_dw_bf16<K0P, true>((const bf16 *)sD, LY::LDH, (const bf16 *)W0, LY::ldw(0), w, lane, epi_t);

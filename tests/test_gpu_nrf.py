@@ -151,6 +151,35 @@ def test_nrf_zero_last_layer_gives_zero():
         assert float(out.abs().max()) == 0.0
 
 
+def test_nrf_grid_table_alignment_checked():
+    """An entry's two features are read as one 8-byte word, and two
+    neighbouring table-gradient entries sharing a 16-byte word take one atomic:
+    a table not 8-byte aligned or a table gradient not 16-byte aligned is
+    refused before any launch (MG_ERR_INVALID_ARG); a table 8 bytes past a
+    16-byte boundary works and gives the same result."""
+    from paper_2603_00145_b300 import mg_nrf_bwd, mg_nrf_fwd
+    from paper_2603_00145_b300._lib import MG_ERR_INVALID_ARG, MgError
+
+    net, _ = _nets("grid", "fp32")
+    m = net.table.numel()
+    xyz = torch.from_numpy(_points(256, 3)).cuda()
+    out = torch.empty(256, device="cuda")
+    buf = torch.zeros(m + 4, device="cuda")
+    with pytest.raises(MgError) as ei:
+        mg_nrf_fwd(net, xyz, out, table=buf[1:1 + m])  # 4 bytes off
+    assert ei.value.status == MG_ERR_INVALID_ARG
+    gp = torch.empty(net.params.numel(), device="cuda")
+    with pytest.raises(MgError) as ei:
+        mg_nrf_bwd(net, xyz, torch.ones(256, device="cuda"), gp, buf[2:2 + m])  # 8 bytes off
+    assert ei.value.status == MG_ERR_INVALID_ARG
+    shifted = buf[2:2 + m]
+    shifted.copy_(net.table.reshape(-1))
+    ref = torch.empty(256, device="cuda")
+    mg_nrf_fwd(net, xyz, ref)
+    mg_nrf_fwd(net, xyz, out, table=shifted)
+    assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("preset", ["paper", "grid"])
 def test_nrf_at_indexed_rows(preset):
     """The field at a batch of rows of a coordinate table (the training
