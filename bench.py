@@ -52,7 +52,7 @@ PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (5, 1)}
 # DRAM bytes (read + write) per launch of the evaluation kernels on this
 # workload, from one ncu capture of the current kernels
 # (profiles/render_step_feta256_launches.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": None}
+PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": (243.99 + 60.66) * 1e6}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).
@@ -313,7 +313,7 @@ NRF_FLOPS_BWD = NRF_FLOPS_FWD + 2 * (32 * 64 + 64 * 64 + 64) + 2 * (64 * 64 + 64
 # L2 requests per 2^20 points from one ncu capture of the BF16 grid kernels
 # (profiles/nrf_grid_bf16.md): table gathers (forward) and table-gradient
 # atomics (backward); None once a kernel changes.
-NRF_PROFILED = {"fwd_gather_requests": 83115931, "bwd_red_requests": None, "bwd_gather_requests": None}
+NRF_PROFILED = {"fwd_gather_requests": 83408692, "bwd_red_requests": 101138216, "bwd_gather_requests": 3131437}
 
 
 def nrf_pair_timing(wl, dev, steps: int, warmup: int, n: int = 1 << 20):
