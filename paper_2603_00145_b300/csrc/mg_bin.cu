@@ -1021,7 +1021,8 @@ __global__ void __launch_bounds__(256, 4)
         ((float4 *)rec.mom)[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
         ((float4 *)rec.mom)[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         const bool dg = is_degenerate(sc, f64_ratio);
-        rec.f64[r] = dg ? 1 : 0;
+        // bit 0: FP64 geometry; bit 1: elongated (the backward's centre-out moment sums)
+        rec.f64[r] = (dg ? 1 : 0) | (dg || is_degenerate(sc, ELONG_RATIO) ? 2 : 0);
         if (dg) {
             double2 *m2 = (double2 *)(rec.mom64 + MOM64_STRIDE * r);
             m2[0] = m2[1] = m2[2] = make_double2(0.0, 0.0);

@@ -193,6 +193,9 @@ struct WsLayout {
 // model's background) SPARSE_CLAIM at a time, their records packed into
 // batches of up to 32 lanes, each lane over all rows of its own tile.
 constexpr unsigned SPARSE_MAX = 16;
+// Gaussians with a scale ratio above ELONG_RATIO (flag bit 1 of a record) take
+// the backward's cancellation-free moment sums.
+constexpr float ELONG_RATIO = 16.f;
 constexpr unsigned SPARSE_CLAIM = 8;
 
 // Binning of large records: a record listing more than BIG_AREA tiles is

@@ -216,7 +216,7 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
         na = geo[er];
         nb = geo2[er];
         if (CELLS) nc = rcell[er];
-        if (f64[er]) nr = er;
+        if (f64[er] & 1) nr = er;
     }
     er = (e0 + 32 + lane < e1) ? entries[e0 + 32 + lane] : 0xffffffffu;
     for (unsigned base = e0; base < e1; base += 32) {
@@ -240,7 +240,7 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
             na = geo[er];
             nb = geo2[er];
             if (CELLS) nc = rcell[er];
-            if (f64[er]) nr = er;
+            if (f64[er] & 1) nr = er;
         }
         er = (base + 64 + lane < e1) ? entries[base + 64 + lane] : 0xffffffffu;
         const int m = (int)min(32u, e1 - base);
@@ -412,13 +412,74 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
 // sum y w = -/+(z - a/2) and sum y^2 w = 2 zz + a/4 (no cancellation in the
 // even moments, at most 3x in the odd ones). Two adds per voxel instead of
 // three weighted sums, and no per-row fold.
-template <bool CELLS>
+//
+// CENTRE false: one sweep of the eight rows in order, z += a then zz += z, so
+// that after row 7 (n = 8 - j, y = 4.5 - n) a = sum w, z = sum n w and
+// zz = sum n (n + 1) / 2 w: one closed-form step per record, but the y^2
+// moment 20.25 a - 10 z + 2 zz cancels up to ~80x when the weight sits in the
+// middle rows. The backward takes the centre-out form for any batch holding a
+// record of a Gaussian with a scale ratio above ELONG_RATIO (where the chain
+// amplifies such errors), the single sweep otherwise.
+template <bool CELLS, bool CENTRE>
 __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C, const TileQuad &tq,
                                              const float *gt, const unsigned *srelw, unsigned clo, unsigned chi,
                                              const float2 *xp, const float2 *xq, float &T0, float &T1, float &T2,
                                              float &Y0, float &Y1, float &Y2)
 {
     T0 = T1 = T2 = Y0 = Y1 = Y2 = 0.f;
+    if (!CENTRE) {
+        float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
+#pragma unroll
+        for (int c = 0; c < MG_TILE / 2; ++c) ac[c] = zc[c] = zzc[c] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < MG_TILE; ++j) {
+            const float y = (float)j - TC;
+            const float b1 = fmaf(B, y, tq.D);
+            const float b0 = fmaf(fmaf(C, y, tq.E), y, tq.F);
+            const float4 *gr = (const float4 *)&gt[j * MG_TILE];
+            const uint4 *relr = (const uint4 *)&srelw[CELLS ? j * MG_TILE : 0];
+            const float2 b12 = make_float2(b1, b1), b02 = make_float2(b0, b0);
+#pragma unroll
+            for (int i4 = 0; i4 < MG_TILE / 4; ++i4) {
+                const float4 u = gr[i4];
+                uint4 rl = make_uint4(0u, 0u, 0u, 0u);
+                if (CELLS) rl = relr[i4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = i4 * 2 + h;
+                    const float2 x = xp[c];
+                    const float2 q = __ffma2_rn(__ffma2_rn(A2, x, b12), x, b02);
+                    float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                    if (CELLS) {
+                        if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
+                        if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
+                    }
+                    ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
+                    zc[c] = __fadd2_rn(zc[c], ac[c]);
+                    zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+                }
+            }
+        }
+        float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
+#pragma unroll
+        for (int c = 0; c < MG_TILE / 2; ++c) {
+            sa = __fadd2_rn(sa, ac[c]);
+            sxa = __ffma2_rn(xp[c], ac[c], sxa);
+            sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
+            sz = __fadd2_rn(sz, zc[c]);
+            sxz = __ffma2_rn(xp[c], zc[c], sxz);
+            szz = __fadd2_rn(szz, zzc[c]);
+        }
+        const float SA = sa.x + sa.y, SXA = sxa.x + sxa.y, SZ = sz.x + sz.y, SXZ = sxz.x + sxz.y;
+        const float Yc = (float)MG_TILE - TC;  // y = Yc - n
+        T0 = SA;
+        T1 = SXA;
+        T2 = sxxa.x + sxxa.y;
+        Y0 = fmaf(Yc, SA, -SZ);
+        Y1 = fmaf(Yc, SXA, -SXZ);
+        Y2 = fmaf(Yc * Yc, SA, fmaf(-(2.f * Yc + 1.f), SZ, 2.f * (szz.x + szz.y)));
+        return;
+    }
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         float2 ac[MG_TILE / 2], zc[MG_TILE / 2], zzc[MG_TILE / 2];
@@ -605,6 +666,8 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, unsigned 
             }
             j0 = (lane >> (5 - lg)) << (3 - lg);
         }
+        const bool elong = dbl != 0;  // bit 1: scale ratio above ELONG_RATIO (bit 0, FP64, implies it)
+        dbl &= 1;
         unsigned clo = 0u, chi = 0u;
         if (CELLS && r != 0xffffffffu && !cell_range(cl, cg.R, cb0, cb1, cb2, clo, chi)) r = 0xffffffffu;
         const float A = a.z, B = a.w, C = b.x;
@@ -655,7 +718,10 @@ __device__ __forceinline__ void bwd_tile(const StackTable &tab, int t, unsigned 
             Y2 = fmaf(y * y, R0, Y2);
         };
         if (lg == 0) {
-            record_rows8<CELLS>(A2, B, C, tq, sgvw, srelw, clo, chi, xp, xq, T0, T1, T2, Y0, Y1, Y2);
+            if (__any_sync(0xffffffffu, elong && r != 0xffffffffu))
+                record_rows8<CELLS, true>(A2, B, C, tq, sgvw, srelw, clo, chi, xp, xq, T0, T1, T2, Y0, Y1, Y2);
+            else
+                record_rows8<CELLS, false>(A2, B, C, tq, sgvw, srelw, clo, chi, xp, xq, T0, T1, T2, Y0, Y1, Y2);
         } else {
             const int nrow = MG_TILE >> lg;
             float y = (float)j0 - TC;
@@ -769,6 +835,8 @@ __device__ __forceinline__ void bwd_sparse(const StackTable &tab, const unsigned
         } else {
             r = 0xffffffffu;
         }
+        const bool elong = dbl != 0;  // bit 1: scale ratio above ELONG_RATIO (bit 0, FP64, implies it)
+        dbl &= 1;
         const float x0c = (float)(kx * MG_TILE) + TC, y0c = (float)(ky * MG_TILE) + TC;
         const float A = a.z, B = a.w, C = b.x;
         const float dx0 = x0c - a.x, dy0 = y0c - a.y;
@@ -777,8 +845,11 @@ __device__ __forceinline__ void bwd_sparse(const StackTable &tab, const unsigned
         const double *g64 = mom64 + (size_t)(tdbl ? r : 0u) * MOM64_STRIDE;
         if (__any_sync(0xffffffffu, tdbl) && tdbl) tq = tile_quad_f64(g64 + MOM64_GEO, x0c, y0c);
         float T0, T1, T2, Y0, Y1, Y2;
-        record_rows8<false>(make_float2(A, A), B, C, tq, sgvw + (act ? k : 0) * SG, nullptr, 0u, 0u, xp, xq, T0, T1,
-                            T2, Y0, Y1, Y2);
+        const float *gk = sgvw + (act ? k : 0) * SG;
+        if (__any_sync(0xffffffffu, elong))
+            record_rows8<false, true>(make_float2(A, A), B, C, tq, gk, nullptr, 0u, 0u, xp, xq, T0, T1, T2, Y0, Y1, Y2);
+        else
+            record_rows8<false, false>(make_float2(A, A), B, C, tq, gk, nullptr, 0u, 0u, xp, xq, T0, T1, T2, Y0, Y1, Y2);
         if (r != 0xffffffffu) record_add(r, dbl, g64, x0c, y0c, dx0, dy0, T0, T1, T2, Y0, Y1, Y2, mom, mom64);
         s = e + 1;
     }
@@ -1108,7 +1179,7 @@ __global__ void k_zero_mom(float4 *mom, const unsigned char *__restrict__ f64, d
     if (n > cap_records) n = cap_records;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         mom[2 * r] = mom[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);  // 8 floats per record
-        if (f64[r]) {
+        if (f64[r] & 1) {
             double2 *m2 = mom64 + (MOM64_STRIDE / 2) * r;
             m2[0] = m2[1] = m2[2] = make_double2(0.0, 0.0);
         }
