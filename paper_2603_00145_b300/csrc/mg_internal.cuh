@@ -136,7 +136,7 @@ struct WsHeader {
     unsigned int n_idle;       // tiles without records (back of the tile list)
     unsigned long long n_big;  // records listed apart from their chunks (large records)
     unsigned int moving;       // bit s: stack s has slices of different rotations (set by k1_emit)
-    unsigned int pad1;
+    unsigned int fwd_sparse_ctr;  // forward work counter over the sparse tiles
     unsigned int n_dense;      // tiles with more than SPARSE_MAX records (dense list)
     unsigned int n_sparse;     // tiles with 1..SPARSE_MAX records (sparse list)
     unsigned long long reserved[18];

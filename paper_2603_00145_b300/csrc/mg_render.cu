@@ -311,6 +311,126 @@ __device__ __forceinline__ void fwd_tile(const StackTable &tab, int t, int lane,
     }
 }
 
+// Up to SPARSE_CLAIM_FWD tiles of at most SPARSE_MAX records each (a fitted
+// model's background), one claim: their records (at most 64) are staged once,
+// each already in its tile's frame (A, B, C, amp | D, E, F), in the warp's
+// FwdStage memory; then lane l computes pixels (2 (l mod 4), 2 (l mod 4) + 1)
+// of row l / 4 of each tile over that tile's records in list order, with no
+// reduce-scatter, writes them and the tile's loss partials. The tiles' loads
+// overlap, where one tile at a time would wait on its own chain of loads.
+constexpr unsigned SPARSE_CLAIM_FWD = 4;
+template <bool LOSS>
+__device__ __forceinline__ void fwd_sparse(const StackTable &tab, const unsigned *__restrict__ sparse_list, unsigned i0,
+                                           unsigned nt, int lane, FwdStage &sw,
+                                           const unsigned *__restrict__ tile_off, long long cap_entries,
+                                           const unsigned *__restrict__ entries, long long cap_records,
+                                           const float4 *__restrict__ geo, const float2 *__restrict__ geo2,
+                                           const unsigned char *__restrict__ f64, const double *__restrict__ mom64,
+                                           float *__restrict__ out, const FwdLoss &ls)
+{
+    // lane k < nt: tile k's entry range and position
+    unsigned e0 = 0, e1 = 0;
+    int t = 0, tx = 0, ty = 0, W = 0, H = 0;
+    long long pb = 0;
+    if ((unsigned)lane < nt) {
+        t = (int)sparse_list[i0 + lane];
+        e0 = tile_off[t];
+        e1 = tile_off[t + 1];
+        if ((long long)e1 > cap_entries) e1 = (unsigned)cap_entries;
+        if (e0 > e1) e0 = e1;
+        const TileId d = tile_id(tab, t);
+        tx = d.tx;
+        ty = d.ty;
+        W = d.W;
+        H = d.H;
+        pb = d.pixbase;
+    }
+    const unsigned cnt = e1 - e0;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned excl = incl - cnt;
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);  // at most SPARSE_CLAIM_FWD * SPARSE_MAX
+    float4 *sab = sw.ab, *sdef = sw.cd;  // 64 records: sw.ab | sw.cd, sw.ef | sw.am
+    // stage the claim's records, 32 at a time (record gi of the claim: tile k, entry gi - excl_k)
+    for (unsigned base = 0; base < total; base += 32) {
+        const unsigned gi = base + lane;
+        int k = 0;
+#pragma unroll
+        for (int kk = 0; kk < (int)SPARSE_CLAIM_FWD; ++kk) k += (kk < (int)nt && gi >= __shfl_sync(0xffffffffu, incl, kk)) ? 1 : 0;
+        const unsigned ek = __shfl_sync(0xffffffffu, e0, k), xk = __shfl_sync(0xffffffffu, excl, k);
+        const unsigned ck = __shfl_sync(0xffffffffu, cnt, k);
+        const int kx = __shfl_sync(0xffffffffu, tx, k), ky = __shfl_sync(0xffffffffu, ty, k);
+        const bool act = gi < total && k < (int)nt && gi - xk < ck;
+        unsigned r = act ? entries[ek + (gi - xk)] : 0xffffffffu;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 b = make_float2(0.f, 0.f);
+        bool dbl = false;
+        if ((long long)r < cap_records) {
+            a = geo[r];
+            b = geo2[r];
+            dbl = f64[r] & 1;
+        } else {
+            r = 0xffffffffu;
+        }
+        const float x0c = (float)(kx * MG_TILE) + TC, y0c = (float)(ky * MG_TILE) + TC;
+        TileQuad tq = tile_quad(a.z, a.w, b.x, x0c - a.x, y0c - a.y);
+        if (__any_sync(0xffffffffu, dbl) && dbl) tq = tile_quad_f64(mom64 + (size_t)r * MOM64_STRIDE + MOM64_GEO, x0c, y0c);
+        const float amp = r != 0xffffffffu ? b.y : 0.f;
+        float4 *d0 = gi < 32 ? sab : sw.ef, *d1 = gi < 32 ? sdef : sw.am;
+        if (gi < 64u) {
+            d0[gi & 31u] = make_float4(a.z, a.w, b.x, amp);
+            d1[gi & 31u] = make_float4(tq.D, tq.E, tq.F, 0.f);
+        }
+    }
+    __syncwarp();
+    // lane l: row l / 4, columns 2 (l mod 4), 2 (l mod 4) + 1 of each tile (tile-centred)
+    const float y = (float)(lane >> 2) - TC;
+    const float2 x2 = make_float2((float)(2 * (lane & 3)) - TC, (float)(2 * (lane & 3) + 1) - TC);
+    for (unsigned k = 0; k < nt; ++k) {
+        const unsigned lo = __shfl_sync(0xffffffffu, excl, k), hi = __shfl_sync(0xffffffffu, incl, k);
+        float2 acc = make_float2(0.f, 0.f);
+        for (unsigned i = lo; i < hi; ++i) {
+            const float4 c0 = i < 32 ? sab[i] : sw.ef[i - 32], c1 = i < 32 ? sdef[i] : sw.am[i - 32];
+            const float b1 = fmaf(c0.y, y, c1.x);                // B y + D
+            const float b0 = fmaf(fmaf(c0.z, y, c1.y), y, c1.z);  // (C y + E) y + F
+            const float2 q = __ffma2_rn(__ffma2_rn(make_float2(c0.x, c0.x), x2, make_float2(b1, b1)), x2,
+                                        make_float2(b0, b0));
+            const float2 e = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+            acc = __ffma2_rn(make_float2(c0.w, c0.w), e, acc);
+        }
+        const int kx = __shfl_sync(0xffffffffu, tx, k), ky = __shfl_sync(0xffffffffu, ty, k);
+        const int kW = __shfl_sync(0xffffffffu, W, k), kH = __shfl_sync(0xffffffffu, H, k);
+        const long long kp = __shfl_sync(0xffffffffu, pb, k);
+        const int px = kx * MG_TILE + 2 * (lane & 3), py = ky * MG_TILE + (lane >> 2);
+        float f1 = 0.f, f2 = 0.f;
+        if (py < kH) {
+            const long long o = kp + (long long)py * kW;
+            if (px < kW) {
+                out[o + px] = acc.x;
+                if (LOSS) l1l2_voxel(acc.x, ls.target[o + px], ls.inv_n, ls.grad ? ls.grad + o + px : nullptr, f1, f2);
+            }
+            if (px + 1 < kW) {
+                out[o + px + 1] = acc.y;
+                if (LOSS)
+                    l1l2_voxel(acc.y, ls.target[o + px + 1], ls.inv_n, ls.grad ? ls.grad + o + px + 1 : nullptr, f1, f2);
+            }
+        }
+        if (LOSS) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+                f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+            }
+            const int tk = __shfl_sync(0xffffffffu, t, k);
+            if (lane == 0) ls.tile_part[tk] = make_double2((double)f1, (double)f2);
+        }
+    }
+}
+
 // Persistent warps pull the tiles with records from a counter (tiles carry
 // very different numbers of records); a warp that finds none left pulls the
 // tiles without records 32 at a time from a second counter and writes their
@@ -325,32 +445,50 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
                                                           const SliceDev *__restrict__ slices, CellGrid cg,
                                                           const int4 *__restrict__ rcell,
                                                           const unsigned *__restrict__ tile_list,
+                                                          const unsigned *__restrict__ dense_list,
+                                                          const unsigned *__restrict__ sparse_list,
                                                           const WsHeader *__restrict__ hdr,
                                                           const unsigned char *__restrict__ f64,
                                                           const double *__restrict__ mom64, float *__restrict__ out,
-                                                          FwdLoss ls, unsigned *counter)
+                                                          FwdLoss ls, unsigned *counter, unsigned *sparse_ctr)
 {
     __shared__ FwdStage sg[RW];
     __shared__ int4 sgc[CELLS ? RW : 1][32];
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n_tiles = tab.n_tiles_total;
-    const long long n_idle = hdr->n_idle, n_busy = hdr->n_busy;
-    const long long n_bulk = max(0ll, n_busy - (long long)TILE_RESERVE * gridDim.x * RW);
+    const long long n_idle = hdr->n_idle, n_dense = hdr->n_dense, n_sparse = hdr->n_sparse;
+    const long long n_bulk = max(0ll, n_dense - (long long)TILE_RESERVE * gridDim.x * RW);
+    auto tile = [&](int t) {
+        fwd_tile<CELLS, LOSS>(tab, t, lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0], tile_off, entries,
+                              cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64, mom64, out, ls);
+        __syncwarp();
+    };
+    // the dense tiles (more than SPARSE_MAX records): claims of two, then a reserve of single tiles
     for (unsigned part = 0; part < 2; ++part) {
-        const long long lo = part ? n_bulk : 0, hi = part ? n_busy : n_bulk;
+        const long long lo = part ? n_bulk : 0, hi = part ? n_dense : n_bulk;
         const unsigned step = part ? 1u : TILE_CLAIM;
         for (;;) {
             unsigned i0 = 0;
             if (lane == 0) i0 = atomicAdd(part ? counter + 5 : counter, step);  // tile_ctr[0], tile_ctr[5]
             i0 = __shfl_sync(0xffffffffu, i0, 0);
             if (lo + (long long)i0 >= hi) break;
-            for (long long i = lo + i0; i < lo + i0 + step && i < hi; ++i) {
-                fwd_tile<CELLS, LOSS>(tab, (int)tile_list[i], lane, sg[w], sgc[CELLS ? w : 0], srel[CELLS ? w : 0],
-                                      tile_off, entries, cap_entries, cap_records, geo, geo2, slices, cg, rcell, f64,
-                                      mom64, out, ls);
-                __syncwarp();
-            }
+            for (long long i = lo + i0; i < lo + i0 + step && i < hi; ++i) tile((int)dense_list[i]);
+        }
+    }
+    // the sparse tiles, SPARSE_CLAIM_FWD at a time (the cell-grid form one at a time)
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(sparse_ctr, CELLS ? 1u : SPARSE_CLAIM_FWD);
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if ((long long)i0 >= n_sparse) break;
+        if (CELLS) {
+            tile((int)sparse_list[i0]);
+        } else {
+            fwd_sparse<LOSS>(tab, sparse_list, i0,
+                             (unsigned)min((long long)SPARSE_CLAIM_FWD, n_sparse - (long long)i0), lane, sg[w],
+                             tile_off, cap_entries, entries, cap_records, geo, geo2, f64, mom64, out, ls);
+            __syncwarp();
         }
     }
     for (;;) {
@@ -1751,8 +1889,10 @@ static void launch_fwd(const WsLayout &L, char *ws, const StackTable &tab, const
     k_render_fwd<CELLS, LOSS><<<grid, 32 * RW, 0, st>>>(
         tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
         (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg,
-        cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr, (const unsigned *)(ws + L.tile_list), hdr,
-        (const unsigned char *)(ws + L.rec_f64), (const double *)(ws + L.rec_mom64), out, ls, &hdr->tile_ctr[0]);
+        cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr, (const unsigned *)(ws + L.tile_list),
+        (const unsigned *)(ws + L.dense_list), (const unsigned *)(ws + L.sparse_list), hdr,
+        (const unsigned char *)(ws + L.rec_f64), (const double *)(ws + L.rec_mom64), out, ls, &hdr->tile_ctr[0],
+        &hdr->fwd_sparse_ctr);
 }
 
 // target != NULL: the L1 + L2 slice loss of mg_loss_l1l2 fused into the
