@@ -1203,11 +1203,11 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
 }
 
 // per (slice, tile): exclusive prefix over the slice's chunks; tile totals;
-// and the tile list of the render kernels: tiles with records appended at
-// the front, tiles without at the back; the tiles with records also go to the
-// backward's dense (more than SPARSE_MAX records) or sparse list (counts
-// aggregated per block, one atomic per block and list; the order within each
-// list is arbitrary and does not change any result)
+// and the tile lists of the render kernels: tiles without records at the back
+// of the tile list, tiles with records on the dense (more than SPARSE_MAX
+// records) or the sparse list (counts aggregated per block, one atomic per
+// block and list; the order within each list is arbitrary and does not change
+// any result)
 constexpr int COLSCAN_NT = 256;
 __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slices, int S, const unsigned *chunk_base,
                                                             unsigned *hist, int Tmax, long long cap_chunks,
@@ -1217,8 +1217,8 @@ __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slic
                                                             unsigned *dense_list, unsigned *sparse_list)
 {
     const bool any_big = hdr->n_big > 0;  // tile_big is written only then
-    __shared__ unsigned wb[COLSCAN_NT / 32], wi[COLSCAN_NT / 32], wd[COLSCAN_NT / 32], ws_[COLSCAN_NT / 32];
-    __shared__ unsigned base_b, base_i, base_d, base_s;
+    __shared__ unsigned wi[COLSCAN_NT / 32], wd[COLSCAN_NT / 32], ws_[COLSCAN_NT / 32];
+    __shared__ unsigned base_i, base_d, base_s;
     const long long total = (long long)S * Tmax;
     const unsigned lt = lanemask_lt();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1255,40 +1255,35 @@ __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slic
         }
         const bool busy = real && run > 0, idle = real && run == 0;
         const bool dense = busy && run > SPARSE_MAX, sparse = busy && run <= SPARSE_MAX;
-        const unsigned bb = __ballot_sync(0xffffffffu, busy), ib = __ballot_sync(0xffffffffu, idle);
+        const unsigned ib = __ballot_sync(0xffffffffu, idle);
         const unsigned db = __ballot_sync(0xffffffffu, dense), sbm = __ballot_sync(0xffffffffu, sparse);
         if (lane == 0) {
-            wb[w] = __popc(bb);
             wi[w] = __popc(ib);
             wd[w] = __popc(db);
             ws_[w] = __popc(sbm);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned sb = 0, si = 0, sd = 0, ss = 0;
+            unsigned si = 0, sd = 0, ss = 0;
             for (int i = 0; i < COLSCAN_NT / 32; ++i) {
-                const unsigned a = wb[i], b = wi[i], c = wd[i], e = ws_[i];
-                wb[i] = sb;
+                const unsigned b = wi[i], c = wd[i], e = ws_[i];
                 wi[i] = si;
                 wd[i] = sd;
                 ws_[i] = ss;
-                sb += a;
                 si += b;
                 sd += c;
                 ss += e;
             }
-            base_b = sb ? atomicAdd(&hdr->n_busy, sb) : 0u;
             base_i = si ? atomicAdd(&hdr->n_idle, si) : 0u;
             base_d = sd ? atomicAdd(&hdr->n_dense, sd) : 0u;
             base_s = ss ? atomicAdd(&hdr->n_sparse, ss) : 0u;
         }
         __syncthreads();
         const unsigned tid = (unsigned)(slices[k].tile_base + t);
-        if (busy) tile_list[base_b + wb[w] + __popc(bb & lt)] = tid;
         if (idle) tile_list[n_tiles - 1 - (long long)(base_i + wi[w] + __popc(ib & lt))] = tid;
         if (dense) dense_list[base_d + wd[w] + __popc(db & lt)] = tid;
         if (sparse) sparse_list[base_s + ws_[w] + __popc(sbm & lt)] = tid;
-        __syncthreads();  // wb, wi and the bases are rewritten by the next round
+        __syncthreads();  // the per-warp counts and the bases are rewritten by the next round
     }
 }
 

@@ -132,7 +132,7 @@ struct WsHeader {
     unsigned int tile_ctr[6];  // work counters: [0] forward busy tiles (bulk), [1] backward dense tiles
                                // (bulk), [2] forward empty tiles, then backward sparse tiles, [3] loss
                                // ticket, [4] backward dense tiles (reserve), [5] forward busy tiles (reserve)
-    unsigned int n_busy;       // tiles with records (front of the tile list)
+    unsigned int pad2;
     unsigned int n_idle;       // tiles without records (back of the tile list)
     unsigned long long n_big;  // records listed apart from their chunks (large records)
     unsigned int moving;       // bit s: stack s has slices of different rotations (set by k1_emit)
