@@ -156,7 +156,7 @@ enum { MG_LOCAL_KSIGMA = 0, MG_LOCAL_CELLS = 1 };
 
 typedef struct {
     float cutoff_k;      /* K of the K-sigma record predicate; default 3 */
-    float f64_ratio;     /* record geometry in FP64 when max(scale)/min(scale) > f64_ratio; default 100; <= 0: never */
+    float f64_ratio;     /* record geometry and moments in FP64 when max(scale)/min(scale) > f64_ratio; default 16; <= 0: never */
     int64_t cap_records; /* workspace capacity in records; 0 = n * total slices (upper bound) capped at 2^28 */
     int64_t cap_entries; /* workspace capacity in (record, tile) entries; 0 = 8 * cap_records capped at 2^30 */
     int32_t local_set;   /* MG_LOCAL_KSIGMA (0, default) or MG_LOCAL_CELLS */
@@ -176,7 +176,7 @@ typedef struct {
     int32_t reserved;
 } mg_render_stats;
 
-/* Default options (K = 3, f64_ratio = 100, capacities from the bounds above). */
+/* Default options (K = 3, f64_ratio = 16, capacities from the bounds above). */
 mg_opts mg_default_opts(void);
 
 /*

@@ -433,7 +433,7 @@ mg_opts mg_default_opts(void)
 {
     mg_opts o;
     o.cutoff_k = 3.0f;
-    o.f64_ratio = 100.0f;
+    o.f64_ratio = 16.0f;
     o.cap_records = 0;
     o.cap_entries = 0;
     o.local_set = MG_LOCAL_KSIGMA;

@@ -44,7 +44,7 @@ def _gauss(mean, quat, scale, alpha) -> L.MgGaussians:
                          _dev(scale, "scale", numel=3 * n), _dev(alpha, "alpha", numel=n))
 
 
-def _opts(cutoff_k=3.0, f64_ratio=100.0, cap_records=0, cap_entries=0, cells=None) -> L.MgOpts:
+def _opts(cutoff_k=3.0, f64_ratio=16.0, cap_records=0, cap_entries=0, cells=None) -> L.MgOpts:
     """``cells``: None for the K-sigma local set, or a dict(grid_res, block_radius,
     centre (mm, 3), half (mm)) for the paper's cell-grid local set (Eqs. E4-E6)."""
     o = L.MgOpts(float(cutoff_k), float(f64_ratio), int(cap_records), int(cap_entries))
@@ -340,7 +340,7 @@ class SliceRenderer:
     reported need. ``check`` reads the device counters after every forward
     (one stream synchronisation)."""
 
-    def __init__(self, stacks: Sequence, device="cuda", cutoff_k: float = 3.0, f64_ratio: float = 100.0,
+    def __init__(self, stacks: Sequence, device="cuda", cutoff_k: float = 3.0, f64_ratio: float = 16.0,
                  records_per_gaussian: int = 32, entries_per_record: int = 8, check: bool = True, cells=None):
         self.cells = cells
         self.dev = DeviceStacks(stacks, device)
@@ -526,7 +526,7 @@ class VolumeSampler:
     """Inference sampling onto the isotropic G^3 grid (mg_sample_volume)."""
 
     def __init__(self, G: int, spacing: float, centre=(0.0, 0.0, 0.0), device="cuda", cutoff_k: float = 3.0,
-                 f64_ratio: float = 100.0, records_per_gaussian: int = 64, cells=None):
+                 f64_ratio: float = 16.0, records_per_gaussian: int = 64, cells=None):
         self.cells = cells
         self.G, self.h, self.centre = int(G), float(spacing), tuple(float(c) for c in centre)
         self.device, self.K, self.f64 = device, cutoff_k, f64_ratio

@@ -67,7 +67,7 @@ def assert_grads_close(got, ref, G, what=""):
     return out
 
 
-def render_gpu(G: ms.Gaussians, stacks, K=3.0, f64_ratio=100.0, caps=None, renderer=None):
+def render_gpu(G: ms.Gaussians, stacks, K=3.0, f64_ratio=16.0, caps=None, renderer=None):
     from paper_2603_00145_b300 import SliceRenderer
 
     R = renderer or SliceRenderer(stacks, cutoff_k=K, f64_ratio=f64_ratio)

@@ -46,7 +46,7 @@ def test_library_is_sm_103a(lib):
 def test_host_entry_points(lib):
     from paper_2603_00145_b300 import _lib as L
     o = lib.mg_default_opts()
-    assert o.cutoff_k == 3.0 and o.f64_ratio == 100.0
+    assert o.cutoff_k == 3.0 and o.f64_ratio == 16.0
     g = L.MgGaussians(1000, None, None, None, None)
     st = (L.MgStack * 2)(L.MgStack(10, 40, 33, 1.0, 1.0, 3.0, None), L.MgStack(5, 17, 64, 0.5, 0.5, 0.0, None))
     n1 = lib.mg_render_workspace_size(ctypes.byref(g), st, 2, ctypes.byref(o))
