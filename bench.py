@@ -49,10 +49,14 @@ KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 2, "k1_emit": 1
 # adds) + 1 ex2 (batches of more than 16 records; smaller batches split rows
 # over lanes and take one more FP32 op per pair).
 PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (5, 1)}
-# DRAM bytes (read + write) per launch of the evaluation kernels on this
-# workload, from one ncu capture of the current kernels
-# (profiles/render_step_feta256_launches.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"render_fwd": (187.06 + 55.63) * 1e6, "render_bwd": (243.99 + 60.66) * 1e6}
+# DRAM bytes (read + write) per launch of the evaluation kernels on the
+# FeTA-shaped workload, from ncu captures of the current kernels: the initial
+# Gaussians (dram__bytes_read.sum + dram__bytes_write.sum,
+# profiles/k_render_fwd_bwd_feta256_full.md) and the Gaussians after the
+# 2000-iteration L1 + L2 fit (DRAM rate x duration,
+# profiles/binning_fitted_feta256.md); None once a kernel changes.
+PROFILED_TRAFFIC = {"initial": {"render_fwd": (190.25 + 54.55) * 1e6, "render_bwd": (239.03 + 58.03) * 1e6},
+                    "fitted": {"render_fwd": 240.8e6, "render_bwd": 334.7e6}}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).
@@ -190,7 +194,7 @@ def fitted_gaussians(wl, G, target, dev, iterations: int = 2000):
 # ---------------------------------------------------------------------------
 # the mgauss arm
 # ---------------------------------------------------------------------------
-def device_step_timing(G, wl, target, dev, args, dist=None):
+def device_step_timing(G, wl, target, dev, args, dist=None, state="initial"):
     """The device-resident step on Gaussians G: record pass + binning + forward
     with the fused L1 + L2 loss + adjoint, captured once as a CUDA graph and
     replayed ``args.steps`` times (L2 flushed between steps, CUDA events on
@@ -275,7 +279,7 @@ def device_step_timing(G, wl, target, dev, args, dist=None):
     st = R.stats()
     assert st["status"] == 0, f"device status {st['status']} during the timed steps"
     stages = {k: v for k, v in prof.items() if v[1] > 0}
-    roof = roofline(stages, pairs_eval, traffic=PROFILED_TRAFFIC if args.workload == "feta" and not args.fitted else None)
+    roof = roofline(stages, pairs_eval, traffic=PROFILED_TRAFFIC.get(state) if args.workload == "feta" else None)
     del flush, graph
     return {"R": R, "out": out, "grad": grad, "loss": loss, "dev_in": (m, q, s, a), "value": value,
             "ms_step": ms_step, "pairs_inside": pairs_inside, "pairs_eval": pairs_eval, "stats": st, "stages": stages,
@@ -299,7 +303,7 @@ def roofline(stages, pairs_eval, traffic=None):
         if k in stages and k != dom:
             t_ = stages[k][0] / stages[k][1]
             other[k] = {"ms": t_, "Gpair_s": pairs_eval / (t_ / 1e3) / 1e9,
-                        "frac": pairs_eval / (t_ / 1e3) / alu_peak_pairs(k)}
+                        "frac": pairs_eval / (t_ / 1e3) / alu_peak_pairs(k), "traffic": (traffic or {}).get(k)}
     roof["other"] = other
     return roof
 
@@ -392,7 +396,8 @@ def run_mgauss(args, rank, world, local_rank):
         G = fitted_gaussians(wl, G, target, dev)
     if args.save_gaussians and rank == 0:
         np.savez(args.save_gaussians, mean=G.mean, quat=G.quat, scale=G.scale, alpha=G.alpha)
-    T = device_step_timing(G, wl, target, dev, args, dist)
+    T = device_step_timing(G, wl, target, dev, args, dist, state="fitted" if args.fitted else
+                           "loaded" if args.gaussians else "initial")
     R, out, grad, loss = T["R"], T["out"], T["grad"], T["loss"]
     value, ms_step, pairs_inside, pairs_eval = T["value"], T["ms_step"], T["pairs_inside"], T["pairs_eval"]
     stages, roof, clk, st = T["stages"], T["roofline"], T["clocks"], T["stats"]
@@ -508,7 +513,7 @@ def run_mgauss(args, rank, world, local_rank):
         t0 = time.perf_counter()
         Gf = fitted_gaussians(wl, G, target, dev, iterations=args.fit_iters)
         fit_s = time.perf_counter() - t0
-        F = device_step_timing(Gf, wl, target, dev, args, None)
+        F = device_step_timing(Gf, wl, target, dev, args, None, state="fitted")
         line["fitted"] = {"state": f"after {args.fit_iters} L1+L2 Adam iterations ({fit_s:.1f} s incl. set-up)",
                           "value": F["value"], "unit": UNIT, "ms_per_step": F["ms_step"],
                           "records": F["stats"]["records"], "entries": F["stats"]["entries"],
