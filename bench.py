@@ -15,6 +15,9 @@ input. The evaluated (tile-level) pair count is reported beside it.
 
 The line's "fitted" sub-record times the same step on the Gaussians after a
 2000-iteration L1+L2 fit (the state a reconstruction spends its iterations in).
+The "sampler" records (top level on the initial Gaussians, in "fitted" on the
+fitted ones) time the inference sampling onto the workload's isotropic target
+grid.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgauss|reference]
 Under torchrun each rank renders its own independent replica (seed = rank):
@@ -320,6 +323,41 @@ NRF_FLOPS_BWD = NRF_FLOPS_FWD + 2 * (32 * 64 + 64 * 64 + 64) + 2 * (64 * 64 + 64
 NRF_PROFILED = {"fwd_gather_requests": 83408692, "bwd_red_requests": 101138216, "bwd_gather_requests": 3131437}
 
 
+def sampler_timing(G, wl, dev, steps: int, warmup: int):
+    """Inference sampling (mg_sample_volume: records, binning and the forward
+    over the planes of the isotropic target grid) of Gaussians G onto the
+    workload's target grid; CUDA events around each call, L2 flushed between
+    calls. Evaluated pairs = (record, 8x8 tile) entries x 64 (the grid's edge is
+    a multiple of 8)."""
+    import torch
+
+    from paper_2603_00145_b300.ops import VolumeSampler, _opts, mg_sample_volume
+
+    m, q, s_, a = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (G.mean, G.quat, G.scale, G.alpha)]
+    S = VolumeSampler(wl.target_G, wl.target_spacing, device=dev)
+    out = torch.empty(wl.target_G ** 3, dtype=torch.float32, device=dev)
+    S(m, q, s_, a, out=out)  # sizes the workspace
+    o = _opts(S.K, S.f64, *S.caps)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    t = 0.0
+    for k in range(warmup + steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mg_sample_volume(m, q, s_, a, S.centre, S.h, S.G, o, out, S.ws, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            t += e0.elapsed_time(e1)
+    ms_ = t / steps
+    st = S.last_stats
+    pairs = int(st["entries"]) * 64
+    return {"grid": f"{wl.target_G}^3 at {wl.target_spacing} mm", "gaussians": G.n, "ms": ms_,
+            "voxels_per_s": wl.target_G ** 3 / (ms_ * 1e-3), "records": int(st["records"]),
+            "entries": int(st["entries"]), "evaluated_pairs": pairs, "evaluated_pairs_per_s": pairs / (ms_ * 1e-3)}
+
+
 def nrf_pair_timing(wl, dev, steps: int, warmup: int, n: int = 1 << 20):
     """The neural residual field's training pair as the reconstruction runs it
     once the field is on: mg_nrf_fwd_at (BF16 hash grid, adds r at 2^20 random
@@ -523,8 +561,14 @@ def run_mgauss(args, rank, world, local_rank):
                           "clocks": F["clocks"]}
         del F
         torch.cuda.empty_cache()
+        if args.sampler:
+            line["fitted"]["sampler"] = sampler_timing(Gf, wl, dev, args.steps, args.warmup)
+            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.nrf:
         line["nrf"] = nrf_pair_timing(wl, dev, args.steps, args.warmup)
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.sampler:
+        line["sampler"] = sampler_timing(G, wl, dev, args.steps, args.warmup)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.recon_iters > 0:
         line["recon"] = run_recon(args, dev)
@@ -773,6 +817,7 @@ def main():
     ap.add_argument("--fit-iters", type=int, default=2000,
                     help="iterations of the fit whose Gaussians the 'fitted' sub-record times (0: skip it)")
     ap.add_argument("--nrf", type=int, default=1, help="time the NRF training pair (1) or not (0)")
+    ap.add_argument("--sampler", type=int, default=1, help="time the volume sampler on the target grid (1) or not (0)")
     ap.add_argument("--only", choices=["nrf"], default=None,
                     help="nrf: time only the NRF training pair and print its line")
     ap.add_argument("--gaussians", default=None,
