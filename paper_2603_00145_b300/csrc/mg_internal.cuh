@@ -170,7 +170,8 @@ struct Records {
     float *mom;         // [cap][8] backward moments (6 used)
     float *thr;         // q threshold of the K-sigma ellipsoid (log2 units), for pair counts
     int4 *cell;         // MG_LOCAL_CELLS: the Gaussian's cell (x, y, z, 0); else unused
-    unsigned char *f64; // 1: near-degenerate Gaussian (FP64 geometry and FP64 moments)
+    unsigned char *f64; // bit 0: near-degenerate Gaussian (FP64 geometry and FP64 moments);
+                        // bit 1: scale ratio above ELONG_RATIO (the backward's centre-out sums)
     double *mom64;      // [cap][12] of the FP64 records: [0..5] backward moments (FP64
                         // accumulation), [6..10] FP64 geometry (pcx, pcy, A, B2, C)
     long long cap;
@@ -194,7 +195,9 @@ struct WsLayout {
 // batches of up to 32 lanes, each lane over all rows of its own tile.
 constexpr unsigned SPARSE_MAX = 16;
 // Gaussians with a scale ratio above ELONG_RATIO (flag bit 1 of a record) take
-// the backward's cancellation-free moment sums.
+// the backward's cancellation-free moment sums. With the default FP64
+// threshold (a ratio of 16) the same records also take the FP64 path; the
+// flag matters where a caller raises that threshold.
 constexpr float ELONG_RATIO = 16.f;
 constexpr unsigned SPARSE_CLAIM = 8;
 
