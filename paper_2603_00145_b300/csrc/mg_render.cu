@@ -592,9 +592,16 @@ __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C,
                         if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
                         if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
                     }
-                    ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
-                    zc[c] = __fadd2_rn(zc[c], ac[c]);
-                    zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+                    const float2 g2 = h ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
+                    if (j == 0) {  // first row: the three sums start at w
+                        ac[c] = __fmul2_rn(g2, e);
+                        zc[c] = ac[c];
+                        zzc[c] = ac[c];
+                    } else {
+                        ac[c] = __ffma2_rn(g2, e, ac[c]);
+                        zc[c] = __fadd2_rn(zc[c], ac[c]);
+                        zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+                    }
                 }
             }
         }
@@ -647,9 +654,19 @@ __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C,
                         if (!cell_member(h ? rl.z : rl.x, clo, chi)) e.x = 0.f;
                         if (!cell_member(h ? rl.w : rl.y, clo, chi)) e.y = 0.f;
                     }
-                    ac[c] = __ffma2_rn(h ? make_float2(u.z, u.w) : make_float2(u.x, u.y), e, ac[c]);
-                    zzc[c] = __fadd2_rn(zzc[c], zc[c]);
-                    zc[c] = __fadd2_rn(zc[c], ac[c]);
+                    const float2 g2 = h ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
+                    if (i == 0) {  // the half's first row: a = z = w, zz = 0
+                        ac[c] = __fmul2_rn(g2, e);
+                        zc[c] = ac[c];
+                    } else if (i == 1) {  // zz = z of the first row
+                        ac[c] = __ffma2_rn(g2, e, ac[c]);
+                        zzc[c] = zc[c];
+                        zc[c] = __fadd2_rn(zc[c], ac[c]);
+                    } else {
+                        ac[c] = __ffma2_rn(g2, e, ac[c]);
+                        zzc[c] = __fadd2_rn(zzc[c], zc[c]);
+                        zc[c] = __fadd2_rn(zc[c], ac[c]);
+                    }
                 }
             }
         }
