@@ -605,9 +605,10 @@ __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C,
                 }
             }
         }
-        float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
+        float2 sa = ac[0], sxa = __fmul2_rn(xp[0], ac[0]), sxxa = __fmul2_rn(xq[0], ac[0]), sz = zc[0],
+               sxz = __fmul2_rn(xp[0], zc[0]), szz = zzc[0];
 #pragma unroll
-        for (int c = 0; c < MG_TILE / 2; ++c) {
+        for (int c = 1; c < MG_TILE / 2; ++c) {
             sa = __fadd2_rn(sa, ac[c]);
             sxa = __ffma2_rn(xp[c], ac[c], sxa);
             sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
@@ -670,9 +671,10 @@ __device__ __forceinline__ void record_rows8(const float2 &A2, float B, float C,
                 }
             }
         }
-        float2 sa = make_float2(0.f, 0.f), sxa = sa, sxxa = sa, sz = sa, sxz = sa, szz = sa;
+        float2 sa = ac[0], sxa = __fmul2_rn(xp[0], ac[0]), sxxa = __fmul2_rn(xq[0], ac[0]), sz = zc[0],
+               sxz = __fmul2_rn(xp[0], zc[0]), szz = zzc[0];
 #pragma unroll
-        for (int c = 0; c < MG_TILE / 2; ++c) {
+        for (int c = 1; c < MG_TILE / 2; ++c) {
             sa = __fadd2_rn(sa, ac[c]);
             sxa = __ffma2_rn(xp[c], ac[c], sxa);
             sxxa = __ffma2_rn(xq[c], ac[c], sxxa);
