@@ -58,8 +58,8 @@ PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (5, 1)}
 # profiles/k_render_fwd_bwd_feta256_full.md) and the Gaussians after the
 # 2000-iteration L1 + L2 fit (DRAM rate x duration,
 # profiles/binning_fitted_feta256.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"initial": {"render_fwd": (190.25 + 54.55) * 1e6, "render_bwd": (240.10 + 58.60) * 1e6},
-                    "fitted": {"render_fwd": 240.8e6, "render_bwd": 333.9e6}}
+PROFILED_TRAFFIC = {"initial": {"render_fwd": (190.25 + 54.55) * 1e6, "render_bwd": (238.98 + 57.57) * 1e6},
+                    "fitted": {"render_fwd": 240.8e6, "render_bwd": 333.5e6}}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).
