@@ -22,6 +22,7 @@
 // ---------------------------------------------------------------------------
 __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
 {
+    pdl_entry();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
     int s = 0, base = 0, tile_base = 0;
@@ -77,7 +78,7 @@ __global__ void k_build_slices(StackIn in, SliceDev *out, int S)
 void mg_launch_build_slices(const StackIn &in, SliceDev *out, int S, cudaStream_t st)
 {
     MG_PROF(MG_ST_SLICES, st);
-    k_build_slices<<<(S + 127) / 128, 128, 0, st>>>(in, out, S);
+    launch_pdl(k_build_slices, dim3((S + 127) / 128), dim3(128), 0, st, in, out, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -126,6 +127,7 @@ struct ScanPair {
 
 __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(ScanPair sp, unsigned long long *parts)
 {
+    pdl_entry();
     const unsigned *in = sp.in[blockIdx.y];
     const long long n = sp.n[blockIdx.y];
     unsigned long long *part = parts + (size_t)blockIdx.y * gridDim.x;
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(ScanPair sp, unsigned l
 
 __global__ void __launch_bounds__(SCAN_NT) k_scan_down(ScanPair sp, const unsigned long long *parts, int write_end)
 {
+    pdl_entry();
     const unsigned *in = sp.in[blockIdx.y];
     unsigned *out = sp.out[blockIdx.y];
     const long long n = sp.n[blockIdx.y];
@@ -189,8 +192,8 @@ void mg_launch_scan_u32(const unsigned *in, unsigned *out, long long n_host, con
     sp.n[0] = sp.n[1] = n_host;
     sp.total[0] = sp.total[1] = total_out;
     int nb = MG_SCAN_BLOCKS;
-    k_scan_reduce<<<nb, SCAN_NT, 0, st>>>(sp, part);
-    k_scan_down<<<nb, SCAN_NT, 0, st>>>(sp, part, 1);
+    launch_pdl(k_scan_reduce, dim3(nb), dim3(SCAN_NT), 0, st, sp, part);
+    launch_pdl(k_scan_down, dim3(nb), dim3(SCAN_NT), 0, st, sp, part, 1);
 }
 
 // two independent exclusive scans in the same two launches (part holds
@@ -209,8 +212,8 @@ void mg_launch_scan2_u32(const unsigned *in0, unsigned *out0, long long n0, unsi
     sp.n[1] = n1;
     sp.total[1] = total1;
     int nb = MG_SCAN_BLOCKS;
-    k_scan_reduce<<<dim3(nb, 2), SCAN_NT, 0, st>>>(sp, part);
-    k_scan_down<<<dim3(nb, 2), SCAN_NT, 0, st>>>(sp, part, 1);
+    launch_pdl(k_scan_reduce, dim3(nb, 2), dim3(SCAN_NT), 0, st, sp, part);
+    launch_pdl(k_scan_down, dim3(nb, 2), dim3(SCAN_NT), 0, st, sp, part, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -724,6 +727,7 @@ __global__ void __launch_bounds__(K1_NT) k1_count(const SliceDev *__restrict__ s
                                                   unsigned *cnt, long long NW, unsigned *gcnt, unsigned *bits,
                                                   WsHeader *hdr)
 {
+    pdl_entry();
     __shared__ SliceDev ssl[32];
     __shared__ float sent[32];
     __shared__ int run_end[32], run_dir[32];  // at a run's first slice: its last slice, +1/-1 monotone, 0 not
@@ -892,6 +896,7 @@ __global__ void __launch_bounds__(K1_NT) k1_count_cells(const SliceDev *__restri
                                                         long long n, float f64_ratio, CellGrid cg, unsigned *cnt,
                                                         long long NW, unsigned *gcnt, unsigned *bits, WsHeader *hdr)
 {
+    pdl_entry();
     __shared__ SliceDev ssl[K1_SMEM_SLICES];
     const long long g = (long long)blockIdx.x * K1_NT + threadIdx.x;
     const long long wg = g >> 5;
@@ -934,6 +939,7 @@ __global__ void __launch_bounds__(K1_NT) k1_emit(int S, long long n, const unsig
                                                  const unsigned *__restrict__ goff, Records rec, unsigned *gmap,
                                                  const SliceDev *__restrict__ slices, WsHeader *hdr)
 {
+    pdl_entry();
     // block 0 also marks the stacks whose slices do not all share one rotation
     if (blockIdx.x == 0)
         for (int k = 1 + threadIdx.x; k < S; k += K1_NT)
@@ -979,6 +985,7 @@ __global__ void __launch_bounds__(256, 4)
     k_rec_fill(const WsHeader *hdr, const SliceDev *__restrict__ slices, const float *mean, const float *quat,
                const float *scale, const float *alpha, float K2, float f64_ratio, CellGrid cg, Records rec)
 {
+    pdl_entry();
     long long nr = (long long)hdr->n_records;
     if (nr > rec.cap) nr = rec.cap;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
@@ -1044,6 +1051,7 @@ __global__ void k_rec_geom_f64(const WsHeader *hdr, long long n, const SliceDev 
                                float f64_ratio, const unsigned *__restrict__ goff, const unsigned *__restrict__ gmap,
                                Records rec)
 {
+    pdl_entry();
     if (!(hdr->flags & MG_FLAG_DEGENERATE)) return;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
         float sc[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
@@ -1081,6 +1089,7 @@ __global__ void __launch_bounds__(1024) k_chunk_setup(const unsigned *rec_off, i
                                                       unsigned *slice_rs, unsigned *chunk_base, long long cap_rec,
                                                       long long cap_chunks, WsHeader *hdr)
 {
+    pdl_entry();
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -1155,6 +1164,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS) k_bin_hist(const SliceDev *sli
                                                              unsigned *hist, int Tmax, long long cap_chunks,
                                                              unsigned *big_n, unsigned *big_list, WsHeader *hdr)
 {
+    pdl_entry();
     extern __shared__ unsigned smem_u[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
@@ -1216,6 +1226,7 @@ __global__ void __launch_bounds__(COLSCAN_NT) k_bin_colscan(const SliceDev *slic
                                                             const unsigned *tile_big, unsigned *tile_small,
                                                             unsigned *dense_list, unsigned *sparse_list)
 {
+    pdl_entry();
     const bool any_big = hdr->n_big > 0;  // tile_big is written only then
     __shared__ unsigned wi[COLSCAN_NT / 32], wd[COLSCAN_NT / 32], ws_[COLSCAN_NT / 32];
     __shared__ unsigned base_i, base_d, base_s;
@@ -1295,6 +1306,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 12) k_bin_scatter(const SliceD
                                                                 unsigned *entries, long long cap_entries,
                                                                 WsHeader *hdr)
 {
+    pdl_entry();
     extern __shared__ unsigned smem_u[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && hdr->n_entries > (unsigned long long)cap_entries)
@@ -1421,6 +1433,7 @@ __global__ void __launch_bounds__(BIG_NT) k_bin_big(const SliceDev *__restrict__
                                                     const unsigned *__restrict__ tile_small, unsigned *entries,
                                                     long long cap_entries, const WsHeader *hdr)
 {
+    pdl_entry();
     __shared__ unsigned offs[BIG_NT + 1];
     __shared__ unsigned wsum[BIG_NT / 32];
     __shared__ uint4 srt[BIG_STAGE];
@@ -1537,11 +1550,13 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     {
         MG_PROF(MG_ST_K1_COUNT, st);
         if (cg.on) {
-            k1_count_cells<<<g1, K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, f64_ratio, cg, cnt, NW, gcnt,
+            launch_pdl(k1_count_cells, dim3(g1), dim3(K1_NT), 0, st,
+                slices, S, mean, quat, scale, alpha, n, f64_ratio, cg, cnt, NW, gcnt,
                                                  bits, hdr);
         } else {
             cudaMemsetAsync(gcnt, 0, sizeof(unsigned) * (size_t)n, st);
-            k1_count<<<dim3(g1, (unsigned)L.SW), K1_NT, 0, st>>>(slices, S, mean, quat, scale, alpha, n, K2, f64_ratio,
+            launch_pdl(k1_count, dim3(g1, (unsigned)L.SW), dim3(K1_NT), 0, st,
+                slices, S, mean, quat, scale, alpha, n, K2, f64_ratio,
                                                                  cnt, NW, gcnt, bits, hdr);
         }
     }
@@ -1551,26 +1566,30 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_K1_EMIT, st);
-        k1_emit<<<g1, K1_NT, 0, st>>>(S, n, bits, cnt, NW, gcnt, rec, gmap, slices, hdr);
+        launch_pdl(k1_emit, dim3(g1), dim3(K1_NT), 0, st, S, n, bits, cnt, NW, gcnt, rec, gmap, slices, hdr);
     }
     {
         MG_PROF(MG_ST_REC_FILL, st);
         long long want_r = (L.cap_records + 255) / 256;
         int gr = (int)(want_r < 148 * 16 ? (want_r > 0 ? want_r : 1) : 148 * 16);
         if (cg.on)
-            k_rec_fill<true><<<gr, 256, 0, st>>>(hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, cg, rec);
+            launch_pdl(k_rec_fill<true>, dim3(gr), dim3(256), 0, st,
+                hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, cg, rec);
         else
-            k_rec_fill<false><<<gr, 256, 0, st>>>(hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, cg, rec);
+            launch_pdl(k_rec_fill<false>, dim3(gr), dim3(256), 0, st,
+                hdr, slices, mean, quat, scale, alpha, K2, f64_ratio, cg, rec);
     }
     if (f64_ratio > 0.f) {
         MG_PROF(MG_ST_REC_GEOM, st);
         // grid-strided: two blocks per SM; most steps have no near-degenerate Gaussian and every block returns at once
         int gg = (int)((n + 255) / 256 < 148 * 2 ? (n + 255) / 256 : 148 * 2);
-        k_rec_geom_f64<<<gg, 256, 0, st>>>(hdr, n, slices, mean, quat, scale, alpha, K2, f64_ratio, gcnt, gmap, rec);
+        launch_pdl(k_rec_geom_f64, dim3(gg), dim3(256), 0, st,
+            hdr, n, slices, mean, quat, scale, alpha, K2, f64_ratio, gcnt, gmap, rec);
     }
     {
         MG_PROF(MG_ST_CHUNKS, st);
-        k_chunk_setup<<<1, 1024, 0, st>>>(cnt, S, (int)NW, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
+        launch_pdl(k_chunk_setup, dim3(1), dim3(1024), 0, st,
+            cnt, S, (int)NW, slice_rs, chunk_base, L.cap_records, L.cap_chunks, hdr);
     }
     const int Tmax = (int)L.max_tiles;
     int bw = BIN_WARPS;
@@ -1584,7 +1603,8 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     int gb = (int)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
     {
         MG_PROF(MG_ST_BIN_HIST, st);
-        k_bin_hist<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
+        launch_pdl(k_bin_hist, dim3(gb), dim3(32 * bw), smem, st,
+            slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
                                                      L.cap_chunks, big_n, big_list, hdr);
     }
     // the large records' tile counts: jobs of 1024 tiles of a slice (the
@@ -1592,13 +1612,15 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     // (every block returns at once when no record was listed apart)
     const long long big_jobs = (long long)S * ((Tmax + BIG_NT - 1) / BIG_NT);
     const int gbig = (int)(big_jobs < 148 * 2 ? (big_jobs > 0 ? big_jobs : 1) : 148 * 2);
-    k_bin_big<false><<<gbig, BIG_NT, 0, st>>>(slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
+    launch_pdl(k_bin_big<false>, dim3(gbig), dim3(BIG_NT), 0, st,
+        slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
                                               tile_big, tile_off, tile_small, entries, L.cap_entries, hdr);
     long long tot = (long long)S * Tmax;
     int gc = (int)((tot + 255) / 256 < 148 * 32 ? (tot + 255) / 256 : 148 * 32);
     {
         MG_PROF(MG_ST_BIN_COLSCAN, st);
-        k_bin_colscan<<<gc, COLSCAN_NT, 0, st>>>(slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt,
+        launch_pdl(k_bin_colscan, dim3(gc), dim3(COLSCAN_NT), 0, st,
+            slices, S, chunk_base, hist, Tmax, L.cap_chunks, tile_cnt,
                                           (unsigned *)(ws + L.tile_list), L.n_tiles, hdr, tile_big, tile_small,
                                           (unsigned *)(ws + L.dense_list), (unsigned *)(ws + L.sparse_list));
     }
@@ -1608,9 +1630,11 @@ void mg_launch_bin(const WsLayout &L, char *ws, const SliceDev *slices, const St
     }
     {
         MG_PROF(MG_ST_BIN_SCATTER, st);
-        k_bin_scatter<<<gb, 32 * bw, smem, st>>>(slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
+        launch_pdl(k_bin_scatter, dim3(gb), dim3(32 * bw), smem, st,
+            slices, S, slice_rs, chunk_base, rec.tiles, hist, Tmax,
                                                         L.cap_chunks, tile_off, entries, L.cap_entries, hdr);
     }
-    k_bin_big<true><<<gbig, BIG_NT, 0, st>>>(slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
+    launch_pdl(k_bin_big<true>, dim3(gbig), dim3(BIG_NT), 0, st,
+        slices, S, Tmax, chunk_base, L.cap_chunks, big_n, big_list, rec.tiles,
                                              tile_big, tile_off, tile_small, entries, L.cap_entries, hdr);
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "mgauss.h"
 
 #define MG_TILE MG_TILE_EDGE    // tile edge in pixels (record rectangles are in tiles)
@@ -211,6 +213,37 @@ constexpr int BIG_MAX = 64;
 // FP64 slots of a near-degenerate record: moments, then its FP64 geometry
 constexpr int MOM64_STRIDE = 12;
 constexpr int MOM64_GEO = 6;
+
+// Programmatic dependent launch between the kernels of a step: a kernel
+// launched through launch_pdl is set up while its predecessor's last blocks
+// finish (no explicit trigger: the predecessor's blocks release it as they
+// exit), which hides the launch gap. It starts with pdl_entry(): wait until
+// the predecessor grid has completed and its writes are visible, before any
+// other statement (early returns included), so that completion stays
+// transitive along the stream. Where the preceding stream operation is not a
+// kernel the wait returns at once. (Triggering the successor at the start of
+// every kernel was slower: its waiting blocks took SM slots from the tail.)
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ float ex2_approx(float x)
 {

@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(32 * RW, CELLS ? 4 : 8) k_render_fwd(StackTabl
                                                           const double *__restrict__ mom64, float *__restrict__ out,
                                                           FwdLoss ls, unsigned *counter, unsigned *sparse_ctr)
 {
+    pdl_entry();
     __shared__ FwdStage sg[RW];
     __shared__ int4 sgc[CELLS ? RW : 1][32];
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
@@ -1026,6 +1027,7 @@ __global__ void __launch_bounds__(32 * RW, 5) k_render_bwd(StackTable tab, const
                                                           const float *__restrict__ grad_out, float *__restrict__ mom,
                                                           double *__restrict__ mom64, unsigned *counter)
 {
+    pdl_entry();
     __shared__ __align__(16) float sgv[RW][SPARSE_CLAIM * SG];
     __shared__ __align__(16) unsigned srel[CELLS ? RW : 1][CELLS ? NV : 4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1332,6 +1334,7 @@ __device__ void geometry_adjoint(const float *mu, const float *q, const float *s
 __global__ void k_zero_mom(float4 *mom, const unsigned char *__restrict__ f64, double2 *mom64, const WsHeader *hdr,
                            long long cap_records)
 {
+    pdl_entry();
     long long n = (long long)hdr->n_records;
     if (n > cap_records) n = cap_records;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
@@ -1642,6 +1645,7 @@ __global__ void __launch_bounds__(128, 4) k_chain_fused(StackTable tab, const Ws
                                                      float f64_ratio, float *g_mean, float *g_quat, float *g_scale,
                                                      float *g_alpha)
 {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const unsigned moving = hdr->moving;  // bit s: the slices of stack s do not share one rotation
     for (long long gb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); gb < n;
@@ -1864,6 +1868,7 @@ __global__ void __launch_bounds__(LT_NT) k_loss_tiles(const double2 *__restrict_
                                                       double2 *__restrict__ bsum, unsigned *ticket, double inv_n,
                                                       double *__restrict__ out)
 {
+    pdl_entry();
     __shared__ double sh[2 * LT_NT / 32];
     __shared__ bool last;
     const long long i0 = (long long)blockIdx.x * per, i1 = min(n, i0 + per);
@@ -1905,8 +1910,8 @@ static void launch_fwd(const WsLayout &L, char *ws, const StackTable &tab, const
     int grid = resident_grid((const void *)k_render_fwd<CELLS, LOSS>, 32 * RW);
     const int nt = tab.n_tiles_total;
     if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
-    k_render_fwd<CELLS, LOSS><<<grid, 32 * RW, 0, st>>>(
-        tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
+    launch_pdl(k_render_fwd<CELLS, LOSS>, dim3(grid), dim3(32 * RW), 0,
+        st, tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries, L.cap_records,
         (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg,
         cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr, (const unsigned *)(ws + L.tile_list),
         (const unsigned *)(ws + L.dense_list), (const unsigned *)(ws + L.sparse_list), hdr,
@@ -1950,7 +1955,7 @@ void mg_launch_render_fwd(const WsLayout &L, char *ws, const StackTable &tab, co
         const long long per = 8 * LT_NT;
         const int nb = (int)((nt + per - 1) / per);
         double2 *bsum = ls.tile_part + nt;
-        k_loss_tiles<<<nb, LT_NT, 0, st>>>(ls.tile_part, nt, per, bsum, &hdr->tile_ctr[3],
+        launch_pdl(k_loss_tiles, dim3(nb), dim3(LT_NT), 0, st, ls.tile_part, nt, per, bsum, &hdr->tile_ctr[3],
                                            n_vox > 0 ? 1.0 / (double)n_vox : 0.0, loss_out);
     }
 }
@@ -1991,7 +1996,8 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
         int gz = (int)((capv + 255) / 256 < 148 * 16 ? (capv + 255) / 256 : 148 * 16);
         if (gz < 1) gz = 1;
         MG_PROF(MG_ST_ZERO, st);
-        k_zero_mom<<<gz, 256, 0, st>>>((float4 *)(ws + L.rec_mom), (const unsigned char *)(ws + L.rec_f64),
+        launch_pdl(k_zero_mom, dim3(gz), dim3(256), 0, st,
+            (float4 *)(ws + L.rec_mom), (const unsigned char *)(ws + L.rec_f64),
                                        (double2 *)(ws + L.rec_mom64), hdr, L.cap_records);
     }
     int nt = tab.n_tiles_total;
@@ -2006,14 +2012,14 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
         if (grid > (nt + RW - 1) / RW) grid = (nt + RW - 1) / RW;
         const int4 *rcell = cg.on ? (const int4 *)(ws + L.rec_cell) : nullptr;
         if (cg.on)
-            k_render_bwd<true><<<grid, 32 * RW, 0, st>>>(
+            launch_pdl(k_render_bwd<true>, dim3(grid), dim3(32 * RW), 0, st,
                 tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
                 (const unsigned *)(ws + L.dense_list), (const unsigned *)(ws + L.sparse_list), hdr,
                 (const unsigned char *)(ws + L.rec_f64), grad_out, (float *)(ws + L.rec_mom),
                 (double *)(ws + L.rec_mom64), (unsigned *)&hdr->tile_ctr[1]);
         else
-            k_render_bwd<false><<<grid, 32 * RW, 0, st>>>(
+            launch_pdl(k_render_bwd<false>, dim3(grid), dim3(32 * RW), 0, st,
                 tab, (const unsigned *)(ws + L.tile_off), (const unsigned *)(ws + L.entries), L.cap_entries,
                 L.cap_records, (const float4 *)(ws + L.rec_geo), (const float2 *)(ws + L.rec_geo2), slices, cg, rcell,
                 (const unsigned *)(ws + L.dense_list), (const unsigned *)(ws + L.sparse_list), hdr,
@@ -2023,7 +2029,8 @@ void mg_launch_render_bwd(const WsLayout &L, char *ws, const SliceDev *slices, c
     MG_PROF(MG_ST_CHAIN, st);
     long long wg = (n + 127) / 128;
     int gc = (int)(wg < 148 * 32 ? (wg > 0 ? wg : 1) : 148 * 32);
-    k_chain_fused<<<gc, 128, 0, st>>>(tab, hdr, n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
+    launch_pdl(k_chain_fused, dim3(gc), dim3(128), 0, st,
+        tab, hdr, n, (const unsigned *)(ws + L.gcnt), (const unsigned *)(ws + L.gmap),
                                       L.cap_records, (const float4 *)(ws + L.rec_geo),
                                       (const float2 *)(ws + L.rec_geo2), (const int *)(ws + L.rec_slice),
                                       (const float *)(ws + L.rec_mom), (const double *)(ws + L.rec_mom64), slices,
