@@ -53,13 +53,14 @@ KERNELS_PER_STAGE = {"slices": 1, "k1_count": 1, "scan_records": 2, "k1_emit": 1
 # over lanes and take one more FP32 op per pair).
 PAIR_OPS = {"render_fwd": (3, 1), "render_bwd": (5, 1)}
 # DRAM bytes (read + write) per launch of the evaluation kernels on the
-# FeTA-shaped workload, from ncu captures of the current kernels: the initial
-# Gaussians (dram__bytes_read.sum + dram__bytes_write.sum,
-# profiles/k_render_fwd_bwd_feta256_full.md) and the Gaussians after the
-# 2000-iteration L1 + L2 fit (DRAM rate x duration,
-# profiles/binning_fitted_feta256.md); None once a kernel changes.
-PROFILED_TRAFFIC = {"initial": {"render_fwd": (190.25 + 54.55) * 1e6, "render_bwd": (238.98 + 57.57) * 1e6},
-                    "fitted": {"render_fwd": 240.8e6, "render_bwd": 333.5e6}}
+# FeTA-shaped workload, from ncu captures of the kernels as built
+# (dram__bytes_read.sum + dram__bytes_write.sum of the backward on the initial
+# Gaussians, profiles/k_render_fwd_bwd_feta256_full.md); None where a kernel
+# has changed since its last capture (the forward, and both kernels on the
+# Gaussians of the 2000-iteration fit, whose last captures predate the
+# dependent-launch wait at their entry).
+PROFILED_TRAFFIC = {"initial": {"render_fwd": None, "render_bwd": (238.94 + 58.37) * 1e6},
+                    "fitted": {"render_fwd": None, "render_bwd": None}}
 # B300 unit counts per SM and clock: 148 SMs, 128 FP32 lanes per SM per
 # clock, 2032 MHz maximum SM clock; ex2.approx issues at 32 per SM per clock
 # (measured on this part: 9.5e12 ex2/s at 2032 MHz over 148 SMs).

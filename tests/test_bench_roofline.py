@@ -35,7 +35,7 @@ def test_roofline_takes_the_slower_kernel_and_its_traffic(state):
     fwd = r["other"]["render_fwd"]
     assert fwd["ms"] == pytest.approx(0.22)
     assert fwd["frac"] == pytest.approx(pairs / 0.22e-3 / bench.alu_peak_pairs("render_fwd"))
-    assert fwd["traffic"] == traffic["render_fwd"]
+    assert fwd["traffic"] == traffic["render_fwd"]  # None once the kernel changed since its capture
 
 
 def test_roofline_without_a_capture_reports_no_traffic():
