@@ -78,8 +78,11 @@
  *   The caller owns every buffer; the library never allocates device memory
  *   in a compute call. Scratch comes from a caller-provided workspace of the
  *   size the matching *_workspace_size query returns (256-byte aligned).
- *   Calls are asynchronous on `stream` (NULL = the legacy default stream):
- *   host-visible argument errors return immediately; capacity overflow and
+ *   Calls are asynchronous on `stream` (NULL = the legacy default stream),
+ *   in stream order with the caller's work: the render kernels are
+ *   programmatic dependent launches, each waiting for the completion of the
+ *   work before it on the stream as its first action. Host-visible argument
+ *   errors return immediately; capacity overflow and
  *   non-finite inputs are detected on the device, recorded in the workspace
  *   and reported by mg_render_stats_get (which synchronises the stream).
  *   On MG_ERR_CUDA the message of the CUDA error is in mg_last_error().
